@@ -1,0 +1,421 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle (oracle/epll_oracle.c) against a closed form, a
+published value, brute force, or an independent dense formulation of the
+paper's equations, so that a dropped term, a wrong sign, index or transposed
+operand in the oracle fails at least one of them:
+
+* Algorithm 1 written literally in covariance form (dense solves and
+  log-determinants, explicit extraction matrices P_i) vs the oracle's
+  eigenspace (Eqs. 7-10) and flat-tail (Eqs. 13-16) forms;
+* exact ties and brute-force argmin on tiny inputs;
+* K = 1: the whole denoising restoration is a linear shift-invariant filter
+  whose Fourier-domain recursion is computed by a separate route;
+* beta -> infinity: patch extraction + reprojection is the identity;
+* the FFT image update / initialisation vs dense N x N solves (Eq. 6);
+* conjugate gradients vs a dense solve;
+* lambda's closed forms (Sec. "Parameter settings");
+* the samplers' coverage / count invariants and the published splitmix64
+  outputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# dense literal Algorithm 1 (covariance form), numpy
+# --------------------------------------------------------------------------
+def flat_cov(U, S, r, lam):
+    """Sigma_k with the eigenvalues after r replaced by lam (Sec. flat tail)."""
+    s = S.copy()
+    if r < len(S):
+        s[r:] = lam
+    return (U * s[None, :]) @ U.T
+
+
+def extraction_matrix(H, W, a):
+    Pm = np.zeros((64, H * W))
+    ai, aj = divmod(int(a), W)
+    for u in range(8):
+        for v in range(8):
+            Pm[u * 8 + v, ((ai + u) % H) * W + (aj + v) % W] = 1.0
+    return Pm
+
+
+def dense_patch_step(g, r, lam, beta, x, anchors, forced=None):
+    H, W = x.shape
+    K = g.K
+    covs = [flat_cov(g.U[k], g.S[k], int(r[k]), lam[k]) for k in range(K)]
+    I = np.eye(64)
+    num = np.zeros(H * W)
+    den = np.zeros((H * W, H * W))
+    ks, gaps, allsc = [], [], []
+    for n, a in enumerate(anchors):
+        Pm = extraction_matrix(H, W, a)
+        z = Pm @ x.ravel()
+        mu = z.mean()
+        zt = z - mu
+        sc = np.array([-2 * np.log(g.w[k]) + np.linalg.slogdet(covs[k] + I / beta)[1]
+                       + zt @ np.linalg.solve(covs[k] + I / beta, zt) for k in range(K)])
+        k = int(np.argmin(sc)) if forced is None else int(forced[n])
+        srt = np.sort(sc)
+        ks.append(k)
+        gaps.append(srt[1] - srt[0] if K > 1 else np.inf)
+        allsc.append(sc)
+        zh = np.linalg.solve(covs[k] + I / beta, covs[k] @ zt) + mu
+        num += Pm.T @ zh
+        den += Pm.T @ Pm
+    d = np.diag(den)
+    xt = np.where(d > 0, num / np.where(d > 0, d, 1), x.ravel())
+    return xt.reshape(H, W), np.array(ks), np.array(gaps), np.array(allsc)
+
+
+@pytest.mark.parametrize("mode,param", [("fixed", 64), ("fixed", 8), ("fixed", 3), ("rho", 0.9)])
+def test_patch_step_matches_dense_literal(mode, param):
+    g = synth.tiny_gmm(4, seed=11)
+    m = oracle.Model(g.w, g.U, g.S, mode, param)
+    rng = np.random.default_rng(5)
+    x = rng.random((10, 11))
+    beta = 1.0 / 0.004
+    anchors = np.arange(110)
+    xt, ks, gap, best = oracle.patch_step(m, beta, x, anchors)
+    dxt, dks, dgap, dsc = dense_patch_step(g, m.r, m.lam, beta, x, anchors)
+    assert np.array_equal(ks, dks)
+    np.testing.assert_allclose(best, dsc.min(axis=1), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(gap, dgap, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(xt, dxt, rtol=0, atol=1e-12)
+    sc = oracle.scores(m, beta, x, anchors)
+    np.testing.assert_allclose(sc, dsc, rtol=0, atol=1e-9)
+
+
+def test_patch_step_subset_and_forced():
+    g = synth.tiny_gmm(3, seed=12)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 5)
+    x = np.random.default_rng(6).random((12, 9))
+    anchors = np.array([0, 7, 13, 50, 51, 99, 107])
+    forced = np.array([2, 0, 1, 1, 0, 2, 2])
+    xt, ks, _, _ = oracle.patch_step(m, 300.0, x, anchors, forced)
+    dxt, _, _, _ = dense_patch_step(g, m.r, m.lam, 300.0, x, anchors, forced)
+    assert np.array_equal(ks, forced)
+    np.testing.assert_allclose(xt, dxt, atol=1e-12)
+
+
+def test_flat_tail_full_rank_is_exact_form():
+    """r = P in the fixed mode reproduces the exact (covariance) form."""
+    g = synth.tiny_gmm(3, seed=13)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 64)
+    assert np.all(m.r == 64) and np.all(m.lam == 0)
+    x = np.random.default_rng(7).random((9, 9))
+    covs = [(g.U[k] * g.S[k]) @ g.U[k].T for k in range(3)]
+    beta = 80.0
+    sc = oracle.scores(m, beta, x, [0, 40])
+    for n, a in enumerate([0, 40]):
+        z = extraction_matrix(9, 9, a) @ x.ravel()
+        zt = z - z.mean()
+        for k in range(3):
+            C = covs[k] + np.eye(64) / beta
+            ref = -2 * np.log(g.w[k]) + np.linalg.slogdet(C)[1] + zt @ np.linalg.solve(C, zt)
+            assert abs(sc[n, k] - ref) < 1e-9
+
+
+def test_flat_tail_ranks():
+    S = synth.spectrum()[None, :]
+    r, lam = oracle.flat_tail(S, "rho", 0.95)
+    cum = np.cumsum(S[0])
+    assert r[0] == int(np.searchsorted(cum, 0.95 * cum[-1]) + 1)
+    assert r[0] == 10
+    np.testing.assert_allclose(lam[0], S[0, 10:].mean(), rtol=1e-15)
+    r8, lam8 = oracle.flat_tail(S, "fixed", 8)
+    assert r8[0] == 8 and abs(lam8[0] - S[0, 8:].mean()) < 1e-18
+    with pytest.raises(ValueError):
+        oracle.flat_tail(S, "fixed", 0)
+
+
+def test_exact_tie_goes_to_lowest_index():
+    g = synth.tiny_gmm(2, seed=14)
+    # components 1, 2 and 3 identical (same weight, basis, spectrum)
+    w = np.array([g.w[0], 0.3, 0.3, 0.3])
+    U = np.stack([g.U[0], g.U[1], g.U[1], g.U[1]])
+    S = np.stack([g.S[0], g.S[1], g.S[1], g.S[1]])
+    m = oracle.Model(w / w.sum(), U, S, "fixed", 64)
+    x = np.random.default_rng(8).random((8, 8)) * 0.05
+    sc = oracle.scores(m, 500.0, x, np.arange(64))
+    _, ks, gap, _ = oracle.patch_step(m, 500.0, x)
+    for n in range(64):
+        assert sc[n, 1] == sc[n, 2] == sc[n, 3]
+        assert ks[n] == int(np.argmin(sc[n]))  # numpy: first minimum
+        if ks[n] in (1, 2, 3):
+            assert ks[n] == 1 and gap[n] == 0.0
+
+
+def test_brute_force_argmin_tiny():
+    g = synth.tiny_gmm(4, seed=15)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 6)
+    x = np.random.default_rng(9).random((8, 12))
+    sc = oracle.scores(m, 1000.0, x, np.arange(96))
+    _, ks, gap, best = oracle.patch_step(m, 1000.0, x)
+    for n in range(96):
+        order = sorted(range(4), key=lambda k: (sc[n, k], k))
+        assert ks[n] == order[0]
+        assert gap[n] == sc[n, order[1]] - sc[n, order[0]]
+        assert best[n] == sc[n, order[0]]
+
+
+def test_identity_when_beta_is_infinite():
+    """gamma -> 1: the patch step reproduces the image (extraction followed by
+    reprojection is the identity, Sec. Algorithm)."""
+    g = synth.synthetic_gmm(5)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 8)
+    x = synth.image(3, 24, 20)
+    xt, _, _, _ = oracle.patch_step(m, 1e13, x)
+    np.testing.assert_allclose(xt, x, atol=1e-9)
+    sub = oracle.sample(24, 20, oracle.JITTER, 6, seed=3, t=1)
+    xt2, _, _, _ = oracle.patch_step(m, 1e13, x, sub)
+    np.testing.assert_allclose(xt2, x, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# K = 1: a linear shift-invariant filter (Fourier-domain recursion)
+# --------------------------------------------------------------------------
+def k1_fourier_restore(U, S, r, lam, y, sigma, mults):
+    H, W = y.shape
+    s = S.copy()
+    if r < 64:
+        s[r:] = lam
+    Y = np.fft.fft2(y)
+    X = Y.copy()
+    for mt in mults:
+        beta = mt / sigma ** 2            # lambda = 1 for denoising
+        gam = s / (s + 1.0 / beta)
+        Wm = (U * gam[None, :]) @ U.T
+        Cm = np.eye(64) - np.ones((64, 64)) / 64
+        G = Wm @ Cm + np.ones((64, 64)) / 64
+        # xtilde(p) = sum_delta h(delta) x(p + delta), delta = b - a
+        h = np.zeros((H, W))
+        for a in range(64):
+            for b in range(64):
+                du = b // 8 - a // 8
+                dv = b % 8 - a % 8
+                h[du % H, dv % W] += G[a, b] / 64.0
+        # DFT of x(p + delta) is exp(+2 pi i omega delta) X
+        Hh = np.conj(np.fft.fft2(h))
+        X = (Y + mt * Hh * X) / (1.0 + mt)
+    return np.real(np.fft.ifft2(X))
+
+
+@pytest.mark.parametrize("r", [64, 8])
+def test_k1_reduces_to_wiener_filter_recursion(r):
+    g = synth.synthetic_gmm(1)
+    w1 = np.array([1.0])
+    m = oracle.Model(w1, g.U, g.S, "fixed", r)
+    sigma = 20 / 255
+    _, y = synth.denoise_problem(0, 32, sigma)
+    xo = oracle.restore(m, y, sigma)
+    xf = k1_fourier_restore(g.U[0], g.S[0], r, m.lam[0], y, sigma, [1, 4, 8, 16, 32])
+    np.testing.assert_allclose(xo, xf, atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# image estimation and initialisation vs dense solves (Eq. 6)
+# --------------------------------------------------------------------------
+def circulant_blur(kernel, H, W):
+    A = np.zeros((H * W, H * W))
+    kh, kw = kernel.shape
+    for i in range(H):
+        for j in range(W):
+            for u in range(kh):
+                for v in range(kw):
+                    q = ((i - (u - kh // 2)) % H) * W + (j - (v - kw // 2)) % W
+                    A[i * W + j, q] += kernel[u, v]
+    return A
+
+
+def neg_laplacian(H, W):
+    L = np.zeros((H * W, H * W))
+    for i in range(H):
+        for j in range(W):
+            p = i * W + j
+            L[p, p] += 4
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                L[p, ((i + di) % H) * W + (j + dj) % W] -= 1
+    return L
+
+
+def test_dft_matches_numpy():
+    rng = np.random.default_rng(1)
+    for H, W in [(16, 16), (12, 18), (7, 5), (24, 9)]:
+        x = rng.standard_normal((H, W))
+        np.testing.assert_allclose(oracle.dft2(x), np.fft.fft2(x), atol=1e-9)
+
+
+def test_conv_update_matches_dense_solve():
+    H = W = 16
+    k = synth.gaussian_kernel(7, 1.2)
+    A = circulant_blur(k, H, W)
+    rng = np.random.default_rng(2)
+    x = rng.random((H, W))
+    y = (A @ x.ravel()).reshape(H, W) + 0.01 * rng.standard_normal((H, W))
+    np.testing.assert_allclose(synth.blur_periodic(x, k).ravel(), A @ x.ravel(), atol=1e-12)
+    xt = rng.random((H, W))
+    bs = 0.37
+    ref = np.linalg.solve(A.T @ A + bs * np.eye(H * W), A.T @ y.ravel() + bs * xt.ravel())
+    np.testing.assert_allclose(oracle.xupdate_conv(k, y, xt, bs).ravel(), ref, atol=1e-10)
+    c = 0.013
+    ref0 = np.linalg.solve(A.T @ A + c * neg_laplacian(H, W), A.T @ y.ravel())
+    np.testing.assert_allclose(oracle.init_conv(k, y, c).ravel(), ref0, atol=1e-9)
+
+
+def test_pixelwise_update_and_cg_match_dense_solve():
+    H, W = 12, 10
+    rng = np.random.default_rng(3)
+    a = (rng.random((H, W)) < 0.7).astype(float)
+    y = a * rng.random((H, W))
+    xt = rng.random((H, W))
+    bs = 2.5
+    ref = np.linalg.solve(np.diag(a.ravel() ** 2) + bs * np.eye(H * W),
+                          a.ravel() * y.ravel() + bs * xt.ravel())
+    np.testing.assert_allclose(oracle.xupdate_pixelwise(y, xt, bs, a).ravel(), ref, atol=1e-13)
+    c = 0.05
+    ref0 = np.linalg.solve(np.diag(a.ravel() ** 2) + c * neg_laplacian(H, W), a.ravel() * y.ravel())
+    np.testing.assert_allclose(oracle.init_cg(a, y, c, 600).ravel(), ref0, atol=1e-9)
+
+
+def test_lambda_closed_forms():
+    H = W = 16
+    assert oracle.lam(oracle.DENOISE, H, W, 20 / 255) == 1.0
+    a = synth.observed_mask(0, H, W, 0.7)
+    assert abs(oracle.lam(oracle.PIXELWISE, H, W, 20 / 255, a=a) - a.mean()) < 1e-15
+    k = synth.gaussian_kernel(25, 1.6)
+    A = circulant_blur(k, H, W)
+    AtA = A.T @ A
+    ref = np.linalg.norm(AtA, "fro") ** 2 / (H * W) / np.linalg.norm(A, 2) ** 2
+    assert abs(oracle.lam(oracle.CONV, H, W, 2 / 255, kernel=k) - ref) < 1e-12
+    assert abs(oracle.lam(oracle.CONV, 512, 512, 2 / 255, kernel=k) - 0.01554) < 5e-6
+    # the 250 sigma^2 cap, sigma in grey levels
+    assert abs(oracle.lam(oracle.DENOISE, H, W, 0.01 / 255) - 250 * 0.01 ** 2) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# whole restorations vs a dense literal restoration (tiny)
+# --------------------------------------------------------------------------
+def dense_restore(g, r, lam_k, y, sigma, mults, deg, a=None, kernel=None, anchors_fn=None,
+                  cg_exact=True):
+    H, W = y.shape
+    N = H * W
+    if deg == oracle.DENOISE:
+        A = np.eye(N)
+    elif deg == oracle.PIXELWISE:
+        A = np.diag(a.ravel())
+    else:
+        A = circulant_blur(kernel, H, W)
+    AtA = A.T @ A
+    lm = min(np.linalg.norm(AtA, "fro") ** 2 / N / np.linalg.norm(A, 2) ** 2, 250 * (255 * sigma) ** 2)
+    c = 0.2 * sigma ** 2 / lm
+    if deg == oracle.DENOISE:
+        x = y.ravel().copy()
+    else:
+        x = np.linalg.solve(AtA + c * neg_laplacian(H, W), A.T @ y.ravel())
+    for t, mt in enumerate(mults):
+        bs = lm * mt
+        beta = bs / sigma ** 2
+        anchors = np.arange(N) if anchors_fn is None else anchors_fn(t)
+        xt, _, _, _ = dense_patch_step(g, r, lam_k, beta, x.reshape(H, W), anchors)
+        x = np.linalg.solve(AtA + bs * np.eye(N), A.T @ y.ravel() + bs * xt.ravel())
+    return x.reshape(H, W), lm
+
+
+def test_restore_deblur_matches_dense():
+    g = synth.tiny_gmm(2, seed=21)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 6)
+    k = synth.gaussian_kernel(5, 1.0)
+    x = synth.image(5, 10, 10)
+    sigma = 5 / 255
+    y = synth.blur_periodic(x, k) + synth.noise(5, 10, 10, sigma)
+    xo = oracle.restore(m, y, sigma, [1, 4, 8], deg=oracle.CONV, kernel=k)
+    xd, _ = dense_restore(g, m.r, m.lam, y, sigma, [1, 4, 8], oracle.CONV, kernel=k)
+    np.testing.assert_allclose(xo, xd, atol=1e-8)
+
+
+def test_restore_inpaint_subset_matches_dense():
+    g = synth.tiny_gmm(2, seed=22)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 64)
+    H, W = 10, 9
+    x = synth.image(6, H, W)
+    a = synth.observed_mask(6, H, W, 0.7)
+    sigma = 10 / 255
+    y = a * x + synth.noise(6, H, W, sigma)
+    xo = oracle.restore(m, y, sigma, [1, 4], deg=oracle.PIXELWISE, a=a,
+                        subset=oracle.FRACTION, subset_param=1 / 3, seed=9, cg_iters=400)
+    fn = lambda t: oracle.sample(H, W, oracle.FRACTION, 1 / 3, seed=9, t=t)
+    xd, lm = dense_restore(g, m.r, m.lam, y, sigma, [1, 4], oracle.PIXELWISE, a=a, anchors_fn=fn)
+    assert abs(lm - a.mean()) < 1e-15
+    np.testing.assert_allclose(xo, xd, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# samplers and random numbers
+# --------------------------------------------------------------------------
+def test_splitmix64_published_values():
+    vals = [int(l, 16) for l in open(os.path.join(GOLD, "splitmix64.txt")) if l.startswith("0x")]
+    assert [oracle.splitmix64_nth(0, n) for n in (1, 2, 3)] == vals
+
+
+@pytest.mark.parametrize("H,W,s", [(64, 64, 6), (50, 37, 6), (33, 40, 4), (20, 20, 8), (17, 23, 5)])
+def test_jitter_covers_every_pixel(H, W, s):
+    J = (8 - s) // 2
+    for t in range(4):
+        an = oracle.sample(H, W, oracle.JITTER, s, seed=123, t=t)
+        ni, nj = -(-H // s), -(-W // s)
+        assert an.shape[0] == ni * nj
+        cov = np.zeros((H, W), int)
+        for a in an:
+            i, j = divmod(int(a), W)
+            for u in range(8):
+                for v in range(8):
+                    cov[(i + u) % H, (j + v) % W] += 1
+        assert cov.min() >= 1
+        # offsets from the shifted grid stay within [-J, J]
+        gi = [oracle.rng_u64(123, t, 0) >> 32, oracle.rng_u64(123, t, 1) >> 32]
+        gi = [(v * s) >> 32 for v in gi]
+        for g_, a in enumerate(an):
+            n, mm = divmod(g_, nj)
+            i, j = divmod(int(a), W)
+            di = (i - (gi[0] + s * n)) % H
+            dj = (j - (gi[1] + s * mm)) % W
+            assert min(di, H - di) <= J and min(dj, W - dj) <= J
+
+
+def test_jitter_expected_coverage_is_uniform():
+    """The random global shift makes every pixel's expected coverage equal
+    (Sec. on the random subset of patches)."""
+    H = W = 24
+    acc = np.zeros((H, W))
+    T = 600
+    for t in range(T):
+        for a in oracle.sample(H, W, oracle.JITTER, 6, seed=5, t=t):
+            i, j = divmod(int(a), W)
+            acc[np.ix_((np.arange(8) + i) % H, (np.arange(8) + j) % W)] += 1
+    acc /= T
+    expect = 64 * (H // 6) * (W // 6) / (H * W)
+    assert abs(acc.mean() - expect) < 1e-12
+    assert acc.std() / acc.mean() < 0.05
+
+
+def test_fraction_sampler_count_and_order():
+    H, W = 40, 37
+    for t in range(3):
+        an = oracle.sample(H, W, oracle.FRACTION, 1 / 3, seed=77, t=t)
+        M = math.ceil(H * W / 3)
+        assert an.shape[0] == M
+        assert np.all(np.diff(an) > 0)
+        keys = np.array([oracle.rng_u64(77, t, a) >> 32 for a in range(H * W)], dtype=np.uint64)
+        order = np.lexsort((np.arange(H * W), keys))
+        assert np.array_equal(np.sort(order[:M]), an)
