@@ -1,0 +1,181 @@
+/*
+ * epll.h -- C ABI of libepll, a CUDA (sm_103a) implementation of the patch
+ * step of EPLL / fast-EPLL half-quadratic-splitting image restoration
+ * (Parameswaran, Deledalle, Denis & Nguyen, "Accelerating GMM-based patch
+ * priors for image restoration: three ingredients for a 100x speed-up").
+ *
+ * Equation numbers follow their order of appearance in the paper: Eq. 1
+ * EPLL objective, Eq. 2 GMM prior, Eqs. 3-5 half-quadratic splitting,
+ * Algorithm 1 (patch extraction, Gaussian selection, patch estimation, patch
+ * reprojection, image estimation), Eq. 6 closed-form image update, Eqs. 7-10
+ * eigenspace form, Eqs. 11-16 flat-tail form, Eq. 20 jittered sampling.
+ *
+ * Conventions for every entry point:
+ *  - images are H x W row-major float32, grey levels in [0, 1];
+ *  - "device" pointers are CUDA global memory of the current device, "host"
+ *    pointers are ordinary (pageable or pinned) host memory;
+ *  - the caller owns every image buffer; the library owns the model handle
+ *    and a scratch workspace cached inside it (grown on demand, freed with
+ *    the handle); a handle must not be used by two host threads at once;
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream); work is
+ *    enqueued on it and the call returns without synchronising unless stated;
+ *  - no C++ exception crosses the ABI; every call validates its arguments and
+ *    returns an epll_status; epll_last_error() gives a thread-local message;
+ *    asynchronous CUDA faults surface as EPLL_ECUDA at the next call that
+ *    synchronises.
+ */
+#ifndef EPLL_H
+#define EPLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EPLL_OK = 0,
+    EPLL_EINVAL = -1,       /* bad argument: the call did nothing */
+    EPLL_ENOMEM = -2,       /* device allocation failed */
+    EPLL_ECUDA = -3,        /* a CUDA runtime / cuFFT call failed */
+    EPLL_ETIMEOUT = -4,     /* a bounded device wait gave up */
+    EPLL_EUNSUPPORTED = -5  /* valid request this build cannot serve */
+} epll_status;
+
+/* flat-tail rank selection (Sec. "Speed-up via flat tail spectrum approximation") */
+enum { EPLL_RANK_FIXED = 0, EPLL_RANK_RHO = 1 };
+/* degradation operator A of y = A x + w (Sec. 2) */
+enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2 };
+/* patch subset (Sec. "Speed-up via the restriction to a random subset of patches") */
+enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
+/* arithmetic of the projection that drives the Gaussian selection */
+enum { EPLL_FP32 = 0, EPLL_BF16 = 1 };
+
+typedef struct epll_gmm epll_gmm; /* opaque, library-owned */
+
+/* Degradation A.  PIXELWISE: A = diag(a) (a = 0/1 mask for inpainting, a
+ * smooth gain for devignetting).  CONV_PERIODIC: circular convolution with a
+ * kh x kw kernel whose centre (kh/2, kw/2) maps to pixel offset (0, 0). */
+typedef struct {
+    int kind;
+    const float *a;      /* PIXELWISE: H*W gains; device for epll_restore, host for epll_restore_host */
+    const float *kernel; /* CONV_PERIODIC: host, kh*kw row-major, copied during the call */
+    int kh, kw;          /* 1..min(H, W) each */
+} epll_degradation;
+
+typedef struct {
+    int precision;      /* EPLL_FP32 (SIMT FP32 scores) or EPLL_BF16 (tcgen05 tensor cores) */
+    float tie_gap;      /* patches whose top-2 score gap is below this are rescored in
+                           compensated FP32 over all K; < 0 selects the default
+                           (1e-2 for FP32, 3.0 for BF16) */
+    int subset;         /* EPLL_SUBSET_* */
+    float subset_param; /* FRACTION: fraction in (0, 1]; JITTER: grid spacing s in 1..8 */
+    uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
+    int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
+} epll_options;
+
+/* Fills *o with the defaults: FP32, default tie gap, all patches, seed 0, 100 CG iterations. */
+void epll_options_default(epll_options *o);
+
+/*
+ * Loads a zero-mean GMM patch prior (Eq. 2) given in eigen form and prepares
+ * its flat-tail approximation.
+ *   K            number of components, 1..4096
+ *   P            patch dimension; must be 64 (8 x 8 patches)
+ *   weights      host [K], > 0; renormalised to sum 1
+ *   eigvecs      host [K][P][P] row-major: eigvecs[k][e][j] is entry e of the
+ *                j-th eigenvector of Sigma_k (orthonormal columns)
+ *   eigvals      host [K][P], > 0 and non-increasing in j
+ *   rank_mode    EPLL_RANK_FIXED: r_k = (int)rank_param in 1..P for every k;
+ *                EPLL_RANK_RHO: r_k = smallest r whose leading eigenvalues hold
+ *                a fraction rank_param in (0, 1] of the trace.  Eigenvalues
+ *                after r_k are replaced by their mean lambda_k; r_k = P keeps
+ *                the exact eigenspace form (Eqs. 7-10).
+ *   out          receives the handle; free with epll_gmm_free.
+ * Host arrays are copied; nothing is retained.  Synchronous.
+ * Errors: EPLL_EINVAL on a bad size/value, EPLL_ENOMEM, EPLL_ECUDA.
+ */
+epll_status epll_gmm_load(int K, int P, const double *weights, const double *eigvecs,
+                          const double *eigvals, int rank_mode, double rank_param,
+                          epll_gmm **out);
+
+/* Frees the handle and its workspace (synchronises the device). NULL is a no-op. */
+void epll_gmm_free(epll_gmm *g);
+
+/* Copies the chosen ranks r_k (host int[K]) and tail eigenvalues lambda_k
+ * (host double[K], 0 where r_k = P) out of the handle; either may be NULL. */
+epll_status epll_gmm_ranks(const epll_gmm *g, int *ranks, double *lambdas);
+
+/*
+ * Restores x from y = A x + w (Algorithm 1 iterated T times, Sec. "Parameter
+ * settings"): beta_t = lambda * beta_mult[t] / sigma^2 with
+ * lambda = min{N^-1 ||A^T A||_F^2 / ||A||_2^2, 250 sigma_255^2} computed on the
+ * device; initialisation x = y for denoising, (A^T A + 0.2 sigma^2/lambda L)^-1
+ * A^T y otherwise (FFT for CONV_PERIODIC, conjugate gradients for PIXELWISE).
+ * Each iteration: per-beta tables (FP64), patch sampling, extraction,
+ * projection + Gaussian selection (FP32 SIMT or BF16 tcgen05 with a fused
+ * score/argmin epilogue), near-tie rescoring, Wiener patch estimation
+ * (Eqs. 15-16), reprojection by overlap-add averaging and the closed-form
+ * image update (Eq. 6).
+ *   y, x_out     device [H][W]; x_out may alias y
+ *   H, W         8 <= H, W and H*W <= 2^26
+ *   sigma        noise standard deviation in image units, > 0
+ *   beta_mult    host [T], > 0 (the paper uses {1, 4, 8, 16, 32}); T in 1..64
+ *   opt          NULL = defaults
+ * Asynchronous on `stream`.  Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA.
+ */
+epll_status epll_restore(epll_gmm *g, const float *y, int H, int W,
+                         const epll_degradation *deg, float sigma,
+                         const double *beta_mult, int T, const epll_options *opt,
+                         float *x_out, void *stream);
+
+/* Same as epll_restore with HOST buffers: y, deg->a (PIXELWISE) and x_out are
+ * host pointers; the copies to and from the workspace are part of the call,
+ * which returns after x_out is written (synchronises `stream`). */
+epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W,
+                              const epll_degradation *deg, float sigma,
+                              const double *beta_mult, int T, const epll_options *opt,
+                              float *x_out, void *stream);
+
+/*
+ * One patch step (the first four steps of Algorithm 1) at a given beta, for
+ * testing and instrumentation.
+ *   xhat         device [H][W], current estimate
+ *   beta         > 0 (the paper's beta, i.e. 1/beta is the added variance)
+ *   t            iteration index fed to the sampler's counter-based draws
+ *   xtilde       device [H][W] out: reprojected patch average (uncovered
+ *                pixels copy xhat)
+ *   anchors      device int[H*W] out (nullable): sampled anchors (i*W + j of
+ *                the top-left pixel), in sampler order
+ *   kstar, gap   device int[H*W] / float[H*W] out (nullable): selected
+ *                component and top-2 score gap of each sampled patch
+ *   forced_k     device int (nullable): per sampled patch, a component that
+ *                replaces the selection (teacher forcing)
+ *   n_out        host out (nullable): number of sampled patches; when
+ *                non-NULL the call synchronises `stream`
+ */
+epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double beta,
+                            const epll_options *opt, int t, float *xtilde, int *anchors,
+                            int *kstar, float *gap, const int *forced_k, int *n_out,
+                            void *stream);
+
+/* Patch sampling alone (for tests): writes the anchors of iteration t to the
+ * device buffer `anchors` (capacity H*W) and their count to *n_out (host);
+ * synchronises `stream`. */
+epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *anchors,
+                        int *n_out, void *stream);
+
+/* Counters of the last epll_restore / epll_patch_step on this handle (host
+ * out; synchronises the device): patch evaluations, near-tie rescored
+ * patches, and kernel launches issued. */
+epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *rescored,
+                               long long *launches);
+
+/* Thread-local message describing the last error of this thread ("" if none). */
+const char *epll_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPLL_H */

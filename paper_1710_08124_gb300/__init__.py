@@ -1,0 +1,244 @@
+"""Python binding of libepll (argument marshalling only).
+
+Every computation happens in the CUDA library built from ``csrc/`` (see
+``include/epll.h`` for the C ABI).  PyTorch supplies device memory and
+streams; numpy arrays are accepted for the host-buffer entry point.  The
+binding raises if the library is missing -- there is no CPU fallback.
+
+Names mirror the C ABI without the ``epll_`` prefix: ``gmm_load``,
+``restore``, ``restore_host``, ``patch_step``, ``sample``, ``last_counters``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libepll.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+RANK_FIXED, RANK_RHO = 0, 1
+DENOISE, PIXELWISE, CONV_PERIODIC = 0, 1, 2
+SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER = 0, 1, 2
+FP32, BF16 = 0, 1
+PAPER_BETA = (1.0, 4.0, 8.0, 16.0, 32.0)
+
+
+class EpllError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"epll status {status}: {msg}")
+        self.status = status
+
+
+class _Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tie_gap", C.c_float), ("subset", C.c_int),
+                ("subset_param", C.c_float), ("seed", C.c_uint64), ("cg_iters", C.c_int)]
+
+
+class _Degradation(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_void_p), ("kernel", C.c_void_p),
+                ("kh", C.c_int), ("kw", C.c_int)]
+
+
+@dataclass
+class Options:
+    """Mirror of ``epll_options``."""
+    precision: int = FP32
+    tie_gap: float = -1.0
+    subset: int = SUBSET_ALL
+    subset_param: float = 0.0
+    seed: int = 0
+    cg_iters: int = 100
+
+    def _c(self) -> _Options:
+        return _Options(self.precision, self.tie_gap, self.subset, self.subset_param,
+                        self.seed, self.cg_iters)
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """The loaded libepll (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libepll is not built ({LIB_PATH} missing); run build()")
+        L = C.CDLL(LIB_PATH)
+        i, d, vp = C.c_int, C.c_double, C.c_void_p
+        L.epll_last_error.restype = C.c_char_p
+        L.epll_gmm_load.argtypes = [i, i, vp, vp, vp, i, d, C.POINTER(vp)]
+        L.epll_gmm_free.argtypes = [vp]
+        L.epll_gmm_free.restype = None
+        L.epll_gmm_ranks.argtypes = [vp, vp, vp]
+        L.epll_restore.argtypes = [vp, vp, i, i, C.POINTER(_Degradation), C.c_float, vp, i,
+                                   C.POINTER(_Options), vp, vp]
+        L.epll_restore_host.argtypes = L.epll_restore.argtypes
+        L.epll_patch_step.argtypes = [vp, vp, i, i, d, C.POINTER(_Options), i, vp, vp, vp, vp,
+                                      vp, C.POINTER(C.c_int), vp]
+        L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
+        L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                         C.POINTER(C.c_longlong)]
+        L.epll_options_default.argtypes = [C.POINTER(_Options)]
+        L.epll_options_default.restype = None
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().epll_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise EpllError(status, last_error())
+
+
+def _dptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class GMM:
+    """A loaded GMM patch prior (``epll_gmm_load``)."""
+
+    def __init__(self, w, U, S, rank_mode: int = RANK_FIXED, rank_param: float = 64):
+        self.w = np.ascontiguousarray(w, np.float64)
+        self.U = np.ascontiguousarray(U, np.float64)
+        self.S = np.ascontiguousarray(S, np.float64)
+        self.K = int(self.w.shape[0])
+        h = C.c_void_p()
+        _check(lib().epll_gmm_load(self.K, int(self.U.shape[1]), self.w.ctypes.data,
+                                   self.U.ctypes.data, self.S.ctypes.data, int(rank_mode),
+                                   float(rank_param), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def ranks(self):
+        r = np.zeros(self.K, np.int32)
+        lam = np.zeros(self.K)
+        _check(lib().epll_gmm_ranks(self._h, r.ctypes.data, lam.ctypes.data))
+        return r, lam
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().epll_gmm_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gmm_load(w, U, S, rank_mode: int = RANK_FIXED, rank_param: float = 64) -> GMM:
+    return GMM(w, U, S, rank_mode, rank_param)
+
+
+def _degradation(kind, a_ptr, kernel):
+    if kernel is not None:
+        k = np.ascontiguousarray(kernel, np.float32)
+        deg = _Degradation(kind, a_ptr, k.ctypes.data, k.shape[0], k.shape[1])
+        return deg, k
+    return _Degradation(kind, a_ptr, None, 0, 0), None
+
+
+def restore(g: GMM, y, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE, a=None,
+            kernel=None, options: Options | None = None, out=None, stream=None):
+    """Device-buffer restoration; y (and a) are float32 CUDA tensors [H, W]."""
+    import torch
+    H, W = y.shape
+    out = torch.empty_like(y) if out is None else out
+    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel)
+    bm = np.ascontiguousarray(beta_mult, np.float64)
+    opt = (options or Options())._c()
+    _check(lib().epll_restore(g.handle, _dptr(y, torch.float32), H, W, C.byref(deg), float(sigma),
+                              bm.ctypes.data, bm.shape[0], C.byref(opt), _dptr(out, torch.float32),
+                              _stream(stream)))
+    del keep
+    return out
+
+
+def restore_host(g: GMM, y: np.ndarray, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE,
+                 a=None, kernel=None, options: Options | None = None, out=None, stream=None):
+    """Host-buffer restoration (copies inside the call); y, a, out are float32 arrays
+    (pinned torch CPU tensors are accepted too)."""
+    def hptr(v):
+        if v is None:
+            return None
+        if isinstance(v, np.ndarray):
+            if v.dtype != np.float32 or not v.flags.c_contiguous:
+                raise ValueError("host arrays must be C-contiguous float32")
+            return v.ctypes.data
+        return v.data_ptr()
+
+    H, W = y.shape
+    if out is None:
+        out = np.empty((H, W), np.float32)
+    deg, keep = _degradation(kind, hptr(a), kernel)
+    bm = np.ascontiguousarray(beta_mult, np.float64)
+    opt = (options or Options())._c()
+    _check(lib().epll_restore_host(g.handle, hptr(y), H, W, C.byref(deg), float(sigma),
+                                   bm.ctypes.data, bm.shape[0], C.byref(opt), hptr(out),
+                                   _stream(stream)))
+    del keep
+    return out
+
+
+def patch_step(g: GMM, xhat, beta: float, options: Options | None = None, t: int = 0,
+               forced_k=None, stream=None):
+    """One patch step; returns (xtilde, anchors, kstar, gap) as CUDA tensors."""
+    import torch
+    H, W = xhat.shape
+    dev = xhat.device
+    xt = torch.empty_like(xhat)
+    an = torch.empty(H * W, dtype=torch.int32, device=dev)
+    ks = torch.empty(H * W, dtype=torch.int32, device=dev)
+    gp = torch.empty(H * W, dtype=torch.float32, device=dev)
+    n = C.c_int(0)
+    opt = (options or Options())._c()
+    _check(lib().epll_patch_step(g.handle, _dptr(xhat, torch.float32), H, W, float(beta),
+                                 C.byref(opt), int(t), _dptr(xt), _dptr(an), _dptr(ks), _dptr(gp),
+                                 _dptr(forced_k, torch.int32), C.byref(n), _stream(stream)))
+    m = n.value
+    return xt, an[:m], ks[:m], gp[:m]
+
+
+def sample(H: int, W: int, options: Options | None = None, t: int = 0, device="cuda", stream=None):
+    import torch
+    an = torch.empty(H * W, dtype=torch.int32, device=device)
+    n = C.c_int(0)
+    opt = (options or Options())._c()
+    _check(lib().epll_sample(H, W, C.byref(opt), int(t), _dptr(an), C.byref(n), _stream(stream)))
+    return an[:n.value]
+
+
+def last_counters(g: GMM):
+    """(patch evaluations, near-tie rescored patches, kernel launches) of the last call."""
+    a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check(lib().epll_last_counters(g.handle, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value

@@ -1,0 +1,498 @@
+// C ABI of libepll: model loading (flat-tail preparation), workspace
+// management and the restoration loop (Algorithm 1 iterated over the beta
+// schedule of Sec. "Parameter settings").
+#include "epll_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace epll {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+static epll_status fail(epll_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * count);
+}
+
+static void free_workspace(Workspace &ws)
+{
+    void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors, ws.mult, ws.kstar, ws.gap,
+                    ws.flag, ws.perm, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
+                    ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
+    if (ws.plan_c2r) cufftDestroy(ws.plan_c2r);
+    ws = Workspace();
+}
+
+epll_status ensure_workspace(epll_gmm *g, size_t N)
+{
+    Workspace &ws = g->ws;
+    if (N <= ws.capN) return EPLL_OK;
+    EPLL_CU(cudaDeviceSynchronize());
+    free_workspace(ws);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&ws.xhat, N)); A(dalloc(&ws.xtil, N)); A(dalloc(&ws.y, N)); A(dalloc(&ws.a, N));
+    A(dalloc(&ws.anchors, N)); A(dalloc(&ws.mult, N)); A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
+    A(dalloc(&ws.flag, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
+    A(dalloc(&ws.Zb, N * PD)); A(dalloc(&ws.zz, N)); A(dalloc(&ws.cg, 4 * N));
+    A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16));
+    A(dalloc(&ws.sampler, 1040 + 2 * (N / 2048 + 2)));
+    A(dalloc(&ws.counts, 2 * (size_t)g->K + 8)); A(dalloc(&ws.ctr, 4));
+    A(dalloc(&ws.Yh, N)); A(dalloc(&ws.Hh, N)); A(dalloc(&ws.Xh, N)); A(dalloc(&ws.kern, N));
+    if (e != cudaSuccess) {
+        free_workspace(ws);
+        cudaGetLastError();
+        return fail(EPLL_ENOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    }
+    ws.capN = N;
+    EPLL_CU(cudaMemset(ws.ctr, 0, sizeof(long long) * 4));
+    return EPLL_OK;
+}
+
+static void free_model(epll_gmm *g)
+{
+    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo,
+                    g->tab.cst_hi, g->tab.cst_lo, g->tab.t_hi, g->tab.t_lo, g->tab.gp, g->tab.sgn,
+                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.Bs};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete[] g->h_r;
+    delete[] g->h_lam;
+    delete[] g->h_roff;
+}
+
+static epll_status check_options(const epll_options &o, int H, int W)
+{
+    if (o.precision != EPLL_FP32 && o.precision != EPLL_BF16)
+        return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32 or EPLL_BF16");
+    if (!(std::isfinite(o.tie_gap)))
+        return fail(EPLL_EINVAL, "options.tie_gap must be finite");
+    if (o.subset == EPLL_SUBSET_FRACTION) {
+        if (!(o.subset_param > 0.0f && o.subset_param <= 1.0f))
+            return fail(EPLL_EINVAL, "options.subset_param: fraction must be in (0, 1]");
+    } else if (o.subset == EPLL_SUBSET_JITTER) {
+        int s = (int)o.subset_param;
+        if ((float)s != o.subset_param || s < 1 || s > PS)
+            return fail(EPLL_EINVAL, "options.subset_param: jitter spacing must be an integer in 1..8");
+        (void)H; (void)W;
+    } else if (o.subset != EPLL_SUBSET_ALL) {
+        return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION or _JITTER");
+    }
+    if (o.cg_iters < 0 || o.cg_iters > 100000) return fail(EPLL_EINVAL, "options.cg_iters out of range");
+    return EPLL_OK;
+}
+
+static epll_status check_image(int H, int W)
+{
+    if (H < PS || W < PS) return fail(EPLL_EINVAL, "image must be at least 8 x 8");
+    if ((long long)H * W > (1LL << 26)) return fail(EPLL_EINVAL, "image larger than 2^26 pixels");
+    return EPLL_OK;
+}
+
+static float default_tau(const epll_options &o)
+{
+    if (o.tie_gap >= 0.0f) return o.tie_gap;
+    return o.precision == EPLL_BF16 ? 3.0f : 1e-2f;
+}
+
+// One patch step: tables, sampling, selection, rescoring, estimation.  The
+// reprojection is left to the caller (it may be fused with the image update).
+static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, const epll_options &o,
+                               int t, const double *d_lambda, double mult, double sigma2,
+                               double beta_direct, const int *forced_k, int *n_out,
+                               cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const bool bf16 = o.precision == EPLL_BF16;
+    epll_status s;
+    if ((s = launch_tables(g, d_lambda, mult, sigma2, beta_direct, bf16, st))) return s;
+    int n = 0;
+    if ((s = launch_sample(g, H, W, o, t, &n, ws.anchors, ws.mult, st))) return s;
+    const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
+    const float tau = default_tau(o);
+    if (bf16) {
+        if ((s = launch_select_bf16(g, xhat, H, W, anchors, n, tau, st))) return s;
+    } else {
+        if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau, st))) return s;
+    }
+    if ((s = launch_rescore(g, xhat, H, W, anchors, n, st))) return s;
+    if (forced_k)
+        EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
+    g->last_evals += n;
+    *n_out = n;
+    return EPLL_OK;
+}
+
+static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
+                               const epll_degradation *deg, float sigma, const double *beta_mult,
+                               int T, const epll_options &o, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int kind = deg ? deg->kind : EPLL_DENOISE;
+    epll_status s;
+    g->launches = 0;
+    g->last_evals = 0;
+    EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
+    if (kind == EPLL_CONV_PERIODIC) {
+        if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
+    }
+    if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;
+    if (kind == EPLL_DENOISE) {
+        EPLL_CU(cudaMemcpyAsync(ws.xhat, y, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
+    } else if (kind == EPLL_CONV_PERIODIC) {
+        if ((s = fft_init(g, H, W, sigma, st))) return s;
+    } else {
+        if ((s = cg_init(g, a, y, H, W, sigma, o.cg_iters, st))) return s;
+    }
+    const double s2 = (double)sigma * sigma;
+    for (int t = 0; t < T; ++t) {
+        int n = 0;
+        if ((s = patch_phase(g, ws.xhat, H, W, o, t, ws.scal, beta_mult[t], s2, 0.0, nullptr, &n, st)))
+            return s;
+        const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
+        if (kind == EPLL_CONV_PERIODIC) {
+            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, ws.xtil, st)))
+                return s;
+            if ((s = fft_update(g, H, W, beta_mult[t], st))) return s;
+        } else {
+            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, y, kind == EPLL_PIXELWISE ? a : nullptr,
+                                      ws.scal, beta_mult[t], ws.xhat, st)))
+                return s;
+        }
+    }
+    g->last_launches = g->launches;
+    return EPLL_OK;
+}
+
+static epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
+                                      const epll_degradation *deg, float sigma,
+                                      const double *beta_mult, int T, const epll_options &o,
+                                      const float *x_out)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (!y || !x_out) return fail(EPLL_EINVAL, "null image pointer");
+    epll_status s;
+    if ((s = check_image(H, W))) return s;
+    if (!(sigma > 0.0f) || !std::isfinite(sigma)) return fail(EPLL_EINVAL, "sigma must be positive");
+    if (!beta_mult || T < 1 || T > 64) return fail(EPLL_EINVAL, "beta schedule must have 1..64 entries");
+    for (int t = 0; t < T; ++t)
+        if (!(beta_mult[t] > 0.0) || !std::isfinite(beta_mult[t]))
+            return fail(EPLL_EINVAL, "beta multipliers must be positive");
+    if ((s = check_options(o, H, W))) return s;
+    if (deg) {
+        if (deg->kind == EPLL_PIXELWISE) {
+            if (!deg->a) return fail(EPLL_EINVAL, "PIXELWISE degradation needs gains a");
+        } else if (deg->kind == EPLL_CONV_PERIODIC) {
+            if (!deg->kernel || deg->kh < 1 || deg->kw < 1 || deg->kh > H || deg->kw > W)
+                return fail(EPLL_EINVAL, "CONV_PERIODIC kernel must be 1..H x 1..W");
+            double sum = 0.0;
+            for (int q = 0; q < deg->kh * deg->kw; ++q) {
+                if (!std::isfinite(deg->kernel[q])) return fail(EPLL_EINVAL, "kernel is not finite");
+                sum += deg->kernel[q];
+            }
+            if (!(sum > 0.0)) return fail(EPLL_EINVAL, "blur kernel must have a positive sum");
+        } else if (deg->kind != EPLL_DENOISE) {
+            return fail(EPLL_EINVAL, "unknown degradation kind");
+        }
+    }
+    return EPLL_OK;
+}
+
+}  // namespace epll
+
+using namespace epll;
+
+extern "C" {
+
+const char *epll_last_error(void) { return g_err.c_str(); }
+
+void epll_options_default(epll_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = EPLL_FP32;
+    o->tie_gap = -1.0f;
+    o->subset = EPLL_SUBSET_ALL;
+    o->subset_param = 0.0f;
+    o->seed = 0;
+    o->cg_iters = 100;
+}
+
+epll_status epll_gmm_load(int K, int P, const double *weights, const double *eigvecs,
+                          const double *eigvals, int rank_mode, double rank_param, epll_gmm **out)
+{
+    if (!out) return fail(EPLL_EINVAL, "null output handle pointer");
+    *out = nullptr;
+    if (K < 1 || K > 4096) return fail(EPLL_EINVAL, "K must be in 1..4096");
+    if (P != PD) return fail(EPLL_EINVAL, "P must be 64 (8x8 patches)");
+    if (!weights || !eigvecs || !eigvals) return fail(EPLL_EINVAL, "null model array");
+    if (rank_mode == EPLL_RANK_FIXED) {
+        if (!(rank_param >= 1.0 && rank_param <= PD) || rank_param != std::floor(rank_param))
+            return fail(EPLL_EINVAL, "fixed rank must be an integer in 1..64");
+    } else if (rank_mode == EPLL_RANK_RHO) {
+        if (!(rank_param > 0.0 && rank_param <= 1.0)) return fail(EPLL_EINVAL, "rho must be in (0, 1]");
+    } else {
+        return fail(EPLL_EINVAL, "unknown rank mode");
+    }
+    double wsum = 0.0;
+    for (int k = 0; k < K; ++k) {
+        if (!(weights[k] > 0.0) || !std::isfinite(weights[k])) return fail(EPLL_EINVAL, "weights must be positive");
+        wsum += weights[k];
+        for (int j = 0; j < PD; ++j) {
+            double s = eigvals[(size_t)k * PD + j];
+            if (!(s > 0.0) || !std::isfinite(s)) return fail(EPLL_EINVAL, "eigenvalues must be positive");
+            if (j && s > eigvals[(size_t)k * PD + j - 1]) return fail(EPLL_EINVAL, "eigenvalues must be non-increasing");
+        }
+    }
+    for (size_t q = 0; q < (size_t)K * PD * PD; ++q)
+        if (!std::isfinite(eigvecs[q])) return fail(EPLL_EINVAL, "eigenvectors must be finite");
+
+    epll_gmm *g = new epll_gmm();
+    g->K = K;
+    g->rank_mode = rank_mode;
+    g->rank_param = rank_param;
+    g->h_r = new int[K];
+    g->h_lam = new double[K];
+    g->h_roff = new int[K + 1];
+    // flat tail (Sec. "Speed-up via flat tail spectrum approximation")
+    for (int k = 0; k < K; ++k) {
+        const double *s = eigvals + (size_t)k * PD;
+        int rk = PD;
+        if (rank_mode == EPLL_RANK_FIXED) {
+            rk = (int)rank_param;
+        } else {
+            double tot = 0.0, acc = 0.0;
+            for (int j = 0; j < PD; ++j) tot += s[j];
+            for (int j = 0; j < PD; ++j) {
+                acc += s[j];
+                if (acc >= rank_param * tot) { rk = j + 1; break; }
+            }
+        }
+        double tail = 0.0;
+        for (int j = rk; j < PD; ++j) tail += s[j];
+        g->h_r[k] = rk;
+        g->h_lam[k] = rk < PD ? tail / (double)(PD - rk) : 0.0;
+    }
+    g->h_roff[0] = 0;
+    for (int k = 0; k < K; ++k)
+        g->h_roff[k + 1] = g->h_roff[k] + (g->h_r[k] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
+    g->Rtot = (g->h_roff[K] + RTOT_ALIGN - 1) / RTOT_ALIGN * RTOT_ALIGN;
+    g->h_roff[K] = g->Rtot;  // trailing padding columns belong to the last component
+    const int R = g->Rtot;
+
+    std::vector<double> w(K);
+    for (int k = 0; k < K; ++k) w[k] = weights[k] / wsum;
+    std::vector<float> B((size_t)PD * R, 0.0f), Blo((size_t)PD * R, 0.0f);
+    std::vector<int> colk(R);
+    for (int k = 0; k < K; ++k) {
+        for (int c = g->h_roff[k]; c < g->h_roff[k + 1]; ++c) colk[c] = k;
+        for (int e = 0; e < PD; ++e)
+            for (int j = 0; j < g->h_r[k]; ++j) {
+                const double u = eigvecs[((size_t)k * PD + e) * PD + j];
+                const float h = (float)u;
+                B[(size_t)e * R + g->h_roff[k] + j] = h;
+                Blo[(size_t)e * R + g->h_roff[k] + j] = (float)(u - (double)h);
+            }
+    }
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R));
+    A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
+    A(dalloc(&g->d_B, (size_t)PD * R)); A(dalloc(&g->d_Blo, (size_t)PD * R));
+    A(dalloc(&g->tab.cst_hi, K)); A(dalloc(&g->tab.cst_lo, K)); A(dalloc(&g->tab.t_hi, K));
+    A(dalloc(&g->tab.t_lo, K)); A(dalloc(&g->tab.gp, K)); A(dalloc(&g->tab.sgn, K));
+    A(dalloc(&g->tab.q_hi, R)); A(dalloc(&g->tab.q_lo, R)); A(dalloc(&g->tab.gw, R));
+    A(dalloc(&g->tab.Bs, (size_t)R * PD));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_model(g);
+        delete g;
+        return fail(EPLL_ENOMEM, std::string("model allocation: ") + cudaGetErrorString(e));
+    }
+    A(cudaMemcpy(g->d_r, g->h_r, sizeof(int) * K, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_roff, g->h_roff, sizeof(int) * (K + 1), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_colk, colk.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_S, eigvals, sizeof(double) * K * PD, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
+    A(cudaMemset(g->tab.Bs, 0, sizeof(__nv_bfloat16) * (size_t)R * PD));
+    if (e != cudaSuccess) {
+        free_model(g);
+        delete g;
+        return fail(EPLL_ECUDA, std::string("model upload: ") + cudaGetErrorString(e));
+    }
+    *out = g;
+    return EPLL_OK;
+}
+
+void epll_gmm_free(epll_gmm *g)
+{
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_workspace(g->ws);
+    free_model(g);
+    delete g;
+}
+
+epll_status epll_gmm_ranks(const epll_gmm *g, int *ranks, double *lambdas)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (ranks) std::memcpy(ranks, g->h_r, sizeof(int) * g->K);
+    if (lambdas) std::memcpy(lambdas, g->h_lam, sizeof(double) * g->K);
+    return EPLL_OK;
+}
+
+epll_status epll_restore(epll_gmm *g, const float *y, int H, int W, const epll_degradation *deg,
+                         float sigma, const double *beta_mult, int T, const epll_options *opt,
+                         float *x_out, void *stream)
+{
+    epll_options o;
+    if (opt) o = *opt; else epll_options_default(&o);
+    epll_status s;
+    if ((s = check_restore_args(g, y, H, W, deg, sigma, beta_mult, T, o, x_out))) return s;
+    if ((s = ensure_workspace(g, (size_t)H * W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *a = (deg && deg->kind == EPLL_PIXELWISE) ? deg->a : nullptr;
+    if ((s = run_restore(g, y, a, H, W, deg, sigma, beta_mult, T, o, st))) return s;
+    EPLL_CU(cudaMemcpyAsync(x_out, g->ws.xhat, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
+    return EPLL_OK;
+}
+
+epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W, const epll_degradation *deg,
+                              float sigma, const double *beta_mult, int T, const epll_options *opt,
+                              float *x_out, void *stream)
+{
+    epll_options o;
+    if (opt) o = *opt; else epll_options_default(&o);
+    epll_status s;
+    if ((s = check_restore_args(g, y, H, W, deg, sigma, beta_mult, T, o, x_out))) return s;
+    if ((s = ensure_workspace(g, (size_t)H * W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &ws = g->ws;
+    const size_t bytes = sizeof(float) * (size_t)H * W;
+    EPLL_CU(cudaMemcpyAsync(ws.y, y, bytes, cudaMemcpyHostToDevice, st));
+    const float *a = nullptr;
+    if (deg && deg->kind == EPLL_PIXELWISE) {
+        EPLL_CU(cudaMemcpyAsync(ws.a, deg->a, bytes, cudaMemcpyHostToDevice, st));
+        a = ws.a;
+    }
+    if ((s = run_restore(g, ws.y, a, H, W, deg, sigma, beta_mult, T, o, st))) return s;
+    EPLL_CU(cudaMemcpyAsync(x_out, ws.xhat, bytes, cudaMemcpyDeviceToHost, st));
+    EPLL_CU(cudaStreamSynchronize(st));
+    return EPLL_OK;
+}
+
+__global__ void k_iota(int *out, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i;
+}
+
+epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double beta,
+                            const epll_options *opt, int t, float *xtilde, int *anchors,
+                            int *kstar, float *gap, const int *forced_k, int *n_out, void *stream)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (!xhat || !xtilde) return fail(EPLL_EINVAL, "null image pointer");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(EPLL_EINVAL, "beta must be positive");
+    epll_options o;
+    if (opt) o = *opt; else epll_options_default(&o);
+    epll_status s;
+    if ((s = check_image(H, W))) return s;
+    if ((s = check_options(o, H, W))) return s;
+    if ((s = ensure_workspace(g, (size_t)H * W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &ws = g->ws;
+    g->launches = 0;
+    g->last_evals = 0;
+    EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
+    int n = 0;
+    if ((s = patch_phase(g, xhat, H, W, o, t, ws.scal, 1.0, 1.0, beta, forced_k, &n, st))) return s;
+    const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
+    if ((s = launch_aggregate(g, xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, xtilde, st))) return s;
+    if (anchors) {
+        if (o.subset == EPLL_SUBSET_ALL) {
+            k_iota<<<(n + 255) / 256, 256, 0, st>>>(anchors, n);
+            EPLL_LAUNCHED(g);
+        } else {
+            EPLL_CU(cudaMemcpyAsync(anchors, ws.anchors, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    if (kstar) EPLL_CU(cudaMemcpyAsync(kstar, ws.kstar, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (gap) EPLL_CU(cudaMemcpyAsync(gap, ws.gap, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    g->last_launches = g->launches;
+    if (n_out) {
+        EPLL_CU(cudaStreamSynchronize(st));
+        *n_out = n;
+    }
+    return EPLL_OK;
+}
+
+epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *anchors, int *n_out,
+                        void *stream)
+{
+    if (!anchors || !n_out) return fail(EPLL_EINVAL, "null output pointer");
+    epll_options o;
+    if (opt) o = *opt; else epll_options_default(&o);
+    epll_status s;
+    if ((s = check_image(H, W))) return s;
+    if ((s = check_options(o, H, W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)H * W;
+    epll_gmm tmp;
+    unsigned *mult = nullptr;
+    if (dalloc(&tmp.ws.sampler, 1040 + 2 * (N / 2048 + 2)) != cudaSuccess || dalloc(&mult, N) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(tmp.ws.sampler);
+        cudaFree(mult);
+        return fail(EPLL_ENOMEM, "sampler scratch allocation failed");
+    }
+    int n = 0;
+    s = launch_sample(&tmp, H, W, o, t, &n, anchors, mult, st);
+    if (s == EPLL_OK && o.subset == EPLL_SUBSET_ALL) {
+        k_iota<<<(n + 255) / 256, 256, 0, st>>>(anchors, n);
+        if (cudaGetLastError() != cudaSuccess) s = fail(EPLL_ECUDA, "iota launch failed");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(tmp.ws.sampler);
+    cudaFree(mult);
+    tmp.ws.sampler = nullptr;
+    if (s) return s;
+    if (e != cudaSuccess) return fail(EPLL_ECUDA, std::string("sampler: ") + cudaGetErrorString(e));
+    *n_out = n;
+    return EPLL_OK;
+}
+
+epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *rescored,
+                               long long *launches)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    EPLL_CU(cudaDeviceSynchronize());
+    long long c[4] = {0, 0, 0, 0};
+    if (g->ws.ctr) EPLL_CU(cudaMemcpy(c, g->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (patch_evals) *patch_evals = g->last_evals;
+    if (rescored) *rescored = c[0];
+    if (launches) *launches = g->last_launches;
+    return EPLL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Internal declarations of libepll: the model handle, its workspace, the
+// per-beta tables, and the kernels' host-side launchers.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <string>
+
+#include "epll.h"
+
+namespace epll {
+
+constexpr int PS = 8;   // patch side
+constexpr int PD = 64;  // patch dimension P
+constexpr int COL_ALIGN = 8;    // each component's columns are padded to a multiple of this
+constexpr int RTOT_ALIGN = 256; // total column count is padded to a multiple of this
+
+// Per-beta quantities of Eq. 14 (flat-tail Gaussian selection) and Eq. 15-16
+// (patch estimation), written by the FP64 tables kernel every iteration.
+//   score_k(z) = cst_k + t_k |z|^2 + sum_j q_kj c_kj^2,  c_k = Ubar_k^T z
+//   cst_k = -2 log w_k + sum_{j<r} log nu_kj + (P - r_k) log nu_kP - cst_0
+//   t_k = 1/nu_kP (0 when r_k = P),  q_kj = 1/nu_kj - t_k
+//   gw_kj = gamma_kj - gamma_kP,  gp_k = gamma_kP (0 when r_k = P)
+// The shared offset cst_0 (component 0's constant) keeps FP32 scores small;
+// it does not change the argmin or any gap.  hi/lo pairs hold the FP64 value
+// as an unevaluated float sum for the compensated rescoring.
+struct Tables {
+    float *cst_hi = nullptr, *cst_lo = nullptr;  // [K]
+    float *t_hi = nullptr, *t_lo = nullptr;      // [K]
+    float *gp = nullptr;                         // [K]
+    float *sgn = nullptr;                        // [K]: sign of q_kj (+1 full rank, -1 flat tail)
+    float *q_hi = nullptr, *q_lo = nullptr;      // [Rtot]
+    float *gw = nullptr;                         // [Rtot]
+    __nv_bfloat16 *Bs = nullptr;                 // [Rtot][64]: bf16(Ubar * sqrt|q|), K-major
+};
+
+struct Workspace {
+    size_t capN = 0;
+    float *xhat = nullptr, *xtil = nullptr;   // [N]
+    float *y = nullptr, *a = nullptr;         // [N], host-buffer entry point only
+    int *anchors = nullptr;                   // [N]
+    unsigned *mult = nullptr;                 // [N] multiplicity of each anchor in the subset
+    int *kstar = nullptr;                     // [N]
+    float *gap = nullptr;                     // [N]
+    int *flag = nullptr;                      // [N] near-tie list
+    int *perm = nullptr;                      // [N] list entries grouped by component
+    float *zrow = nullptr;                    // [N][64] patch estimates, row per anchor
+    __nv_bfloat16 *Zb = nullptr;              // [N][64] bf16 DC-free patches (tensor path)
+    float *zz = nullptr;                      // [N] |z|^2 (tensor path)
+    float *cg = nullptr;                      // [4N] CG vectors r, d, q, spare
+    float *red = nullptr;                     // reduction partials
+    double *scal = nullptr;                   // device scalars (lambda, CG state)
+    unsigned *sampler = nullptr;              // radix-select histograms and state
+    int *counts = nullptr;                    // [2K+8] bucket counts/cursors + counters
+    long long *ctr = nullptr;                 // [4] device counters: rescored patches
+    cufftComplex *Yh = nullptr, *Hh = nullptr, *Xh = nullptr;  // [H][W/2+1]
+    float *kern = nullptr;                    // [H][W] wrapped blur kernel
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+    int planH = 0, planW = 0;
+};
+
+}  // namespace epll
+
+struct epll_gmm {
+    int K = 0;
+    int Rtot = 0;                 // padded total number of basis columns
+    int rank_mode = 0;
+    double rank_param = 0.0;
+    int *h_r = nullptr;           // [K]
+    double *h_lam = nullptr;      // [K]
+    int *h_roff = nullptr;        // [K+1] column offsets (padded)
+    // device model
+    int *d_r = nullptr, *d_roff = nullptr, *d_colk = nullptr;   // colk: [Rtot] component of each column
+    double *d_S = nullptr, *d_w = nullptr, *d_lam = nullptr;     // [K][64], [K], [K]
+    float *d_B = nullptr;         // [64][Rtot] Ubar_k concatenated (FP32 rounding of U)
+    float *d_Blo = nullptr;       // [64][Rtot] U - B (the FP32 rounding error)
+    epll::Tables tab;
+    epll::Workspace ws;
+    long long last_evals = 0, last_launches = 0;
+    long long launches = 0;
+};
+
+namespace epll {
+
+// ---------------------------------------------------------------- error state
+void set_error(const std::string &msg);
+#define EPLL_CU(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            epll::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+            return EPLL_ECUDA;                                                         \
+        }                                                                              \
+    } while (0)
+#define EPLL_LAUNCHED(g)                                                               \
+    do {                                                                               \
+        ++(g)->launches;                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            epll::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));   \
+            return EPLL_ECUDA;                                                         \
+        }                                                                              \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers
+// Each returns EPLL_OK or an error after setting the message.  All enqueue on st.
+epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
+                          double beta_direct, bool bf16, cudaStream_t st);
+
+// Sampler: writes ws.anchors (FRACTION/JITTER) and ws.mult; returns n via *n.
+// FULL leaves anchors untouched (identity) and mult unused.
+epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t, int *n,
+                          int *anchors_out, unsigned *mult_out, cudaStream_t st);
+int sample_count(int H, int W, const epll_options &o);
+
+epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                               int n, float tau, cudaStream_t st);
+epll_status launch_select_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                               int n, float tau, cudaStream_t st);
+epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                           int n, cudaStream_t st);
+epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                            int n, cudaStream_t st);
+// Reprojection.  When y != nullptr the pixelwise image update is fused
+// (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult; a == nullptr means a = 1),
+// otherwise xtilde is written to xout.
+epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
+                             const float *y, const float *a, const double *d_lambda, double bmult,
+                             float *xout, cudaStream_t st);
+
+// Image-domain steps (k_image.cu)
+epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
+                          cudaStream_t st);   // writes ws.scal[0]
+epll_status fft_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *y,
+                        int H, int W, cudaStream_t st);  // plans, Hh, Yh
+epll_status fft_init(epll_gmm *g, int H, int W, double sigma, cudaStream_t st);    // ws.xhat
+epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st);  // ws.xtil -> ws.xhat
+epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, double sigma,
+                    int iters, cudaStream_t st);  // ws.xhat
+
+epll_status ensure_workspace(epll_gmm *g, size_t N);
+
+}  // namespace epll

@@ -1,0 +1,513 @@
+// Patch-step kernels of Algorithm 1: patch extraction, Gaussian selection
+// (FP32 SIMT form), near-tie rescoring in compensated FP32, grouping of the
+// patches by selected component, Wiener patch estimation (Eqs. 15-16) and
+// patch reprojection by overlap-add averaging fused with the image update.
+#include "epll_internal.cuh"
+
+#include <cfloat>
+
+namespace epll {
+
+// Periodic 8x8 patch at anchor a (top-left pixel), element e = 8u + v.
+__device__ __forceinline__ size_t pix(int ai, int aj, int u, int v, int H, int W)
+{
+    int i = ai + u;
+    if (i >= H) i -= H;
+    int j = aj + v;
+    if (j >= W) j -= W;
+    return (size_t)i * W + j;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ============================================================================
+// Gaussian selection, FP32 SIMT form.  One thread per sampled patch: the
+// thread extracts its DC-free patch into registers, then streams the
+// concatenated bases [Ubar_1 ... Ubar_K] (64 x Rtot) through shared memory in
+// chunks of SEL_CH columns, forming c = Ubar^T z (Eq. 13) and the score of
+// Eq. 14 component by component, keeping the best and second-best score.
+// Patches whose top-2 gap is below tau are appended to the near-tie list.
+// ============================================================================
+constexpr int SEL_THREADS = 128;
+constexpr int SEL_CH = 32;
+
+__global__ void __launch_bounds__(SEL_THREADS)
+k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
+              const float *__restrict__ B, int Rtot, const int *__restrict__ colk, Tables tab,
+              float tau, int *__restrict__ kstar, float *__restrict__ gap,
+              int *__restrict__ flag, int *__restrict__ nflag)
+{
+    __shared__ __align__(16) float Bs[PD][SEL_CH];
+    __shared__ float qs[SEL_CH];
+    __shared__ int ks[SEL_CH];
+    const int i = blockIdx.x * SEL_THREADS + threadIdx.x;
+    const bool valid = i < n;
+
+    float z[PD];
+    float zz = 0.0f;
+    {
+        const int a = valid ? (anchors ? anchors[i] : i) : 0;
+        const int ai = a / W, aj = a % W;
+        float m = 0.0f;
+#pragma unroll
+        for (int u = 0; u < PS; ++u)
+#pragma unroll
+            for (int v = 0; v < PS; ++v) {
+                z[u * PS + v] = xhat[pix(ai, aj, u, v, H, W)];
+                m += z[u * PS + v];
+            }
+        m *= (1.0f / PD);
+#pragma unroll
+        for (int e = 0; e < PD; ++e) {
+            z[e] -= m;
+            zz = fmaf(z[e], z[e], zz);
+        }
+    }
+
+    float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
+    int k1 = 0, curk = -1;
+    for (int c0 = 0; c0 < Rtot; c0 += SEL_CH) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < PD * SEL_CH / 4; idx += SEL_THREADS) {
+            const int e = idx / (SEL_CH / 4), c4 = idx % (SEL_CH / 4);
+            reinterpret_cast<float4 *>(&Bs[e][0])[c4] =
+                *reinterpret_cast<const float4 *>(B + (size_t)e * Rtot + c0 + 4 * c4);
+        }
+        if (threadIdx.x < SEL_CH) {
+            qs[threadIdx.x] = tab.q_hi[c0 + threadIdx.x];
+            ks[threadIdx.x] = colk[c0 + threadIdx.x];
+        }
+        __syncthreads();
+        float c[SEL_CH];
+#pragma unroll
+        for (int cc = 0; cc < SEL_CH; ++cc) c[cc] = 0.0f;
+#pragma unroll
+        for (int e = 0; e < PD; ++e) {
+            const float ze = z[e];
+#pragma unroll
+            for (int c4 = 0; c4 < SEL_CH / 4; ++c4) {
+                const float4 b = reinterpret_cast<const float4 *>(&Bs[e][0])[c4];
+                c[4 * c4 + 0] = fmaf(ze, b.x, c[4 * c4 + 0]);
+                c[4 * c4 + 1] = fmaf(ze, b.y, c[4 * c4 + 1]);
+                c[4 * c4 + 2] = fmaf(ze, b.z, c[4 * c4 + 2]);
+                c[4 * c4 + 3] = fmaf(ze, b.w, c[4 * c4 + 3]);
+            }
+        }
+#pragma unroll
+        for (int cc = 0; cc < SEL_CH; ++cc) {
+            const int k = ks[cc];
+            if (k != curk) {
+                if (curk >= 0) {
+                    const float s = tab.cst_hi[curk] + tab.t_hi[curk] * zz + acc;
+                    if (s < s1) { s2 = s1; s1 = s; k1 = curk; }
+                    else if (s < s2) { s2 = s; }
+                }
+                curk = k;
+                acc = 0.0f;
+            }
+            acc = fmaf(qs[cc] * c[cc], c[cc], acc);
+        }
+    }
+    {
+        const float s = tab.cst_hi[curk] + tab.t_hi[curk] * zz + acc;
+        if (s < s1) { s2 = s1; s1 = s; k1 = curk; }
+        else if (s < s2) { s2 = s; }
+    }
+    if (valid) {
+        kstar[i] = k1;
+        const float gp = s2 - s1;
+        gap[i] = gp;
+        if (gp < tau) flag[atomicAdd(nflag, 1)] = i;
+    }
+}
+
+epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                               int n, float tau, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    int *nflag = ws.counts + 2 * g->K;
+    EPLL_CU(cudaMemsetAsync(nflag, 0, sizeof(int), st));
+    k_select_fp32<<<(n + SEL_THREADS - 1) / SEL_THREADS, SEL_THREADS, 0, st>>>(
+        xhat, H, W, anchors, n, g->d_B, g->Rtot, g->d_colk, g->tab, tau, ws.kstar, ws.gap, ws.flag,
+        nflag);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+// ============================================================================
+// Near-tie rescoring.  One warp per listed patch.  Pass 1 recomputes all K
+// scores in FP32 (lanes over basis columns); every component within
+// RESCORE_BAND of the best is then rescored in compensated arithmetic: the
+// patch, its mean, the basis (float value + float rounding error of the FP64
+// eigenvectors) and the FP64 tables are carried as unevaluated sums of two
+// floats (Dekker's TwoSum / TwoProduct with FMA), which resolves the
+// selection like FP64 arithmetic would.  The winner and its gap overwrite
+// kstar / gap.
+// ============================================================================
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    float s = a + b;
+    float e = b - (s - a);
+    return {s, e};
+}
+__device__ __forceinline__ df df_add(df x, df y)
+{
+    df s = two_sum(x.hi, y.hi);
+    df t = two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y)
+{
+    float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_shfl_xor(df v, int o)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ df df_warp_sum(df v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+    return v;
+}
+// x < y for unevaluated sums
+__device__ __forceinline__ bool df_less(df x, df y)
+{
+    df d = df_add(x, {-y.hi, -y.lo});
+    return d.hi < 0.0f || (d.hi == 0.0f && d.lo < 0.0f);
+}
+
+constexpr float RESCORE_BAND = 1e-2f;
+constexpr int RS_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * RS_WARPS)
+k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+          const int *__restrict__ flag, const int *__restrict__ nflag, int K, int Rtot,
+          const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
+          const float *__restrict__ Blo, Tables tab, int *__restrict__ kstar,
+          float *__restrict__ gap, long long *__restrict__ ctr)
+{
+    extern __shared__ float dyn[];
+    __shared__ float zh[RS_WARPS][PD], zl[RS_WARPS][PD], zf[RS_WARPS][PD];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sc = dyn + (size_t)w * K;
+    const int total = *nflag;
+    const int gw = blockIdx.x * RS_WARPS + w, nw = gridDim.x * RS_WARPS;
+    if (gw == 0 && lane == 0 && total > 0) atomicAdd((unsigned long long *)ctr, (unsigned long long)total);
+    for (int f = gw; f < total; f += nw) {
+        const int i = flag[f];
+        const int a = anchors ? anchors[i] : i;
+        const int ai = a / W, aj = a % W;
+        const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
+        const float x1 = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+        // mean and DC-free patch, compensated
+        df sx = df_warp_sum(two_sum(x0, x1));
+        df mu = {sx.hi * (1.0f / PD), sx.lo * (1.0f / PD)};
+        df z0 = df_add({x0, 0.0f}, {-mu.hi, -mu.lo});
+        df z1 = df_add({x1, 0.0f}, {-mu.hi, -mu.lo});
+        df zz = df_warp_sum(df_add(df_mul(z0, z0), df_mul(z1, z1)));
+        zh[w][lane] = z0.hi; zl[w][lane] = z0.lo;
+        zh[w][lane + 32] = z1.hi; zl[w][lane + 32] = z1.lo;
+        zf[w][lane] = z0.hi + z0.lo; zf[w][lane + 32] = z1.hi + z1.lo;
+        const float zzf = zz.hi + zz.lo;
+        __syncwarp();
+        // pass 1: FP32 scores of all components
+        float best = FLT_MAX;
+        for (int k = 0; k < K; ++k) {
+            const int o = roff[k], r = rk_[k];
+            float part = 0.0f;
+            for (int j = lane; j < r; j += 32) {
+                float c = 0.0f;
+#pragma unroll 8
+                for (int e = 0; e < PD; ++e) c = fmaf(B[(size_t)e * Rtot + o + j], zf[w][e], c);
+                part = fmaf(tab.q_hi[o + j] * c, c, part);
+            }
+            const float s = tab.cst_hi[k] + tab.t_hi[k] * zzf + warp_sum(part);
+            if (lane == 0) sc[k] = s;
+            best = fminf(best, s);
+        }
+        __syncwarp();
+        // pass 2: compensated scores of the components within the band
+        df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
+        int kb = -1;
+        float outside = FLT_MAX;
+        for (int k = 0; k < K; ++k) {
+            const float sk = sc[k];
+            if (sk > best + RESCORE_BAND) {
+                outside = fminf(outside, sk);
+                continue;
+            }
+            const int o = roff[k], r = rk_[k];
+            df part = {0.0f, 0.0f};
+            for (int j = lane; j < r; j += 32) {
+                df c = {0.0f, 0.0f};
+                for (int e = 0; e < PD; ++e) {
+                    df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
+                    c = df_add(c, df_mul(u, {zh[w][e], zl[w][e]}));
+                }
+                df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
+                part = df_add(part, df_mul(q, df_mul(c, c)));
+            }
+            df s = df_warp_sum(part);
+            s = df_add(s, df_mul({tab.t_hi[k], tab.t_lo[k]}, zz));
+            s = df_add(s, {tab.cst_hi[k], tab.cst_lo[k]});
+            if (df_less(s, b1)) { b2 = b1; b1 = s; kb = k; }
+            else if (df_less(s, b2)) { b2 = s; }
+        }
+        if (lane == 0 && kb >= 0) {  // kb < 0 only if every score was NaN
+            kstar[i] = kb;
+            float g2 = (b2.hi == FLT_MAX) ? outside - (b1.hi + b1.lo)
+                                          : (b2.hi - b1.hi) + (b2.lo - b1.lo);
+            gap[i] = fminf(g2, outside - (b1.hi + b1.lo));
+        }
+        __syncwarp();
+    }
+}
+
+epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                           int n, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const size_t smem = sizeof(float) * (size_t)RS_WARPS * g->K;
+    if (smem > 48 * 1024)
+        EPLL_CU(cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = (n + RS_WARPS - 1) / RS_WARPS;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) blocks = 1;
+    k_rescore<<<blocks, 32 * RS_WARPS, smem, st>>>(xhat, H, W, anchors, ws.flag, ws.counts + 2 * g->K,
+                                                    g->K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->d_Blo,
+                                                    g->tab, ws.kstar, ws.gap, ws.ctr);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+// Component indices handed in by the caller (teacher forcing) are clamped
+// into range before they index anything.
+__device__ __forceinline__ int clamp_k(int k, int K) { return k < 0 ? 0 : (k >= K ? K - 1 : k); }
+
+// ============================================================================
+// Grouping by component (counting sort): histogram, exclusive scan, scatter.
+// The order inside a group does not matter: every patch's estimate depends
+// only on the patch and its component.
+// ============================================================================
+__global__ void k_bucket_hist(const int *__restrict__ kstar, int n, int K, int *__restrict__ counts)
+{
+    extern __shared__ int h[];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[clamp_k(kstar[i], K)], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (h[k]) atomicAdd(&counts[k], h[k]);
+}
+
+__global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ counts)
+{
+    // counts[0..K) -> cursors (exclusive prefix), in place
+    __shared__ int c[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < K; b0 += 1024) {
+        int k = b0 + threadIdx.x;
+        int v = k < K ? counts[k] : 0;
+        c[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int u = threadIdx.x >= off ? c[threadIdx.x - off] : 0;
+            __syncthreads();
+            c[threadIdx.x] += u;
+            __syncthreads();
+        }
+        if (k < K) counts[k] = carry + c[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += c[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, int *__restrict__ cursor,
+                                 int *__restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[atomicAdd(&cursor[clamp_k(kstar[i], K)], 1)] = i;
+}
+
+// ============================================================================
+// Patch estimation (Eqs. 15-16): chat_j = (gamma_j - gamma_P) c_j,
+// zhat = Ubar chat + gamma_P z + mean.  A block takes 64 consecutive entries
+// of the component-grouped list; for every run of equal components it stages
+// Ubar_k (and its transpose) in shared memory, then each warp estimates one
+// patch at a time (lanes over basis columns, then over pixels).  The estimate
+// is written as a 64-float row at the patch's anchor.
+// ============================================================================
+constexpr int EST_WARPS = 4;
+constexpr int EST_ENTRIES = 64;
+
+__global__ void __launch_bounds__(32 * EST_WARPS)
+k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
+           const int *__restrict__ perm, const int *__restrict__ kstar, int K, int Rtot,
+           const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
+           Tables tab, float *__restrict__ zrow)
+{
+    __shared__ float Us[PD][PD + 1];   // Us[e][j]
+    __shared__ float UT[PD][PD + 1];   // UT[j][e]
+    __shared__ float gws[PD];
+    __shared__ float zs[EST_WARPS][PD], cs[EST_WARPS][PD];
+    __shared__ int run_end;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int begin = blockIdx.x * EST_ENTRIES;
+    const int end = min(n, begin + EST_ENTRIES);
+    int pos = begin;
+    while (pos < end) {
+        const int k = clamp_k(kstar[perm[pos]], K);
+        if (threadIdx.x == 0) run_end = end;
+        __syncthreads();
+        for (int q = pos + threadIdx.x; q < end; q += blockDim.x)
+            if (clamp_k(kstar[perm[q]], K) != k) atomicMin(&run_end, q);
+        const int o = roff[k], r = rk_[k];
+        for (int idx = threadIdx.x; idx < PD * r; idx += blockDim.x) {
+            const int e = idx / r, j = idx % r;
+            const float u = B[(size_t)e * Rtot + o + j];
+            Us[e][j] = u;
+            UT[j][e] = u;
+        }
+        for (int j = threadIdx.x; j < r; j += blockDim.x) gws[j] = tab.gw[o + j];
+        __syncthreads();
+        const float gp = tab.gp[k];
+        const int stop = run_end;
+        for (int q = pos + w; q < stop; q += EST_WARPS) {
+            const int i = perm[q];
+            const int a = anchors ? anchors[i] : i;
+            const int ai = a / W, aj = a % W;
+            const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
+            const float x1 = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+            const float mu = warp_sum(x0 + x1) * (1.0f / PD);
+            zs[w][lane] = x0 - mu;
+            zs[w][lane + 32] = x1 - mu;
+            __syncwarp();
+            for (int j = lane; j < r; j += 32) {
+                float c = 0.0f;
+#pragma unroll 8
+                for (int e = 0; e < PD; ++e) c = fmaf(Us[e][j], zs[w][e], c);
+                cs[w][j] = gws[j] * c;
+            }
+            __syncwarp();
+            float v0 = gp * zs[w][lane], v1 = gp * zs[w][lane + 32];
+            for (int j = 0; j < r; ++j) {
+                const float cj = cs[w][j];
+                v0 = fmaf(UT[j][lane], cj, v0);
+                v1 = fmaf(UT[j][lane + 32], cj, v1);
+            }
+            float *dst = zrow + (size_t)a * PD;
+            dst[lane] = v0 + mu;
+            dst[lane + 32] = v1 + mu;
+            __syncwarp();
+        }
+        __syncthreads();
+        pos = stop;
+    }
+}
+
+epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                            int n, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int K = g->K;
+    int *counts = ws.counts;  // [K] counts -> cursors
+    EPLL_CU(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)K, st));
+    int hb = (n + 255) / 256;
+    if (hb > 152 * 2) hb = 152 * 2;
+    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(ws.kstar, n, K, counts);
+    EPLL_LAUNCHED(g);
+    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts);
+    EPLL_LAUNCHED(g);
+    k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(ws.kstar, n, K, counts, ws.perm);
+    EPLL_LAUNCHED(g);
+    k_estimate<<<(n + EST_ENTRIES - 1) / EST_ENTRIES, 32 * EST_WARPS, 0, st>>>(
+        xhat, H, W, anchors, n, ws.perm, ws.kstar, K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab,
+        ws.zrow);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+// ============================================================================
+// Patch reprojection (Algorithm 1; Eq. 6 with the per-pixel patch count),
+// written as a gather: every pixel sums, in a fixed order, the estimates of
+// the sampled patches that cover it (weighted by their multiplicity in the
+// subset), divides by their number, and keeps the current estimate where no
+// sampled patch covers it.  Optionally fused with the pixelwise image update
+// xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult.
+// ============================================================================
+__global__ void __launch_bounds__(256)
+k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
+            const float *xhat, int H, int W, const float *__restrict__ y,
+            const float *__restrict__ a, const double *__restrict__ d_lambda, double bmult,
+            float *xout)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    const int i = p / W, j = p % W;
+    float sum = 0.0f;
+    unsigned cnt = 0;
+#pragma unroll
+    for (int u = 0; u < PS; ++u) {
+        int ai = i - u;
+        if (ai < 0) ai += H;
+#pragma unroll
+        for (int v = 0; v < PS; ++v) {
+            int aj = j - v;
+            if (aj < 0) aj += W;
+            const size_t an = (size_t)ai * W + aj;
+            const unsigned m = mult ? mult[an] : 1u;
+            if (m) {
+                sum = fmaf((float)m, zrow[an * PD + u * PS + v], sum);
+                cnt += m;
+            }
+        }
+    }
+    const float xt = cnt ? sum / (float)cnt : xhat[p];
+    if (y) {
+        const float bs = (float)(d_lambda[0] * bmult);
+        const float ap = a ? a[p] : 1.0f;
+        xout[p] = (ap * y[p] + bs * xt) / (ap * ap + bs);
+    } else {
+        xout[p] = xt;
+    }
+}
+
+epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
+                             const float *y, const float *a, const double *d_lambda, double bmult,
+                             float *xout, cudaStream_t st)
+{
+    const int N = H * W;
+    k_aggregate<<<(N + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, d_lambda, bmult,
+                                                 xout);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+}  // namespace epll

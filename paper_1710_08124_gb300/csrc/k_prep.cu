@@ -1,0 +1,359 @@
+// Per-iteration preparation kernels: the FP64 per-beta tables of the
+// Gaussian selection / patch estimation steps, and the patch samplers.
+#include "epll_internal.cuh"
+
+namespace epll {
+
+// ============================================================================
+// Per-beta tables (Sec. "Complexity via eigenspace implementation", Eq. 8;
+// flat-tail form Eqs. 14-16).  One block per component, 64 threads; FP64
+// throughout, results rounded to float (plus the float rounding error for the
+// compensated rescoring).  1/beta = sigma^2 / (lambda * mult) with lambda read
+// from device memory, or 1/beta_direct when beta_direct > 0.
+// ============================================================================
+__device__ double block64_sum(double v, double *red)
+{
+    int j = threadIdx.x;
+    red[j] = v;
+    __syncthreads();
+    for (int s = 32; s > 0; s >>= 1) {
+        if (j < s) red[j] += red[j + s];
+        __syncthreads();
+    }
+    double tot = red[0];
+    __syncthreads();
+    return tot;
+}
+
+// -2 log w_k + sum_{j<r} log(S_kj + ib) + (P - r) log(lambda_k + ib)
+__device__ double component_constant(int k, const int *r, const double *S, const double *w,
+                                     const double *lam, double ib, double *red)
+{
+    int j = threadIdx.x;
+    int rk = r[k];
+    double v = (j < rk) ? log(S[(size_t)k * PD + j] + ib) : 0.0;
+    double c = block64_sum(v, red) - 2.0 * log(w[k]);
+    if (rk < PD) c += (double)(PD - rk) * log(lam[k] + ib);
+    return c;
+}
+
+__global__ void __launch_bounds__(64)
+k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ roff,
+         const double *__restrict__ S, const double *__restrict__ w, const double *__restrict__ lam,
+         const double *__restrict__ d_lambda, double mult, double sigma2, double beta_direct,
+         const float *__restrict__ B, Tables tab, int want_bf16)
+{
+    __shared__ double red[64];
+    __shared__ float sq[64 + RTOT_ALIGN];
+    const int k = blockIdx.x, j = threadIdx.x;
+    const double ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
+
+    const double c0 = component_constant(0, r, S, w, lam, ib, red);
+    const double ck = component_constant(k, r, S, w, lam, ib, red);
+    const int rk = r[k];
+    const double nuP = lam[k] + ib;
+    const double t = rk < PD ? 1.0 / nuP : 0.0;
+    const double gP = rk < PD ? lam[k] / nuP : 0.0;
+    if (j == 0) {
+        double cst = ck - c0;
+        float h = (float)cst;
+        tab.cst_hi[k] = h;
+        tab.cst_lo[k] = (float)(cst - (double)h);
+        float th = (float)t;
+        tab.t_hi[k] = th;
+        tab.t_lo[k] = (float)(t - (double)th);
+        tab.gp[k] = (float)gP;
+        tab.sgn[k] = rk < PD ? -1.0f : 1.0f;
+    }
+    const int o = roff[k], rp = roff[k + 1] - o;
+    for (int jj = j; jj < rp; jj += 64) {
+        double q = 0.0, gw = 0.0;
+        if (jj < rk) {
+            double nu = S[(size_t)k * PD + jj] + ib;
+            q = 1.0 / nu - t;
+            gw = S[(size_t)k * PD + jj] / nu - gP;
+        }
+        float qh = (float)q;
+        tab.q_hi[o + jj] = qh;
+        tab.q_lo[o + jj] = (float)(q - (double)qh);
+        tab.gw[o + jj] = (float)gw;
+        sq[jj] = (float)sqrt(fabs(q));
+    }
+    if (!want_bf16) return;
+    __syncthreads();
+    // scaled basis, K-major: Bs[col][e] = bf16(U[e][col] * sqrt|q_col|)
+    for (int jj = 0; jj < rp; ++jj) {
+        float v = (jj < rk) ? B[(size_t)j * Rtot + o + jj] * sq[jj] : 0.0f;
+        tab.Bs[(size_t)(o + jj) * PD + j] = __float2bfloat16_rn(v);
+    }
+}
+
+epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
+                          double beta_direct, bool bf16, cudaStream_t st)
+{
+    k_tables<<<g->K, 64, 0, st>>>(g->K, g->Rtot, g->d_r, g->d_roff, g->d_S, g->d_w, g->d_lam,
+                                  d_lambda, mult, sigma2, beta_direct, g->d_B, g->tab, bf16 ? 1 : 0);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+// ============================================================================
+// Counter-based random numbers: splitmix64 (Steele, Lea & Flood, OOPSLA 2014;
+// output-function constants of Vigna's public-domain splitmix64.c).
+// Draw idx of stream s for seed x: state = mix(x + (s+1) G), draw = mix(state + (idx+1) G).
+// ============================================================================
+__device__ __forceinline__ uint64_t smix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+constexpr uint64_t GOLDEN = 0x9e3779b97f4a7c15ULL;
+
+__device__ __forceinline__ uint64_t stream_state(uint64_t seed, uint64_t s)
+{
+    return smix(seed + (s + 1) * GOLDEN);
+}
+__device__ __forceinline__ uint64_t draw(uint64_t state, uint64_t idx)
+{
+    return smix(state + (idx + 1) * GOLDEN);
+}
+__device__ __forceinline__ int uniform_int(uint64_t u, int m)
+{
+    return (int)(((u >> 32) * (uint64_t)m) >> 32);
+}
+
+// ---------------------------------------------------------------- jitter
+// Jittered grid of Eq. 20: spacing s, global shift from draws 0/1, per-point
+// offsets in [-J, J] from draws 2+2g / 3+2g; raster order of grid points.
+__global__ void k_jitter(int H, int W, int s, uint64_t seed, int t, int ni, int nj,
+                         int *__restrict__ anchors, unsigned *__restrict__ mult)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ni * nj) return;
+    const uint64_t st = stream_state(seed, (uint64_t)t);
+    const int J = (PS - s) / 2;
+    const int gi = uniform_int(draw(st, 0), s), gj = uniform_int(draw(st, 1), s);
+    const int n = g / nj, m = g % nj;
+    const int di = uniform_int(draw(st, 2 + 2 * (uint64_t)g), 2 * J + 1) - J;
+    const int dj = uniform_int(draw(st, 3 + 2 * (uint64_t)g), 2 * J + 1) - J;
+    const int i = ((gi + s * n + di) % H + H) % H;
+    const int j = ((gj + s * m + dj) % W + W) % W;
+    const int a = i * W + j;
+    anchors[g] = a;
+    atomicAdd(&mult[a], 1u);
+}
+
+// ---------------------------------------------------------------- fraction
+// Exactly M = ceil(frac N) anchors: those with the smallest (key, anchor),
+// key = high 32 bits of draw(anchor).  A 4-pass radix select (8-bit digits,
+// most significant first) finds the key of rank M-1 and its rank among equal
+// keys; a 3-phase stream compaction then writes the selection in anchor order.
+// sel = {prefix, mask, rank} of the partially determined threshold key.
+__device__ __forceinline__ uint32_t frac_key(uint64_t st, int a)
+{
+    return (uint32_t)(draw(st, (uint64_t)a) >> 32);
+}
+
+__global__ void __launch_bounds__(256)
+k_frac_hist(int N, uint64_t seed, int t, int pass, const unsigned *__restrict__ sel,
+            unsigned *__restrict__ hist)
+{
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t st = stream_state(seed, (uint64_t)t);
+    const int shift = 24 - 8 * pass;
+    const unsigned prefix = pass ? sel[0] : 0u, mask = pass ? sel[1] : 0u;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
+        uint32_t key = frac_key(st, a);
+        if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[pass * 256 + threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256)
+k_frac_pick(int pass, int M, unsigned *__restrict__ sel, const unsigned *__restrict__ hist)
+{
+    __shared__ unsigned c[256];
+    const int d = threadIdx.x;
+    const unsigned hd = hist[pass * 256 + d];
+    c[d] = hd;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele)
+    for (int off = 1; off < 256; off <<= 1) {
+        unsigned v = d >= off ? c[d - off] : 0u;
+        __syncthreads();
+        c[d] += v;
+        __syncthreads();
+    }
+    const unsigned before = c[d] - hd;
+    const unsigned R = pass ? sel[2] : (unsigned)(M - 1);
+    const unsigned prefix = pass ? sel[0] : 0u, mask = pass ? sel[1] : 0u;
+    __syncthreads();
+    if (hd && before <= R && R < before + hd) {
+        const int shift = 24 - 8 * pass;
+        sel[0] = prefix | ((unsigned)d << shift);
+        sel[1] = mask | (255u << shift);
+        sel[2] = R - before;
+    }
+}
+
+constexpr int FRAC_ITEMS = 8;
+constexpr int FRAC_TILE = 256 * FRAC_ITEMS;
+
+// phase 1: per-tile counts of keys below / equal to the threshold
+__global__ void __launch_bounds__(256)
+k_frac_count(int N, uint64_t seed, int t, const unsigned *__restrict__ sel,
+             unsigned long long *__restrict__ tile)
+{
+    __shared__ unsigned long long red[256];
+    const uint64_t st = stream_state(seed, (uint64_t)t);
+    const uint32_t thr = sel[0];
+    unsigned less = 0, eq = 0;
+    const int base = blockIdx.x * FRAC_TILE + threadIdx.x * FRAC_ITEMS;
+    for (int q = 0; q < FRAC_ITEMS; ++q) {
+        int a = base + q;
+        if (a < N) {
+            uint32_t key = frac_key(st, a);
+            less += key < thr;
+            eq += key == thr;
+        }
+    }
+    red[threadIdx.x] = ((unsigned long long)less << 32) | eq;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tile[blockIdx.x] = red[0];
+}
+
+// phase 2: exclusive scan of the tile counts (one block)
+__global__ void __launch_bounds__(1024)
+k_frac_scan(int ntiles, unsigned long long *__restrict__ tile)
+{
+    __shared__ unsigned long long c[1024];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+        int b = b0 + threadIdx.x;
+        unsigned long long v = b < ntiles ? tile[b] : 0ull;
+        c[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            unsigned long long u = threadIdx.x >= off ? c[threadIdx.x - off] : 0ull;
+            __syncthreads();
+            c[threadIdx.x] += u;
+            __syncthreads();
+        }
+        if (b < ntiles) tile[b] = carry + c[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += c[1023];
+        __syncthreads();
+    }
+}
+
+// phase 3: write the selected anchors in increasing order
+__global__ void __launch_bounds__(256)
+k_frac_write(int N, uint64_t seed, int t, const unsigned *__restrict__ sel,
+             const unsigned long long *__restrict__ tile, int *__restrict__ anchors,
+             unsigned *__restrict__ mult)
+{
+    __shared__ unsigned long long c[256];
+    const uint64_t st = stream_state(seed, (uint64_t)t);
+    const uint32_t thr = sel[0];
+    const unsigned need = sel[2] + 1u;  // keys equal to thr that are selected
+    const int base = blockIdx.x * FRAC_TILE + threadIdx.x * FRAC_ITEMS;
+    uint32_t keys[FRAC_ITEMS];
+    unsigned less = 0, eq = 0;
+    for (int q = 0; q < FRAC_ITEMS; ++q) {
+        int a = base + q;
+        keys[q] = a < N ? frac_key(st, a) : 0xffffffffu;
+        if (a < N) {
+            less += keys[q] < thr;
+            eq += keys[q] == thr;
+        }
+    }
+    const unsigned long long mine = ((unsigned long long)less << 32) | eq;
+    c[threadIdx.x] = mine;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        unsigned long long u = threadIdx.x >= off ? c[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        c[threadIdx.x] += u;
+        __syncthreads();
+    }
+    unsigned long long before = tile[blockIdx.x] + c[threadIdx.x] - mine;
+    unsigned lb = (unsigned)(before >> 32), eb = (unsigned)(before & 0xffffffffu);
+    for (int q = 0; q < FRAC_ITEMS; ++q) {
+        int a = base + q;
+        if (a >= N) break;
+        bool take = false;
+        if (keys[q] < thr) {
+            take = true;
+        } else if (keys[q] == thr) {
+            take = eb < need;
+        }
+        if (take) anchors[lb + (eb < need ? eb : need)] = a;
+        mult[a] = take ? 1u : 0u;
+        lb += keys[q] < thr;
+        eb += keys[q] == thr;
+    }
+}
+
+int sample_count(int H, int W, const epll_options &o)
+{
+    const int N = H * W;
+    if (o.subset == EPLL_SUBSET_FRACTION) {
+        int M = (int)ceil((double)o.subset_param * (double)N);
+        return M > N ? N : (M < 1 ? 1 : M);
+    }
+    if (o.subset == EPLL_SUBSET_JITTER) {
+        int s = (int)o.subset_param;
+        return ((H + s - 1) / s) * ((W + s - 1) / s);
+    }
+    return N;
+}
+
+epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t, int *n,
+                          int *anchors, unsigned *mult, cudaStream_t st)
+{
+    const int N = H * W;
+    *n = sample_count(H, W, o);
+    Workspace &ws = g->ws;
+    if (o.subset == EPLL_SUBSET_ALL) return EPLL_OK;
+    if (o.subset == EPLL_SUBSET_JITTER) {
+        const int s = (int)o.subset_param;
+        EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N, st));
+        const int ni = (H + s - 1) / s, nj = (W + s - 1) / s;
+        k_jitter<<<(ni * nj + 255) / 256, 256, 0, st>>>(H, W, s, o.seed, t, ni, nj, anchors, mult);
+        EPLL_LAUNCHED(g);
+        return EPLL_OK;
+    }
+    // FRACTION
+    unsigned *hist = ws.sampler;        // [4][256]
+    unsigned *sel = ws.sampler + 1024;  // [3]
+    unsigned long long *tile = reinterpret_cast<unsigned long long *>(ws.sampler + 1040);
+    EPLL_CU(cudaMemsetAsync(hist, 0, sizeof(unsigned) * 1024, st));
+    int hb = (N + 255) / 256;
+    if (hb > 152 * 8) hb = 152 * 8;
+    for (int pass = 0; pass < 4; ++pass) {
+        k_frac_hist<<<hb, 256, 0, st>>>(N, o.seed, t, pass, sel, hist);
+        EPLL_LAUNCHED(g);
+        k_frac_pick<<<1, 256, 0, st>>>(pass, *n, sel, hist);
+        EPLL_LAUNCHED(g);
+    }
+    const int ntiles = (N + FRAC_TILE - 1) / FRAC_TILE;
+    k_frac_count<<<ntiles, 256, 0, st>>>(N, o.seed, t, sel, tile);
+    EPLL_LAUNCHED(g);
+    k_frac_scan<<<1, 1024, 0, st>>>(ntiles, tile);
+    EPLL_LAUNCHED(g);
+    k_frac_write<<<ntiles, 256, 0, st>>>(N, o.seed, t, sel, tile, anchors, mult);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+}  // namespace epll
