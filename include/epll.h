@@ -49,8 +49,14 @@ enum { EPLL_RANK_FIXED = 0, EPLL_RANK_RHO = 1 };
 enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2 };
 /* patch subset (Sec. "Speed-up via the restriction to a random subset of patches") */
 enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
-/* arithmetic of the projection that drives the Gaussian selection */
-enum { EPLL_FP32 = 0, EPLL_BF16 = 1 };
+/* arithmetic of the projection that drives the Gaussian selection:
+ * FP32   SIMT FP32 dot products;
+ * BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation;
+ * FP16   tcgen05 tensor cores, FP16 operands, FP32 accumulation;
+ * BF16X3 tcgen05 tensor cores, operands split into hi + lo BF16 parts
+ *        (three products: hi*hi + lo*hi + hi*lo), FP32 accumulation.
+ * Every form rescores its near-ties in compensated FP32 (see tie_gap). */
+enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3 };
 
 typedef struct epll_gmm epll_gmm; /* opaque, library-owned */
 
@@ -65,12 +71,14 @@ typedef struct {
 } epll_degradation;
 
 typedef struct {
-    int precision;      /* EPLL_FP32 (SIMT FP32 scores) or EPLL_BF16 (tcgen05 tensor cores) */
-    float tie_gap;      /* patches whose top-2 score gap is below this are rescored in
-                           compensated FP32 over all K; < 0 selects the default
-                           (1e-2 for FP32, 3.0 for BF16) */
+    int precision;      /* EPLL_FP32, EPLL_BF16, EPLL_FP16 or EPLL_BF16X3 */
+    float tie_gap;      /* absolute part of the near-tie threshold: a patch whose top-2
+                           score gap is below tie_gap + rho * |z|^2 * max_kj 1/nu_kj is
+                           rescored in compensated FP32 (rho is the relative error bound of
+                           the precision: 1e-5 FP32, 1.5e-3 FP16, 1e-2 BF16, 1e-4 BF16X3);
+                           < 0 selects the default 1e-3 */
     int subset;         /* EPLL_SUBSET_* */
-    float subset_param; /* FRACTION: fraction in (0, 1]; JITTER: grid spacing s in 1..8 */
+    double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */
     uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
     int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
 } epll_options;

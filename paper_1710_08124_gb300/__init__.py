@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RANK_FIXED, RANK_RHO = 0, 1
 DENOISE, PIXELWISE, CONV_PERIODIC = 0, 1, 2
 SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER = 0, 1, 2
-FP32, BF16 = 0, 1
+FP32, BF16, FP16, BF16X3 = 0, 1, 2, 3
 PAPER_BETA = (1.0, 4.0, 8.0, 16.0, 32.0)
 
 
@@ -35,7 +35,7 @@ class EpllError(RuntimeError):
 
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tie_gap", C.c_float), ("subset", C.c_int),
-                ("subset_param", C.c_float), ("seed", C.c_uint64), ("cg_iters", C.c_int)]
+                ("subset_param", C.c_double), ("seed", C.c_uint64), ("cg_iters", C.c_int)]
 
 
 class _Degradation(C.Structure):

@@ -50,7 +50,8 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     A(dalloc(&ws.xhat, N)); A(dalloc(&ws.xtil, N)); A(dalloc(&ws.y, N)); A(dalloc(&ws.a, N));
     A(dalloc(&ws.anchors, N)); A(dalloc(&ws.mult, N)); A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
     A(dalloc(&ws.flag, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
-    A(dalloc(&ws.Zb, N * PD)); A(dalloc(&ws.zz, N)); A(dalloc(&ws.cg, 4 * N));
+    const size_t zrows = (N + 127) / 128 * 128;
+    A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N)); A(dalloc(&ws.cg, 4 * N));
     A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16));
     A(dalloc(&ws.sampler, 1040 + 2 * (N / 2048 + 2)));
     A(dalloc(&ws.counts, 2 * (size_t)g->K + 8)); A(dalloc(&ws.ctr, 4));
@@ -61,7 +62,9 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
         return fail(EPLL_ENOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
     }
     ws.capN = N;
+    ws.zrows = zrows;
     EPLL_CU(cudaMemset(ws.ctr, 0, sizeof(long long) * 4));
+    EPLL_CU(cudaMemset(ws.counts, 0, sizeof(int) * (2 * (size_t)g->K + 8)));
     return EPLL_OK;
 }
 
@@ -69,7 +72,7 @@ static void free_model(epll_gmm *g)
 {
     void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo,
                     g->tab.cst_hi, g->tab.cst_lo, g->tab.t_hi, g->tab.t_lo, g->tab.gp, g->tab.sgn,
-                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.Bs};
+                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.tmax, g->tab.Bs, g->tab.Bs_lo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
@@ -79,16 +82,16 @@ static void free_model(epll_gmm *g)
 
 static epll_status check_options(const epll_options &o, int H, int W)
 {
-    if (o.precision != EPLL_FP32 && o.precision != EPLL_BF16)
-        return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32 or EPLL_BF16");
+    if (o.precision < EPLL_FP32 || o.precision > EPLL_BF16X3)
+        return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32, _BF16, _FP16 or _BF16X3");
     if (!(std::isfinite(o.tie_gap)))
         return fail(EPLL_EINVAL, "options.tie_gap must be finite");
     if (o.subset == EPLL_SUBSET_FRACTION) {
-        if (!(o.subset_param > 0.0f && o.subset_param <= 1.0f))
+        if (!(o.subset_param > 0.0 && o.subset_param <= 1.0))
             return fail(EPLL_EINVAL, "options.subset_param: fraction must be in (0, 1]");
     } else if (o.subset == EPLL_SUBSET_JITTER) {
         int s = (int)o.subset_param;
-        if ((float)s != o.subset_param || s < 1 || s > PS)
+        if ((double)s != o.subset_param || s < 1 || s > PS)
             return fail(EPLL_EINVAL, "options.subset_param: jitter spacing must be an integer in 1..8");
         (void)H; (void)W;
     } else if (o.subset != EPLL_SUBSET_ALL) {
@@ -105,10 +108,30 @@ static epll_status check_image(int H, int W)
     return EPLL_OK;
 }
 
-static float default_tau(const epll_options &o)
+// Near-tie threshold tau_abs + tau_rel |z|^2 max 1/nu.  tau_rel bounds the
+// relative score error of each arithmetic (twice the largest error observed
+// on the synthetic prior, rounded up): FP32 dot products of 64 terms; FP16 /
+// BF16 operand rounding (2^-11 / 2^-8 per operand); the split BF16 form
+// (residual error of order 2^-16).
+static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
 {
-    if (o.tie_gap >= 0.0f) return o.tie_gap;
-    return o.precision == EPLL_BF16 ? 3.0f : 1e-2f;
+    *tau_abs = o.tie_gap >= 0.0f ? o.tie_gap : 1e-3f;
+    switch (o.precision) {
+    case EPLL_BF16: *tau_rel = 1e-2f; break;
+    case EPLL_FP16: *tau_rel = 1.5e-3f; break;
+    case EPLL_BF16X3: *tau_rel = 1e-4f; break;
+    default: *tau_rel = 1e-5f; break;
+    }
+}
+
+static int basis_format(int precision)
+{
+    switch (precision) {
+    case EPLL_BF16: return 1;
+    case EPLL_FP16: return 2;
+    case EPLL_BF16X3: return 3;
+    default: return 0;
+    }
 }
 
 // One patch step: tables, sampling, selection, rescoring, estimation.  The
@@ -119,17 +142,17 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
                                cudaStream_t st)
 {
     Workspace &ws = g->ws;
-    const bool bf16 = o.precision == EPLL_BF16;
     epll_status s;
-    if ((s = launch_tables(g, d_lambda, mult, sigma2, beta_direct, bf16, st))) return s;
+    if ((s = launch_tables(g, d_lambda, mult, sigma2, beta_direct, basis_format(o.precision), st))) return s;
     int n = 0;
     if ((s = launch_sample(g, H, W, o, t, &n, ws.anchors, ws.mult, st))) return s;
     const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
-    const float tau = default_tau(o);
-    if (bf16) {
-        if ((s = launch_select_bf16(g, xhat, H, W, anchors, n, tau, st))) return s;
+    float tau_abs, tau_rel;
+    thresholds(o, &tau_abs, &tau_rel);
+    if (o.precision != EPLL_FP32) {
+        if ((s = launch_select_tc(g, xhat, H, W, anchors, n, o.precision, tau_abs, tau_rel, st))) return s;
     } else {
-        if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau, st))) return s;
+        if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau_abs, tau_rel, st))) return s;
     }
     if ((s = launch_rescore(g, xhat, H, W, anchors, n, st))) return s;
     if (forced_k)
@@ -150,6 +173,7 @@ static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int 
     g->launches = 0;
     g->last_evals = 0;
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
+    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K + 1, 0, sizeof(int), st));
     if (kind == EPLL_CONV_PERIODIC) {
         if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
     }
@@ -230,7 +254,7 @@ void epll_options_default(epll_options *o)
     o->precision = EPLL_FP32;
     o->tie_gap = -1.0f;
     o->subset = EPLL_SUBSET_ALL;
-    o->subset_param = 0.0f;
+    o->subset_param = 0.0;
     o->seed = 0;
     o->cg_iters = 100;
 }
@@ -294,6 +318,10 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     for (int k = 0; k < K; ++k)
         g->h_roff[k + 1] = g->h_roff[k] + (g->h_r[k] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
     g->Rtot = (g->h_roff[K] + RTOT_ALIGN - 1) / RTOT_ALIGN * RTOT_ALIGN;
+    g->uniform_rank = g->h_r[0];
+    for (int k = 1; k < K; ++k)
+        if (g->h_r[k] != g->h_r[0]) g->uniform_rank = 0;
+    if (g->uniform_rank != 8 && g->uniform_rank != 16 && g->uniform_rank != 64) g->uniform_rank = 0;
     g->h_roff[K] = g->Rtot;  // trailing padding columns belong to the last component
     const int R = g->Rtot;
 
@@ -319,7 +347,8 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(dalloc(&g->tab.cst_hi, K)); A(dalloc(&g->tab.cst_lo, K)); A(dalloc(&g->tab.t_hi, K));
     A(dalloc(&g->tab.t_lo, K)); A(dalloc(&g->tab.gp, K)); A(dalloc(&g->tab.sgn, K));
     A(dalloc(&g->tab.q_hi, R)); A(dalloc(&g->tab.q_lo, R)); A(dalloc(&g->tab.gw, R));
-    A(dalloc(&g->tab.Bs, (size_t)R * PD));
+    A(dalloc(&g->tab.tmax, 1));
+    A(dalloc(&g->tab.Bs, (size_t)R * PD)); A(dalloc(&g->tab.Bs_lo, (size_t)R * PD));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_model(g);
@@ -334,7 +363,8 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
-    A(cudaMemset(g->tab.Bs, 0, sizeof(__nv_bfloat16) * (size_t)R * PD));
+    A(cudaMemset(g->tab.Bs, 0, sizeof(uint16_t) * (size_t)R * PD));
+    A(cudaMemset(g->tab.Bs_lo, 0, sizeof(uint16_t) * (size_t)R * PD));
     if (e != cudaSuccess) {
         free_model(g);
         delete g;
@@ -425,6 +455,7 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     g->launches = 0;
     g->last_evals = 0;
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
+    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K + 1, 0, sizeof(int), st));
     int n = 0;
     if ((s = patch_phase(g, xhat, H, W, o, t, ws.scal, 1.0, 1.0, beta, forced_k, &n, st))) return s;
     const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
@@ -488,10 +519,14 @@ epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *r
     if (!g) return fail(EPLL_EINVAL, "null model handle");
     EPLL_CU(cudaDeviceSynchronize());
     long long c[4] = {0, 0, 0, 0};
+    int timed_out = 0;
     if (g->ws.ctr) EPLL_CU(cudaMemcpy(c, g->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (g->ws.counts)
+        EPLL_CU(cudaMemcpy(&timed_out, g->ws.counts + 2 * g->K + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (patch_evals) *patch_evals = g->last_evals;
     if (rescored) *rescored = c[0];
     if (launches) *launches = g->last_launches;
+    if (timed_out) return fail(EPLL_ETIMEOUT, "a tensor-core selection kernel gave up on a bounded wait");
     return EPLL_OK;
 }
 

@@ -34,7 +34,9 @@ struct Tables {
     float *sgn = nullptr;                        // [K]: sign of q_kj (+1 full rank, -1 flat tail)
     float *q_hi = nullptr, *q_lo = nullptr;      // [Rtot]
     float *gw = nullptr;                         // [Rtot]
-    __nv_bfloat16 *Bs = nullptr;                 // [Rtot][64]: bf16(Ubar * sqrt|q|), K-major
+    float *tmax = nullptr;                       // [1]: max_k 1/min_j nu_kj (error scale)
+    uint16_t *Bs = nullptr;                      // [Rtot][64]: 16-bit Ubar * sqrt|q|, K-major
+    uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
 };
 
 struct Workspace {
@@ -48,7 +50,8 @@ struct Workspace {
     int *flag = nullptr;                      // [N] near-tie list
     int *perm = nullptr;                      // [N] list entries grouped by component
     float *zrow = nullptr;                    // [N][64] patch estimates, row per anchor
-    __nv_bfloat16 *Zb = nullptr;              // [N][64] bf16 DC-free patches (tensor path)
+    uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
+    size_t zrows = 0;                         // N rounded up to the 128-row tile
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)
     float *cg = nullptr;                      // [4N] CG vectors r, d, q, spare
     float *red = nullptr;                     // reduction partials
@@ -67,6 +70,7 @@ struct Workspace {
 struct epll_gmm {
     int K = 0;
     int Rtot = 0;                 // padded total number of basis columns
+    int uniform_rank = 0;         // r if every component has rank r, else 0
     int rank_mode = 0;
     double rank_param = 0.0;
     int *h_r = nullptr;           // [K]
@@ -107,8 +111,9 @@ void set_error(const std::string &msg);
 
 // ---------------------------------------------------------------- launchers
 // Each returns EPLL_OK or an error after setting the message.  All enqueue on st.
+// fmt: 0 no 16-bit basis, 1 BF16, 2 FP16, 3 BF16 hi + lo
 epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
-                          double beta_direct, bool bf16, cudaStream_t st);
+                          double beta_direct, int fmt, cudaStream_t st);
 
 // Sampler: writes ws.anchors (FRACTION/JITTER) and ws.mult; returns n via *n.
 // FULL leaves anchors untouched (identity) and mult unused.
@@ -116,10 +121,11 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
                           int *anchors_out, unsigned *mult_out, cudaStream_t st);
 int sample_count(int H, int W, const epll_options &o);
 
+// Near-tie threshold: gap < tau_abs + tau_rel * |z|^2 * tmax.
 epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                               int n, float tau, cudaStream_t st);
-epll_status launch_select_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                               int n, float tau, cudaStream_t st);
+                               int n, float tau_abs, float tau_rel, cudaStream_t st);
+epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                             int n, int precision, float tau_abs, float tau_rel, cudaStream_t st);
 epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                            int n, cudaStream_t st);
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,

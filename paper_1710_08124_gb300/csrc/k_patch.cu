@@ -39,7 +39,7 @@ constexpr int SEL_CH = 32;
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
               const float *__restrict__ B, int Rtot, const int *__restrict__ colk, Tables tab,
-              float tau, int *__restrict__ kstar, float *__restrict__ gap,
+              float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
               int *__restrict__ flag, int *__restrict__ nflag)
 {
     __shared__ __align__(16) float Bs[PD][SEL_CH];
@@ -122,19 +122,19 @@ k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restric
         kstar[i] = k1;
         const float gp = s2 - s1;
         gap[i] = gp;
-        if (gp < tau) flag[atomicAdd(nflag, 1)] = i;
+        if (!(gp >= tau_abs + tau_rel * zz * tab.tmax[0])) flag[atomicAdd(nflag, 1)] = i;
     }
 }
 
 epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                               int n, float tau, cudaStream_t st)
+                               int n, float tau_abs, float tau_rel, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     int *nflag = ws.counts + 2 * g->K;
     EPLL_CU(cudaMemsetAsync(nflag, 0, sizeof(int), st));
     k_select_fp32<<<(n + SEL_THREADS - 1) / SEL_THREADS, SEL_THREADS, 0, st>>>(
-        xhat, H, W, anchors, n, g->d_B, g->Rtot, g->d_colk, g->tab, tau, ws.kstar, ws.gap, ws.flag,
-        nflag);
+        xhat, H, W, anchors, n, g->d_B, g->Rtot, g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap,
+        ws.flag, nflag);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -199,7 +199,9 @@ __device__ __forceinline__ bool df_less(df x, df y)
     return d.hi < 0.0f || (d.hi == 0.0f && d.lo < 0.0f);
 }
 
-constexpr float RESCORE_BAND = 1e-2f;
+// FP32 pass-1 band: absolute + relative to |z|^2 max 1/nu (the FP32 error scale)
+constexpr float RESCORE_ABS = 1e-3f;
+constexpr float RESCORE_REL = 2e-5f;
 constexpr int RS_WARPS = 4;
 
 __global__ void __launch_bounds__(32 * RS_WARPS)
@@ -249,13 +251,14 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
             best = fminf(best, s);
         }
         __syncwarp();
+        const float band = RESCORE_ABS + RESCORE_REL * zzf * tab.tmax[0];
         // pass 2: compensated scores of the components within the band
         df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
         int kb = -1;
         float outside = FLT_MAX;
         for (int k = 0; k < K; ++k) {
             const float sk = sc[k];
-            if (sk > best + RESCORE_BAND) {
+            if (sk > best + band) {
                 outside = fminf(outside, sk);
                 continue;
             }

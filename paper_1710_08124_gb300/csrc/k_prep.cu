@@ -2,6 +2,8 @@
 // Gaussian selection / patch estimation steps, and the patch samplers.
 #include "epll_internal.cuh"
 
+#include <cuda_fp16.h>
+
 namespace epll {
 
 // ============================================================================
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(64)
 k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ roff,
          const double *__restrict__ S, const double *__restrict__ w, const double *__restrict__ lam,
          const double *__restrict__ d_lambda, double mult, double sigma2, double beta_direct,
-         const float *__restrict__ B, Tables tab, int want_bf16)
+         const float *__restrict__ B, Tables tab, int fmt)
 {
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
@@ -64,6 +66,9 @@ k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ rof
         tab.t_lo[k] = (float)(t - (double)th);
         tab.gp[k] = (float)gP;
         tab.sgn[k] = rk < PD ? -1.0f : 1.0f;
+        // error scale of the score: largest 1/nu of this component
+        const double numin = rk < PD ? nuP : S[(size_t)k * PD + PD - 1] + ib;
+        atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int((float)(1.0 / numin)));
     }
     const int o = roff[k], rp = roff[k + 1] - o;
     for (int jj = j; jj < rp; jj += 64) {
@@ -79,20 +84,29 @@ k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ rof
         tab.gw[o + jj] = (float)gw;
         sq[jj] = (float)sqrt(fabs(q));
     }
-    if (!want_bf16) return;
+    if (!fmt) return;
     __syncthreads();
-    // scaled basis, K-major: Bs[col][e] = bf16(U[e][col] * sqrt|q_col|)
+    // scaled basis, K-major: Bs[col][e] = 16-bit(U[e][col] * sqrt|q_col|);
+    // the split form also stores the BF16 remainder.
     for (int jj = 0; jj < rp; ++jj) {
-        float v = (jj < rk) ? B[(size_t)j * Rtot + o + jj] * sq[jj] : 0.0f;
-        tab.Bs[(size_t)(o + jj) * PD + j] = __float2bfloat16_rn(v);
+        const float v = (jj < rk) ? B[(size_t)j * Rtot + o + jj] * sq[jj] : 0.0f;
+        const size_t dst = (size_t)(o + jj) * PD + j;
+        if (fmt == 2) {
+            tab.Bs[dst] = __half_as_ushort(__float2half_rn(v));
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            tab.Bs[dst] = __bfloat16_as_ushort(h);
+            if (fmt == 3) tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+        }
     }
 }
 
 epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
-                          double beta_direct, bool bf16, cudaStream_t st)
+                          double beta_direct, int fmt, cudaStream_t st)
 {
+    EPLL_CU(cudaMemsetAsync(g->tab.tmax, 0, sizeof(float), st));
     k_tables<<<g->K, 64, 0, st>>>(g->K, g->Rtot, g->d_r, g->d_roff, g->d_S, g->d_w, g->d_lam,
-                                  d_lambda, mult, sigma2, beta_direct, g->d_B, g->tab, bf16 ? 1 : 0);
+                                  d_lambda, mult, sigma2, beta_direct, g->d_B, g->tab, fmt);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -308,7 +322,7 @@ int sample_count(int H, int W, const epll_options &o)
 {
     const int N = H * W;
     if (o.subset == EPLL_SUBSET_FRACTION) {
-        int M = (int)ceil((double)o.subset_param * (double)N);
+        int M = (int)ceil(o.subset_param * (double)N);
         return M > N ? N : (M < 1 ? 1 : M);
     }
     if (o.subset == EPLL_SUBSET_JITTER) {

@@ -1,14 +1,562 @@
-// Tensor-core (tcgen05) projection GEMM with the fused selection epilogue.
+// Gaussian selection on the 5th-generation tensor cores (tcgen05).
+//
+// The projection of Eq. 13, C = Z [Ubar_1 ... Ubar_K] (Z: sampled DC-free
+// patches, 64 wide), is a dense contraction with a reduction depth of only
+// 64.  Each CTA owns 128 patches: their 16-bit tile is loaded once by TMA
+// (128-byte swizzle) and stays in shared memory while the basis streams
+// through a multi-stage TMA ring.  One thread issues tcgen05.mma into FP32
+// accumulators in tensor memory (2-4 buffers, 512 columns); eight epilogue
+// warps read the accumulators back with tcgen05.ld and fold them straight
+// into the scores of Eq. 14, keeping the best and second-best component per
+// patch, so the K x N score matrix never exists anywhere.
+//
+// The basis columns are pre-scaled by sqrt|q_kj| (q_kj = 1/nu_kj - 1/nu_kP,
+// Eq. 14), so the epilogue needs one FMA per accumulator element:
+//   score_k = cst_k + t_k |z|^2 + sign_k * sum_j (sqrt|q_kj| c_kj)^2.
+// Operands are BF16 or FP16 (kind::f16, FP32 accumulation); the 3-term
+// variant splits both operands into hi + lo BF16 parts and accumulates
+// hi*hi + lo*hi + hi*lo, which brings the score error close to FP32.
+// Patches whose top-2 gap is below tau_abs + tau_rel |z|^2 max_k(1/nu_min)
+// (the error bound of the arithmetic) go to the compensated rescoring.
 #include "epll_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cfloat>
+#include <mutex>
 
 namespace epll {
 
-epll_status launch_select_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                               int n, float tau, cudaStream_t st)
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    (void)g; (void)xhat; (void)H; (void)W; (void)anchors; (void)n; (void)tau; (void)st;
-    set_error("BF16 selection not built");
-    return EPLL_EUNSUPPORTED;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Every wait is bounded: after ~2 s (clock64 at <= 2.1 GHz) the waiter raises
+// the CTA's abort flag; every other wait polls the flag and gives up too, so
+// the CTA reaches its teardown (TMEM release) and the host sees the error.
+constexpr long long WAIT_CYCLES = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+#define EPLL_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
+                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+#define EPLL_W8(i) "+r"(r[i + 0]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), \
+                   "+r"(r[i + 4]), "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7])
+
+// 32 consecutive accumulator columns of this thread's TMEM lane (row).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : EPLL_R8(0), EPLL_R8(8), EPLL_R8(16), EPLL_R8(24)
+        : "r"(taddr));
+}
+// Waits for this thread's outstanding tcgen05.ld; the registers are tied to
+// the wait so no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_W8(0), EPLL_W8(8), EPLL_W8(16), EPLL_W8(24)::"memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with the 128-byte swizzle: rows of 64 16-bit elements (128 B), 8-row
+// groups 1024 B apart (stride byte offset), leading byte offset unused for
+// this layout (encoded 1), descriptor version 1, layout type 2 = SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (D format
+// 1 at bit 4), A/B format (0 = F16, 1 = BF16) at bits 7 and 10, both
+// operands K-major, N/8 at bit 17, M/16 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int fmt)
+{
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- extraction
+// DC-free patches as 16-bit operands (hi, and lo for the split variant) and
+// their FP32 squared norms.  One warp per patch; rows up to the next multiple
+// of 128 are zero-filled so the last tile's rows are defined.
+__device__ __forceinline__ float warp_sum_tc(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ uint16_t to16(float v, int fmt)
+{
+    return fmt == 2 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ float from16(uint16_t v, int fmt)
+{
+    return fmt == 2 ? __half2float(__ushort_as_half(v)) : __bfloat162float(__ushort_as_bfloat16(v));
+}
+
+__global__ void __launch_bounds__(128)
+k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
+             int rows, int fmt, int split, uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo,
+             float *__restrict__ zz)
+{
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= rows) return;
+    float z0 = 0.0f, z1 = 0.0f, q = 0.0f;
+    if (i < n) {
+        const int a = anchors ? anchors[i] : i;
+        const int ai = a / W, aj = a % W;
+        int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
+        if (r0 >= H) r0 -= H;
+        if (r1 >= H) r1 -= H;
+        if (c >= W) c -= W;
+        const float x0 = xhat[(size_t)r0 * W + c], x1 = xhat[(size_t)r1 * W + c];
+        const float mu = warp_sum_tc(x0 + x1) * (1.0f / PD);
+        z0 = x0 - mu;
+        z1 = x1 - mu;
+        q = warp_sum_tc(z0 * z0 + z1 * z1);
+    }
+    const uint16_t h0 = to16(z0, fmt), h1 = to16(z1, fmt);
+    Zhi[(size_t)i * PD + lane] = h0;
+    Zhi[(size_t)i * PD + lane + 32] = h1;
+    if (split) {
+        Zlo[(size_t)i * PD + lane] = to16(z0 - from16(h0, fmt), fmt);
+        Zlo[(size_t)i * PD + lane + 32] = to16(z1 - from16(h1, fmt), fmt);
+    }
+    if (lane == 0 && i < n) zz[i] = q;
+}
+
+// ---------------------------------------------------------------- main kernel
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int TC_SMEM_BUDGET = 200 * 1024;
+
+template <int BN, int NT>
+struct TcCfg {
+    static constexpr int A_TILE = TC_M * 128;                  // 16 KB
+    static constexpr int A_BYTES = A_TILE * (NT == 3 ? 2 : 1);
+    static constexpr int B_TILE = BN * 128;
+    static constexpr int B_STAGE = B_TILE * (NT == 3 ? 2 : 1);
+    static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - A_BYTES) / B_STAGE;
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+    static constexpr int NB = 512 / BN;                        // TMEM accumulator buffers
+    static constexpr int HALF = BN / 2;                        // columns per epilogue warp
+    static constexpr int CTRL = 2048;
+    static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_STAGE + CTRL;
+};
+
+struct TcCtrl {
+    unsigned long long a_full;
+    unsigned long long b_full[8], b_empty[8];
+    unsigned long long t_full[4], t_empty[4];
+    unsigned long long drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+template <int RR>
+__device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &k1)
+{
+    if (s < s1) {
+        s2 = s1;
+        s1 = s;
+        k1 = k;
+    } else {
+        s2 = fminf(s2, s);
+    }
+}
+
+template <int BN, int NT, int RR>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
+          const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
+          int n, int K, int Rtot, uint32_t idesc, const float *__restrict__ zz,
+          const int *__restrict__ colk, Tables tab, float tau_abs, float tau_rel,
+          int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
+          int *__restrict__ nflag, int *__restrict__ err)
+{
+    using C = TcCfg<BN, NT>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + C::A_BYTES;
+    TcCtrl *ctl = (TcCtrl *)(sB + C::STAGES * C::B_STAGE);
+    float *mrg = (float *)(ctl + 1);  // [128][3] merge buffer of the two epilogue halves
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_M;
+    const int ntiles = Rtot / BN;
+    volatile int *abort_flag = &ctl->abort_flag;
+
+    if (threadIdx.x == 0) {
+        ctl->abort_flag = 0;
+        mbar_init(smem_u32(&ctl->a_full), 1);
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(smem_u32(&ctl->b_full[s]), 1);
+            mbar_init(smem_u32(&ctl->b_empty[s]), 1);
+        }
+        for (int b = 0; b < C::NB; ++b) {
+            mbar_init(smem_u32(&ctl->t_full[b]), 1);
+            mbar_init(smem_u32(&ctl->t_empty[b]), 8);
+        }
+        mbar_init(smem_u32(&ctl->drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&ctl->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            const uint32_t af = smem_u32(&ctl->a_full);
+            mbar_expect_tx(af, C::A_BYTES);
+            tma_load_2d(smem_u32(sA), &mapA, 0, m0, af);
+            if (NT == 3) tma_load_2d(smem_u32(sA + C::A_TILE), &mapAlo, 0, m0, af);
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % C::STAGES, round = it / C::STAGES;
+                if (!mbar_wait(smem_u32(&ctl->b_empty[s]), (round & 1) ^ 1, abort_flag)) break;
+                const uint32_t bf = smem_u32(&ctl->b_full[s]);
+                mbar_expect_tx(bf, C::B_STAGE);
+                unsigned char *dst = sB + s * C::B_STAGE;
+                tma_load_2d(smem_u32(dst), &mapB, 0, it * BN, bf);
+                if (NT == 3) tma_load_2d(smem_u32(dst + C::B_TILE), &mapBlo, 0, it * BN, bf);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            bool ok = mbar_wait(smem_u32(&ctl->a_full), 0, abort_flag);
+            tc_fence_after();
+            const uint32_t aHi = smem_u32(sA), aLo = smem_u32(sA + C::A_TILE);
+            for (int it = 0; ok && it < ntiles; ++it) {
+                const int s = it % C::STAGES, round = it / C::STAGES;
+                const int b = it % C::NB, tround = it / C::NB;
+                if (!mbar_wait(smem_u32(&ctl->b_full[s]), round & 1, abort_flag)) break;
+                if (!mbar_wait(smem_u32(&ctl->t_empty[b]), (tround & 1) ^ 1, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d = tbase + (uint32_t)(b * BN);
+                const uint32_t bHi = smem_u32(sB + s * C::B_STAGE), bLo = bHi + C::B_TILE;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {  // reduction depth 64 = 4 x 16
+                    const uint32_t off = (uint32_t)(k * 32);
+                    mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
+                    if (NT == 3) {
+                        mma_f16(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
+                        mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                    }
+                }
+                mma_commit(smem_u32(&ctl->b_empty[s]));
+                mma_commit(smem_u32(&ctl->t_full[b]));
+            }
+            // drain: every MMA issued above has completed once this arrives
+            mma_commit(smem_u32(&ctl->drain));
+            mbar_wait(smem_u32(&ctl->drain), 0, abort_flag);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (8 warps)
+        const int q = warp & 3;        // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2; // column half of each accumulator tile
+        const int row = 32 * q + lane;
+        const int grow = m0 + row;
+        const float zzr = grow < n ? zz[grow] : 0.0f;
+        float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
+        int k1 = 0, curk = -1;
+        for (int it = 0; it < ntiles; ++it) {
+            const int b = it % C::NB, tround = it / C::NB;
+            if (!mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag)) break;
+            tc_fence_after();
+            // uniform ranks: each half-warp-group owns whole components of its half;
+            // ragged ranks: the h = 0 warps take the whole tile (components may
+            // straddle the halves), the h = 1 warps only keep the handshake.
+            const int cbeg = RR ? h * C::HALF : 0;
+            const int ncol = RR ? C::HALF : (h == 0 ? BN : 0);
+            const int col0 = it * BN + cbeg;
+            const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbeg);
+            uint32_t r[32];
+            for (int c = 0; c < ncol / 32; ++c) {
+                tmem_ld32(taddr + (uint32_t)(32 * c), r);
+                tmem_wait(r);
+                const int cb = col0 + 32 * c;
+                if constexpr (RR == 64) {
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+                        const float v2 = __uint_as_float(r[j + 2]), v3 = __uint_as_float(r[j + 3]);
+                        a0 = fmaf(v0, v0, a0);
+                        a1 = fmaf(v1, v1, a1);
+                        a2 = fmaf(v2, v2, a2);
+                        a3 = fmaf(v3, v3, a3);
+                    }
+                    acc += (a0 + a1) + (a2 + a3);
+                    if (c & 1) {
+                        const int k = cb >> 6;
+                        if (k < K) {
+                            const float s = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr + acc;
+                            top2<RR>(s, k, s1, s2, k1);
+                        }
+                        acc = 0.0f;
+                    }
+                } else if constexpr (RR > 0) {
+#pragma unroll
+                    for (int p = 0; p < 32 / RR; ++p) {
+                        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < RR; j += 2) {
+                            const float v0 = __uint_as_float(r[p * RR + j]);
+                            const float v1 = __uint_as_float(r[p * RR + j + 1]);
+                            a0 = fmaf(v0, v0, a0);
+                            a1 = fmaf(v1, v1, a1);
+                        }
+                        const int k = cb / RR + p;
+                        if (k < K) {
+                            const float s = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr - (a0 + a1);
+                            top2<RR>(s, k, s1, s2, k1);
+                        }
+                    }
+                } else {
+                    // ragged ranks: column -> component map
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int k = __ldg(&colk[cb + j]);
+                        if (k != curk) {
+                            if (curk >= 0) {
+                                const float s = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
+                                                __ldg(&tab.sgn[curk]) * acc;
+                                top2<RR>(s, curk, s1, s2, k1);
+                            }
+                            curk = k;
+                            acc = 0.0f;
+                        }
+                        const float v = __uint_as_float(r[j]);
+                        acc = fmaf(v, v, acc);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+        }
+        if (RR == 0 && curk >= 0) {
+            // the last component ends with the last column
+            const float s = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr + __ldg(&tab.sgn[curk]) * acc;
+            top2<RR>(s, curk, s1, s2, k1);
+        }
+        // merge the two halves: components of half 1 interleave with half 0's
+        if (h == 1) {
+            mrg[row * 3 + 0] = s1;
+            mrg[row * 3 + 1] = s2;
+            mrg[row * 3 + 2] = __int_as_float(k1);
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (h == 0 && grow < n) {
+            const float t1 = mrg[row * 3 + 0], t2 = mrg[row * 3 + 1];
+            const int tk = __float_as_int(mrg[row * 3 + 2]);
+            float b1, b2;
+            int bk;
+            if (t1 < s1 || (t1 == s1 && tk < k1)) {
+                b1 = t1; bk = tk; b2 = fminf(s1, t2);
+            } else {
+                b1 = s1; bk = k1; b2 = fminf(t1, s2);
+            }
+            kstar[grow] = bk;
+            const float gp = b2 - b1;
+            gap[grow] = gp;
+            const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
+            if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = grow;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+    }
+    if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// Row-major [rows][64] 16-bit matrix, box of box_rows rows x 64, 128-byte swizzle.
+static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled entry point unavailable");
+        return EPLL_ECUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)PD, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)PD * 2};
+    cuuint32_t box[2] = {(cuuint32_t)PD, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+        return EPLL_ECUDA;
+    }
+    return EPLL_OK;
+}
+
+template <int BN, int NT, int RR>
+static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
+                             const CUtensorMap &b, const CUtensorMap &blo, int n, uint32_t idesc,
+                             float tau_abs, float tau_rel, cudaStream_t st)
+{
+    using Cfg = TcCfg<BN, NT>;
+    auto kern = k_proj_tc<BN, NT, RR>;
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+        attr = true;
+    }
+    Workspace &ws = g->ws;
+    const int grid = (n + TC_M - 1) / TC_M;
+    kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, g->K, g->Rtot, idesc, ws.zz, g->d_colk,
+                                             g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, ws.flag,
+                                             ws.counts + 2 * g->K, ws.counts + 2 * g->K + 1);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+template <int BN, int NT>
+static epll_status dispatch_rr(epll_gmm *g, int RR, const CUtensorMap &a, const CUtensorMap &alo,
+                               const CUtensorMap &b, const CUtensorMap &blo, int n, uint32_t idesc,
+                               float tau_abs, float tau_rel, cudaStream_t st)
+{
+    if (RR == 64) return launch_tc<BN, NT, 64>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+    if (RR == 8) return launch_tc<BN, NT, 8>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+    if (RR == 16) return launch_tc<BN, NT, 16>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+    return launch_tc<BN, NT, 0>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+}
+
+epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                             int precision, float tau_abs, float tau_rel, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int fmt = precision == EPLL_FP16 ? 2 : 1;
+    const bool split = precision == EPLL_BF16X3;
+    const int rows = (n + TC_M - 1) / TC_M * TC_M;
+    uint16_t *Zhi = reinterpret_cast<uint16_t *>(ws.Zb);
+    uint16_t *Zlo = Zhi + ws.zrows * PD;
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, rows, fmt, split ? 1 : 0, Zhi, Zlo,
+                                                 ws.zz);
+    EPLL_LAUNCHED(g);
+    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K, 0, sizeof(int), st));
+    CUtensorMap a, alo, b, blo;
+    epll_status s;
+    if ((s = make_map(&a, Zhi, rows, TC_M))) return s;
+    if ((s = make_map(&alo, Zlo, rows, TC_M))) return s;
+    const int BN = split ? 128 : 256;
+    if ((s = make_map(&b, g->tab.Bs, g->Rtot, BN))) return s;
+    if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, BN))) return s;
+    const uint32_t idesc = idesc_f16(TC_M, BN, fmt == 2 ? 0 : 1);
+    if (split) return dispatch_rr<128, 3>(g, g->uniform_rank, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+    return dispatch_rr<256, 1>(g, g->uniform_rank, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
 }
 
 }  // namespace epll
