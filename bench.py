@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the FEPLL denoising workload on GB300.
+
+Workload (one step = 6 restorations): 512x512 dead-leaves images with
+additive Gaussian noise sigma in {10, 25, 50}/255, the synthetic K = 200
+Gaussian patch prior with flat-tail rank r in {64, 8} (every sigma x rank
+pair), the random 1/3 subset of patch positions redrawn every iteration,
+5 half-quadratic-splitting iterations (beta = sigma^-2 {1, 4, 8, 16, 32}).
+
+Prints one JSON line: restorations per second (device-timed, inputs resident),
+the same through the host-buffer C ABI call (e2e), the roofline of the
+dominant kernel (the tensor-core selection GEMM), the CPU oracle on the host
+cores, and the plain-FP32 form of the same restorations for comparison.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+H = W = 512
+K = 200
+RANKS = (64, 8)
+SIGMAS = (10 / 255, 25 / 255, 50 / 255)
+FRACTION = 1 / 3
+BETA = (1.0, 4.0, 8.0, 16.0, 32.0)
+N_PIX = H * W
+M_PATCH = math.ceil(FRACTION * N_PIX)
+RESTORES_PER_STEP = len(RANKS) * len(SIGMAS)
+WORKLOAD = ("FEPLL denoise 512x512 dead leaves, sigma {10,25,50}/255, synthetic GMM K=200, "
+            "flat-tail rank r in {64,8}, random 1/3 patch subset per iteration, 5 HQS iterations")
+METRIC = "512x512 restores/s (FEPLL denoise, K=200, r in {64,8}, 1/3 subset)"
+PREC_NAMES = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "bf16x3": "bf16"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=list(PREC_NAMES), default="bf16x3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain-FP32 comparison leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def problems(rank: int):
+    """Per sigma: (clean, noisy) float32 images; replicas use distinct images."""
+    out = []
+    for s_i, sig in enumerate(SIGMAS):
+        x, y = synth.denoise_problem(s_i + 3 * rank, H, sig)
+        out.append((x, y.astype(np.float32)))
+    return out
+
+
+def psnr(x, ref):
+    return -10.0 * math.log10(float(np.mean((np.asarray(x, np.float64) - ref) ** 2)))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_rate(max_seconds: float = 12.0):
+    """Restores/s of the FP64 oracle on this host, from timed patch steps on a
+    bounded sample of each rank's 1/3 subset (the per-patch cost is independent
+    of sigma; reprojection and the image update are included per sampled patch)."""
+    import oracle
+
+    g = synth.synthetic_gmm(K)
+    x = synth.image(0, H) + synth.noise(0, H, W, SIGMAS[1])
+    anchors = oracle.sample(H, W, oracle.FRACTION, FRACTION, seed=1, t=0)
+    per_patch = {}
+    sample = {}
+    budget = max_seconds / len(RANKS)
+    for r in RANKS:
+        m = oracle.Model(g.w, g.U, g.S, "fixed", r)
+        n = 64
+        while True:
+            t0 = time.perf_counter()
+            oracle.patch_step(m, 8 / SIGMAS[1] ** 2, x, anchors[:n])
+            dt = time.perf_counter() - t0
+            if dt > budget / 3 or n >= len(anchors):
+                break
+            n = min(len(anchors), int(n * max(2.0, 0.5 * budget / max(dt, 1e-3))))
+        per_patch[r] = dt / n
+        sample[r] = n
+    sec_per_step = sum(len(SIGMAS) * len(BETA) * M_PATCH * per_patch[r] for r in RANKS)
+    cores = os.cpu_count() or 1
+    desc = ("oracle patch steps (FP64, OpenMP over patches) on the first "
+            + ", ".join(f"{sample[r]} anchors at r={r}" for r in RANKS)
+            + f" of the 1/3 subset of a 512x512 image, scaled to {len(BETA)} iterations x "
+            f"{M_PATCH} patches x {RESTORES_PER_STEP} restores")
+    return RESTORES_PER_STEP / sec_per_step, cores, desc
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    rates = []
+    cores, desc = 1, ""
+    for s in range(args.warmup + args.steps):
+        r, cores, desc = oracle_rate(max_seconds=6.0)
+        if s >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "restores/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": RESTORES_PER_STEP / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "restores_per_step": RESTORES_PER_STEP},
+        "cpu_baseline": {"value": value, "unit": "restores/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "restores/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def traffic_record(kernel_src_hash: str, precision: str):
+    """DRAM bytes per selection-kernel launch from the committed ncu summary,
+    or None when the kernel changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "selection_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p))
+    except ValueError:
+        return None
+    if rec.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return rec.get("per_launch_bytes_full_size", {}).get(precision)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+
+    import paper_1710_08124_gb300 as ep
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    ep.build()
+    prec = PREC_NAMES[args.precision]
+    g = synth.synthetic_gmm(K)
+    models = {r: ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r) for r in RANKS}
+    probs = problems(rank)
+    dev = torch.device("cuda", local)
+    ys = [torch.as_tensor(y, device=dev) for _, y in probs]
+    outs = [torch.empty_like(y) for y in ys]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    jobs = [(r, si) for r in RANKS for si in range(len(SIGMAS))]
+
+    def one_step(options):
+        for r, si in jobs:
+            ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=options, out=outs[(si)])
+
+    opts = ep.Options(precision=prec, subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=7)
+    launches_per_step = 0
+    rescored_per_step = 0
+    for w in range(max(args.warmup, 3)):
+        flush.zero_()
+        one_step(opts)
+        if w == 0:
+            for r, si in jobs:
+                ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=opts, out=outs[si])
+                _, resc, la = ep.last_counters(models[r])
+                launches_per_step += la
+                rescored_per_step += resc
+    torch.cuda.synchronize()
+    for m in models.values():
+        ep.profile_enable(m, True)
+        ep.profile_read(m)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()  # outside the events: L2 holds nothing of the previous step
+        evs[s][0].record(stream)
+        one_step(opts)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(step_ms) / 1e3
+    if pg:
+        tt = torch.tensor([dev_s], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        dev_s = float(tt.item())
+    sel_ms = sel_n = sel_flops = 0.0
+    for m in models.values():
+        a, b, c = ep.profile_read(m)
+        sel_ms += a
+        sel_n += b
+        sel_flops += c
+        ep.profile_enable(m, False)
+
+    # accuracy of this arithmetic vs the plain FP32 form, and the FP32 form's rate
+    fp32_line = None
+    if not args.no_fp32:
+        o32 = ep.Options(precision=ep.FP32, subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=7)
+        deltas = []
+        for r, si in jobs:
+            a = ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=opts).cpu().numpy()
+            b = ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=o32).cpu().numpy()
+            deltas.append(abs(psnr(a, probs[si][0]) - psnr(b, probs[si][0])))
+        n32 = max(2, args.steps // 5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t32 = 0.0
+        for s in range(n32):
+            flush.zero_()
+            e0.record(stream)
+            one_step(o32)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t32 += e0.elapsed_time(e1) / 1e3
+        r32 = n32 * RESTORES_PER_STEP / t32
+        fp32_line = {"restores_per_s": r32, "speedup": None, "max_psnr_delta_db": max(deltas)}
+
+    # end to end through the host-buffer C ABI call (pinned host memory)
+    hy = [torch.from_numpy(y).pin_memory() for _, y in probs]
+    hx = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in probs]
+    n_e2e = max(2, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(n_e2e):
+        for r, si in jobs:
+            ep.restore_host(models[r], hy[si], SIGMAS[si], BETA, options=opts, out=hx[si])
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        tt = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    restores = args.steps * RESTORES_PER_STEP * ws
+    value = restores / dev_s
+    if fp32_line:
+        fp32_line["speedup"] = value / (fp32_line["restores_per_s"] * ws)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_note = "measured (sustained, cuBLAS bf16)"
+    if peak is None:
+        peak, peak_note = 1700.0, "fallback"
+    if args.precision == "fp32":
+        peak_note += "; FP32 SIMT path measured against the BF16 tensor peak"
+    achieved = (sel_flops / (sel_ms / 1e3) / 1e12) if sel_ms > 0 else None
+    ksrc = open(os.path.join(ROOT, "paper_1710_08124_gb300", "csrc", "k_proj_tc.cu"), "rb").read()
+    khash = hashlib.sha256(ksrc).hexdigest()
+    traffic = traffic_record(khash, args.precision)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "restores/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "restores_per_step": RESTORES_PER_STEP,
+                   "precision": args.precision, "patches_per_iteration": M_PATCH,
+                   "l2": "256 MB buffer written before each step, outside the timed events",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "mpatch_evals_per_s": restores * len(BETA) * M_PATCH / dev_s / 1e6,
+        "e2e": {"value": n_e2e * RESTORES_PER_STEP * ws / e2e_s, "unit": "restores/s",
+                "h2d_bytes_per_step": RESTORES_PER_STEP * N_PIX * 4,
+                "d2h_bytes_per_step": RESTORES_PER_STEP * N_PIX * 4},
+        "gpu_launches": launches_per_step * args.steps,
+        "rescored_patches_per_step": rescored_per_step,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "selection (projection GEMM + fused score/argmin)",
+                     "launches": int(sel_n), "kernel_ms": sel_ms,
+                     "share_of_step": sel_ms / 1e3 / (dev_s / ws) if dev_s else None,
+                     "peak_source": peak_note},
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if fp32_line:
+        line["vs_fp32"] = fp32_line
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_rate()
+        line["cpu_baseline"] = {"value": v, "unit": "restores/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

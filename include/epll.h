@@ -161,7 +161,8 @@ epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W,
  *   forced_k     device int (nullable): per sampled patch, a component that
  *                replaces the selection (teacher forcing)
  *   n_out        host out (nullable): number of sampled patches; when
- *                non-NULL the call synchronises `stream`
+ *                non-NULL the call synchronises `stream` and returns
+ *                EPLL_ETIMEOUT if a bounded device wait gave up
  */
 epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double beta,
                             const epll_options *opt, int t, float *xtilde, int *anchors,
@@ -179,6 +180,17 @@ epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *ancho
  * patches, and kernel launches issued. */
 epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *rescored,
                                long long *launches);
+
+/* Instrumentation of the selection kernel (the projection + score contraction,
+ * the step that dominates the restoration's arithmetic).  While enabled, the
+ * library records a pair of CUDA events on the call's stream around every
+ * launch of that kernel (at most 8192 launches between reads; later launches
+ * are not recorded).  epll_profile_read synchronises the device, returns the
+ * summed device time in milliseconds, the number of recorded launches and
+ * their algorithmic floating-point operations (2 * 64 * sum_k r_k per patch,
+ * whatever the arithmetic), then clears the record.  Any output may be NULL. */
+epll_status epll_profile_enable(epll_gmm *g, int enable);
+epll_status epll_profile_read(epll_gmm *g, double *ms, long long *launches, double *flops);
 
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char *epll_last_error(void);

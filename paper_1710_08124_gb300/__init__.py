@@ -87,6 +87,9 @@ def lib():
         L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
         L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                          C.POINTER(C.c_longlong)]
+        L.epll_profile_enable.argtypes = [vp, i]
+        L.epll_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double)]
         L.epll_options_default.argtypes = [C.POINTER(_Options)]
         L.epll_options_default.restype = None
         _lib = L
@@ -242,3 +245,14 @@ def last_counters(g: GMM):
     a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
     _check(lib().epll_last_counters(g.handle, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def profile_enable(g: GMM, enable: bool = True):
+    _check(lib().epll_profile_enable(g.handle, int(enable)))
+
+
+def profile_read(g: GMM):
+    """(selection-kernel device ms, launches, algorithmic FLOPs) since the last read."""
+    ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
+    _check(lib().epll_profile_read(g.handle, C.byref(ms), C.byref(n), C.byref(fl)))
+    return ms.value, n.value, fl.value

@@ -10,6 +10,19 @@
 
 namespace epll {
 
+void prof_begin(epll_gmm *g, cudaStream_t st)
+{
+    if (g->prof_on && g->prof_n < PROF_MAX) cudaEventRecord(g->prof_ev[2 * g->prof_n], st);
+}
+void prof_end(epll_gmm *g, cudaStream_t st, int n)
+{
+    if (g->prof_on && g->prof_n < PROF_MAX) {
+        cudaEventRecord(g->prof_ev[2 * g->prof_n + 1], st);
+        g->prof_flops += 2.0 * PD * (double)g->rank_sum * (double)n;
+        ++g->prof_n;
+    }
+}
+
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -30,7 +43,8 @@ static cudaError_t dalloc(T **p, size_t count)
 static void free_workspace(Workspace &ws)
 {
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors, ws.mult, ws.kstar, ws.gap,
-                    ws.flag, ws.perm, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
+                    ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.fscore,
+                    ws.perm, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -49,9 +63,16 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     A(dalloc(&ws.xhat, N)); A(dalloc(&ws.xtil, N)); A(dalloc(&ws.y, N)); A(dalloc(&ws.a, N));
     A(dalloc(&ws.anchors, N)); A(dalloc(&ws.mult, N)); A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
-    A(dalloc(&ws.flag, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
+    A(dalloc(&ws.flag, N)); A(dalloc(&ws.flag1, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
     const size_t zrows = (N + 127) / 128 * 128;
-    A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N)); A(dalloc(&ws.cg, 4 * N));
+    A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N));
+    A(dalloc(&ws.Z2, 2 * zrows * PD)); A(dalloc(&ws.zz2, N));
+    // FP32 scores of near-tie rows: at most this many rows per rescoring pass
+    size_t fcap = (size_t)1 << 26;
+    fcap /= (size_t)g->K;
+    if (fcap < 4096) fcap = 4096;
+    if (fcap > N) fcap = N;
+    A(dalloc(&ws.fscore, fcap * (size_t)g->K)); A(dalloc(&ws.cg, 4 * N));
     A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16));
     A(dalloc(&ws.sampler, 1040 + 2 * (N / 2048 + 2)));
     A(dalloc(&ws.counts, 2 * (size_t)g->K + 8)); A(dalloc(&ws.ctr, 4));
@@ -63,6 +84,7 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     }
     ws.capN = N;
     ws.zrows = zrows;
+    ws.fcap = fcap;
     EPLL_CU(cudaMemset(ws.ctr, 0, sizeof(long long) * 4));
     EPLL_CU(cudaMemset(ws.counts, 0, sizeof(int) * (2 * (size_t)g->K + 8)));
     return EPLL_OK;
@@ -72,12 +94,16 @@ static void free_model(epll_gmm *g)
 {
     void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo,
                     g->tab.cst_hi, g->tab.cst_lo, g->tab.t_hi, g->tab.t_lo, g->tab.gp, g->tab.sgn,
-                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.tmax, g->tab.Bs, g->tab.Bs_lo};
+                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.tmax, g->tab.B1, g->tab.Bs, g->tab.Bs_lo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
     delete[] g->h_lam;
     delete[] g->h_roff;
+    if (g->prof_ev) {
+        for (int i = 0; i < 2 * PROF_MAX; ++i) cudaEventDestroy(g->prof_ev[i]);
+        delete[] g->prof_ev;
+    }
 }
 
 static epll_status check_options(const epll_options &o, int H, int W)
@@ -124,12 +150,13 @@ static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
     }
 }
 
+// Bases the tables kernel writes for each arithmetic (bit mask, see launch_tables).
 static int basis_format(int precision)
 {
     switch (precision) {
-    case EPLL_BF16: return 1;
-    case EPLL_FP16: return 2;
-    case EPLL_BF16X3: return 3;
+    case EPLL_BF16: return 1 | 4;
+    case EPLL_FP16: return 2 | 4;
+    case EPLL_BF16X3: return 4;
     default: return 0;
     }
 }
@@ -173,7 +200,7 @@ static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int 
     g->launches = 0;
     g->last_evals = 0;
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
-    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K + 1, 0, sizeof(int), st));
+    EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
     if (kind == EPLL_CONV_PERIODIC) {
         if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
     }
@@ -318,6 +345,8 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     for (int k = 0; k < K; ++k)
         g->h_roff[k + 1] = g->h_roff[k] + (g->h_r[k] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
     g->Rtot = (g->h_roff[K] + RTOT_ALIGN - 1) / RTOT_ALIGN * RTOT_ALIGN;
+    g->rank_sum = 0;
+    for (int k = 0; k < K; ++k) g->rank_sum += g->h_r[k];
     g->uniform_rank = g->h_r[0];
     for (int k = 1; k < K; ++k)
         if (g->h_r[k] != g->h_r[0]) g->uniform_rank = 0;
@@ -341,13 +370,17 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     }
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R));
+    // column arrays carry COL_PAD trailing zero entries: a 32-column chunk that
+    // starts at an 8-aligned column below Rtot stays inside the allocation
+    constexpr int COL_PAD = 64;
+    A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R + COL_PAD));
     A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
-    A(dalloc(&g->d_B, (size_t)PD * R)); A(dalloc(&g->d_Blo, (size_t)PD * R));
+    A(dalloc(&g->d_B, (size_t)PD * R + COL_PAD)); A(dalloc(&g->d_Blo, (size_t)PD * R + COL_PAD));
     A(dalloc(&g->tab.cst_hi, K)); A(dalloc(&g->tab.cst_lo, K)); A(dalloc(&g->tab.t_hi, K));
     A(dalloc(&g->tab.t_lo, K)); A(dalloc(&g->tab.gp, K)); A(dalloc(&g->tab.sgn, K));
-    A(dalloc(&g->tab.q_hi, R)); A(dalloc(&g->tab.q_lo, R)); A(dalloc(&g->tab.gw, R));
+    A(dalloc(&g->tab.q_hi, R + COL_PAD)); A(dalloc(&g->tab.q_lo, R + COL_PAD)); A(dalloc(&g->tab.gw, R + COL_PAD));
     A(dalloc(&g->tab.tmax, 1));
+    A(dalloc(&g->tab.B1, (size_t)R * PD));
     A(dalloc(&g->tab.Bs, (size_t)R * PD)); A(dalloc(&g->tab.Bs_lo, (size_t)R * PD));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -357,12 +390,17 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     }
     A(cudaMemcpy(g->d_r, g->h_r, sizeof(int) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_roff, g->h_roff, sizeof(int) * (K + 1), cudaMemcpyHostToDevice));
+    A(cudaMemset(g->d_colk, 0, sizeof(int) * (R + COL_PAD)));
+    A(cudaMemset(g->d_B, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
+    A(cudaMemset(g->d_Blo, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
+    A(cudaMemset(g->tab.q_hi, 0, sizeof(float) * (R + COL_PAD)));
     A(cudaMemcpy(g->d_colk, colk.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_S, eigvals, sizeof(double) * K * PD, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
+    A(cudaMemset(g->tab.B1, 0, sizeof(uint16_t) * (size_t)R * PD));
     A(cudaMemset(g->tab.Bs, 0, sizeof(uint16_t) * (size_t)R * PD));
     A(cudaMemset(g->tab.Bs_lo, 0, sizeof(uint16_t) * (size_t)R * PD));
     if (e != cudaSuccess) {
@@ -455,7 +493,7 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     g->launches = 0;
     g->last_evals = 0;
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
-    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K + 1, 0, sizeof(int), st));
+    EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
     int n = 0;
     if ((s = patch_phase(g, xhat, H, W, o, t, ws.scal, 1.0, 1.0, beta, forced_k, &n, st))) return s;
     const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
@@ -473,6 +511,9 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     g->last_launches = g->launches;
     if (n_out) {
         EPLL_CU(cudaStreamSynchronize(st));
+        int timed_out = 0;
+        EPLL_CU(cudaMemcpy(&timed_out, cnt(g, CNT_ERR), sizeof(int), cudaMemcpyDeviceToHost));
+        if (timed_out) return fail(EPLL_ETIMEOUT, "a tensor-core selection kernel gave up on a bounded wait");
         *n_out = n;
     }
     return EPLL_OK;
@@ -513,6 +554,35 @@ epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *ancho
     return EPLL_OK;
 }
 
+epll_status epll_profile_enable(epll_gmm *g, int enable)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (enable && !g->prof_ev) {
+        g->prof_ev = new cudaEvent_t[2 * PROF_MAX];
+        for (int i = 0; i < 2 * PROF_MAX; ++i) EPLL_CU(cudaEventCreate(&g->prof_ev[i]));
+    }
+    g->prof_on = enable != 0;
+    return EPLL_OK;
+}
+
+epll_status epll_profile_read(epll_gmm *g, double *ms, long long *launches, double *flops)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    EPLL_CU(cudaDeviceSynchronize());
+    double tot = 0.0;
+    for (int i = 0; i < g->prof_n; ++i) {
+        float t = 0.0f;
+        EPLL_CU(cudaEventElapsedTime(&t, g->prof_ev[2 * i], g->prof_ev[2 * i + 1]));
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = g->prof_n;
+    if (flops) *flops = g->prof_flops;
+    g->prof_n = 0;
+    g->prof_flops = 0.0;
+    return EPLL_OK;
+}
+
 epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *rescored,
                                long long *launches)
 {
@@ -522,7 +592,7 @@ epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *r
     int timed_out = 0;
     if (g->ws.ctr) EPLL_CU(cudaMemcpy(c, g->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     if (g->ws.counts)
-        EPLL_CU(cudaMemcpy(&timed_out, g->ws.counts + 2 * g->K + 1, sizeof(int), cudaMemcpyDeviceToHost));
+        EPLL_CU(cudaMemcpy(&timed_out, cnt(g, CNT_ERR), sizeof(int), cudaMemcpyDeviceToHost));
     if (patch_evals) *patch_evals = g->last_evals;
     if (rescored) *rescored = c[0];
     if (launches) *launches = g->last_launches;

@@ -35,9 +35,13 @@ struct Tables {
     float *q_hi = nullptr, *q_lo = nullptr;      // [Rtot]
     float *gw = nullptr;                         // [Rtot]
     float *tmax = nullptr;                       // [1]: max_k 1/min_j nu_kj (error scale)
-    uint16_t *Bs = nullptr;                      // [Rtot][64]: 16-bit Ubar * sqrt|q|, K-major
+    uint16_t *B1 = nullptr;                      // [Rtot][64]: 16-bit Ubar * sqrt|q| (BF16 or FP16), K-major
+    uint16_t *Bs = nullptr;                      // [Rtot][64]: BF16 hi part of Ubar * sqrt|q| (split form)
     uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
 };
+
+// Slots of Workspace::counts after the K bucket counters.
+enum { CNT_NFLAG = 0, CNT_ERR = 1, CNT_NFLAG1 = 2 };
 
 struct Workspace {
     size_t capN = 0;
@@ -47,7 +51,12 @@ struct Workspace {
     unsigned *mult = nullptr;                 // [N] multiplicity of each anchor in the subset
     int *kstar = nullptr;                     // [N]
     float *gap = nullptr;                     // [N]
-    int *flag = nullptr;                      // [N] near-tie list
+    int *flag = nullptr;                      // [N] near-tie list for the compensated rescoring
+    int *flag1 = nullptr;                     // [N] near-tie list of a one-term tensor pass
+    uint16_t *Z2 = nullptr;                   // [2][zrows][64] split operands of listed rows
+    float *zz2 = nullptr;                     // [N] |z|^2 of listed rows
+    float *fscore = nullptr;                  // [fcap][K] FP32 scores of listed rows
+    size_t fcap = 0;
     int *perm = nullptr;                      // [N] list entries grouped by component
     float *zrow = nullptr;                    // [N][64] patch estimates, row per anchor
     uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
@@ -85,6 +94,12 @@ struct epll_gmm {
     epll::Workspace ws;
     long long last_evals = 0, last_launches = 0;
     long long launches = 0;
+    long long rank_sum = 0;       // sum_k r_k (algorithmic columns)
+    // instrumentation of the selection kernel
+    bool prof_on = false;
+    int prof_n = 0;
+    cudaEvent_t *prof_ev = nullptr;   // [2 * PROF_MAX]
+    double prof_flops = 0.0;
 };
 
 namespace epll {
@@ -111,7 +126,7 @@ void set_error(const std::string &msg);
 
 // ---------------------------------------------------------------- launchers
 // Each returns EPLL_OK or an error after setting the message.  All enqueue on st.
-// fmt: 0 no 16-bit basis, 1 BF16, 2 FP16, 3 BF16 hi + lo
+// fmt bit mask: 1 = B1 as BF16, 2 = B1 as FP16, 4 = split BF16 basis (Bs, Bs_lo)
 epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
                           double beta_direct, int fmt, cudaStream_t st);
 
@@ -126,8 +141,10 @@ epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, con
                                int n, float tau_abs, float tau_rel, cudaStream_t st);
 epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                              int n, int precision, float tau_abs, float tau_rel, cudaStream_t st);
+// Compensated rescoring of ws.flag (count in counts[2K + CNT_NFLAG]).
 epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                            int n, cudaStream_t st);
+inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; }
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);
 // Reprojection.  When y != nullptr the pixelwise image update is fused
@@ -148,5 +165,10 @@ epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, d
                     int iters, cudaStream_t st);  // ws.xhat
 
 epll_status ensure_workspace(epll_gmm *g, size_t N);
+
+// Selection-kernel instrumentation (no-ops unless enabled).
+constexpr int PROF_MAX = 8192;
+void prof_begin(epll_gmm *g, cudaStream_t st);
+void prof_end(epll_gmm *g, cudaStream_t st, int n);
 
 }  // namespace epll

@@ -36,17 +36,37 @@ __device__ __forceinline__ float warp_sum(float v)
 constexpr int SEL_THREADS = 128;
 constexpr int SEL_CH = 32;
 
+// DUMP = true: the patches are entries [f0, f0 + fcap) of a device list (count
+// *nlist) and every component's score is written to scores[(f - f0) * K + k].
+// In list mode blockIdx.y selects a slice of whole components (columns
+// [roff[k0], roff[k1])) so that a short list still spreads over many blocks.
+template <bool DUMP>
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
               const float *__restrict__ B, int Rtot, const int *__restrict__ colk, Tables tab,
               float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
-              int *__restrict__ flag, int *__restrict__ nflag)
+              int *__restrict__ flag, int *__restrict__ nflag, const int *__restrict__ list,
+              const int *__restrict__ nlist, int f0, int fcap, int K, const int *__restrict__ roff,
+              float *__restrict__ scores)
 {
     __shared__ __align__(16) float Bs[PD][SEL_CH];
     __shared__ float qs[SEL_CH];
     __shared__ int ks[SEL_CH];
-    const int i = blockIdx.x * SEL_THREADS + threadIdx.x;
-    const bool valid = i < n;
+    int i = blockIdx.x * SEL_THREADS + threadIdx.x;
+    bool valid = i < n;
+    int f = 0, cbeg = 0, cend = Rtot;
+    if (DUMP) {
+        const int count = min(*nlist - f0, fcap);
+        if ((int)(blockIdx.x * SEL_THREADS) >= count) return;  // whole block idle
+        f = i;
+        valid = f < count;
+        i = valid ? list[f0 + f] : 0;
+        const int k0 = (int)((long long)K * blockIdx.y / gridDim.y);
+        const int k1 = (int)((long long)K * (blockIdx.y + 1) / gridDim.y);
+        if (k0 == k1) return;
+        cbeg = roff[k0];
+        cend = roff[k1];
+    }
 
     float z[PD];
     float zz = 0.0f;
@@ -71,7 +91,7 @@ k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restric
 
     float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
     int k1 = 0, curk = -1;
-    for (int c0 = 0; c0 < Rtot; c0 += SEL_CH) {
+    for (int c0 = cbeg; c0 < cend; c0 += SEL_CH) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < PD * SEL_CH / 4; idx += SEL_THREADS) {
             const int e = idx / (SEL_CH / 4), c4 = idx % (SEL_CH / 4);
@@ -100,11 +120,14 @@ k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restric
         }
 #pragma unroll
         for (int cc = 0; cc < SEL_CH; ++cc) {
+            if (DUMP && c0 + cc >= cend) break;  // slice ends inside the chunk (uniform)
             const int k = ks[cc];
             if (k != curk) {
                 if (curk >= 0) {
                     const float s = tab.cst_hi[curk] + tab.t_hi[curk] * zz + acc;
-                    if (s < s1) { s2 = s1; s1 = s; k1 = curk; }
+                    if (DUMP) {
+                        if (valid) scores[(size_t)f * K + curk] = s;
+                    } else if (s < s1) { s2 = s1; s1 = s; k1 = curk; }
                     else if (s < s2) { s2 = s; }
                 }
                 curk = k;
@@ -115,6 +138,10 @@ k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restric
     }
     {
         const float s = tab.cst_hi[curk] + tab.t_hi[curk] * zz + acc;
+        if (DUMP) {
+            if (valid) scores[(size_t)f * K + curk] = s;
+            return;
+        }
         if (s < s1) { s2 = s1; s1 = s; k1 = curk; }
         else if (s < s2) { s2 = s; }
     }
@@ -130,19 +157,22 @@ epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, con
                                int n, float tau_abs, float tau_rel, cudaStream_t st)
 {
     Workspace &ws = g->ws;
-    int *nflag = ws.counts + 2 * g->K;
+    int *nflag = cnt(g, CNT_NFLAG);
     EPLL_CU(cudaMemsetAsync(nflag, 0, sizeof(int), st));
-    k_select_fp32<<<(n + SEL_THREADS - 1) / SEL_THREADS, SEL_THREADS, 0, st>>>(
+    prof_begin(g, st);
+    k_select_fp32<false><<<(n + SEL_THREADS - 1) / SEL_THREADS, SEL_THREADS, 0, st>>>(
         xhat, H, W, anchors, n, g->d_B, g->Rtot, g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap,
-        ws.flag, nflag);
+        ws.flag, nflag, nullptr, nullptr, 0, 0, g->K, g->d_roff, nullptr);
+    prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
 
 // ============================================================================
-// Near-tie rescoring.  One warp per listed patch.  Pass 1 recomputes all K
-// scores in FP32 (lanes over basis columns); every component within
-// RESCORE_BAND of the best is then rescored in compensated arithmetic: the
+// Near-tie rescoring.  The FP32 kernel above, in list mode, first writes all
+// K scores of every listed patch (block-tiled, the bases streamed through
+// shared memory).  Then one warp per listed patch rescores, in compensated
+// arithmetic, every component within the FP32 error band of the best: the
 // patch, its mean, the basis (float value + float rounding error of the FP64
 // eigenvectors) and the FP64 tables are carried as unevaluated sums of two
 // floats (Dekker's TwoSum / TwoProduct with FMA), which resolves the
@@ -204,22 +234,23 @@ constexpr float RESCORE_ABS = 1e-3f;
 constexpr float RESCORE_REL = 2e-5f;
 constexpr int RS_WARPS = 4;
 
+// Entries [f0, f0 + fcap) of the near-tie list; scores[(f - f0) * K + k] holds
+// each component's FP32 score (written by the FP32 kernel in list mode).
 __global__ void __launch_bounds__(32 * RS_WARPS)
 k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
-          const int *__restrict__ flag, const int *__restrict__ nflag, int K, int Rtot,
-          const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
-          const float *__restrict__ Blo, Tables tab, int *__restrict__ kstar,
-          float *__restrict__ gap, long long *__restrict__ ctr)
+          const int *__restrict__ flag, const int *__restrict__ nflag, int f0, int fcap, int K,
+          int Rtot, const int *__restrict__ roff, const int *__restrict__ rk_,
+          const float *__restrict__ B, const float *__restrict__ Blo, Tables tab,
+          const float *__restrict__ scores, int *__restrict__ kstar, float *__restrict__ gap,
+          long long *__restrict__ ctr)
 {
-    extern __shared__ float dyn[];
-    __shared__ float zh[RS_WARPS][PD], zl[RS_WARPS][PD], zf[RS_WARPS][PD];
+    __shared__ float zh[RS_WARPS][PD], zl[RS_WARPS][PD];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *sc = dyn + (size_t)w * K;
-    const int total = *nflag;
+    const int total = min(*nflag - f0, fcap);
     const int gw = blockIdx.x * RS_WARPS + w, nw = gridDim.x * RS_WARPS;
     if (gw == 0 && lane == 0 && total > 0) atomicAdd((unsigned long long *)ctr, (unsigned long long)total);
     for (int f = gw; f < total; f += nw) {
-        const int i = flag[f];
+        const int i = flag[f0 + f];
         const int a = anchors ? anchors[i] : i;
         const int ai = a / W, aj = a % W;
         const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
@@ -232,27 +263,14 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
         df zz = df_warp_sum(df_add(df_mul(z0, z0), df_mul(z1, z1)));
         zh[w][lane] = z0.hi; zl[w][lane] = z0.lo;
         zh[w][lane + 32] = z1.hi; zl[w][lane + 32] = z1.lo;
-        zf[w][lane] = z0.hi + z0.lo; zf[w][lane + 32] = z1.hi + z1.lo;
-        const float zzf = zz.hi + zz.lo;
         __syncwarp();
-        // pass 1: FP32 scores of all components
+        const float *sc = scores + (size_t)f * K;
         float best = FLT_MAX;
-        for (int k = 0; k < K; ++k) {
-            const int o = roff[k], r = rk_[k];
-            float part = 0.0f;
-            for (int j = lane; j < r; j += 32) {
-                float c = 0.0f;
-#pragma unroll 8
-                for (int e = 0; e < PD; ++e) c = fmaf(B[(size_t)e * Rtot + o + j], zf[w][e], c);
-                part = fmaf(tab.q_hi[o + j] * c, c, part);
-            }
-            const float s = tab.cst_hi[k] + tab.t_hi[k] * zzf + warp_sum(part);
-            if (lane == 0) sc[k] = s;
-            best = fminf(best, s);
-        }
-        __syncwarp();
-        const float band = RESCORE_ABS + RESCORE_REL * zzf * tab.tmax[0];
-        // pass 2: compensated scores of the components within the band
+        for (int k = lane; k < K; k += 32) best = fminf(best, sc[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        const float band = RESCORE_ABS + RESCORE_REL * (zz.hi + zz.lo) * tab.tmax[0];
+        // compensated scores of the components within the band of the FP32 best
         df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
         int kb = -1;
         float outside = FLT_MAX;
@@ -293,16 +311,21 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
                            int n, cudaStream_t st)
 {
     Workspace &ws = g->ws;
-    const size_t smem = sizeof(float) * (size_t)RS_WARPS * g->K;
-    if (smem > 48 * 1024)
-        EPLL_CU(cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int blocks = (n + RS_WARPS - 1) / RS_WARPS;
-    if (blocks > 152 * 4) blocks = 152 * 4;
-    if (blocks < 1) blocks = 1;
-    k_rescore<<<blocks, 32 * RS_WARPS, smem, st>>>(xhat, H, W, anchors, ws.flag, ws.counts + 2 * g->K,
-                                                    g->K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->d_Blo,
-                                                    g->tab, ws.kstar, ws.gap, ws.ctr);
-    EPLL_LAUNCHED(g);
+    const int fcap = (int)ws.fcap;
+    for (int f0 = 0; f0 < n; f0 += fcap) {
+        const int rows = min(fcap, n - f0);
+        const dim3 grid((rows + SEL_THREADS - 1) / SEL_THREADS, g->K < 16 ? g->K : 16);
+        k_select_fp32<true><<<grid, SEL_THREADS, 0, st>>>(
+            xhat, H, W, anchors, 0, g->d_B, g->Rtot, g->d_colk, g->tab, 0.0f, 0.0f, nullptr, nullptr,
+            nullptr, nullptr, ws.flag, cnt(g, CNT_NFLAG), f0, fcap, g->K, g->d_roff, ws.fscore);
+        EPLL_LAUNCHED(g);
+        int blocks = (rows + RS_WARPS - 1) / RS_WARPS;
+        if (blocks > 152 * 4) blocks = 152 * 4;
+        k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
+                                                    fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
+                                                    g->d_Blo, g->tab, ws.fscore, ws.kstar, ws.gap, ws.ctr);
+        EPLL_LAUNCHED(g);
+    }
     return EPLL_OK;
 }
 

@@ -86,17 +86,17 @@ k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ rof
     }
     if (!fmt) return;
     __syncthreads();
-    // scaled basis, K-major: Bs[col][e] = 16-bit(U[e][col] * sqrt|q_col|);
-    // the split form also stores the BF16 remainder.
+    // scaled basis, K-major: B[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
+    // split form stores the BF16 value and the BF16 remainder.
     for (int jj = 0; jj < rp; ++jj) {
         const float v = (jj < rk) ? B[(size_t)j * Rtot + o + jj] * sq[jj] : 0.0f;
         const size_t dst = (size_t)(o + jj) * PD + j;
-        if (fmt == 2) {
-            tab.Bs[dst] = __half_as_ushort(__float2half_rn(v));
-        } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        if (fmt & 1) tab.B1[dst] = __bfloat16_as_ushort(h);
+        if (fmt & 2) tab.B1[dst] = __half_as_ushort(__float2half_rn(v));
+        if (fmt & 4) {
             tab.Bs[dst] = __bfloat16_as_ushort(h);
-            if (fmt == 3) tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+            tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
         }
     }
 }

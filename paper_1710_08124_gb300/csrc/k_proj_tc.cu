@@ -173,16 +173,21 @@ __device__ __forceinline__ float from16(uint16_t v, int fmt)
     return fmt == 2 ? __half2float(__ushort_as_half(v)) : __bfloat162float(__ushort_as_bfloat16(v));
 }
 
+// Row i of the operand is sampled patch i, or patch rowmap[i] when a row map
+// (a device list with device count *n_dev) is given.
 __global__ void __launch_bounds__(128)
 k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
-             int rows, int fmt, int split, uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo,
-             float *__restrict__ zz)
+             const int *__restrict__ rowmap, const int *__restrict__ n_dev, int fmt, int split,
+             uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz)
 {
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (n_dev) n = *n_dev;
+    const int rows = (n + 127) / 128 * 128;
     if (i >= rows) return;
     float z0 = 0.0f, z1 = 0.0f, q = 0.0f;
     if (i < n) {
-        const int a = anchors ? anchors[i] : i;
+        const int p = rowmap ? rowmap[i] : i;
+        const int a = anchors ? anchors[p] : p;
         const int ai = a / W, aj = a % W;
         int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
         if (r0 >= H) r0 -= H;
@@ -248,12 +253,14 @@ template <int BN, int NT, int RR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
           const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
-          int n, int K, int Rtot, uint32_t idesc, const float *__restrict__ zz,
-          const int *__restrict__ colk, Tables tab, float tau_abs, float tau_rel,
-          int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
-          int *__restrict__ nflag, int *__restrict__ err)
+          int n, const int *__restrict__ rowmap, const int *__restrict__ n_dev, int K, int Rtot,
+          uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk, Tables tab,
+          float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
+          int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err)
 {
     using C = TcCfg<BN, NT>;
+    if (n_dev) n = *n_dev;                       // rows listed on the device
+    if ((int)(blockIdx.x * TC_M) >= n) return;   // whole CTA idle, before any setup
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = smem;
@@ -438,6 +445,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (h == 0 && grow < n) {
+            const int out = rowmap ? rowmap[grow] : grow;
             const float t1 = mrg[row * 3 + 0], t2 = mrg[row * 3 + 1];
             const int tk = __float_as_int(mrg[row * 3 + 2]);
             float b1, b2;
@@ -447,11 +455,11 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             } else {
                 b1 = s1; bk = k1; b2 = fminf(t1, s2);
             }
-            kstar[grow] = bk;
+            kstar[out] = bk;
             const float gp = b2 - b1;
-            gap[grow] = gp;
+            gap[out] = gp;
             const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
-            if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = grow;
+            if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = out;
         }
     }
 
@@ -504,8 +512,9 @@ static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_
 
 template <int BN, int NT, int RR>
 static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
-                             const CUtensorMap &b, const CUtensorMap &blo, int n, uint32_t idesc,
-                             float tau_abs, float tau_rel, cudaStream_t st)
+                             const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
+                             const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
+                             float tau_rel, int *flag, int *nflag, cudaStream_t st)
 {
     using Cfg = TcCfg<BN, NT>;
     auto kern = k_proj_tc<BN, NT, RR>;
@@ -516,47 +525,84 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     }
     Workspace &ws = g->ws;
     const int grid = (n + TC_M - 1) / TC_M;
-    kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, g->K, g->Rtot, idesc, ws.zz, g->d_colk,
-                                             g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, ws.flag,
-                                             ws.counts + 2 * g->K, ws.counts + 2 * g->K + 1);
+    // the instrumentation covers the pass over every sampled patch only
+    if (!n_dev) prof_begin(g, st);
+    kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
+                                             g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
+                                             nflag, cnt(g, CNT_ERR));
+    if (!n_dev) prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
 
 template <int BN, int NT>
-static epll_status dispatch_rr(epll_gmm *g, int RR, const CUtensorMap &a, const CUtensorMap &alo,
-                               const CUtensorMap &b, const CUtensorMap &blo, int n, uint32_t idesc,
-                               float tau_abs, float tau_rel, cudaStream_t st)
+static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
+                               const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
+                               const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
+                               float tau_rel, int *flag, int *nflag, cudaStream_t st)
 {
-    if (RR == 64) return launch_tc<BN, NT, 64>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
-    if (RR == 8) return launch_tc<BN, NT, 8>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
-    if (RR == 16) return launch_tc<BN, NT, 16>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
-    return launch_tc<BN, NT, 0>(g, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+#define EPLL_TC_ARGS g, a, alo, b, blo, n, rowmap, n_dev, zz, idesc, tau_abs, tau_rel, flag, nflag, st
+    switch (g->uniform_rank) {
+    case 64: return launch_tc<BN, NT, 64>(EPLL_TC_ARGS);
+    case 16: return launch_tc<BN, NT, 16>(EPLL_TC_ARGS);
+    case 8: return launch_tc<BN, NT, 8>(EPLL_TC_ARGS);
+    default: return launch_tc<BN, NT, 0>(EPLL_TC_ARGS);
+    }
+#undef EPLL_TC_ARGS
 }
 
+// Relative error bound of the split form (see thresholds() in api.cu).
+constexpr float SPLIT_REL = 1e-4f;
+
+// Gaussian selection on the tensor cores.  A one-term pass (BF16 or FP16)
+// scores every sampled patch; the rows it cannot decide (top-2 gap within its
+// error bound) are rescored by the split-BF16 pass; what that pass cannot
+// decide goes to the compensated FP32 rescoring (ws.flag).  With the split
+// form as the first pass the second is skipped.
 epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                              int precision, float tau_abs, float tau_rel, cudaStream_t st)
 {
     Workspace &ws = g->ws;
+    const bool split_first = precision == EPLL_BF16X3;
     const int fmt = precision == EPLL_FP16 ? 2 : 1;
-    const bool split = precision == EPLL_BF16X3;
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
-    uint16_t *Zhi = reinterpret_cast<uint16_t *>(ws.Zb);
-    uint16_t *Zlo = Zhi + ws.zrows * PD;
-    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, rows, fmt, split ? 1 : 0, Zhi, Zlo,
-                                                 ws.zz);
-    EPLL_LAUNCHED(g);
-    EPLL_CU(cudaMemsetAsync(ws.counts + 2 * g->K, 0, sizeof(int), st));
-    CUtensorMap a, alo, b, blo;
+    uint16_t *Zhi = ws.Zb, *Zlo = ws.Zb + ws.zrows * PD;
     epll_status s;
+    // ---- first pass over every sampled patch
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, fmt,
+                                                 split_first ? 1 : 0, Zhi, Zlo, ws.zz);
+    EPLL_LAUNCHED(g);
+    int *flag1 = split_first ? ws.flag : ws.flag1;
+    int *nflag1 = cnt(g, split_first ? CNT_NFLAG : CNT_NFLAG1);
+    EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
+    CUtensorMap a, alo, b, blo;
     if ((s = make_map(&a, Zhi, rows, TC_M))) return s;
     if ((s = make_map(&alo, Zlo, rows, TC_M))) return s;
-    const int BN = split ? 128 : 256;
-    if ((s = make_map(&b, g->tab.Bs, g->Rtot, BN))) return s;
-    if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, BN))) return s;
-    const uint32_t idesc = idesc_f16(TC_M, BN, fmt == 2 ? 0 : 1);
-    if (split) return dispatch_rr<128, 3>(g, g->uniform_rank, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
-    return dispatch_rr<256, 1>(g, g->uniform_rank, a, alo, b, blo, n, idesc, tau_abs, tau_rel, st);
+    if (split_first) {
+        if ((s = make_map(&b, g->tab.Bs, g->Rtot, 128))) return s;
+        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, 128))) return s;
+        return dispatch_rr<128, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 1),
+                                   tau_abs, tau_rel, flag1, nflag1, st);
+    }
+    if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
+    // one-term pass: no lo operands (the lo map arguments are unused)
+    if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz,
+                                 idesc_f16(TC_M, 256, fmt == 2 ? 0 : 1), tau_abs, tau_rel, flag1, nflag1,
+                                 st)))
+        return s;
+    // ---- split-BF16 pass over the rows the first pass could not decide
+    uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, flag1, nflag1, 1, 1, Z2hi, Z2lo,
+                                                 ws.zz2);
+    EPLL_LAUNCHED(g);
+    EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
+    CUtensorMap a2, a2lo, bs, bslo;
+    if ((s = make_map(&a2, Z2hi, rows, TC_M))) return s;
+    if ((s = make_map(&a2lo, Z2lo, rows, TC_M))) return s;
+    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 128))) return s;
+    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 128))) return s;
+    return dispatch_rr<128, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 128, 1),
+                               tau_abs, SPLIT_REL, ws.flag, cnt(g, CNT_NFLAG), st);
 }
 
 }  // namespace epll

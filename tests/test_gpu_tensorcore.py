@@ -119,6 +119,7 @@ def test_restore_matches_oracle_psnr(prec):
     xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, subset=oracle.FRACTION,
                         subset_param=1 / 3, seed=2)
     xg = ep.restore(gm, dev(y), sigma, options=o).cpu().numpy()
+    ep.last_counters(gm)  # raises if a bounded device wait gave up
     ps = lambda a: -10 * math.log10(np.mean((a - x) ** 2))
     assert abs(ps(xg) - ps(xo)) <= 0.05
     evals, rescored, launches = ep.last_counters(gm)
