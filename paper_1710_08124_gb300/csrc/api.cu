@@ -3,6 +3,7 @@
 // schedule of Sec. "Parameter settings").
 #include "epll_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -42,7 +43,7 @@ static cudaError_t dalloc(T **p, size_t count)
 
 static void free_workspace(Workspace &ws)
 {
-    void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors, ws.mult, ws.kstar, ws.gap,
+    void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.fscore,
                     ws.perm, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern};
@@ -62,7 +63,8 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     A(dalloc(&ws.xhat, N)); A(dalloc(&ws.xtil, N)); A(dalloc(&ws.y, N)); A(dalloc(&ws.a, N));
-    A(dalloc(&ws.anchors, N)); A(dalloc(&ws.mult, N)); A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
+    A(dalloc(&ws.anchors_all, TB_MAX * N)); A(dalloc(&ws.mult_all, TB_MAX * N));
+    A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
     A(dalloc(&ws.flag, N)); A(dalloc(&ws.flag1, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
     const size_t zrows = (N + 127) / 128 * 128;
     A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N));
@@ -74,7 +76,8 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     if (fcap > N) fcap = N;
     A(dalloc(&ws.fscore, fcap * (size_t)g->K)); A(dalloc(&ws.cg, 4 * N));
     A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16));
-    A(dalloc(&ws.sampler, 1040 + 2 * (N / 2048 + 2)));
+    const size_t sstride = sampler_stride(N);
+    A(dalloc(&ws.sampler, TB_MAX * sstride));
     A(dalloc(&ws.counts, 2 * (size_t)g->K + 8)); A(dalloc(&ws.ctr, 4));
     A(dalloc(&ws.Yh, N)); A(dalloc(&ws.Hh, N)); A(dalloc(&ws.Xh, N)); A(dalloc(&ws.kern, N));
     if (e != cudaSuccess) {
@@ -85,6 +88,9 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     ws.capN = N;
     ws.zrows = zrows;
     ws.fcap = fcap;
+    ws.sstride = sstride;
+    ws.anchors = ws.anchors_all;
+    ws.mult = ws.mult_all;
     EPLL_CU(cudaMemset(ws.ctr, 0, sizeof(long long) * 4));
     EPLL_CU(cudaMemset(ws.counts, 0, sizeof(int) * (2 * (size_t)g->K + 8)));
     return EPLL_OK;
@@ -93,8 +99,9 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
 static void free_model(epll_gmm *g)
 {
     void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo,
-                    g->tab.cst_hi, g->tab.cst_lo, g->tab.t_hi, g->tab.t_lo, g->tab.gp, g->tab.sgn,
-                    g->tab.q_hi, g->tab.q_lo, g->tab.gw, g->tab.tmax, g->tab.B1, g->tab.Bs, g->tab.Bs_lo};
+                    g->tab0.cst_hi, g->tab0.cst_lo, g->tab0.t_hi, g->tab0.t_lo, g->tab0.gp, g->tab0.sgn,
+                    g->tab0.q_hi, g->tab0.q_lo, g->tab0.gw, g->tab0.tmax, g->tab0.B1, g->tab0.Bs,
+                    g->tab0.Bs_lo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
@@ -138,14 +145,14 @@ static epll_status check_image(int H, int W)
 // relative score error of each arithmetic (twice the largest error observed
 // on the synthetic prior, rounded up): FP32 dot products of 64 terms; FP16 /
 // BF16 operand rounding (2^-11 / 2^-8 per operand); the split BF16 form
-// (residual error of order 2^-16).
+// (residual error of order 2^-16; at most 8e-6 relative measured).
 static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
 {
     *tau_abs = o.tie_gap >= 0.0f ? o.tie_gap : 1e-3f;
     switch (o.precision) {
     case EPLL_BF16: *tau_rel = 1e-2f; break;
     case EPLL_FP16: *tau_rel = 1.5e-3f; break;
-    case EPLL_BF16X3: *tau_rel = 1e-4f; break;
+    case EPLL_BF16X3: *tau_rel = 4e-5f; break;
     default: *tau_rel = 1e-5f; break;
     }
 }
@@ -161,18 +168,32 @@ static int basis_format(int precision)
     }
 }
 
-// One patch step: tables, sampling, selection, rescoring, estimation.  The
-// reprojection is left to the caller (it may be fused with the image update).
-static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, const epll_options &o,
-                               int t, const double *d_lambda, double mult, double sigma2,
-                               double beta_direct, const int *forced_k, int *n_out,
-                               cudaStream_t st)
+// Per-beta tables and patch subsets of iterations t0 .. t0+nb-1 (one batch).
+static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb,
+                                 const double *d_lambda, const double *mult, double sigma2,
+                                 double beta_direct, int *n, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     epll_status s;
-    if ((s = launch_tables(g, d_lambda, mult, sigma2, beta_direct, basis_format(o.precision), st))) return s;
-    int n = 0;
-    if ((s = launch_sample(g, H, W, o, t, &n, ws.anchors, ws.mult, st))) return s;
+    if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o.precision), st))) return s;
+    return launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, st);
+}
+
+// Points the current-iteration views (tables, subset) at batch slot b.
+static void use_slot(epll_gmm *g, int b, size_t N)
+{
+    g->tab = slot_tables(g->tab0, b, g->K, g->Rp, g->Rtot);
+    g->ws.anchors = g->ws.anchors_all + (size_t)b * N;
+    g->ws.mult = g->ws.mult_all + (size_t)b * N;
+}
+
+// One patch step on prepared tables/subset: selection, rescoring, estimation.
+// The reprojection is left to the caller (it may be fused with the image update).
+static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, const epll_options &o,
+                               int n, const int *forced_k, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    epll_status s;
     const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
     float tau_abs, tau_rel;
     thresholds(o, &tau_abs, &tau_rel);
@@ -181,12 +202,11 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     } else {
         if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau_abs, tau_rel, st))) return s;
     }
-    if ((s = launch_rescore(g, xhat, H, W, anchors, n, st))) return s;
+    if ((s = launch_rescore(g, xhat, H, W, anchors, n, o.precision != EPLL_FP32, tau_abs, st))) return s;
     if (forced_k)
         EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
     g->last_evals += n;
-    *n_out = n;
     return EPLL_OK;
 }
 
@@ -213,10 +233,19 @@ static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int 
         if ((s = cg_init(g, a, y, H, W, sigma, o.cg_iters, st))) return s;
     }
     const double s2 = (double)sigma * sigma;
+    const size_t N = (size_t)H * W;
+    size_t nbmax = ((size_t)1 << 23) / N;
+    if (nbmax < 1) nbmax = 1;
+    if (nbmax > (size_t)TB_MAX) nbmax = TB_MAX;
+    int n = 0;
     for (int t = 0; t < T; ++t) {
-        int n = 0;
-        if ((s = patch_phase(g, ws.xhat, H, W, o, t, ws.scal, beta_mult[t], s2, 0.0, nullptr, &n, st)))
-            return s;
+        const int b = (int)(t % nbmax);
+        if (b == 0) {
+            const int nb = (int)std::min<size_t>(nbmax, (size_t)(T - t));
+            if ((s = prepare_batch(g, H, W, o, t, nb, ws.scal, beta_mult + t, s2, 0.0, &n, st))) return s;
+        }
+        use_slot(g, b, N);
+        if ((s = patch_phase(g, ws.xhat, H, W, o, n, nullptr, st))) return s;
         const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
         if (kind == EPLL_CONV_PERIODIC) {
             if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, ws.xtil, st)))
@@ -376,12 +405,17 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R + COL_PAD));
     A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
     A(dalloc(&g->d_B, (size_t)PD * R + COL_PAD)); A(dalloc(&g->d_Blo, (size_t)PD * R + COL_PAD));
-    A(dalloc(&g->tab.cst_hi, K)); A(dalloc(&g->tab.cst_lo, K)); A(dalloc(&g->tab.t_hi, K));
-    A(dalloc(&g->tab.t_lo, K)); A(dalloc(&g->tab.gp, K)); A(dalloc(&g->tab.sgn, K));
-    A(dalloc(&g->tab.q_hi, R + COL_PAD)); A(dalloc(&g->tab.q_lo, R + COL_PAD)); A(dalloc(&g->tab.gw, R + COL_PAD));
-    A(dalloc(&g->tab.tmax, 1));
-    A(dalloc(&g->tab.B1, (size_t)R * PD));
-    A(dalloc(&g->tab.Bs, (size_t)R * PD)); A(dalloc(&g->tab.Bs_lo, (size_t)R * PD));
+    // per-beta tables of TB_MAX iterations, slot-major (see slot_tables)
+    const int Rp = R + COL_PAD;
+    g->Rp = Rp;
+    Tables &T0 = g->tab0;
+    A(dalloc(&T0.cst_hi, TB_MAX * K)); A(dalloc(&T0.cst_lo, TB_MAX * K)); A(dalloc(&T0.t_hi, TB_MAX * K));
+    A(dalloc(&T0.t_lo, TB_MAX * K)); A(dalloc(&T0.gp, TB_MAX * K)); A(dalloc(&T0.sgn, TB_MAX * K));
+    A(dalloc(&T0.q_hi, (size_t)TB_MAX * Rp)); A(dalloc(&T0.q_lo, (size_t)TB_MAX * Rp));
+    A(dalloc(&T0.gw, (size_t)TB_MAX * Rp));
+    A(dalloc(&T0.tmax, TB_MAX));
+    A(dalloc(&T0.B1, (size_t)TB_MAX * R * PD));
+    A(dalloc(&T0.Bs, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.Bs_lo, (size_t)TB_MAX * R * PD));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_model(g);
@@ -393,16 +427,19 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(cudaMemset(g->d_colk, 0, sizeof(int) * (R + COL_PAD)));
     A(cudaMemset(g->d_B, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
     A(cudaMemset(g->d_Blo, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
-    A(cudaMemset(g->tab.q_hi, 0, sizeof(float) * (R + COL_PAD)));
+    A(cudaMemset(T0.q_hi, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.q_lo, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.gw, 0, sizeof(float) * (size_t)TB_MAX * Rp));
     A(cudaMemcpy(g->d_colk, colk.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_S, eigvals, sizeof(double) * K * PD, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
-    A(cudaMemset(g->tab.B1, 0, sizeof(uint16_t) * (size_t)R * PD));
-    A(cudaMemset(g->tab.Bs, 0, sizeof(uint16_t) * (size_t)R * PD));
-    A(cudaMemset(g->tab.Bs_lo, 0, sizeof(uint16_t) * (size_t)R * PD));
+    A(cudaMemset(T0.B1, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    A(cudaMemset(T0.Bs, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    A(cudaMemset(T0.Bs_lo, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    g->tab = slot_tables(T0, 0, K, Rp, R);
     if (e != cudaSuccess) {
         free_model(g);
         delete g;
@@ -495,7 +532,10 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
     int n = 0;
-    if ((s = patch_phase(g, xhat, H, W, o, t, ws.scal, 1.0, 1.0, beta, forced_k, &n, st))) return s;
+    const double one = 1.0;
+    if ((s = prepare_batch(g, H, W, o, t, 1, ws.scal, &one, 1.0, beta, &n, st))) return s;
+    use_slot(g, 0, (size_t)H * W);
+    if ((s = patch_phase(g, xhat, H, W, o, n, forced_k, st))) return s;
     const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
     if ((s = launch_aggregate(g, xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, xtilde, st))) return s;
     if (anchors) {
@@ -532,14 +572,15 @@ epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *ancho
     const size_t N = (size_t)H * W;
     epll_gmm tmp;
     unsigned *mult = nullptr;
-    if (dalloc(&tmp.ws.sampler, 1040 + 2 * (N / 2048 + 2)) != cudaSuccess || dalloc(&mult, N) != cudaSuccess) {
+    const size_t sstride = sampler_stride(N);
+    if (dalloc(&tmp.ws.sampler, sstride) != cudaSuccess || dalloc(&mult, N) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(tmp.ws.sampler);
         cudaFree(mult);
         return fail(EPLL_ENOMEM, "sampler scratch allocation failed");
     }
     int n = 0;
-    s = launch_sample(&tmp, H, W, o, t, &n, anchors, mult, st);
+    s = launch_sample(&tmp, H, W, o, t, 1, &n, anchors, mult, tmp.ws.sampler, sstride, st);
     if (s == EPLL_OK && o.subset == EPLL_SUBSET_ALL) {
         k_iota<<<(n + 255) / 256, 256, 0, st>>>(anchors, n);
         if (cudaGetLastError() != cudaSuccess) s = fail(EPLL_ECUDA, "iota launch failed");

@@ -40,6 +40,23 @@ struct Tables {
     uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
 };
 
+// Iterations prepared together (tables of every beta, patch subsets).
+constexpr int TB_MAX = 8;
+
+// Tables of batch slot `slot` inside storage laid out slot-major: K-sized
+// arrays with stride K, column arrays with stride Rp (Rtot + padding), bases
+// with stride Rtot * 64, tmax with stride 1.
+__host__ __device__ inline Tables slot_tables(Tables t, int slot, int K, int Rp, int Rtot)
+{
+    t.cst_hi += (size_t)slot * K; t.cst_lo += (size_t)slot * K;
+    t.t_hi += (size_t)slot * K; t.t_lo += (size_t)slot * K;
+    t.gp += (size_t)slot * K; t.sgn += (size_t)slot * K;
+    t.q_hi += (size_t)slot * Rp; t.q_lo += (size_t)slot * Rp; t.gw += (size_t)slot * Rp;
+    t.tmax += slot;
+    t.B1 += (size_t)slot * Rtot * 64; t.Bs += (size_t)slot * Rtot * 64; t.Bs_lo += (size_t)slot * Rtot * 64;
+    return t;
+}
+
 // Slots of Workspace::counts after the K bucket counters.
 enum { CNT_NFLAG = 0, CNT_ERR = 1, CNT_NFLAG1 = 2 };
 
@@ -47,8 +64,11 @@ struct Workspace {
     size_t capN = 0;
     float *xhat = nullptr, *xtil = nullptr;   // [N]
     float *y = nullptr, *a = nullptr;         // [N], host-buffer entry point only
-    int *anchors = nullptr;                   // [N]
-    unsigned *mult = nullptr;                 // [N] multiplicity of each anchor in the subset
+    int *anchors = nullptr;                   // current iteration's subset: anchors_all + slot * N
+    unsigned *mult = nullptr;                 // multiplicity of each anchor in the current subset
+    int *anchors_all = nullptr;               // [TB_MAX][N]
+    unsigned *mult_all = nullptr;             // [TB_MAX][N]
+    size_t sstride = 0;                       // sampler scratch per batch slot (uint32 words)
     int *kstar = nullptr;                     // [N]
     float *gap = nullptr;                     // [N]
     int *flag = nullptr;                      // [N] near-tie list for the compensated rescoring
@@ -90,7 +110,9 @@ struct epll_gmm {
     double *d_S = nullptr, *d_w = nullptr, *d_lam = nullptr;     // [K][64], [K], [K]
     float *d_B = nullptr;         // [64][Rtot] Ubar_k concatenated (FP32 rounding of U)
     float *d_Blo = nullptr;       // [64][Rtot] U - B (the FP32 rounding error)
-    epll::Tables tab;
+    epll::Tables tab;             // tables of the current iteration (a slot of tab0)
+    epll::Tables tab0;            // storage of TB_MAX iterations' tables
+    int Rp = 0;                   // Rtot + column padding
     epll::Workspace ws;
     long long last_evals = 0, last_launches = 0;
     long long launches = 0;
@@ -126,14 +148,18 @@ void set_error(const std::string &msg);
 
 // ---------------------------------------------------------------- launchers
 // Each returns EPLL_OK or an error after setting the message.  All enqueue on st.
-// fmt bit mask: 1 = B1 as BF16, 2 = B1 as FP16, 4 = split BF16 basis (Bs, Bs_lo)
-epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
-                          double beta_direct, int fmt, cudaStream_t st);
+// Tables of nb iterations at once (slot b: multiplier mult[b], or 1/beta =
+// 1/beta_direct when beta_direct > 0).  fmt bit mask: 1 = B1 as BF16,
+// 2 = B1 as FP16, 4 = split BF16 basis (Bs, Bs_lo).
+epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mult, int nb,
+                          double sigma2, double beta_direct, int fmt, cudaStream_t st);
 
-// Sampler: writes ws.anchors (FRACTION/JITTER) and ws.mult; returns n via *n.
-// FULL leaves anchors untouched (identity) and mult unused.
-epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t, int *n,
-                          int *anchors_out, unsigned *mult_out, cudaStream_t st);
+// Patch subsets of iterations t0 .. t0+nb-1 into anchors[b * N ...] and
+// mult[b * N ...]; *n = patches per iteration.  FULL writes nothing.
+epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb, int *n,
+                          int *anchors, unsigned *mult, unsigned *scratch, size_t sstride,
+                          cudaStream_t st);
+size_t sampler_stride(size_t N);
 int sample_count(int H, int W, const epll_options &o);
 
 // Near-tie threshold: gap < tau_abs + tau_rel * |z|^2 * tmax.
@@ -141,9 +167,12 @@ epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, con
                                int n, float tau_abs, float tau_rel, cudaStream_t st);
 epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                              int n, int precision, float tau_abs, float tau_rel, cudaStream_t st);
-// Compensated rescoring of ws.flag (count in counts[2K + CNT_NFLAG]).
+// Compensated rescoring of ws.flag (count in counts[2K + CNT_NFLAG]).  With
+// split_scores the candidate scores come from the split-BF16 tensor pass.
 epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                           int n, cudaStream_t st);
+                           int n, bool split_scores, float tau_abs, cudaStream_t st);
+epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                              cudaStream_t st);
 inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; }
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);

@@ -241,8 +241,8 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
           const int *__restrict__ flag, const int *__restrict__ nflag, int f0, int fcap, int K,
           int Rtot, const int *__restrict__ roff, const int *__restrict__ rk_,
           const float *__restrict__ B, const float *__restrict__ Blo, Tables tab,
-          const float *__restrict__ scores, int *__restrict__ kstar, float *__restrict__ gap,
-          long long *__restrict__ ctr)
+          const float *__restrict__ scores, float band_abs, float band_rel, int *__restrict__ kstar,
+          float *__restrict__ gap, long long *__restrict__ ctr)
 {
     __shared__ float zh[RS_WARPS][PD], zl[RS_WARPS][PD];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,34 +269,40 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
         for (int k = lane; k < K; k += 32) best = fminf(best, sc[k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
-        const float band = RESCORE_ABS + RESCORE_REL * (zz.hi + zz.lo) * tab.tmax[0];
-        // compensated scores of the components within the band of the FP32 best
+        const float band = band_abs + band_rel * (zz.hi + zz.lo) * tab.tmax[0];
+        // compensated scores of the components within the band of the best;
+        // lanes scan 32 components at a time, a ballot lists the candidates
         df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
         int kb = -1;
         float outside = FLT_MAX;
-        for (int k = 0; k < K; ++k) {
-            const float sk = sc[k];
-            if (sk > best + band) {
-                outside = fminf(outside, sk);
-                continue;
-            }
-            const int o = roff[k], r = rk_[k];
-            df part = {0.0f, 0.0f};
-            for (int j = lane; j < r; j += 32) {
-                df c = {0.0f, 0.0f};
-                for (int e = 0; e < PD; ++e) {
-                    df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
-                    c = df_add(c, df_mul(u, {zh[w][e], zl[w][e]}));
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const float sk = k0 + lane < K ? sc[k0 + lane] : FLT_MAX;
+            const bool cand = k0 + lane < K && !(sk > best + band);
+            if (!cand) outside = fminf(outside, sk);
+            unsigned m = __ballot_sync(0xffffffffu, cand);
+            while (m) {
+                const int k = k0 + __ffs(m) - 1;
+                m &= m - 1;
+                const int o = roff[k], r = rk_[k];
+                df part = {0.0f, 0.0f};
+                for (int j = lane; j < r; j += 32) {
+                    df c = {0.0f, 0.0f};
+                    for (int e = 0; e < PD; ++e) {
+                        df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
+                        c = df_add(c, df_mul(u, {zh[w][e], zl[w][e]}));
+                    }
+                    df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
+                    part = df_add(part, df_mul(q, df_mul(c, c)));
                 }
-                df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
-                part = df_add(part, df_mul(q, df_mul(c, c)));
+                df sv = df_warp_sum(part);
+                sv = df_add(sv, df_mul({tab.t_hi[k], tab.t_lo[k]}, zz));
+                sv = df_add(sv, {tab.cst_hi[k], tab.cst_lo[k]});
+                if (df_less(sv, b1)) { b2 = b1; b1 = sv; kb = k; }
+                else if (df_less(sv, b2)) { b2 = sv; }
             }
-            df s = df_warp_sum(part);
-            s = df_add(s, df_mul({tab.t_hi[k], tab.t_lo[k]}, zz));
-            s = df_add(s, {tab.cst_hi[k], tab.cst_lo[k]});
-            if (df_less(s, b1)) { b2 = b1; b1 = s; kb = k; }
-            else if (df_less(s, b2)) { b2 = s; }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) outside = fminf(outside, __shfl_xor_sync(0xffffffffu, outside, o));
         if (lane == 0 && kb >= 0) {  // kb < 0 only if every score was NaN
             kstar[i] = kb;
             float g2 = (b2.hi == FLT_MAX) ? outside - (b1.hi + b1.lo)
@@ -308,10 +314,25 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
 }
 
 epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                           int n, cudaStream_t st)
+                           int n, bool split_scores, float tau_abs, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     const int fcap = (int)ws.fcap;
+    if (split_scores) {
+        epll_status s = launch_dump_split(g, xhat, H, W, anchors, n, st);
+        if (s == EPLL_OK) {
+            // band: twice the split form's near-tie threshold (its error bound is half of it)
+            int blocks = (n + RS_WARPS - 1) / RS_WARPS;
+            if (blocks > 152 * 4) blocks = 152 * 4;
+            k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), 0,
+                                                        fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
+                                                        g->d_Blo, g->tab, ws.fscore, 2.0f * tau_abs, 8e-5f,
+                                                        ws.kstar, ws.gap, ws.ctr);
+            EPLL_LAUNCHED(g);
+            return EPLL_OK;
+        }
+        if (s != EPLL_EUNSUPPORTED) return s;
+    }
     for (int f0 = 0; f0 < n; f0 += fcap) {
         const int rows = min(fcap, n - f0);
         const dim3 grid((rows + SEL_THREADS - 1) / SEL_THREADS, g->K < 16 ? g->K : 16);
@@ -323,7 +344,8 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
         if (blocks > 152 * 4) blocks = 152 * 4;
         k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
                                                     fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
-                                                    g->d_Blo, g->tab, ws.fscore, ws.kstar, ws.gap, ws.ctr);
+                                                    g->d_Blo, g->tab, ws.fscore, RESCORE_ABS, RESCORE_REL,
+                                                    ws.kstar, ws.gap, ws.ctr);
         EPLL_LAUNCHED(g);
     }
     return EPLL_OK;
@@ -378,80 +400,153 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ c
 __global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, int *__restrict__ cursor,
                                  int *__restrict__ perm)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) perm[atomicAdd(&cursor[clamp_k(kstar[i], K)], 1)] = i;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = i < n ? clamp_k(kstar[i], K) : -1;
+    // lanes with the same component share one atomic: the lowest such lane
+    // reserves the group's slots, the others take consecutive ones
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader && k >= 0) base = atomicAdd(&cursor[k], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (k >= 0) perm[base + rank] = i;
 }
 
 // ============================================================================
 // Patch estimation (Eqs. 15-16): chat_j = (gamma_j - gamma_P) c_j,
-// zhat = Ubar chat + gamma_P z + mean.  A block takes 64 consecutive entries
-// of the component-grouped list; for every run of equal components it stages
-// Ubar_k (and its transpose) in shared memory, then each warp estimates one
-// patch at a time (lanes over basis columns, then over pixels).  The estimate
-// is written as a 64-float row at the patch's anchor.
+// zhat = Ubar chat + gamma_P z + mean.  A block takes 128 consecutive entries
+// of the component-grouped list, one patch per thread (the DC-free patch and
+// its coefficients live in registers).  For every run of equal components in
+// the block's range Ubar_k is staged in shared memory and read back as float4
+// broadcasts, four FMAs per load, in the order of the definitions (c_j sums
+// over the pixels in order, zhat_e over the coefficients in order).  The
+// estimate is written as a 64-float row at the patch's anchor.
 // ============================================================================
-constexpr int EST_WARPS = 4;
-constexpr int EST_ENTRIES = 64;
+constexpr int EST_T = 128;
 
-__global__ void __launch_bounds__(32 * EST_WARPS)
+__global__ void __launch_bounds__(EST_T)
 k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
            const int *__restrict__ perm, const int *__restrict__ kstar, int K, int Rtot,
            const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
            Tables tab, float *__restrict__ zrow)
 {
-    __shared__ float Us[PD][PD + 1];   // Us[e][j]
-    __shared__ float UT[PD][PD + 1];   // UT[j][e]
+    // The block's DC-free patches are gathered warp-cooperatively (coalesced
+    // 8-pixel row segments) into zs, padded to 65 floats so that thread t
+    // reading its own row hits distinct banks; Ubar_k later reuses the space.
+    __shared__ __align__(16) union {
+        float zs[EST_T][PD + 1];
+        float Us[PD][PD];  // Us[e][j], zero beyond the rank
+    } sm;
+    __shared__ float mus[EST_T];
     __shared__ float gws[PD];
-    __shared__ float zs[EST_WARPS][PD], cs[EST_WARPS][PD];
     __shared__ int run_end;
+    const int begin = blockIdx.x * EST_T;
+    const int end = min(n, begin + EST_T);
+    const int q = begin + threadIdx.x;
+    const bool valid = q < end;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int begin = blockIdx.x * EST_ENTRIES;
-    const int end = min(n, begin + EST_ENTRIES);
+    __shared__ int s_anchor[EST_T];
+    if (valid) {
+        const int i = perm[q];
+        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+    }
+    __syncthreads();
+    // each warp gathers its 32 patches four at a time (8 loads in flight per lane)
+    const int cnt_p = end - begin;
+    for (int p0 = w * 32; p0 < min(cnt_p, w * 32 + 32); p0 += 4) {
+        float x0[4], x1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = min(p0 + u, cnt_p - 1);
+            const int a = s_anchor[p];
+            const int ai = a / W, aj = a % W;
+            x0[u] = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
+            x1[u] = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u;
+            const float m = warp_sum(x0[u] + x1[u]) * (1.0f / PD);
+            if (p < cnt_p) {
+                sm.zs[p][lane] = x0[u] - m;
+                sm.zs[p][lane + 32] = x1[u] - m;
+                if (lane == 0) mus[p] = m;
+            }
+        }
+    }
+    __syncthreads();
+    int mi = 0, mk = -1, a = 0;
+    float z[PD];
+    float mu = 0.0f;
+    if (valid) {
+        mi = perm[q];
+        mk = clamp_k(kstar[mi], K);
+        a = s_anchor[threadIdx.x];
+        mu = mus[threadIdx.x];
+#pragma unroll
+        for (int e = 0; e < PD; ++e) z[e] = sm.zs[threadIdx.x][e];
+    }
+    __syncthreads();
     int pos = begin;
     while (pos < end) {
         const int k = clamp_k(kstar[perm[pos]], K);
         if (threadIdx.x == 0) run_end = end;
         __syncthreads();
-        for (int q = pos + threadIdx.x; q < end; q += blockDim.x)
-            if (clamp_k(kstar[perm[q]], K) != k) atomicMin(&run_end, q);
+        for (int q2 = pos + threadIdx.x; q2 < end; q2 += EST_T)
+            if (clamp_k(kstar[perm[q2]], K) != k) atomicMin(&run_end, q2);
         const int o = roff[k], r = rk_[k];
-        for (int idx = threadIdx.x; idx < PD * r; idx += blockDim.x) {
-            const int e = idx / r, j = idx % r;
-            const float u = B[(size_t)e * Rtot + o + j];
-            Us[e][j] = u;
-            UT[j][e] = u;
+        for (int idx = threadIdx.x; idx < PD * PD; idx += EST_T) {
+            const int e = idx >> 6, j = idx & 63;
+            sm.Us[e][j] = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
         }
-        for (int j = threadIdx.x; j < r; j += blockDim.x) gws[j] = tab.gw[o + j];
+        if (threadIdx.x < PD) gws[threadIdx.x] = (int)threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
         __syncthreads();
-        const float gp = tab.gp[k];
         const int stop = run_end;
-        for (int q = pos + w; q < stop; q += EST_WARPS) {
-            const int i = perm[q];
-            const int a = anchors ? anchors[i] : i;
-            const int ai = a / W, aj = a % W;
-            const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
-            const float x1 = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
-            const float mu = warp_sum(x0 + x1) * (1.0f / PD);
-            zs[w][lane] = x0 - mu;
-            zs[w][lane + 32] = x1 - mu;
-            __syncwarp();
-            for (int j = lane; j < r; j += 32) {
-                float c = 0.0f;
-#pragma unroll 8
-                for (int e = 0; e < PD; ++e) c = fmaf(Us[e][j], zs[w][e], c);
-                cs[w][j] = gws[j] * c;
+        if (valid && mk == k) {
+            const float gp = tab.gp[k];
+            float c[PD];
+#pragma unroll
+            for (int j4 = 0; j4 < PD / 4; ++j4) {
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                if (4 * j4 < r) {
+#pragma unroll
+                    for (int e = 0; e < PD; ++e) {
+                        const float4 u = reinterpret_cast<const float4 *>(&sm.Us[e][0])[j4];
+                        a0 = fmaf(u.x, z[e], a0);
+                        a1 = fmaf(u.y, z[e], a1);
+                        a2 = fmaf(u.z, z[e], a2);
+                        a3 = fmaf(u.w, z[e], a3);
+                    }
+                }
+                c[4 * j4 + 0] = gws[4 * j4 + 0] * a0;
+                c[4 * j4 + 1] = gws[4 * j4 + 1] * a1;
+                c[4 * j4 + 2] = gws[4 * j4 + 2] * a2;
+                c[4 * j4 + 3] = gws[4 * j4 + 3] * a3;
             }
-            __syncwarp();
-            float v0 = gp * zs[w][lane], v1 = gp * zs[w][lane + 32];
-            for (int j = 0; j < r; ++j) {
-                const float cj = cs[w][j];
-                v0 = fmaf(UT[j][lane], cj, v0);
-                v1 = fmaf(UT[j][lane + 32], cj, v1);
+            float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)a * PD);
+#pragma unroll
+            for (int e4 = 0; e4 < PD / 4; ++e4) {
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int e = 4 * e4 + t;
+                    float acc = gp * z[e];
+#pragma unroll
+                    for (int j4 = 0; j4 < PD / 4; ++j4) {
+                        if (4 * j4 < r) {
+                            const float4 u = reinterpret_cast<const float4 *>(&sm.Us[e][0])[j4];
+                            acc = fmaf(u.x, c[4 * j4 + 0], acc);
+                            acc = fmaf(u.y, c[4 * j4 + 1], acc);
+                            acc = fmaf(u.z, c[4 * j4 + 2], acc);
+                            acc = fmaf(u.w, c[4 * j4 + 3], acc);
+                        }
+                    }
+                    v[t] = acc + mu;
+                }
+                dst[e4] = make_float4(v[0], v[1], v[2], v[3]);
             }
-            float *dst = zrow + (size_t)a * PD;
-            dst[lane] = v0 + mu;
-            dst[lane + 32] = v1 + mu;
-            __syncwarp();
         }
         __syncthreads();
         pos = stop;
@@ -473,7 +568,7 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
     EPLL_LAUNCHED(g);
     k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(ws.kstar, n, K, counts, ws.perm);
     EPLL_LAUNCHED(g);
-    k_estimate<<<(n + EST_ENTRIES - 1) / EST_ENTRIES, 32 * EST_WARPS, 0, st>>>(
+    k_estimate<<<(n + EST_T - 1) / EST_T, EST_T, 0, st>>>(
         xhat, H, W, anchors, n, ws.perm, ws.kstar, K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab,
         ws.zrow);
     EPLL_LAUNCHED(g);

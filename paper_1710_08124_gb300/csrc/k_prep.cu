@@ -39,15 +39,22 @@ __device__ double component_constant(int k, const int *r, const double *S, const
     return c;
 }
 
+struct Mults {
+    double m[TB_MAX];
+};
+
+// Grid (K, nb): component k of batch slot blockIdx.y.
 __global__ void __launch_bounds__(64)
-k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ roff,
+k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restrict__ roff,
          const double *__restrict__ S, const double *__restrict__ w, const double *__restrict__ lam,
-         const double *__restrict__ d_lambda, double mult, double sigma2, double beta_direct,
-         const float *__restrict__ B, Tables tab, int fmt)
+         const double *__restrict__ d_lambda, Mults mults, double sigma2, double beta_direct,
+         const float *__restrict__ B, Tables tab0, int fmt)
 {
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
     const int k = blockIdx.x, j = threadIdx.x;
+    const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
+    const double mult = mults.m[blockIdx.y];
     const double ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
 
     const double c0 = component_constant(0, r, S, w, lam, ib, red);
@@ -101,12 +108,14 @@ k_tables(int K, int Rtot, const int *__restrict__ r, const int *__restrict__ rof
     }
 }
 
-epll_status launch_tables(epll_gmm *g, const double *d_lambda, double mult, double sigma2,
-                          double beta_direct, int fmt, cudaStream_t st)
+epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mult, int nb,
+                          double sigma2, double beta_direct, int fmt, cudaStream_t st)
 {
-    EPLL_CU(cudaMemsetAsync(g->tab.tmax, 0, sizeof(float), st));
-    k_tables<<<g->K, 64, 0, st>>>(g->K, g->Rtot, g->d_r, g->d_roff, g->d_S, g->d_w, g->d_lam,
-                                  d_lambda, mult, sigma2, beta_direct, g->d_B, g->tab, fmt);
+    Mults m{};
+    for (int b = 0; b < nb; ++b) m.m[b] = mult[b];
+    EPLL_CU(cudaMemsetAsync(g->tab0.tmax, 0, sizeof(float) * nb, st));
+    k_tables<<<dim3(g->K, nb), 64, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
+                                            g->d_lam, d_lambda, m, sigma2, beta_direct, g->d_B, g->tab0, fmt);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -140,11 +149,14 @@ __device__ __forceinline__ int uniform_int(uint64_t u, int m)
 // ---------------------------------------------------------------- jitter
 // Jittered grid of Eq. 20: spacing s, global shift from draws 0/1, per-point
 // offsets in [-J, J] from draws 2+2g / 3+2g; raster order of grid points.
-__global__ void k_jitter(int H, int W, int s, uint64_t seed, int t, int ni, int nj,
-                         int *__restrict__ anchors, unsigned *__restrict__ mult)
+__global__ void k_jitter(int H, int W, int s, uint64_t seed, int t0, int ni, int nj,
+                         int *__restrict__ anchors_all, unsigned *__restrict__ mult_all)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ni * nj) return;
+    const int t = t0 + blockIdx.y;
+    int *anchors = anchors_all + (size_t)blockIdx.y * H * W;
+    unsigned *mult = mult_all + (size_t)blockIdx.y * H * W;
     const uint64_t st = stream_state(seed, (uint64_t)t);
     const int J = (PS - s) / 2;
     const int gi = uniform_int(draw(st, 0), s), gj = uniform_int(draw(st, 1), s);
@@ -169,11 +181,15 @@ __device__ __forceinline__ uint32_t frac_key(uint64_t st, int a)
     return (uint32_t)(draw(st, (uint64_t)a) >> 32);
 }
 
+// Scratch of batch slot b (t = t0 + b) starts at scratch + b * sstride:
+// [0, 1024) histograms of the 4 passes, [1024, 1027) sel, from 1040 the tiles.
 __global__ void __launch_bounds__(256)
-k_frac_hist(int N, uint64_t seed, int t, int pass, const unsigned *__restrict__ sel,
-            unsigned *__restrict__ hist)
+k_frac_hist(int N, uint64_t seed, int t0, int pass, unsigned *__restrict__ scratch, size_t sstride)
 {
     __shared__ unsigned h[256];
+    const int t = t0 + blockIdx.y;
+    unsigned *hist = scratch + blockIdx.y * sstride;
+    const unsigned *sel = hist + 1024;
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t st = stream_state(seed, (uint64_t)t);
@@ -188,9 +204,11 @@ k_frac_hist(int N, uint64_t seed, int t, int pass, const unsigned *__restrict__ 
 }
 
 __global__ void __launch_bounds__(256)
-k_frac_pick(int pass, int M, unsigned *__restrict__ sel, const unsigned *__restrict__ hist)
+k_frac_pick(int pass, int M, unsigned *__restrict__ scratch, size_t sstride)
 {
     __shared__ unsigned c[256];
+    const unsigned *hist = scratch + blockIdx.y * sstride;
+    unsigned *sel = scratch + blockIdx.y * sstride + 1024;
     const int d = threadIdx.x;
     const unsigned hd = hist[pass * 256 + d];
     c[d] = hd;
@@ -219,10 +237,12 @@ constexpr int FRAC_TILE = 256 * FRAC_ITEMS;
 
 // phase 1: per-tile counts of keys below / equal to the threshold
 __global__ void __launch_bounds__(256)
-k_frac_count(int N, uint64_t seed, int t, const unsigned *__restrict__ sel,
-             unsigned long long *__restrict__ tile)
+k_frac_count(int N, uint64_t seed, int t0, unsigned *__restrict__ scratch, size_t sstride)
 {
     __shared__ unsigned long long red[256];
+    const int t = t0 + blockIdx.y;
+    const unsigned *sel = scratch + blockIdx.y * sstride + 1024;
+    unsigned long long *tile = reinterpret_cast<unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
     const uint64_t st = stream_state(seed, (uint64_t)t);
     const uint32_t thr = sel[0];
     unsigned less = 0, eq = 0;
@@ -246,8 +266,9 @@ k_frac_count(int N, uint64_t seed, int t, const unsigned *__restrict__ sel,
 
 // phase 2: exclusive scan of the tile counts (one block)
 __global__ void __launch_bounds__(1024)
-k_frac_scan(int ntiles, unsigned long long *__restrict__ tile)
+k_frac_scan(int ntiles, unsigned *__restrict__ scratch, size_t sstride)
 {
+    unsigned long long *tile = reinterpret_cast<unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
     __shared__ unsigned long long c[1024];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
@@ -272,11 +293,16 @@ k_frac_scan(int ntiles, unsigned long long *__restrict__ tile)
 
 // phase 3: write the selected anchors in increasing order
 __global__ void __launch_bounds__(256)
-k_frac_write(int N, uint64_t seed, int t, const unsigned *__restrict__ sel,
-             const unsigned long long *__restrict__ tile, int *__restrict__ anchors,
-             unsigned *__restrict__ mult)
+k_frac_write(int N, uint64_t seed, int t0, const unsigned *__restrict__ scratch, size_t sstride,
+             int *__restrict__ anchors_all, unsigned *__restrict__ mult_all)
 {
     __shared__ unsigned long long c[256];
+    const int t = t0 + blockIdx.y;
+    const unsigned *sel = scratch + blockIdx.y * sstride + 1024;
+    const unsigned long long *tile =
+        reinterpret_cast<const unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
+    int *anchors = anchors_all + (size_t)blockIdx.y * N;
+    unsigned *mult = mult_all + (size_t)blockIdx.y * N;
     const uint64_t st = stream_state(seed, (uint64_t)t);
     const uint32_t thr = sel[0];
     const unsigned need = sel[2] + 1u;  // keys equal to thr that are selected
@@ -332,40 +358,40 @@ int sample_count(int H, int W, const epll_options &o)
     return N;
 }
 
-epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t, int *n,
-                          int *anchors, unsigned *mult, cudaStream_t st)
+size_t sampler_stride(size_t N) { return 1040 + 2 * (N / FRAC_TILE + 2); }
+
+epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb, int *n,
+                          int *anchors, unsigned *mult, unsigned *scratch, size_t sstride,
+                          cudaStream_t st)
 {
     const int N = H * W;
     *n = sample_count(H, W, o);
-    Workspace &ws = g->ws;
     if (o.subset == EPLL_SUBSET_ALL) return EPLL_OK;
     if (o.subset == EPLL_SUBSET_JITTER) {
         const int s = (int)o.subset_param;
-        EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N, st));
+        EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N * nb, st));
         const int ni = (H + s - 1) / s, nj = (W + s - 1) / s;
-        k_jitter<<<(ni * nj + 255) / 256, 256, 0, st>>>(H, W, s, o.seed, t, ni, nj, anchors, mult);
+        k_jitter<<<dim3((ni * nj + 255) / 256, nb), 256, 0, st>>>(H, W, s, o.seed, t0, ni, nj, anchors, mult);
         EPLL_LAUNCHED(g);
         return EPLL_OK;
     }
     // FRACTION
-    unsigned *hist = ws.sampler;        // [4][256]
-    unsigned *sel = ws.sampler + 1024;  // [3]
-    unsigned long long *tile = reinterpret_cast<unsigned long long *>(ws.sampler + 1040);
-    EPLL_CU(cudaMemsetAsync(hist, 0, sizeof(unsigned) * 1024, st));
+    for (int b = 0; b < nb; ++b)
+        EPLL_CU(cudaMemsetAsync(scratch + b * sstride, 0, sizeof(unsigned) * 1024, st));
     int hb = (N + 255) / 256;
-    if (hb > 152 * 8) hb = 152 * 8;
+    if (hb > 152 * 4) hb = 152 * 4;
     for (int pass = 0; pass < 4; ++pass) {
-        k_frac_hist<<<hb, 256, 0, st>>>(N, o.seed, t, pass, sel, hist);
+        k_frac_hist<<<dim3(hb, nb), 256, 0, st>>>(N, o.seed, t0, pass, scratch, sstride);
         EPLL_LAUNCHED(g);
-        k_frac_pick<<<1, 256, 0, st>>>(pass, *n, sel, hist);
+        k_frac_pick<<<dim3(1, nb), 256, 0, st>>>(pass, *n, scratch, sstride);
         EPLL_LAUNCHED(g);
     }
     const int ntiles = (N + FRAC_TILE - 1) / FRAC_TILE;
-    k_frac_count<<<ntiles, 256, 0, st>>>(N, o.seed, t, sel, tile);
+    k_frac_count<<<dim3(ntiles, nb), 256, 0, st>>>(N, o.seed, t0, scratch, sstride);
     EPLL_LAUNCHED(g);
-    k_frac_scan<<<1, 1024, 0, st>>>(ntiles, tile);
+    k_frac_scan<<<dim3(1, nb), 1024, 0, st>>>(ntiles, scratch, sstride);
     EPLL_LAUNCHED(g);
-    k_frac_write<<<ntiles, 256, 0, st>>>(N, o.seed, t, sel, tile, anchors, mult);
+    k_frac_write<<<dim3(ntiles, nb), 256, 0, st>>>(N, o.seed, t0, scratch, sstride, anchors, mult);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

@@ -217,19 +217,19 @@ constexpr int TC_SMEM_BUDGET = 200 * 1024;
 template <int BN, int NT>
 struct TcCfg {
     static constexpr int A_TILE = TC_M * 128;                  // 16 KB
-    static constexpr int A_BYTES = A_TILE * (NT == 3 ? 2 : 1);
+    static constexpr int A_BYTES = A_TILE * (NT == 3 ? 2 : 1); // one A buffer (hi [+ lo])
     static constexpr int B_TILE = BN * 128;
     static constexpr int B_STAGE = B_TILE * (NT == 3 ? 2 : 1);
-    static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - A_BYTES) / B_STAGE;
+    static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - 2 * A_BYTES) / B_STAGE;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int NB = 512 / BN;                        // TMEM accumulator buffers
     static constexpr int HALF = BN / 2;                        // columns per epilogue warp
     static constexpr int CTRL = 2048;
-    static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_STAGE + CTRL;
+    static constexpr int SMEM = 1024 + 2 * A_BYTES + STAGES * B_STAGE + CTRL;
 };
 
 struct TcCtrl {
-    unsigned long long a_full;
+    unsigned long long a_full[2], a_empty[2];
     unsigned long long b_full[8], b_empty[8];
     unsigned long long t_full[4], t_empty[4];
     unsigned long long drain;
@@ -237,7 +237,6 @@ struct TcCtrl {
     int abort_flag;
 };
 
-template <int RR>
 __device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &k1)
 {
     if (s < s1) {
@@ -249,33 +248,52 @@ __device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &
     }
 }
 
-template <int BN, int NT, int RR>
+// Persistent: CTA b takes the 128-row tiles b, b + gridDim.x, ... of the n
+// rows (n read from the device when n_dev is given).  Two A buffers let the
+// next tile's patches load while the current tile is multiplied; the basis
+// ring and the TMEM accumulator buffers run on across tiles, so the epilogue
+// of one tile overlaps the MMAs of the next.
+// DUMP = true: instead of the top-2 selection every component's score is
+// written to scores[row * K + k]; blockIdx.y then takes a slice of the basis
+// tiles (uniform ranks only, so no component straddles two slices).
+template <int BN, int NT, int RR, bool DUMP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
           const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
           int n, const int *__restrict__ rowmap, const int *__restrict__ n_dev, int K, int Rtot,
           uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk, Tables tab,
           float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
-          int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err)
+          int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err,
+          float *__restrict__ scores)
 {
     using C = TcCfg<BN, NT>;
+    static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
     if (n_dev) n = *n_dev;                       // rows listed on the device
-    if ((int)(blockIdx.x * TC_M) >= n) return;   // whole CTA idle, before any setup
+    const int mtiles = (n + TC_M - 1) / TC_M;
+    if ((int)blockIdx.x >= mtiles) return;       // whole CTA idle, before any setup
+    const int ntiles_all = Rtot / BN;
+    const int tile0 = DUMP ? (int)((long long)ntiles_all * blockIdx.y / gridDim.y) : 0;
+    const int tile1 = DUMP ? (int)((long long)ntiles_all * (blockIdx.y + 1) / gridDim.y) : ntiles_all;
+    if (tile1 <= tile0) return;
+    const int ntiles = tile1 - tile0;
+    const int my_m = (mtiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + C::A_BYTES;
+    unsigned char *sA = smem;                      // 2 x A_BYTES
+    unsigned char *sB = smem + 2 * C::A_BYTES;
     TcCtrl *ctl = (TcCtrl *)(sB + C::STAGES * C::B_STAGE);
     float *mrg = (float *)(ctl + 1);  // [128][3] merge buffer of the two epilogue halves
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_M;
-    const int ntiles = Rtot / BN;
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (threadIdx.x == 0) {
         ctl->abort_flag = 0;
-        mbar_init(smem_u32(&ctl->a_full), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&ctl->a_full[i]), 1);
+            mbar_init(smem_u32(&ctl->a_empty[i]), 1);
+        }
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->b_full[s]), 1);
             mbar_init(smem_u32(&ctl->b_empty[s]), 1);
@@ -303,45 +321,65 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            const uint32_t af = smem_u32(&ctl->a_full);
-            mbar_expect_tx(af, C::A_BYTES);
-            tma_load_2d(smem_u32(sA), &mapA, 0, m0, af);
-            if (NT == 3) tma_load_2d(smem_u32(sA + C::A_TILE), &mapAlo, 0, m0, af);
-            for (int it = 0; it < ntiles; ++it) {
-                const int s = it % C::STAGES, round = it / C::STAGES;
-                if (!mbar_wait(smem_u32(&ctl->b_empty[s]), (round & 1) ^ 1, abort_flag)) break;
-                const uint32_t bf = smem_u32(&ctl->b_full[s]);
-                mbar_expect_tx(bf, C::B_STAGE);
-                unsigned char *dst = sB + s * C::B_STAGE;
-                tma_load_2d(smem_u32(dst), &mapB, 0, it * BN, bf);
-                if (NT == 3) tma_load_2d(smem_u32(dst + C::B_TILE), &mapBlo, 0, it * BN, bf);
+            bool ok = true;
+            for (int mt = 0; ok && mt < my_m; ++mt) {
+                const int m0 = ((int)blockIdx.x + mt * (int)gridDim.x) * TC_M;
+                const int ab = mt & 1, around = mt >> 1;
+                if (!mbar_wait(smem_u32(&ctl->a_empty[ab]), (around & 1) ^ 1, abort_flag)) break;
+                const uint32_t af = smem_u32(&ctl->a_full[ab]);
+                unsigned char *dA = sA + ab * C::A_BYTES;
+                mbar_expect_tx(af, C::A_BYTES);
+                tma_load_2d(smem_u32(dA), &mapA, 0, m0, af);
+                if (NT == 3) tma_load_2d(smem_u32(dA + C::A_TILE), &mapAlo, 0, m0, af);
+                for (int it = 0; it < ntiles; ++it) {
+                    const int gi = mt * ntiles + it;
+                    const int s = gi % C::STAGES, round = gi / C::STAGES;
+                    if (!mbar_wait(smem_u32(&ctl->b_empty[s]), (round & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bf = smem_u32(&ctl->b_full[s]);
+                    mbar_expect_tx(bf, C::B_STAGE);
+                    unsigned char *dst = sB + s * C::B_STAGE;
+                    tma_load_2d(smem_u32(dst), &mapB, 0, (tile0 + it) * BN, bf);
+                    if (NT == 3) tma_load_2d(smem_u32(dst + C::B_TILE), &mapBlo, 0, (tile0 + it) * BN, bf);
+                }
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = mbar_wait(smem_u32(&ctl->a_full), 0, abort_flag);
-            tc_fence_after();
-            const uint32_t aHi = smem_u32(sA), aLo = smem_u32(sA + C::A_TILE);
-            for (int it = 0; ok && it < ntiles; ++it) {
-                const int s = it % C::STAGES, round = it / C::STAGES;
-                const int b = it % C::NB, tround = it / C::NB;
-                if (!mbar_wait(smem_u32(&ctl->b_full[s]), round & 1, abort_flag)) break;
-                if (!mbar_wait(smem_u32(&ctl->t_empty[b]), (tround & 1) ^ 1, abort_flag)) break;
+            bool ok = true;
+            for (int mt = 0; ok && mt < my_m; ++mt) {
+                const int ab = mt & 1, around = mt >> 1;
+                if (!mbar_wait(smem_u32(&ctl->a_full[ab]), around & 1, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t d = tbase + (uint32_t)(b * BN);
-                const uint32_t bHi = smem_u32(sB + s * C::B_STAGE), bLo = bHi + C::B_TILE;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {  // reduction depth 64 = 4 x 16
-                    const uint32_t off = (uint32_t)(k * 32);
-                    mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
-                    if (NT == 3) {
-                        mma_f16(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
-                        mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                const uint32_t aHi = smem_u32(sA + ab * C::A_BYTES), aLo = aHi + C::A_TILE;
+                for (int it = 0; it < ntiles; ++it) {
+                    const int gi = mt * ntiles + it;
+                    const int s = gi % C::STAGES, round = gi / C::STAGES;
+                    const int b = gi % C::NB, tround = gi / C::NB;
+                    if (!mbar_wait(smem_u32(&ctl->b_full[s]), round & 1, abort_flag) ||
+                        !mbar_wait(smem_u32(&ctl->t_empty[b]), (tround & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t d = tbase + (uint32_t)(b * BN);
+                    const uint32_t bHi = smem_u32(sB + s * C::B_STAGE), bLo = bHi + C::B_TILE;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // reduction depth 64 = 4 x 16
+                        const uint32_t off = (uint32_t)(k * 32);
+                        mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
+                        if (NT == 3) {
+                            mma_f16(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
+                            mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(smem_u32(&ctl->b_empty[s]));
+                    mma_commit(smem_u32(&ctl->t_full[b]));
                 }
-                mma_commit(smem_u32(&ctl->b_empty[s]));
-                mma_commit(smem_u32(&ctl->t_full[b]));
+                mma_commit(smem_u32(&ctl->a_empty[ab]));  // A buffer free once these MMAs complete
             }
             // drain: every MMA issued above has completed once this arrives
             mma_commit(smem_u32(&ctl->drain));
@@ -352,114 +390,134 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int q = warp & 3;        // TMEM lane quarter this warp may access
         const int h = (warp - 2) >> 2; // column half of each accumulator tile
         const int row = 32 * q + lane;
-        const int grow = m0 + row;
-        const float zzr = grow < n ? zz[grow] : 0.0f;
-        float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
-        int k1 = 0, curk = -1;
-        for (int it = 0; it < ntiles; ++it) {
-            const int b = it % C::NB, tround = it / C::NB;
-            if (!mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag)) break;
-            tc_fence_after();
-            // uniform ranks: each half-warp-group owns whole components of its half;
-            // ragged ranks: the h = 0 warps take the whole tile (components may
-            // straddle the halves), the h = 1 warps only keep the handshake.
-            const int cbeg = RR ? h * C::HALF : 0;
-            const int ncol = RR ? C::HALF : (h == 0 ? BN : 0);
-            const int col0 = it * BN + cbeg;
-            const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbeg);
-            uint32_t r[32];
-            for (int c = 0; c < ncol / 32; ++c) {
-                tmem_ld32(taddr + (uint32_t)(32 * c), r);
-                tmem_wait(r);
-                const int cb = col0 + 32 * c;
-                if constexpr (RR == 64) {
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        bool ok = true;
+        for (int mt = 0; ok && mt < my_m; ++mt) {
+            const int m0 = ((int)blockIdx.x + mt * (int)gridDim.x) * TC_M;
+            const int grow = m0 + row;
+            const float zzr = grow < n ? zz[grow] : 0.0f;
+            float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
+            int k1 = 0, curk = -1;
+            for (int it = 0; it < ntiles; ++it) {
+                const int gi = mt * ntiles + it;
+                const int b = gi % C::NB, tround = gi / C::NB;
+                if (!mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                // uniform ranks: each half-warp-group owns whole components of its half;
+                // ragged ranks: the h = 0 warps take the whole tile (components may
+                // straddle the halves), the h = 1 warps only keep the handshake.
+                const int cbeg = RR ? h * C::HALF : 0;
+                const int ncol = RR ? C::HALF : (h == 0 ? BN : 0);
+                const int col0 = (tile0 + it) * BN + cbeg;
+                const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbeg);
+                uint32_t r[32];
+                for (int c = 0; c < ncol / 32; ++c) {
+                    tmem_ld32(taddr + (uint32_t)(32 * c), r);
+                    tmem_wait(r);
+                    const int cb = col0 + 32 * c;
+                    if constexpr (RR == 64) {
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-                        const float v2 = __uint_as_float(r[j + 2]), v3 = __uint_as_float(r[j + 3]);
-                        a0 = fmaf(v0, v0, a0);
-                        a1 = fmaf(v1, v1, a1);
-                        a2 = fmaf(v2, v2, a2);
-                        a3 = fmaf(v3, v3, a3);
-                    }
-                    acc += (a0 + a1) + (a2 + a3);
-                    if (c & 1) {
-                        const int k = cb >> 6;
-                        if (k < K) {
-                            const float s = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr + acc;
-                            top2<RR>(s, k, s1, s2, k1);
-                        }
-                        acc = 0.0f;
-                    }
-                } else if constexpr (RR > 0) {
-#pragma unroll
-                    for (int p = 0; p < 32 / RR; ++p) {
-                        float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < RR; j += 2) {
-                            const float v0 = __uint_as_float(r[p * RR + j]);
-                            const float v1 = __uint_as_float(r[p * RR + j + 1]);
+                        for (int j = 0; j < 32; j += 4) {
+                            const float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+                            const float v2 = __uint_as_float(r[j + 2]), v3 = __uint_as_float(r[j + 3]);
                             a0 = fmaf(v0, v0, a0);
                             a1 = fmaf(v1, v1, a1);
+                            a2 = fmaf(v2, v2, a2);
+                            a3 = fmaf(v3, v3, a3);
                         }
-                        const int k = cb / RR + p;
-                        if (k < K) {
-                            const float s = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr - (a0 + a1);
-                            top2<RR>(s, k, s1, s2, k1);
-                        }
-                    }
-                } else {
-                    // ragged ranks: column -> component map
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int k = __ldg(&colk[cb + j]);
-                        if (k != curk) {
-                            if (curk >= 0) {
-                                const float s = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
-                                                __ldg(&tab.sgn[curk]) * acc;
-                                top2<RR>(s, curk, s1, s2, k1);
+                        acc += (a0 + a1) + (a2 + a3);
+                        if (c & 1) {
+                            const int k = cb >> 6;
+                            if (k < K) {
+                                const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr + acc;
+                                if (DUMP) {
+                                    if (grow < n) scores[(size_t)grow * K + k] = sc;
+                                } else {
+                                    top2(sc, k, s1, s2, k1);
+                                }
                             }
-                            curk = k;
                             acc = 0.0f;
                         }
-                        const float v = __uint_as_float(r[j]);
-                        acc = fmaf(v, v, acc);
+                    } else if constexpr (RR > 0) {
+#pragma unroll
+                        for (int p = 0; p < 32 / RR; ++p) {
+                            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                            for (int j = 0; j < RR; j += 2) {
+                                const float v0 = __uint_as_float(r[p * RR + j]);
+                                const float v1 = __uint_as_float(r[p * RR + j + 1]);
+                                a0 = fmaf(v0, v0, a0);
+                                a1 = fmaf(v1, v1, a1);
+                            }
+                            const int k = cb / RR + p;
+                            if (k < K) {
+                                const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr - (a0 + a1);
+                                if (DUMP) {
+                                    if (grow < n) scores[(size_t)grow * K + k] = sc;
+                                } else {
+                                    top2(sc, k, s1, s2, k1);
+                                }
+                            }
+                        }
+                    } else {
+                        // ragged ranks: column -> component map
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int k = __ldg(&colk[cb + j]);
+                            if (k != curk) {
+                                if (curk >= 0) {
+                                    const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
+                                                     __ldg(&tab.sgn[curk]) * acc;
+                                    top2(sc, curk, s1, s2, k1);
+                                }
+                                curk = k;
+                                acc = 0.0f;
+                            }
+                            const float v = __uint_as_float(r[j]);
+                            acc = fmaf(v, v, acc);
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
-        }
-        if (RR == 0 && curk >= 0) {
-            // the last component ends with the last column
-            const float s = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr + __ldg(&tab.sgn[curk]) * acc;
-            top2<RR>(s, curk, s1, s2, k1);
-        }
-        // merge the two halves: components of half 1 interleave with half 0's
-        if (h == 1) {
-            mrg[row * 3 + 0] = s1;
-            mrg[row * 3 + 1] = s2;
-            mrg[row * 3 + 2] = __int_as_float(k1);
-        }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        if (h == 0 && grow < n) {
-            const int out = rowmap ? rowmap[grow] : grow;
-            const float t1 = mrg[row * 3 + 0], t2 = mrg[row * 3 + 1];
-            const int tk = __float_as_int(mrg[row * 3 + 2]);
-            float b1, b2;
-            int bk;
-            if (t1 < s1 || (t1 == s1 && tk < k1)) {
-                b1 = t1; bk = tk; b2 = fminf(s1, t2);
-            } else {
-                b1 = s1; bk = k1; b2 = fminf(t1, s2);
+            if (RR == 0 && curk >= 0) {
+                // the last component ends with the last column
+                const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
+                                 __ldg(&tab.sgn[curk]) * acc;
+                top2(sc, curk, s1, s2, k1);
             }
-            kstar[out] = bk;
-            const float gp = b2 - b1;
-            gap[out] = gp;
-            const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
-            if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = out;
+            if (!DUMP) {
+                // merge the two halves: components of half 1 interleave with half 0's
+                if (h == 1) {
+                    mrg[row * 3 + 0] = s1;
+                    mrg[row * 3 + 1] = s2;
+                    mrg[row * 3 + 2] = __int_as_float(k1);
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (h == 0 && grow < n && ok) {
+                    const int out = rowmap ? rowmap[grow] : grow;
+                    const float t1 = mrg[row * 3 + 0], t2 = mrg[row * 3 + 1];
+                    const int tk = __float_as_int(mrg[row * 3 + 2]);
+                    float b1, b2;
+                    int bk;
+                    if (t1 < s1 || (t1 == s1 && tk < k1)) {
+                        b1 = t1; bk = tk; b2 = fminf(s1, t2);
+                    } else {
+                        b1 = s1; bk = k1; b2 = fminf(t1, s2);
+                    }
+                    kstar[out] = bk;
+                    const float gp = b2 - b1;
+                    gap[out] = gp;
+                    const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
+                    if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = out;
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");  // mrg is reused by the next tile
+            }
         }
     }
 
@@ -510,26 +568,37 @@ static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_
     return EPLL_OK;
 }
 
-template <int BN, int NT, int RR>
+template <int BN, int NT, int RR, bool DUMP = false>
 static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                              const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                              const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
-                             float tau_rel, int *flag, int *nflag, cudaStream_t st)
+                             float tau_rel, int *flag, int *nflag, cudaStream_t st,
+                             float *scores = nullptr, int slices = 1)
 {
     using Cfg = TcCfg<BN, NT>;
-    auto kern = k_proj_tc<BN, NT, RR>;
+    auto kern = k_proj_tc<BN, NT, RR, DUMP>;
     static bool attr = false;
     if (!attr) {
         EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
         attr = true;
     }
     Workspace &ws = g->ws;
-    const int grid = (n + TC_M - 1) / TC_M;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        EPLL_CU(cudaGetDevice(&dev));
+        EPLL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int mtiles = (n + TC_M - 1) / TC_M;
+    int gx = slices > 1 ? (sms / slices > 0 ? sms / slices : 1) : sms;
+    if (gx > mtiles) gx = mtiles;
+    if (gx < 1) gx = 1;
+    const dim3 grid(gx, slices);
     // the instrumentation covers the pass over every sampled patch only
     if (!n_dev) prof_begin(g, st);
     kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
                                              g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
-                                             nflag, cnt(g, CNT_ERR));
+                                             nflag, cnt(g, CNT_ERR), scores);
     if (!n_dev) prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
@@ -552,7 +621,40 @@ static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensor
 }
 
 // Relative error bound of the split form (see thresholds() in api.cu).
-constexpr float SPLIT_REL = 1e-4f;
+constexpr float SPLIT_REL = 4e-5f;
+
+// Split-BF16 scores of every component for the rows of the near-tie list
+// (ws.flag, device count): the candidates of the compensated rescoring are the
+// components within the split form's error band of the best.  Returns
+// EPLL_EUNSUPPORTED for ragged ranks (the FP32 list-mode kernel serves them).
+epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                              cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int RR = g->uniform_rank;
+    if (RR == 0 || (size_t)n > ws.fcap) return EPLL_EUNSUPPORTED;
+    const int rows = (n + TC_M - 1) / TC_M * TC_M;
+    uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
+    int *nf = cnt(g, CNT_NFLAG);
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, ws.flag, nf, 1, 1, Z2hi, Z2lo, ws.zz2);
+    EPLL_LAUNCHED(g);
+    CUtensorMap a2, a2lo, bs, bslo;
+    epll_status s;
+    if ((s = make_map(&a2, Z2hi, rows, TC_M))) return s;
+    if ((s = make_map(&a2lo, Z2lo, rows, TC_M))) return s;
+    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 128))) return s;
+    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 128))) return s;
+    const int ntiles = g->Rtot / 128;
+    const int slices = ntiles < 32 ? ntiles : 32;
+    const uint32_t idesc = idesc_f16(TC_M, 128, 1);
+#define EPLL_DUMP_ARGS g, a2, a2lo, bs, bslo, n, ws.flag, nf, ws.zz2, idesc, 0.0f, 0.0f, nullptr, nullptr, st, ws.fscore, slices
+    switch (RR) {
+    case 64: return launch_tc<128, 3, 64, true>(EPLL_DUMP_ARGS);
+    case 16: return launch_tc<128, 3, 16, true>(EPLL_DUMP_ARGS);
+    default: return launch_tc<128, 3, 8, true>(EPLL_DUMP_ARGS);
+    }
+#undef EPLL_DUMP_ARGS
+}
 
 // Gaussian selection on the tensor cores.  A one-term pass (BF16 or FP16)
 // scores every sampled patch; the rows it cannot decide (top-2 gap within its
