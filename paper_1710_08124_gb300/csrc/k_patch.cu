@@ -417,40 +417,50 @@ __global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, in
 // ============================================================================
 // Patch estimation (Eqs. 15-16): chat_j = (gamma_j - gamma_P) c_j,
 // zhat = Ubar chat + gamma_P z + mean.  A block takes 128 consecutive entries
-// of the component-grouped list, one patch per thread (the DC-free patch and
-// its coefficients live in registers).  For every run of equal components in
-// the block's range Ubar_k is staged in shared memory and read back as float4
-// broadcasts, four FMAs per load, in the order of the definitions (c_j sums
-// over the pixels in order, zhat_e over the coefficients in order).  The
-// estimate is written as a 64-float row at the patch's anchor.
+// of the component-grouped list, one patch per thread (the DC-free patch in
+// registers).  For every run of equal components in the block's range
+// Ubar_k and its transpose are staged in shared memory and read back as
+// float4 broadcasts, four FMAs per load, in the order of the definitions
+// (c_j sums over the pixels in order, zhat_e starts from gamma_P z_e and adds
+// the coefficients in order).  Loops over basis columns stay rolled so the
+// kernel fits the instruction cache; the coefficients live in a padded
+// per-thread row of shared memory.  The estimate is written as a 64-float
+// row at the patch's anchor.
 // ============================================================================
 constexpr int EST_T = 128;
+constexpr int EST_LD = PD + 1;  // padded row: thread t's row hits distinct banks
 
-__global__ void __launch_bounds__(EST_T)
+struct EstSmem {
+    union {
+        float zs[EST_T][EST_LD];  // gathered DC-free patches (first phase only)
+        struct {
+            float Us[PD][PD];  // Us[e][j], zero beyond the rank
+            float UT[PD][PD];  // UT[j][e]
+        } u;
+    } a;
+    float cs[EST_T][EST_LD];  // shrunk coefficients of each thread's patch
+    float mus[EST_T];
+    float gws[PD];
+    int anchor[EST_T];
+    int run_end;
+};
+
+__global__ void __launch_bounds__(EST_T, 3)
 k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
            const int *__restrict__ perm, const int *__restrict__ kstar, int K, int Rtot,
            const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
            Tables tab, float *__restrict__ zrow)
 {
-    // The block's DC-free patches are gathered warp-cooperatively (coalesced
-    // 8-pixel row segments) into zs, padded to 65 floats so that thread t
-    // reading its own row hits distinct banks; Ubar_k later reuses the space.
-    __shared__ __align__(16) union {
-        float zs[EST_T][PD + 1];
-        float Us[PD][PD];  // Us[e][j], zero beyond the rank
-    } sm;
-    __shared__ float mus[EST_T];
-    __shared__ float gws[PD];
-    __shared__ int run_end;
+    extern __shared__ __align__(16) unsigned char est_raw[];
+    EstSmem &sm = *reinterpret_cast<EstSmem *>(est_raw);
     const int begin = blockIdx.x * EST_T;
     const int end = min(n, begin + EST_T);
     const int q = begin + threadIdx.x;
     const bool valid = q < end;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ int s_anchor[EST_T];
     if (valid) {
         const int i = perm[q];
-        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+        sm.anchor[threadIdx.x] = anchors ? anchors[i] : i;
     }
     __syncthreads();
     // each warp gathers its 32 patches four at a time (8 loads in flight per lane)
@@ -460,7 +470,7 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int p = min(p0 + u, cnt_p - 1);
-            const int a = s_anchor[p];
+            const int a = sm.anchor[p];
             const int ai = a / W, aj = a % W;
             x0[u] = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
             x1[u] = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
@@ -470,83 +480,81 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
             const int p = p0 + u;
             const float m = warp_sum(x0[u] + x1[u]) * (1.0f / PD);
             if (p < cnt_p) {
-                sm.zs[p][lane] = x0[u] - m;
-                sm.zs[p][lane + 32] = x1[u] - m;
-                if (lane == 0) mus[p] = m;
+                sm.a.zs[p][lane] = x0[u] - m;
+                sm.a.zs[p][lane + 32] = x1[u] - m;
+                if (lane == 0) sm.mus[p] = m;
             }
         }
     }
     __syncthreads();
-    int mi = 0, mk = -1, a = 0;
+    int mk = -1, a = 0;
     float z[PD];
     float mu = 0.0f;
     if (valid) {
-        mi = perm[q];
-        mk = clamp_k(kstar[mi], K);
-        a = s_anchor[threadIdx.x];
-        mu = mus[threadIdx.x];
+        mk = clamp_k(kstar[perm[q]], K);
+        a = sm.anchor[threadIdx.x];
+        mu = sm.mus[threadIdx.x];
 #pragma unroll
-        for (int e = 0; e < PD; ++e) z[e] = sm.zs[threadIdx.x][e];
+        for (int e = 0; e < PD; ++e) z[e] = sm.a.zs[threadIdx.x][e];
     }
     __syncthreads();
     int pos = begin;
     while (pos < end) {
         const int k = clamp_k(kstar[perm[pos]], K);
-        if (threadIdx.x == 0) run_end = end;
+        if (threadIdx.x == 0) sm.run_end = end;
         __syncthreads();
         for (int q2 = pos + threadIdx.x; q2 < end; q2 += EST_T)
-            if (clamp_k(kstar[perm[q2]], K) != k) atomicMin(&run_end, q2);
+            if (clamp_k(kstar[perm[q2]], K) != k) atomicMin(&sm.run_end, q2);
         const int o = roff[k], r = rk_[k];
         for (int idx = threadIdx.x; idx < PD * PD; idx += EST_T) {
             const int e = idx >> 6, j = idx & 63;
-            sm.Us[e][j] = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
+            const float u = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
+            sm.a.u.Us[e][j] = u;
+            sm.a.u.UT[j][e] = u;
         }
-        if (threadIdx.x < PD) gws[threadIdx.x] = (int)threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
+        if (threadIdx.x < PD) sm.gws[threadIdx.x] = (int)threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
         __syncthreads();
-        const int stop = run_end;
+        const int stop = sm.run_end;
         if (valid && mk == k) {
             const float gp = tab.gp[k];
-            float c[PD];
-#pragma unroll
-            for (int j4 = 0; j4 < PD / 4; ++j4) {
+            // c_j = Ubar_j . z, four columns per pass
+#pragma unroll 1
+            for (int j4 = 0; 4 * j4 < r; ++j4) {
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                if (4 * j4 < r) {
 #pragma unroll
-                    for (int e = 0; e < PD; ++e) {
-                        const float4 u = reinterpret_cast<const float4 *>(&sm.Us[e][0])[j4];
-                        a0 = fmaf(u.x, z[e], a0);
-                        a1 = fmaf(u.y, z[e], a1);
-                        a2 = fmaf(u.z, z[e], a2);
-                        a3 = fmaf(u.w, z[e], a3);
-                    }
+                for (int e = 0; e < PD; ++e) {
+                    const float4 u = reinterpret_cast<const float4 *>(&sm.a.u.Us[e][0])[j4];
+                    a0 = fmaf(u.x, z[e], a0);
+                    a1 = fmaf(u.y, z[e], a1);
+                    a2 = fmaf(u.z, z[e], a2);
+                    a3 = fmaf(u.w, z[e], a3);
                 }
-                c[4 * j4 + 0] = gws[4 * j4 + 0] * a0;
-                c[4 * j4 + 1] = gws[4 * j4 + 1] * a1;
-                c[4 * j4 + 2] = gws[4 * j4 + 2] * a2;
-                c[4 * j4 + 3] = gws[4 * j4 + 3] * a3;
+                sm.cs[threadIdx.x][4 * j4 + 0] = sm.gws[4 * j4 + 0] * a0;
+                sm.cs[threadIdx.x][4 * j4 + 1] = sm.gws[4 * j4 + 1] * a1;
+                sm.cs[threadIdx.x][4 * j4 + 2] = sm.gws[4 * j4 + 2] * a2;
+                sm.cs[threadIdx.x][4 * j4 + 3] = sm.gws[4 * j4 + 3] * a3;
+            }
+            // zhat_e = gamma_P z_e + sum_j Ubar_ej chat_j
+            float acc[PD];
+#pragma unroll
+            for (int e = 0; e < PD; ++e) acc[e] = gp * z[e];
+#pragma unroll 1
+            for (int j = 0; j < r; ++j) {
+                const float cj = sm.cs[threadIdx.x][j];
+#pragma unroll
+                for (int e4 = 0; e4 < PD / 4; ++e4) {
+                    const float4 u = reinterpret_cast<const float4 *>(&sm.a.u.UT[j][0])[e4];
+                    acc[4 * e4 + 0] = fmaf(u.x, cj, acc[4 * e4 + 0]);
+                    acc[4 * e4 + 1] = fmaf(u.y, cj, acc[4 * e4 + 1]);
+                    acc[4 * e4 + 2] = fmaf(u.z, cj, acc[4 * e4 + 2]);
+                    acc[4 * e4 + 3] = fmaf(u.w, cj, acc[4 * e4 + 3]);
+                }
             }
             float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)a * PD);
 #pragma unroll
-            for (int e4 = 0; e4 < PD / 4; ++e4) {
-                float v[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int e = 4 * e4 + t;
-                    float acc = gp * z[e];
-#pragma unroll
-                    for (int j4 = 0; j4 < PD / 4; ++j4) {
-                        if (4 * j4 < r) {
-                            const float4 u = reinterpret_cast<const float4 *>(&sm.Us[e][0])[j4];
-                            acc = fmaf(u.x, c[4 * j4 + 0], acc);
-                            acc = fmaf(u.y, c[4 * j4 + 1], acc);
-                            acc = fmaf(u.z, c[4 * j4 + 2], acc);
-                            acc = fmaf(u.w, c[4 * j4 + 3], acc);
-                        }
-                    }
-                    v[t] = acc + mu;
-                }
-                dst[e4] = make_float4(v[0], v[1], v[2], v[3]);
-            }
+            for (int e4 = 0; e4 < PD / 4; ++e4)
+                dst[e4] = make_float4(acc[4 * e4] + mu, acc[4 * e4 + 1] + mu, acc[4 * e4 + 2] + mu,
+                                      acc[4 * e4 + 3] + mu);
         }
         __syncthreads();
         pos = stop;
@@ -568,7 +576,13 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
     EPLL_LAUNCHED(g);
     k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(ws.kstar, n, K, counts, ws.perm);
     EPLL_LAUNCHED(g);
-    k_estimate<<<(n + EST_T - 1) / EST_T, EST_T, 0, st>>>(
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(EstSmem)));
+        attr = true;
+    }
+    k_estimate<<<(n + EST_T - 1) / EST_T, EST_T, sizeof(EstSmem), st>>>(
         xhat, H, W, anchors, n, ws.perm, ws.kstar, K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab,
         ws.zrow);
     EPLL_LAUNCHED(g);
