@@ -45,7 +45,7 @@ static void free_workspace(Workspace &ws)
 {
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.fscore,
-                    ws.perm, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
+                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -66,6 +66,7 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     A(dalloc(&ws.anchors_all, TB_MAX * N)); A(dalloc(&ws.mult_all, TB_MAX * N));
     A(dalloc(&ws.kstar, N)); A(dalloc(&ws.gap, N));
     A(dalloc(&ws.flag, N)); A(dalloc(&ws.flag1, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
+    A(dalloc(&ws.items, 2 + N / 128 + (size_t)g->K));
     const size_t zrows = (N + 127) / 128 * 128;
     A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N));
     A(dalloc(&ws.Z2, 2 * zrows * PD)); A(dalloc(&ws.zz2, N));

@@ -78,6 +78,7 @@ struct Workspace {
     float *fscore = nullptr;                  // [fcap][K] FP32 scores of listed rows
     size_t fcap = 0;
     int *perm = nullptr;                      // [N] list entries grouped by component
+    int4 *items = nullptr;                    // [1 + N/128 + K] estimation work items
     float *zrow = nullptr;                    // [N][64] patch estimates, row per anchor
     uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
     size_t zrows = 0;                         // N rounded up to the 128-row tile

@@ -287,6 +287,7 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
                 df part = {0.0f, 0.0f};
                 for (int j = lane; j < r; j += 32) {
                     df c = {0.0f, 0.0f};
+#pragma unroll 16
                     for (int e = 0; e < PD; ++e) {
                         df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
                         c = df_add(c, df_mul(u, {zh[w][e], zl[w][e]}));
@@ -372,29 +373,49 @@ __global__ void k_bucket_hist(const int *__restrict__ kstar, int n, int K, int *
         if (h[k]) atomicAdd(&counts[k], h[k]);
 }
 
-__global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ counts)
+// Exclusive scan of the per-component counts (in place, they become the
+// scatter cursors) and the work items of the estimation kernel: one item per
+// group of up to EST_T patches of one component, {k, first list position,
+// count}; items[0].w holds the number of items.
+constexpr int EST_T = 128;
+
+__global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ counts,
+                                                      int4 *__restrict__ items)
 {
-    // counts[0..K) -> cursors (exclusive prefix), in place
-    __shared__ int c[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int c[1024], ci[1024];
+    __shared__ int carry, icarry;
+    if (threadIdx.x == 0) carry = icarry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < K; b0 += 1024) {
-        int k = b0 + threadIdx.x;
-        int v = k < K ? counts[k] : 0;
+        const int k = b0 + threadIdx.x;
+        const int v = k < K ? counts[k] : 0;
+        const int nv = (v + EST_T - 1) / EST_T;
         c[threadIdx.x] = v;
+        ci[threadIdx.x] = nv;
         __syncthreads();
         for (int off = 1; off < 1024; off <<= 1) {
-            int u = threadIdx.x >= off ? c[threadIdx.x - off] : 0;
+            const int u = threadIdx.x >= off ? c[threadIdx.x - off] : 0;
+            const int ui = threadIdx.x >= off ? ci[threadIdx.x - off] : 0;
             __syncthreads();
             c[threadIdx.x] += u;
+            ci[threadIdx.x] += ui;
             __syncthreads();
         }
-        if (k < K) counts[k] = carry + c[threadIdx.x] - v;
+        if (k < K) {
+            const int start = carry + c[threadIdx.x] - v;
+            const int item0 = icarry + ci[threadIdx.x] - nv;
+            counts[k] = start;
+            for (int t = 0; t < nv; ++t)
+                items[1 + item0 + t] = make_int4(k, start + t * EST_T, min(EST_T, v - t * EST_T), 0);
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry += c[1023];
+        if (threadIdx.x == 1023) {
+            carry += c[1023];
+            icarry += ci[1023];
+        }
         __syncthreads();
     }
+    if (threadIdx.x == 0) items[0] = make_int4(0, 0, 0, icarry);
 }
 
 __global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, int *__restrict__ cursor,
@@ -416,148 +437,141 @@ __global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, in
 
 // ============================================================================
 // Patch estimation (Eqs. 15-16): chat_j = (gamma_j - gamma_P) c_j,
-// zhat = Ubar chat + gamma_P z + mean.  A block takes 128 consecutive entries
-// of the component-grouped list, one patch per thread (the DC-free patch in
-// registers).  For every run of equal components in the block's range
-// Ubar_k and its transpose are staged in shared memory and read back as
-// float4 broadcasts, four FMAs per load, in the order of the definitions
-// (c_j sums over the pixels in order, zhat_e starts from gamma_P z_e and adds
-// the coefficients in order).  Loops over basis columns stay rolled so the
-// kernel fits the instruction cache; the coefficients live in a padded
-// per-thread row of shared memory.  The estimate is written as a 64-float
-// row at the patch's anchor.
+// zhat = Ubar chat + gamma_P z + mean.  A block takes one work item: up to
+// 128 patches that selected the same component k.  With the patches Z
+// (128 x 64) and Ubar_k in shared memory the two products are register-tiled
+// FP32 GEMMs, C = Z Ubar_k and Zhat = C' Ubar_k^T + gamma_P Z: each thread owns
+// an 8 x 8 block of outputs and does 64 FMAs per 4 vector loads.  The sums
+// run in the order of the definitions (c_j over the pixels in order, zhat_e
+// from gamma_P z_e over the coefficients in order).  The estimate is written
+// as a 64-float row at each patch's anchor.
 // ============================================================================
-constexpr int EST_T = 128;
-constexpr int EST_LD = PD + 1;  // padded row: thread t's row hits distinct banks
+constexpr int EST_LDZ = EST_T + 4;  // padded patch-major rows
 
 struct EstSmem {
-    union {
-        float zs[EST_T][EST_LD];  // gathered DC-free patches (first phase only)
-        struct {
-            float Us[PD][PD];  // Us[e][j], zero beyond the rank
-            float UT[PD][PD];  // UT[j][e]
-        } u;
-    } a;
-    float cs[EST_T][EST_LD];  // shrunk coefficients of each thread's patch
+    float Zt[PD][EST_LDZ];  // Zt[e][p]: DC-free patches, transposed
+    float Ct[PD][EST_LDZ];  // Ct[j][p]: shrunk coefficients
+    float Us[PD][PD];       // Us[e][j], zero beyond the rank
+    float Ut[PD][PD];       // Ut[j][e]
     float mus[EST_T];
     float gws[PD];
     int anchor[EST_T];
-    int run_end;
 };
 
-__global__ void __launch_bounds__(EST_T, 3)
-k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
-           const int *__restrict__ perm, const int *__restrict__ kstar, int K, int Rtot,
+__global__ void __launch_bounds__(EST_T)
+k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+           const int *__restrict__ perm, const int4 *__restrict__ items, int Rtot,
            const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
            Tables tab, float *__restrict__ zrow)
 {
     extern __shared__ __align__(16) unsigned char est_raw[];
     EstSmem &sm = *reinterpret_cast<EstSmem *>(est_raw);
-    const int begin = blockIdx.x * EST_T;
-    const int end = min(n, begin + EST_T);
-    const int q = begin + threadIdx.x;
-    const bool valid = q < end;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (valid) {
-        const int i = perm[q];
-        sm.anchor[threadIdx.x] = anchors ? anchors[i] : i;
+    if ((int)blockIdx.x >= items[0].w) return;
+    const int4 it = items[1 + blockIdx.x];
+    const int k = it.x, first = it.y, cnt_p = it.z;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int o = roff[k], r = rk_[k];
+    if (tid < cnt_p) {
+        const int i = perm[first + tid];
+        sm.anchor[tid] = anchors ? anchors[i] : i;
     }
+    for (int idx = tid; idx < PD * PD; idx += EST_T) {
+        const int e = idx >> 6, j = idx & 63;
+        const float u = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
+        sm.Us[e][j] = u;
+        sm.Ut[j][e] = u;
+    }
+    if (tid < PD) sm.gws[tid] = tid < r ? tab.gw[o + tid] : 0.0f;
     __syncthreads();
-    // each warp gathers its 32 patches four at a time (8 loads in flight per lane)
-    const int cnt_p = end - begin;
-    for (int p0 = w * 32; p0 < min(cnt_p, w * 32 + 32); p0 += 4) {
+    // gather: each warp takes 32 patches, four at a time (8 loads in flight per lane)
+    for (int p0 = w * 32; p0 < w * 32 + 32; p0 += 4) {
         float x0[4], x1[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int p = min(p0 + u, cnt_p - 1);
-            const int a = sm.anchor[p];
-            const int ai = a / W, aj = a % W;
-            x0[u] = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
-            x1[u] = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+            x0[u] = x1[u] = 0.0f;
+            if (p0 + u < cnt_p) {
+                const int a = sm.anchor[p0 + u];
+                const int ai = a / W, aj = a % W;
+                x0[u] = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
+                x1[u] = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int p = p0 + u;
             const float m = warp_sum(x0[u] + x1[u]) * (1.0f / PD);
+            sm.Zt[lane][p] = p < cnt_p ? x0[u] - m : 0.0f;
+            sm.Zt[lane + 32][p] = p < cnt_p ? x1[u] - m : 0.0f;
+            if (lane == 0) sm.mus[p] = m;
+        }
+    }
+    __syncthreads();
+    const int pg = tid >> 3;  // patches 8 pg .. 8 pg + 7
+    const int cg = tid & 7;   // columns (then pixels) 8 cg .. 8 cg + 7
+    // ---- C = Z Ubar_k (only column groups below the rank)
+    if (8 * cg < r) {
+        float acc[8][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+        for (int e = 0; e < PD; ++e) {
+            const float4 z0 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg]);
+            const float4 z1 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg + 4]);
+            const float4 u0 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg]);
+            const float4 u1 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg + 4]);
+            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(zv[a], uv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float gw = sm.gws[8 * cg + b];
+            *reinterpret_cast<float4 *>(&sm.Ct[8 * cg + b][8 * pg]) =
+                make_float4(gw * acc[0][b], gw * acc[1][b], gw * acc[2][b], gw * acc[3][b]);
+            *reinterpret_cast<float4 *>(&sm.Ct[8 * cg + b][8 * pg + 4]) =
+                make_float4(gw * acc[4][b], gw * acc[5][b], gw * acc[6][b], gw * acc[7][b]);
+        }
+    }
+    __syncthreads();
+    // ---- Zhat = gamma_P Z + C' Ubar_k^T, plus the mean
+    {
+        const float gp = tab.gp[k];
+        float acc[8][8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float4 z0 = *reinterpret_cast<const float4 *>(&sm.Zt[8 * cg + b][8 * pg]);
+            const float4 z1 = *reinterpret_cast<const float4 *>(&sm.Zt[8 * cg + b][8 * pg + 4]);
+            acc[0][b] = gp * z0.x; acc[1][b] = gp * z0.y; acc[2][b] = gp * z0.z; acc[3][b] = gp * z0.w;
+            acc[4][b] = gp * z1.x; acc[5][b] = gp * z1.y; acc[6][b] = gp * z1.z; acc[7][b] = gp * z1.w;
+        }
+#pragma unroll 4
+        for (int j = 0; j < r; ++j) {
+            const float4 c0 = *reinterpret_cast<const float4 *>(&sm.Ct[j][8 * pg]);
+            const float4 c1 = *reinterpret_cast<const float4 *>(&sm.Ct[j][8 * pg + 4]);
+            const float4 u0 = *reinterpret_cast<const float4 *>(&sm.Ut[j][8 * cg]);
+            const float4 u1 = *reinterpret_cast<const float4 *>(&sm.Ut[j][8 * cg + 4]);
+            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(uv[b], cv[a], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int p = 8 * pg + a;
             if (p < cnt_p) {
-                sm.a.zs[p][lane] = x0[u] - m;
-                sm.a.zs[p][lane + 32] = x1[u] - m;
-                if (lane == 0) sm.mus[p] = m;
+                const float mu = sm.mus[p];
+                float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)sm.anchor[p] * PD + 8 * cg);
+                dst[0] = make_float4(acc[a][0] + mu, acc[a][1] + mu, acc[a][2] + mu, acc[a][3] + mu);
+                dst[1] = make_float4(acc[a][4] + mu, acc[a][5] + mu, acc[a][6] + mu, acc[a][7] + mu);
             }
         }
-    }
-    __syncthreads();
-    int mk = -1, a = 0;
-    float z[PD];
-    float mu = 0.0f;
-    if (valid) {
-        mk = clamp_k(kstar[perm[q]], K);
-        a = sm.anchor[threadIdx.x];
-        mu = sm.mus[threadIdx.x];
-#pragma unroll
-        for (int e = 0; e < PD; ++e) z[e] = sm.a.zs[threadIdx.x][e];
-    }
-    __syncthreads();
-    int pos = begin;
-    while (pos < end) {
-        const int k = clamp_k(kstar[perm[pos]], K);
-        if (threadIdx.x == 0) sm.run_end = end;
-        __syncthreads();
-        for (int q2 = pos + threadIdx.x; q2 < end; q2 += EST_T)
-            if (clamp_k(kstar[perm[q2]], K) != k) atomicMin(&sm.run_end, q2);
-        const int o = roff[k], r = rk_[k];
-        for (int idx = threadIdx.x; idx < PD * PD; idx += EST_T) {
-            const int e = idx >> 6, j = idx & 63;
-            const float u = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
-            sm.a.u.Us[e][j] = u;
-            sm.a.u.UT[j][e] = u;
-        }
-        if (threadIdx.x < PD) sm.gws[threadIdx.x] = (int)threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
-        __syncthreads();
-        const int stop = sm.run_end;
-        if (valid && mk == k) {
-            const float gp = tab.gp[k];
-            // c_j = Ubar_j . z, four columns per pass
-#pragma unroll 1
-            for (int j4 = 0; 4 * j4 < r; ++j4) {
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-                for (int e = 0; e < PD; ++e) {
-                    const float4 u = reinterpret_cast<const float4 *>(&sm.a.u.Us[e][0])[j4];
-                    a0 = fmaf(u.x, z[e], a0);
-                    a1 = fmaf(u.y, z[e], a1);
-                    a2 = fmaf(u.z, z[e], a2);
-                    a3 = fmaf(u.w, z[e], a3);
-                }
-                sm.cs[threadIdx.x][4 * j4 + 0] = sm.gws[4 * j4 + 0] * a0;
-                sm.cs[threadIdx.x][4 * j4 + 1] = sm.gws[4 * j4 + 1] * a1;
-                sm.cs[threadIdx.x][4 * j4 + 2] = sm.gws[4 * j4 + 2] * a2;
-                sm.cs[threadIdx.x][4 * j4 + 3] = sm.gws[4 * j4 + 3] * a3;
-            }
-            // zhat_e = gamma_P z_e + sum_j Ubar_ej chat_j
-            float acc[PD];
-#pragma unroll
-            for (int e = 0; e < PD; ++e) acc[e] = gp * z[e];
-#pragma unroll 1
-            for (int j = 0; j < r; ++j) {
-                const float cj = sm.cs[threadIdx.x][j];
-#pragma unroll
-                for (int e4 = 0; e4 < PD / 4; ++e4) {
-                    const float4 u = reinterpret_cast<const float4 *>(&sm.a.u.UT[j][0])[e4];
-                    acc[4 * e4 + 0] = fmaf(u.x, cj, acc[4 * e4 + 0]);
-                    acc[4 * e4 + 1] = fmaf(u.y, cj, acc[4 * e4 + 1]);
-                    acc[4 * e4 + 2] = fmaf(u.z, cj, acc[4 * e4 + 2]);
-                    acc[4 * e4 + 3] = fmaf(u.w, cj, acc[4 * e4 + 3]);
-                }
-            }
-            float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)a * PD);
-#pragma unroll
-            for (int e4 = 0; e4 < PD / 4; ++e4)
-                dst[e4] = make_float4(acc[4 * e4] + mu, acc[4 * e4 + 1] + mu, acc[4 * e4 + 2] + mu,
-                                      acc[4 * e4 + 3] + mu);
-        }
-        __syncthreads();
-        pos = stop;
     }
 }
 
@@ -572,7 +586,7 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
     if (hb > 152 * 2) hb = 152 * 2;
     k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(ws.kstar, n, K, counts);
     EPLL_LAUNCHED(g);
-    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts);
+    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, ws.items);
     EPLL_LAUNCHED(g);
     k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(ws.kstar, n, K, counts, ws.perm);
     EPLL_LAUNCHED(g);
@@ -582,9 +596,9 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
                                      (int)sizeof(EstSmem)));
         attr = true;
     }
-    k_estimate<<<(n + EST_T - 1) / EST_T, EST_T, sizeof(EstSmem), st>>>(
-        xhat, H, W, anchors, n, ws.perm, ws.kstar, K, g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab,
-        ws.zrow);
+    const int max_items = (n + EST_T - 1) / EST_T + K;
+    k_estimate<<<max_items, EST_T, sizeof(EstSmem), st>>>(xhat, H, W, anchors, ws.perm, ws.items, g->Rtot,
+                                                          g->d_roff, g->d_r, g->d_B, g->tab, ws.zrow);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
