@@ -175,6 +175,26 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
 epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *anchors,
                         int *n_out, void *stream);
 
+/*
+ * Patch sampling that allocates nothing on the device (the paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory while they run, e.g. between a pool allocator's fixed reservations or
+ * in a loop where cudaMalloc's implicit synchronisation would stall other
+ * streams).  Same arguments and output as epll_sample, except that it does not
+ * synchronise: it enqueues the sampler on `stream` and returns; *n_out is set
+ * on return (the count depends only on H, W and the options).
+ * Scratch: a file-scope device array of about 4.2 MB, present on every device
+ * that loads the library until the process exits; it serves images of up to
+ * 2^20 pixels (larger ones return EPLL_EINVAL).  Every call shares the array
+ * and the work it enqueues clears what must start at zero, so calls whose
+ * device work overlaps (different streams, no ordering between them) race.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  Errors: EPLL_EINVAL, EPLL_ECUDA.
+ */
+epll_status epll_sample_noalloc(int H, int W, const epll_options *opt, int t, int *anchors,
+                                int *n_out, void *stream);
+
 /* Counters of the last epll_restore / epll_patch_step on this handle (host
  * out; synchronises the device): patch evaluations, near-tie rescored
  * patches, and kernel launches issued. */

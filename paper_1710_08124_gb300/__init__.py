@@ -85,6 +85,7 @@ def lib():
         L.epll_patch_step.argtypes = [vp, vp, i, i, d, C.POINTER(_Options), i, vp, vp, vp, vp,
                                       vp, C.POINTER(C.c_int), vp]
         L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
+        L.epll_sample_noalloc.argtypes = L.epll_sample.argtypes
         L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                          C.POINTER(C.c_longlong)]
         L.epll_profile_enable.argtypes = [vp, i]
@@ -237,6 +238,19 @@ def sample(H: int, W: int, options: Options | None = None, t: int = 0, device="c
     n = C.c_int(0)
     opt = (options or Options())._c()
     _check(lib().epll_sample(H, W, C.byref(opt), int(t), _dptr(an), C.byref(n), _stream(stream)))
+    return an[:n.value]
+
+
+def sample_noalloc(H: int, W: int, options: Options | None = None, t: int = 0, out=None, stream=None):
+    """Patch sampling that allocates no device memory inside the library
+    (``epll_sample_noalloc``); ``out`` is a caller-provided int32 CUDA tensor of
+    at least H*W entries.  Returns the filled prefix of ``out``."""
+    import torch
+    an = torch.empty(H * W, dtype=torch.int32, device="cuda") if out is None else out
+    n = C.c_int(0)
+    opt = (options or Options())._c()
+    _check(lib().epll_sample_noalloc(H, W, C.byref(opt), int(t), _dptr(an, torch.int32), C.byref(n),
+                                     _stream(stream)))
     return an[:n.value]
 
 
