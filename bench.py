@@ -54,7 +54,7 @@ DTYPE = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "bf16x3": "bf16"}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(PREC_NAMES), default="bf16x3")
