@@ -130,6 +130,56 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_W8(0), EPLL_W8(8), EPLL_W8(16), EPLL_W8(24)::"memory");
 }
 
+// 64 / 128 consecutive accumulator columns in one instruction (one round trip).
+#define EPLL_OPS64(M) M(0), M(8), M(16), M(24), M(32), M(40), M(48), M(56)
+#define EPLL_OPS128(M) EPLL_OPS64(M), M(64), M(72), M(80), M(88), M(96), M(104), M(112), M(120)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : EPLL_OPS64(EPLL_R8)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait64(uint32_t (&r)[64])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_OPS64(EPLL_W8)::"memory");
+}
+__device__ __forceinline__ void tmem_ld128(uint32_t taddr, uint32_t (&r)[128])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x128.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,"
+        "%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,"
+        "%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,"
+        "%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,"
+        "%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, [%128];"
+        : EPLL_OPS128(EPLL_R8)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait128(uint32_t (&r)[128])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_OPS128(EPLL_W8)::"memory");
+}
+template <int NC>
+__device__ __forceinline__ void tmem_ld_all(uint32_t taddr, uint32_t (&r)[NC])
+{
+    if constexpr (NC == 64) {
+        tmem_ld64(taddr, r);
+        tmem_wait64(r);
+    } else {
+        static_assert(NC == 128, "64 or 128 columns");
+        tmem_ld128(taddr, r);
+        tmem_wait128(r);
+    }
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
 // with the 128-byte swizzle: rows of 64 16-bit elements (128 B), 8-row
 // groups 1024 B apart (stride byte offset), leading byte offset unused for
@@ -412,57 +462,45 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 const int ncol = RR ? C::HALF : (h == 0 ? BN : 0);
                 const int col0 = (tile0 + it) * BN + cbeg;
                 const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbeg);
-                uint32_t r[32];
-                for (int c = 0; c < ncol / 32; ++c) {
-                    tmem_ld32(taddr + (uint32_t)(32 * c), r);
-                    tmem_wait(r);
-                    const int cb = col0 + 32 * c;
-                    if constexpr (RR == 64) {
+                if constexpr (RR > 0) {
+                    // the whole half-tile in one TMEM round trip; the buffer is
+                    // handed back to the MMA warp before the arithmetic
+                    uint32_t r[C::HALF];
+                    tmem_ld_all<C::HALF>(taddr, r);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+#pragma unroll
+                    for (int p = 0; p < C::HALF / RR; ++p) {
                         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            const float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-                            const float v2 = __uint_as_float(r[j + 2]), v3 = __uint_as_float(r[j + 3]);
+                        for (int j = 0; j < RR; j += 4) {
+                            const float v0 = __uint_as_float(r[p * RR + j]), v1 = __uint_as_float(r[p * RR + j + 1]);
+                            const float v2 = __uint_as_float(r[p * RR + j + 2]), v3 = __uint_as_float(r[p * RR + j + 3]);
                             a0 = fmaf(v0, v0, a0);
                             a1 = fmaf(v1, v1, a1);
                             a2 = fmaf(v2, v2, a2);
                             a3 = fmaf(v3, v3, a3);
                         }
-                        acc += (a0 + a1) + (a2 + a3);
-                        if (c & 1) {
-                            const int k = cb >> 6;
-                            if (k < K) {
-                                const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr + acc;
-                                if (DUMP) {
-                                    if (grow < n) scores[(size_t)grow * K + k] = sc;
-                                } else {
-                                    top2(sc, k, s1, s2, k1);
-                                }
-                            }
-                            acc = 0.0f;
-                        }
-                    } else if constexpr (RR > 0) {
-#pragma unroll
-                        for (int p = 0; p < 32 / RR; ++p) {
-                            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                            for (int j = 0; j < RR; j += 2) {
-                                const float v0 = __uint_as_float(r[p * RR + j]);
-                                const float v1 = __uint_as_float(r[p * RR + j + 1]);
-                                a0 = fmaf(v0, v0, a0);
-                                a1 = fmaf(v1, v1, a1);
-                            }
-                            const int k = cb / RR + p;
-                            if (k < K) {
-                                const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr - (a0 + a1);
-                                if (DUMP) {
-                                    if (grow < n) scores[(size_t)grow * K + k] = sc;
-                                } else {
-                                    top2(sc, k, s1, s2, k1);
-                                }
+                        const float sq = (a0 + a1) + (a2 + a3);
+                        const int k = col0 / RR + p;
+                        if (k < K) {
+                            const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr +
+                                             (RR == 64 ? sq : -sq);
+                            if (DUMP) {
+                                if (grow < n) scores[(size_t)grow * K + k] = sc;
+                            } else {
+                                top2(sc, k, s1, s2, k1);
                             }
                         }
-                    } else {
+                    }
+                } else {
+                uint32_t r[32];
+                for (int c = 0; c < ncol / 32; ++c) {
+                    tmem_ld32(taddr + (uint32_t)(32 * c), r);
+                    tmem_wait(r);
+                    const int cb = col0 + 32 * c;
+                    {
                         // ragged ranks: column -> component map
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
@@ -484,6 +522,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+                }
             }
             if (RR == 0 && curk >= 0) {
                 // the last component ends with the last column
