@@ -54,9 +54,13 @@ enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
  * BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation;
  * FP16   tcgen05 tensor cores, FP16 operands, FP32 accumulation;
  * BF16X3 tcgen05 tensor cores, operands split into hi + lo BF16 parts
- *        (three products: hi*hi + lo*hi + hi*lo), FP32 accumulation.
- * Every form rescores its near-ties in compensated FP32 (see tie_gap). */
-enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3 };
+ *        (three products: hi*hi + lo*hi + hi*lo), FP32 accumulation;
+ * FP8    tcgen05 tensor cores (kind::f8f6f4), E4M3 operands with one scale per
+ *        component and one per patch, FP32 accumulation.
+ * The one-term forms (BF16, FP16, FP8) hand the patches they cannot decide to
+ * a BF16X3 pass; every form rescores its remaining near-ties in compensated
+ * FP32 (see tie_gap). */
+enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3, EPLL_FP8 = 4 };
 
 typedef struct epll_gmm epll_gmm; /* opaque, library-owned */
 
@@ -71,11 +75,12 @@ typedef struct {
 } epll_degradation;
 
 typedef struct {
-    int precision;      /* EPLL_FP32, EPLL_BF16, EPLL_FP16 or EPLL_BF16X3 */
+    int precision;      /* EPLL_FP32, EPLL_BF16, EPLL_FP16, EPLL_BF16X3 or EPLL_FP8 */
     float tie_gap;      /* absolute part of the near-tie threshold: a patch whose top-2
                            score gap is below tie_gap + rho * |z|^2 * max_kj 1/nu_kj is
                            rescored in compensated FP32 (rho is the relative error bound of
-                           the precision: 1e-5 FP32, 1.5e-3 FP16, 1e-2 BF16, 4e-5 BF16X3);
+                           the precision: 1e-5 FP32, 1.5e-3 FP16, 1e-2 BF16, 4e-5 BF16X3,
+                           1e-1 FP8);
                            < 0 selects the default 1e-3 */
     int subset;         /* EPLL_SUBSET_* */
     double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */

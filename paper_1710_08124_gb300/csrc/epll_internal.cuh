@@ -38,6 +38,8 @@ struct Tables {
     uint16_t *B1 = nullptr;                      // [Rtot][64]: 16-bit Ubar * sqrt|q| (BF16 or FP16), K-major
     uint16_t *Bs = nullptr;                      // [Rtot][64]: BF16 hi part of Ubar * sqrt|q| (split form)
     uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
+    uint8_t *B8 = nullptr;                       // [Rtot][64]: E4M3 Ubar * sqrt|q| / s_k
+    float *k8s2 = nullptr;                       // [K]: s_k^2 of the E4M3 basis
 };
 
 // Iterations prepared together (tables of every beta, patch subsets).
@@ -54,6 +56,7 @@ __host__ __device__ inline Tables slot_tables(Tables t, int slot, int K, int Rp,
     t.q_hi += (size_t)slot * Rp; t.q_lo += (size_t)slot * Rp; t.gw += (size_t)slot * Rp;
     t.tmax += slot;
     t.B1 += (size_t)slot * Rtot * 64; t.Bs += (size_t)slot * Rtot * 64; t.Bs_lo += (size_t)slot * Rtot * 64;
+    t.B8 += (size_t)slot * Rtot * 64; t.k8s2 += (size_t)slot * K;
     return t;
 }
 
@@ -75,6 +78,7 @@ struct Workspace {
     int *flag1 = nullptr;                     // [N] near-tie list of a one-term tensor pass
     uint16_t *Z2 = nullptr;                   // [2][zrows][64] split operands of listed rows
     float *zz2 = nullptr;                     // [N] |z|^2 of listed rows
+    float *zsc2 = nullptr;                    // [N] squared per-row scale of 8-bit operands
     float *fscore = nullptr;                  // [fcap][K] FP32 scores of listed rows
     size_t fcap = 0;
     int *perm = nullptr;                      // [N] list entries grouped by component

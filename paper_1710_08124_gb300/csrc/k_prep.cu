@@ -3,6 +3,7 @@
 #include "epll_internal.cuh"
 
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 namespace epll {
 
@@ -93,6 +94,20 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     }
     if (!fmt) return;
     __syncthreads();
+    float s8 = 1.0f;
+    if (fmt & 8) {
+        // per-component scale of the E4M3 basis: the largest |value| maps to 448
+        float m = 0.0f;
+        for (int jj = 0; jj < rk; ++jj) m = fmaxf(m, fabsf(B[(size_t)j * Rtot + o + jj] * sq[jj]));
+        red[j] = m;
+        __syncthreads();
+        for (int st = 32; st > 0; st >>= 1) {
+            if (j < st) red[j] = fmax(red[j], red[j + st]);
+            __syncthreads();
+        }
+        s8 = red[0] > 0.0 ? (float)red[0] / 448.0f : 1.0f;
+        if (j == 0) tab.k8s2[k] = s8 * s8;
+    }
     // scaled basis, K-major: B[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
     // split form stores the BF16 value and the BF16 remainder.
     for (int jj = 0; jj < rp; ++jj) {
@@ -105,6 +120,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
             tab.Bs[dst] = __bfloat16_as_ushort(h);
             tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
         }
+        if (fmt & 8) tab.B8[dst] = (uint8_t)__nv_cvt_float_to_fp8(v / s8, __NV_SATFINITE, __NV_E4M3);
     }
 }
 

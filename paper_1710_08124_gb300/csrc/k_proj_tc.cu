@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cfloat>
 #include <mutex>
@@ -194,10 +195,32 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr)
     d |= (uint64_t)2 << 61;
     return d;
 }
+// Same for 8-bit operands: rows of 64 bytes with the 64-byte swizzle, 8-row
+// groups 512 B apart, layout type 4 = SWIZZLE_64B.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (D format
 // 1 at bit 4), A/B format (0 = F16, 1 = BF16) at bits 7 and 10, both
-// operands K-major, N/8 at bit 17, M/16 at bit 24.
+// operands K-major, N/8 at bit 17, M/16 at bit 24.  For kind::f8f6f4 the same
+// fields hold the 8-bit formats (0 = E4M3).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int fmt)
 {
     return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -214,6 +237,16 @@ __device__ __forceinline__ float warp_sum_tc(float v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_max_tc(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ uint8_t to_e4m3(float v)
+{
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
 __device__ __forceinline__ uint16_t to16(float v, int fmt)
 {
     return fmt == 2 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -225,10 +258,13 @@ __device__ __forceinline__ float from16(uint16_t v, int fmt)
 
 // Row i of the operand is sampled patch i, or patch rowmap[i] when a row map
 // (a device list with device count *n_dev) is given.
+// fmt 3: 8-bit E4M3 operands scaled per row (max |z| -> 448), the square of
+// the scale in zsc2; Zhi is then read as bytes.
 __global__ void __launch_bounds__(128)
 k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
              const int *__restrict__ rowmap, const int *__restrict__ n_dev, int fmt, int split,
-             uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz)
+             uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz,
+             float *__restrict__ zsc2)
 {
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (n_dev) n = *n_dev;
@@ -249,6 +285,18 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
         z1 = x1 - mu;
         q = warp_sum_tc(z0 * z0 + z1 * z1);
     }
+    if (fmt == 3) {
+        const float m = warp_max_tc(fmaxf(fabsf(z0), fabsf(z1)));
+        const float sc = m > 0.0f ? m / 448.0f : 1.0f;
+        uint8_t *Z8 = reinterpret_cast<uint8_t *>(Zhi);
+        Z8[(size_t)i * PD + lane] = to_e4m3(z0 / sc);
+        Z8[(size_t)i * PD + lane + 32] = to_e4m3(z1 / sc);
+        if (lane == 0 && i < n) {
+            zz[i] = q;
+            zsc2[i] = sc * sc;
+        }
+        return;
+    }
     const uint16_t h0 = to16(z0, fmt), h1 = to16(z1, fmt);
     Zhi[(size_t)i * PD + lane] = h0;
     Zhi[(size_t)i * PD + lane + 32] = h1;
@@ -266,9 +314,11 @@ constexpr int TC_SMEM_BUDGET = 200 * 1024;
 
 template <int BN, int NT>
 struct TcCfg {
-    static constexpr int A_TILE = TC_M * 128;                  // 16 KB
+    // NT: 1 one 16-bit product, 3 split BF16 (three products), 8 one E4M3 product
+    static constexpr int ROWB = NT == 8 ? 64 : 128;            // bytes per 64-element row
+    static constexpr int A_TILE = TC_M * ROWB;
     static constexpr int A_BYTES = A_TILE * (NT == 3 ? 2 : 1); // one A buffer (hi [+ lo])
-    static constexpr int B_TILE = BN * 128;
+    static constexpr int B_TILE = BN * ROWB;
     static constexpr int B_STAGE = B_TILE * (NT == 3 ? 2 : 1);
     static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - 2 * A_BYTES) / B_STAGE;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
@@ -314,7 +364,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk, Tables tab,
           float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
           int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err,
-          float *__restrict__ scores)
+          float *__restrict__ scores, const float *__restrict__ zsc2)
 {
     using C = TcCfg<BN, NT>;
     static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
@@ -418,12 +468,16 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     const uint32_t d = tbase + (uint32_t)(b * BN);
                     const uint32_t bHi = smem_u32(sB + s * C::B_STAGE), bLo = bHi + C::B_TILE;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {  // reduction depth 64 = 4 x 16
+                    for (int k = 0; k < C::ROWB / 32; ++k) {  // reduction depth 64: 32-byte K steps
                         const uint32_t off = (uint32_t)(k * 32);
-                        mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
-                        if (NT == 3) {
-                            mma_f16(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
-                            mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                        if constexpr (NT == 8) {
+                            mma_f8(d, sdesc_sw64(aHi + off), sdesc_sw64(bHi + off), idesc, k > 0 ? 1u : 0u);
+                        } else {
+                            mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
+                            if (NT == 3) {
+                                mma_f16(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
+                                mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                            }
                         }
                     }
                     mma_commit(smem_u32(&ctl->b_empty[s]));
@@ -445,6 +499,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const int m0 = ((int)blockIdx.x + mt * (int)gridDim.x) * TC_M;
             const int grow = m0 + row;
             const float zzr = grow < n ? zz[grow] : 0.0f;
+            const float rs2 = (NT == 8 && grow < n) ? zsc2[grow] : 1.0f;  // 8-bit: row scale squared
             float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
             int k1 = 0, curk = -1;
             for (int it = 0; it < ntiles; ++it) {
@@ -482,8 +537,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                             a2 = fmaf(v2, v2, a2);
                             a3 = fmaf(v3, v3, a3);
                         }
-                        const float sq = (a0 + a1) + (a2 + a3);
+                        float sq = (a0 + a1) + (a2 + a3);
                         const int k = col0 / RR + p;
+                        if (NT == 8 && k < K) sq *= rs2 * __ldg(&tab.k8s2[k]);
                         if (k < K) {
                             const float sc = __ldg(&tab.cst_hi[k]) + __ldg(&tab.t_hi[k]) * zzr +
                                              (RR == 64 ? sq : -sq);
@@ -507,8 +563,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                             const int k = __ldg(&colk[cb + j]);
                             if (k != curk) {
                                 if (curk >= 0) {
+                                    const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                                     const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
-                                                     __ldg(&tab.sgn[curk]) * acc;
+                                                     __ldg(&tab.sgn[curk]) * a8;
                                     top2(sc, curk, s1, s2, k1);
                                 }
                                 curk = k;
@@ -526,8 +583,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
             if (RR == 0 && curk >= 0) {
                 // the last component ends with the last column
+                const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                 const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
-                                 __ldg(&tab.sgn[curk]) * acc;
+                                 __ldg(&tab.sgn[curk]) * a8;
                 top2(sc, curk, s1, s2, k1);
             }
             if (!DUMP) {
@@ -585,8 +643,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// Row-major [rows][64] 16-bit matrix, box of box_rows rows x 64, 128-byte swizzle.
-static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_rows)
+// Row-major [rows][64] 16-bit matrix (8-bit when eb = 1), box of box_rows rows x
+// 64 elements, 128-byte swizzle (64-byte for 8-bit rows).
+static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_rows, int eb = 2)
 {
     auto fn = encode_fn();
     if (!fn) {
@@ -594,11 +653,12 @@ static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_
         return EPLL_ECUDA;
     }
     cuuint64_t dims[2] = {(cuuint64_t)PD, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)PD * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)PD * eb};
     cuuint32_t box[2] = {(cuuint32_t)PD, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    CUresult r = fn(m, eb == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    eb == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -612,7 +672,7 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
                              const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                              const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
                              float tau_rel, int *flag, int *nflag, cudaStream_t st,
-                             float *scores = nullptr, int slices = 1)
+                             float *scores = nullptr, int slices = 1, const float *zsc2 = nullptr)
 {
     using Cfg = TcCfg<BN, NT>;
     auto kern = k_proj_tc<BN, NT, RR, DUMP>;
@@ -637,7 +697,7 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     if (!n_dev) prof_begin(g, st);
     kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
                                              g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
-                                             nflag, cnt(g, CNT_ERR), scores);
+                                             nflag, cnt(g, CNT_ERR), scores, zsc2);
     if (!n_dev) prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
@@ -647,9 +707,10 @@ template <int BN, int NT>
 static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                                const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                                const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
-                               float tau_rel, int *flag, int *nflag, cudaStream_t st)
+                               float tau_rel, int *flag, int *nflag, cudaStream_t st,
+                               const float *zsc2 = nullptr)
 {
-#define EPLL_TC_ARGS g, a, alo, b, blo, n, rowmap, n_dev, zz, idesc, tau_abs, tau_rel, flag, nflag, st
+#define EPLL_TC_ARGS g, a, alo, b, blo, n, rowmap, n_dev, zz, idesc, tau_abs, tau_rel, flag, nflag, st, nullptr, 1, zsc2
     switch (g->uniform_rank) {
     case 64: return launch_tc<BN, NT, 64>(EPLL_TC_ARGS);
     case 16: return launch_tc<BN, NT, 16>(EPLL_TC_ARGS);
@@ -675,7 +736,8 @@ epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, cons
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
     int *nf = cnt(g, CNT_NFLAG);
-    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, ws.flag, nf, 1, 1, Z2hi, Z2lo, ws.zz2);
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, ws.flag, nf, 1, 1, Z2hi, Z2lo, ws.zz2,
+                                                 nullptr);
     EPLL_LAUNCHED(g);
     CUtensorMap a2, a2lo, bs, bslo;
     epll_status s;
@@ -686,7 +748,7 @@ epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, cons
     const int ntiles = g->Rtot / 128;
     const int slices = ntiles < 32 ? ntiles : 32;
     const uint32_t idesc = idesc_f16(TC_M, 128, 1);
-#define EPLL_DUMP_ARGS g, a2, a2lo, bs, bslo, n, ws.flag, nf, ws.zz2, idesc, 0.0f, 0.0f, nullptr, nullptr, st, ws.fscore, slices
+#define EPLL_DUMP_ARGS g, a2, a2lo, bs, bslo, n, ws.flag, nf, ws.zz2, idesc, 0.0f, 0.0f, nullptr, nullptr, st, ws.fscore, slices, nullptr
     switch (RR) {
     case 64: return launch_tc<128, 3, 64, true>(EPLL_DUMP_ARGS);
     case 16: return launch_tc<128, 3, 16, true>(EPLL_DUMP_ARGS);
@@ -705,13 +767,14 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
 {
     Workspace &ws = g->ws;
     const bool split_first = precision == EPLL_BF16X3;
-    const int fmt = precision == EPLL_FP16 ? 2 : 1;
+    const bool fp8 = precision == EPLL_FP8;
+    const int fmt = precision == EPLL_FP16 ? 2 : (fp8 ? 3 : 1);
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Zhi = ws.Zb, *Zlo = ws.Zb + ws.zrows * PD;
     epll_status s;
     // ---- first pass over every sampled patch
     k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, fmt,
-                                                 split_first ? 1 : 0, Zhi, Zlo, ws.zz);
+                                                 split_first ? 1 : 0, Zhi, Zlo, ws.zz, ws.zsc2);
     EPLL_LAUNCHED(g);
     int *flag1 = split_first ? ws.flag : ws.flag1;
     int *nflag1 = cnt(g, split_first ? CNT_NFLAG : CNT_NFLAG1);
@@ -725,16 +788,26 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
         return dispatch_rr<128, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 1),
                                    tau_abs, tau_rel, flag1, nflag1, st);
     }
-    if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
-    // one-term pass: no lo operands (the lo map arguments are unused)
-    if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz,
-                                 idesc_f16(TC_M, 256, fmt == 2 ? 0 : 1), tau_abs, tau_rel, flag1, nflag1,
-                                 st)))
-        return s;
+    if (fp8) {
+        CUtensorMap a8, b8;
+        if ((s = make_map(&a8, Zhi, rows, TC_M, 1))) return s;
+        if ((s = make_map(&b8, g->tab.B8, g->Rtot, 256, 1))) return s;
+        // one E4M3 product (kind::f8f6f4, E4M3 = format 0); scales folded into the epilogue
+        if ((s = dispatch_rr<256, 8>(g, a8, a8, b8, b8, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 0),
+                                     tau_abs, tau_rel, flag1, nflag1, st, ws.zsc2)))
+            return s;
+    } else {
+        if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
+        // one-term pass: no lo operands (the lo map arguments are unused)
+        if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz,
+                                     idesc_f16(TC_M, 256, fmt == 2 ? 0 : 1), tau_abs, tau_rel, flag1, nflag1,
+                                     st)))
+            return s;
+    }
     // ---- split-BF16 pass over the rows the first pass could not decide
     uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
     k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, flag1, nflag1, 1, 1, Z2hi, Z2lo,
-                                                 ws.zz2);
+                                                 ws.zz2, nullptr);
     EPLL_LAUNCHED(g);
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
     CUtensorMap a2, a2lo, bs, bslo;

@@ -23,8 +23,8 @@ if not torch.cuda.is_available():
 import paper_1710_08124_gb300 as ep  # noqa: E402
 
 TIE = 1e-4
-REL = {ep.BF16: 1e-2, ep.FP16: 1.5e-3, ep.BF16X3: 1e-4}
-PRECS = [ep.BF16X3, ep.FP16, ep.BF16]
+REL = {ep.BF16: 1e-2, ep.FP16: 1.5e-3, ep.BF16X3: 1e-4, ep.FP8: 1e-1}
+PRECS = [ep.BF16X3, ep.FP16, ep.BF16, ep.FP8]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -124,3 +124,20 @@ def test_restore_matches_oracle_psnr(prec):
     assert abs(ps(xg) - ps(xo)) <= 0.05
     evals, rescored, launches = ep.last_counters(gm)
     assert evals == 5 * math.ceil(64 * 64 / 3) and launches > 0
+
+
+def test_fp8_deblur_matches_oracle_psnr():
+    """The FEPLL deblurring configuration in miniature: periodic 25x25 Gaussian
+    blur (sigma_b = 1.6), sigma = 2/255, K = 200, r = 8, E4M3 selection."""
+    g = synth.synthetic_gmm(200)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, 8)
+    om = oracle.Model(g.w, g.U, g.S, "fixed", 8)
+    sigma = 2 / 255
+    x, k, y = synth.deblur_problem(8, 64, sigma)
+    xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, deg=oracle.CONV,
+                        kernel=k.astype(np.float32).astype(np.float64))
+    xg = ep.restore(gm, dev(y), sigma, kind=ep.CONV_PERIODIC, kernel=k,
+                    options=ep.Options(precision=ep.FP8)).cpu().numpy()
+    ep.last_counters(gm)
+    ps = lambda a: -10 * math.log10(np.mean((a - x) ** 2))
+    assert abs(ps(xg) - ps(xo)) <= 0.05
