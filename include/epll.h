@@ -143,6 +143,37 @@ epll_status epll_restore(epll_gmm *g, const float *y, int H, int W,
                          const double *beta_mult, int T, const epll_options *opt,
                          float *x_out, void *stream);
 
+/* One image of a batch (all pointers are device memory of the current device). */
+typedef struct {
+    const float *y;  /* H*W observation */
+    float *x_out;    /* H*W result; must not alias another job's buffers */
+    const float *a;  /* H*W gains for EPLL_PIXELWISE, NULL for EPLL_DENOISE */
+    int H, W;
+    int kind;        /* EPLL_DENOISE or EPLL_PIXELWISE */
+    float sigma;     /* noise standard deviation in image units */
+} epll_job;
+
+enum { EPLL_BATCH_SEQUENTIAL = 0, EPLL_BATCH_GRAPH = 1 };
+
+/*
+ * Restores a batch of images of uneven size, noise level and degradation
+ * (Algorithm 1 for each, as epll_restore; the per-beta tables are per image).
+ *   mode  EPLL_BATCH_SEQUENTIAL: one image after the other on `stream`;
+ *         EPLL_BATCH_GRAPH: the images are spread over `lanes` contexts (each
+ *         with its own tables and workspace, sharing the model) running on
+ *         their own streams, and the whole batch is captured once into a CUDA
+ *         graph that later calls with the same jobs replay with one launch.
+ *         lanes = 0 lets the library pick the lane count: on the first call it
+ *         times the graph for 1, 2, 4 and 8 lanes and keeps the fastest.
+ * The first call for a job list (and any call with a different one) allocates
+ * the lanes' workspaces, runs the batch once eagerly and captures the graph;
+ * those calls synchronise the device.  Replays are asynchronous on `stream`.
+ * Results are identical to epll_restore on each image.
+ * Errors: EPLL_EINVAL (any job invalid: nothing is run), EPLL_ENOMEM, EPLL_ECUDA.
+ */
+epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const double *beta_mult,
+                               int T, const epll_options *opt, int mode, int lanes, void *stream);
+
 /* Same as epll_restore with HOST buffers: y, deg->a (PIXELWISE) and x_out are
  * host pointers; the copies to and from the workspace are part of the call,
  * which returns after x_out is written (synchronises `stream`). */

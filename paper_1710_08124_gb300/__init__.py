@@ -38,6 +38,14 @@ class _Options(C.Structure):
                 ("subset_param", C.c_double), ("seed", C.c_uint64), ("cg_iters", C.c_int)]
 
 
+class _Job(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("x_out", C.c_void_p), ("a", C.c_void_p), ("H", C.c_int),
+                ("W", C.c_int), ("kind", C.c_int), ("sigma", C.c_float)]
+
+
+BATCH_SEQUENTIAL, BATCH_GRAPH = 0, 1
+
+
 class _Degradation(C.Structure):
     _fields_ = [("kind", C.c_int), ("a", C.c_void_p), ("kernel", C.c_void_p),
                 ("kh", C.c_int), ("kw", C.c_int)]
@@ -86,6 +94,7 @@ def lib():
                                       vp, C.POINTER(C.c_int), vp]
         L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
         L.epll_sample_noalloc.argtypes = L.epll_sample.argtypes
+        L.epll_restore_batch.argtypes = [vp, i, C.POINTER(_Job), vp, i, C.POINTER(_Options), i, i, vp]
         L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                          C.POINTER(C.c_longlong)]
         L.epll_profile_enable.argtypes = [vp, i]
@@ -185,6 +194,22 @@ def restore(g: GMM, y, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE, 
                               _stream(stream)))
     del keep
     return out
+
+
+def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = None,
+                  mode: int = BATCH_GRAPH, lanes: int = 0, stream=None):
+    """Batched restoration (``epll_restore_batch``).  ``jobs`` is a list of
+    (y, x_out, a_or_None, kind, sigma) with float32 CUDA tensors."""
+    import torch
+    arr = (_Job * len(jobs))()
+    for i, (y, xo, a, kind, sigma) in enumerate(jobs):
+        H, W = y.shape
+        arr[i] = _Job(_dptr(y, torch.float32), _dptr(xo, torch.float32), _dptr(a, torch.float32), H, W,
+                      int(kind), float(sigma))
+    bm = np.ascontiguousarray(beta_mult, np.float64)
+    opt = (options or Options())._c()
+    _check(lib().epll_restore_batch(g.handle, len(jobs), arr, bm.ctypes.data, bm.shape[0], C.byref(opt),
+                                    int(mode), int(lanes), _stream(stream)))
 
 
 def restore_host(g: GMM, y: np.ndarray, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE,

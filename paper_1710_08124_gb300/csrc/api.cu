@@ -27,7 +27,7 @@ void prof_end(epll_gmm *g, cudaStream_t st, int n)
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 
-static epll_status fail(epll_status s, const std::string &msg)
+epll_status fail(epll_status s, const std::string &msg)
 {
     g_err = msg;
     return s;
@@ -97,12 +97,51 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     return EPLL_OK;
 }
 
-static void free_model(epll_gmm *g)
+// Per-beta tables of TB_MAX iterations, slot-major (see slot_tables).
+cudaError_t alloc_tables(epll_gmm *g)
 {
-    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo,
-                    g->tab0.cst_hi, g->tab0.cst_lo, g->tab0.t_hi, g->tab0.t_lo, g->tab0.gp, g->tab0.sgn,
+    const int K = g->K, R = g->Rtot, Rp = g->Rp;
+    Tables &T0 = g->tab0;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&T0.cst_hi, TB_MAX * K)); A(dalloc(&T0.cst_lo, TB_MAX * K)); A(dalloc(&T0.t_hi, TB_MAX * K));
+    A(dalloc(&T0.t_lo, TB_MAX * K)); A(dalloc(&T0.gp, TB_MAX * K)); A(dalloc(&T0.sgn, TB_MAX * K));
+    A(dalloc(&T0.q_hi, (size_t)TB_MAX * Rp)); A(dalloc(&T0.q_lo, (size_t)TB_MAX * Rp));
+    A(dalloc(&T0.gw, (size_t)TB_MAX * Rp));
+    A(dalloc(&T0.tmax, TB_MAX));
+    A(dalloc(&T0.B1, (size_t)TB_MAX * R * PD));
+    A(dalloc(&T0.Bs, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.Bs_lo, (size_t)TB_MAX * R * PD));
+    A(dalloc(&T0.B8, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.k8s2, TB_MAX * K));
+    if (e != cudaSuccess) return e;
+    A(cudaMemset(T0.q_hi, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.q_lo, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.gw, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.B1, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    A(cudaMemset(T0.Bs, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    A(cudaMemset(T0.Bs_lo, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
+    A(cudaMemset(T0.B8, 0, (size_t)TB_MAX * R * PD));
+    g->tab = slot_tables(T0, 0, K, Rp, R);
+    return e;
+}
+
+static void free_tables(epll_gmm *g)
+{
+    void *ptrs[] = {g->tab0.cst_hi, g->tab0.cst_lo, g->tab0.t_hi, g->tab0.t_lo, g->tab0.gp, g->tab0.sgn,
                     g->tab0.q_hi, g->tab0.q_lo, g->tab0.gw, g->tab0.tmax, g->tab0.B1, g->tab0.Bs,
                     g->tab0.Bs_lo, g->tab0.B8, g->tab0.k8s2};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    g->tab0 = Tables();
+    g->tab = Tables();
+}
+
+
+static void free_model(epll_gmm *g)
+{
+    free_batch(g);
+    free_tables(g);
+    if (g->lane) return;  // lanes share the model arrays of their handle
+    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
@@ -214,7 +253,7 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     return EPLL_OK;
 }
 
-static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
+epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
                                const epll_degradation *deg, float sigma, const double *beta_mult,
                                int T, const epll_options &o, cudaStream_t st)
 {
@@ -265,7 +304,7 @@ static epll_status run_restore(epll_gmm *g, const float *y, const float *a, int 
     return EPLL_OK;
 }
 
-static epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
+epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
                                       const epll_degradation *deg, float sigma,
                                       const double *beta_mult, int T, const epll_options &o,
                                       const float *x_out)
@@ -409,18 +448,8 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R + COL_PAD));
     A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
     A(dalloc(&g->d_B, (size_t)PD * R + COL_PAD)); A(dalloc(&g->d_Blo, (size_t)PD * R + COL_PAD));
-    // per-beta tables of TB_MAX iterations, slot-major (see slot_tables)
-    const int Rp = R + COL_PAD;
-    g->Rp = Rp;
-    Tables &T0 = g->tab0;
-    A(dalloc(&T0.cst_hi, TB_MAX * K)); A(dalloc(&T0.cst_lo, TB_MAX * K)); A(dalloc(&T0.t_hi, TB_MAX * K));
-    A(dalloc(&T0.t_lo, TB_MAX * K)); A(dalloc(&T0.gp, TB_MAX * K)); A(dalloc(&T0.sgn, TB_MAX * K));
-    A(dalloc(&T0.q_hi, (size_t)TB_MAX * Rp)); A(dalloc(&T0.q_lo, (size_t)TB_MAX * Rp));
-    A(dalloc(&T0.gw, (size_t)TB_MAX * Rp));
-    A(dalloc(&T0.tmax, TB_MAX));
-    A(dalloc(&T0.B1, (size_t)TB_MAX * R * PD));
-    A(dalloc(&T0.Bs, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.Bs_lo, (size_t)TB_MAX * R * PD));
-    A(dalloc(&T0.B8, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.k8s2, TB_MAX * K));
+    g->Rp = R + COL_PAD;
+    A(alloc_tables(g));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_model(g);
@@ -432,20 +461,12 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(cudaMemset(g->d_colk, 0, sizeof(int) * (R + COL_PAD)));
     A(cudaMemset(g->d_B, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
     A(cudaMemset(g->d_Blo, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
-    A(cudaMemset(T0.q_hi, 0, sizeof(float) * (size_t)TB_MAX * Rp));
-    A(cudaMemset(T0.q_lo, 0, sizeof(float) * (size_t)TB_MAX * Rp));
-    A(cudaMemset(T0.gw, 0, sizeof(float) * (size_t)TB_MAX * Rp));
     A(cudaMemcpy(g->d_colk, colk.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_S, eigvals, sizeof(double) * K * PD, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
-    A(cudaMemset(T0.B1, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
-    A(cudaMemset(T0.Bs, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
-    A(cudaMemset(T0.Bs_lo, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
-    A(cudaMemset(T0.B8, 0, (size_t)TB_MAX * R * PD));
-    g->tab = slot_tables(T0, 0, K, Rp, R);
     if (e != cudaSuccess) {
         free_model(g);
         delete g;

@@ -99,6 +99,8 @@ struct Workspace {
     int planH = 0, planW = 0;
 };
 
+struct BatchState;  // lanes, streams and the captured graph of epll_restore_batch
+
 }  // namespace epll
 
 struct epll_gmm {
@@ -127,6 +129,10 @@ struct epll_gmm {
     int prof_n = 0;
     cudaEvent_t *prof_ev = nullptr;   // [2 * PROF_MAX]
     double prof_flops = 0.0;
+    // batched restoration: a lane is a context that shares this handle's model
+    // arrays and owns its own tables and workspace
+    bool lane = false;
+    epll::BatchState *batch = nullptr;
 };
 
 namespace epll {
@@ -199,6 +205,16 @@ epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, d
                     int iters, cudaStream_t st);  // ws.xhat
 
 epll_status ensure_workspace(epll_gmm *g, size_t N);
+epll_status fail(epll_status s, const std::string &msg);
+cudaError_t alloc_tables(epll_gmm *g);
+void free_batch(epll_gmm *g);
+// One restoration on g's workspace and tables (no allocation, no synchronisation).
+epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
+                        const epll_degradation *deg, float sigma, const double *beta_mult, int T,
+                        const epll_options &o, cudaStream_t st);
+epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W, const epll_degradation *deg,
+                               float sigma, const double *beta_mult, int T, const epll_options &o,
+                               const float *x_out);
 
 // Selection-kernel instrumentation (no-ops unless enabled).
 constexpr int PROF_MAX = 8192;
