@@ -419,3 +419,76 @@ def test_fraction_sampler_count_and_order():
         keys = np.array([oracle.rng_u64(77, t, a) >> 32 for a in range(H * W)], dtype=np.uint64)
         order = np.lexsort((np.arange(H * W), keys))
         assert np.array_equal(np.sort(order[:M]), an)
+
+
+# --------------------------------------------------------------------------
+# proposal network (oracle/mlp.py): gradient pinned by central differences
+# --------------------------------------------------------------------------
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp
+    K = 7
+    rng = np.random.default_rng(3)
+    theta = rng.standard_normal(mlp.n_params(K)) * 0.1
+    p = mlp.unpack(theta, K)
+    X = rng.standard_normal((5, 64))
+    cond = rng.standard_normal(5)
+    labels = rng.integers(0, K, 5)
+    L, g = mlp.loss_and_grad(p, X, cond, labels)
+    assert abs(L - mlp.loss(p, X, cond, labels)) < 1e-12
+    gv = mlp.pack(g, K)
+    idx = rng.choice(theta.size, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        num = (mlp.loss(mlp.unpack(tp, K), X, cond, labels) - mlp.loss(mlp.unpack(tm, K), X, cond, labels)) / (2 * h)
+        assert abs(num - gv[i]) < 1e-7 + 1e-5 * abs(num), (i, num, gv[i])
+
+
+def test_mlp_gelu_and_softmax_closed_forms():
+    from oracle import mlp
+    from scipy.stats import norm
+    x = np.linspace(-4, 4, 41)
+    np.testing.assert_allclose(mlp.gelu(x), x * norm.cdf(x), atol=1e-15)
+    np.testing.assert_allclose(mlp.gelu_grad(x), norm.cdf(x) + x * norm.pdf(x), atol=1e-14)
+    # uniform logits: loss = log K
+    K = 5
+    p = mlp.unpack(np.zeros(mlp.n_params(K)), K)
+    assert abs(mlp.loss(p, np.ones((3, 64)), np.zeros(3), np.array([0, 2, 4])) - np.log(K)) < 1e-14
+
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-30, 30, 20000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), ref)
+    # halfway cases round to the even mantissa
+    np.testing.assert_array_equal(mlp.bf16(np.array([1 + 2.0**-8, 1 + 3 * 2.0**-8, -(1 + 2.0**-8), 2.0**-133])),
+                                  np.array([1.0, 1 + 2.0**-6, -1.0, 2.0**-133]))
+
+
+def test_mlp_inference_form_scaling_and_topm():
+    """The inference form is the training forward at X = sqrt(beta) z, cond =
+    log(1/beta) up to the BF16 roundings of z and of the hidden activations;
+    top-m takes the lowest index first on equal logits."""
+    from oracle import mlp
+    K = 9
+    rng = np.random.default_rng(5)
+    p = mlp.unpack(rng.standard_normal(mlp.n_params(K)) * 0.1, K)
+    Z = rng.standard_normal((40, 64)) * 0.05
+    ibeta = 0.01
+    li = mlp.forward_infer(p, Z, ibeta)
+    lt, _ = mlp.forward(mlp.round_weights(p), Z / np.sqrt(ibeta), np.full(40, np.log(ibeta)))
+    scale = np.abs(lt).max()
+    assert np.abs(li - lt).max() < 2e-2 * scale
+    # a wrong scaling convention (z / sqrt(beta)) is far off
+    lw, _ = mlp.forward(mlp.round_weights(p), Z * np.sqrt(ibeta), np.full(40, np.log(ibeta)))
+    assert np.abs(lw - lt).max() > 0.2 * scale
+    logits = np.array([[0.0, 2.0, 2.0, 1.0], [3.0, 3.0, 3.0, 3.0]])
+    idx, mass = mlp.topm(logits, 2)
+    np.testing.assert_array_equal(idx, [[1, 2], [0, 1]])
+    e = np.exp(logits[0] - 2.0)
+    np.testing.assert_allclose(mass, [2 / e.sum(), 0.5], rtol=1e-15)
