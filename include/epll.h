@@ -61,8 +61,18 @@ enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
  * a BF16X3 pass; every form rescores its remaining near-ties in compensated
  * FP32 (see tie_gap). */
 enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3, EPLL_FP8 = 4 };
+/* how the Gaussian selection finds its candidates:
+ * EXHAUSTIVE every component is scored (Algorithm 1, step 2);
+ * PROPOSAL   a learned network attached to the model (epll_gmm_attach_proposal)
+ *            proposes m components per patch, which are scored exactly in FP32;
+ *            a patch whose proposals hold too little softmax mass, or whose two
+ *            best rescored proposals are within the FP32 error bound of each
+ *            other, is scored exhaustively (BF16X3, then compensated FP32
+ *            rescoring of its near-ties).  `precision` is ignored. */
+enum { EPLL_SELECT_EXHAUSTIVE = 0, EPLL_SELECT_PROPOSAL = 1 };
 
 typedef struct epll_gmm epll_gmm; /* opaque, library-owned */
+typedef struct epll_proposal epll_proposal; /* opaque, library-owned */
 
 /* Degradation A.  PIXELWISE: A = diag(a) (a = 0/1 mask for inpainting, a
  * smooth gain for devignetting).  CONV_PERIODIC: circular convolution with a
@@ -86,9 +96,11 @@ typedef struct {
     double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */
     uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
     int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
+    int select;         /* EPLL_SELECT_EXHAUSTIVE or EPLL_SELECT_PROPOSAL */
 } epll_options;
 
-/* Fills *o with the defaults: FP32, default tie gap, all patches, seed 0, 100 CG iterations. */
+/* Fills *o with the defaults: FP32, default tie gap, all patches, seed 0, 100 CG
+ * iterations, exhaustive selection. */
 void epll_options_default(epll_options *o);
 
 /*
@@ -247,6 +259,80 @@ epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *r
  * whatever the arithmetic), then clears the record.  Any output may be NULL. */
 epll_status epll_profile_enable(epll_gmm *g, int enable);
 epll_status epll_profile_read(epll_gmm *g, double *ms, long long *launches, double *flops);
+
+/*
+ * Learned top-m proposal for the Gaussian selection (no counterpart in the
+ * paper, which accelerates the selection with a balanced search tree instead;
+ * the label it learns is the exact argmin of Eq. 14).  A network
+ * 64 -> 256 -> 256 -> K with GELU (erf form) reads a patch's DC-free values
+ * z scaled by sqrt(beta); log(1/beta) enters the first layer through a learned
+ * per-unit coefficient wb:
+ *   h1 = gelu(W1 (sqrt(beta) z) + b1 + log(1/beta) wb),  h2 = gelu(W2 h1 + b2),
+ *   logits = W3 h2 + b3.
+ * Parameters: one FP32 vector of epll_proposal_size(K) entries in the order
+ * W1[256][64], b1[256], wb[256], W2[256][256], b2[256], W3[K][256], b3[K]
+ * (matrices row-major [out][in]).  Every forward pass uses W1, W2 and W3
+ * rounded to BF16 (round to nearest even) with FP32 biases and FP32
+ * accumulation; inference also rounds its layer inputs (sqrt(beta) is applied
+ * after the first product: W1 (sqrt(beta) z) = sqrt(beta) (W1 z)) and the
+ * hidden activations to BF16.  Training keeps FP32 master weights.
+ */
+/* Number of parameters for K components (0 if K < 1). */
+size_t epll_proposal_size(int K);
+/* Creates a network for K in 2..256 components, initialised from `seed`
+ * (normal draws scaled by sqrt(2/fan_in), sqrt(1/256) for W3; biases 0).
+ * Synchronous.  Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA. */
+epll_status epll_proposal_create(int K, uint64_t seed, epll_proposal **out);
+/* Frees the network (synchronises the device).  NULL is a no-op.  Detach it
+ * (epll_gmm_attach_proposal with NULL) from every model first. */
+void epll_proposal_free(epll_proposal *p);
+/* Copies the FP32 master parameters to / from host memory (size entries).
+ * set resets the optimiser state.  Synchronous.  Errors: EPLL_EINVAL (NULL, or
+ * a non-finite value for set), EPLL_ECUDA. */
+epll_status epll_proposal_get(const epll_proposal *p, float *params);
+epll_status epll_proposal_set(epll_proposal *p, const float *params);
+/*
+ * Mean softmax cross-entropy of a batch of B labelled patches and its gradient
+ * with respect to the parameters (forward with the BF16-rounded weights,
+ * FP32 activations; gradients are those of the rounded weights).
+ *   images   device [n_img][H][W] float32 (the patches' source images)
+ *   img_idx  device int[n_all]: image of each sample
+ *   anchors  device int[n_all]: top-left pixel i*W + j of each 8x8 patch (periodic)
+ *   log_ib   device float[n_all]: log(1/beta) of each sample
+ *   labels   device int[n_all] in 0..K-1: the exact selection of each sample
+ *   sel      device int[B] (nullable): the batch's samples as indices into the
+ *            n_all-long arrays; NULL means samples 0..B-1 (then n_all == B)
+ *   grad     device float[size] out (nullable)
+ *   loss     host float out (nullable); when given, the call synchronises
+ *            `stream` and returns EPLL_EINVAL if a sample had an index, anchor,
+ *            label or log(1/beta) out of range (such samples contribute nothing)
+ * Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA.
+ */
+epll_status epll_proposal_grad(epll_proposal *p, const float *images, int n_img, int H, int W,
+                               const int *img_idx, const int *anchors, const float *log_ib,
+                               const int *labels, const int *sel, int n_all, int B, float *grad,
+                               float *loss, void *stream);
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay on
+ * W1, W2 and W3 only) on the gradient of the same loss; arguments as
+ * epll_proposal_grad; finite lr > 0 and weight_decay >= 0.  The loss is that
+ * of the parameters before the step. */
+epll_status epll_proposal_train(epll_proposal *p, const float *images, int n_img, int H, int W,
+                                const int *img_idx, const int *anchors, const float *log_ib,
+                                const int *labels, const int *sel, int n_all, int B, float lr,
+                                float weight_decay, float *loss, void *stream);
+/* Attaches (p != NULL) or detaches (p == NULL) a network to a model with the
+ * same K; topm in 1..min(8, K) proposals per patch; a patch whose proposals
+ * hold less than pmin in [0, 1] of the softmax mass is scored exhaustively.
+ * The model does not own the network. */
+epll_status epll_gmm_attach_proposal(epll_gmm *g, const epll_proposal *p, int topm, float pmin);
+/* Runs the attached network (inference kernels) on the patches of xhat
+ * (device [H][W]) at anchors (device int[n], NULL = all H*W positions in
+ * raster order, n = H*W) for the given beta: cand device int[n][topm] gets
+ * the proposed components by decreasing logit (lowest index first on equal
+ * logits), pmass device float[n] their softmax mass (nullable).  Asynchronous.
+ * Errors: EPLL_EINVAL (no network attached, bad sizes), EPLL_ENOMEM, EPLL_ECUDA. */
+epll_status epll_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                               double beta, int *cand, float *pmass, void *stream);
 
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char *epll_last_error(void);

@@ -24,6 +24,7 @@ RANK_FIXED, RANK_RHO = 0, 1
 DENOISE, PIXELWISE, CONV_PERIODIC = 0, 1, 2
 SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER = 0, 1, 2
 FP32, BF16, FP16, BF16X3, FP8 = 0, 1, 2, 3, 4
+SELECT_EXHAUSTIVE, SELECT_PROPOSAL = 0, 1
 PAPER_BETA = (1.0, 4.0, 8.0, 16.0, 32.0)
 
 
@@ -35,7 +36,8 @@ class EpllError(RuntimeError):
 
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tie_gap", C.c_float), ("subset", C.c_int),
-                ("subset_param", C.c_double), ("seed", C.c_uint64), ("cg_iters", C.c_int)]
+                ("subset_param", C.c_double), ("seed", C.c_uint64), ("cg_iters", C.c_int),
+                ("select", C.c_int)]
 
 
 class _Job(C.Structure):
@@ -60,10 +62,11 @@ class Options:
     subset_param: float = 0.0
     seed: int = 0
     cg_iters: int = 100
+    select: int = SELECT_EXHAUSTIVE
 
     def _c(self) -> _Options:
         return _Options(self.precision, self.tie_gap, self.subset, self.subset_param,
-                        self.seed, self.cg_iters)
+                        self.seed, self.cg_iters, self.select)
 
 
 _lib = None
@@ -102,6 +105,18 @@ def lib():
                                         C.POINTER(C.c_double)]
         L.epll_options_default.argtypes = [C.POINTER(_Options)]
         L.epll_options_default.restype = None
+        L.epll_proposal_size.argtypes = [i]
+        L.epll_proposal_size.restype = C.c_size_t
+        L.epll_proposal_create.argtypes = [i, C.c_uint64, C.POINTER(vp)]
+        L.epll_proposal_free.argtypes = [vp]
+        L.epll_proposal_free.restype = None
+        L.epll_proposal_get.argtypes = [vp, vp]
+        L.epll_proposal_set.argtypes = [vp, vp]
+        L.epll_proposal_grad.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, i, i, vp, vp, vp]
+        L.epll_proposal_train.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, i, i, C.c_float, C.c_float,
+                                          vp, vp]
+        L.epll_gmm_attach_proposal.argtypes = [vp, vp, i, C.c_float]
+        L.epll_proposal_topm.argtypes = [vp, vp, i, i, vp, i, d, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -295,3 +310,92 @@ def profile_read(g: GMM):
     ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
     _check(lib().epll_profile_read(g.handle, C.byref(ms), C.byref(n), C.byref(fl)))
     return ms.value, n.value, fl.value
+
+
+class Proposal:
+    """Learned top-m proposal network (``epll_proposal_*``): 64 -> 256 -> 256 -> K."""
+
+    def __init__(self, K: int, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().epll_proposal_create(int(K), int(seed), C.byref(h)))
+        self._h = h
+        self.K = int(K)
+        self.size = int(lib().epll_proposal_size(self.K))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get(self) -> np.ndarray:
+        out = np.empty(self.size, np.float32)
+        _check(lib().epll_proposal_get(self._h, out.ctypes.data))
+        return out
+
+    def set(self, params):
+        v = np.ascontiguousarray(params, np.float32)
+        if v.shape != (self.size,):
+            raise ValueError(f"expected {self.size} parameters")
+        _check(lib().epll_proposal_set(self._h, v.ctypes.data))
+
+    @staticmethod
+    def _batch(images, img_idx, anchors, log_ib, labels, sel):
+        import torch
+        if images.dim() == 2:
+            images = images[None]
+        n_img, H, W = images.shape
+        n_all = int(labels.numel())
+        B = n_all if sel is None else int(sel.numel())
+        return (_dptr(images, torch.float32), n_img, H, W, _dptr(img_idx, torch.int32),
+                _dptr(anchors, torch.int32), _dptr(log_ib, torch.float32), _dptr(labels, torch.int32),
+                _dptr(sel, torch.int32), n_all, B)
+
+    def grad(self, images, img_idx, anchors, log_ib, labels, sel=None, stream=None):
+        """(gradient as a CUDA float32 tensor, mean cross-entropy) of one batch."""
+        import torch
+        g = torch.empty(self.size, dtype=torch.float32, device=images.device)
+        loss = C.c_float(0.0)
+        _check(lib().epll_proposal_grad(self._h, *self._batch(images, img_idx, anchors, log_ib, labels, sel),
+                                        _dptr(g), C.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train_step(self, images, img_idx, anchors, log_ib, labels, sel=None, lr: float = 1e-3,
+                   weight_decay: float = 0.0, want_loss: bool = True, stream=None):
+        """One AdamW step on the samples ``sel`` (None: all); returns the batch
+        loss (before the step) when want_loss."""
+        loss = C.c_float(0.0)
+        _check(lib().epll_proposal_train(self._h, *self._batch(images, img_idx, anchors, log_ib, labels, sel),
+                                         float(lr), float(weight_decay),
+                                         C.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().epll_proposal_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def attach_proposal(g: GMM, p: Proposal | None, topm: int = 4, pmin: float = 0.0):
+    """Attaches (or, with None, detaches) a proposal network to a model."""
+    _check(lib().epll_gmm_attach_proposal(g.handle, p.handle if p is not None else None, int(topm),
+                                          float(pmin)))
+    g._proposal = p
+    g._topm = int(topm)
+
+
+def proposal_topm(g: GMM, xhat, beta: float, anchors=None, stream=None):
+    """Runs the attached network: (cand int32 [n][topm], pmass float32 [n]) as CUDA tensors."""
+    import torch
+    H, W = xhat.shape
+    n = H * W if anchors is None else int(anchors.numel())
+    topm = g._topm
+    cand = torch.empty((n, topm), dtype=torch.int32, device=xhat.device)
+    pmass = torch.empty(n, dtype=torch.float32, device=xhat.device)
+    _check(lib().epll_proposal_topm(g.handle, _dptr(xhat, torch.float32), H, W, _dptr(anchors, torch.int32), n,
+                                    float(beta), _dptr(cand), _dptr(pmass), _stream(stream)))
+    return cand, pmass

@@ -46,7 +46,8 @@ static void free_workspace(Workspace &ws)
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
                     ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
-                    ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern};
+                    ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
+                    ws.H1b, ws.H2b, ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
@@ -108,7 +109,7 @@ cudaError_t alloc_tables(epll_gmm *g)
     A(dalloc(&T0.t_lo, TB_MAX * K)); A(dalloc(&T0.gp, TB_MAX * K)); A(dalloc(&T0.sgn, TB_MAX * K));
     A(dalloc(&T0.q_hi, (size_t)TB_MAX * Rp)); A(dalloc(&T0.q_lo, (size_t)TB_MAX * Rp));
     A(dalloc(&T0.gw, (size_t)TB_MAX * Rp));
-    A(dalloc(&T0.tmax, TB_MAX));
+    A(dalloc(&T0.tmax, TB_MAX)); A(dalloc(&T0.ibeta, TB_MAX));
     A(dalloc(&T0.B1, (size_t)TB_MAX * R * PD));
     A(dalloc(&T0.Bs, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.Bs_lo, (size_t)TB_MAX * R * PD));
     A(dalloc(&T0.B8, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.k8s2, TB_MAX * K));
@@ -127,7 +128,7 @@ cudaError_t alloc_tables(epll_gmm *g)
 static void free_tables(epll_gmm *g)
 {
     void *ptrs[] = {g->tab0.cst_hi, g->tab0.cst_lo, g->tab0.t_hi, g->tab0.t_lo, g->tab0.gp, g->tab0.sgn,
-                    g->tab0.q_hi, g->tab0.q_lo, g->tab0.gw, g->tab0.tmax, g->tab0.B1, g->tab0.Bs,
+                    g->tab0.q_hi, g->tab0.q_lo, g->tab0.gw, g->tab0.tmax, g->tab0.ibeta, g->tab0.B1, g->tab0.Bs,
                     g->tab0.Bs_lo, g->tab0.B8, g->tab0.k8s2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -171,6 +172,15 @@ static epll_status check_options(const epll_options &o, int H, int W)
         return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION or _JITTER");
     }
     if (o.cg_iters < 0 || o.cg_iters > 100000) return fail(EPLL_EINVAL, "options.cg_iters out of range");
+    if (o.select != EPLL_SELECT_EXHAUSTIVE && o.select != EPLL_SELECT_PROPOSAL)
+        return fail(EPLL_EINVAL, "options.select must be EPLL_SELECT_EXHAUSTIVE or _PROPOSAL");
+    return EPLL_OK;
+}
+
+static epll_status check_select(const epll_gmm *g, const epll_options &o)
+{
+    if (o.select == EPLL_SELECT_PROPOSAL && !g->prop)
+        return fail(EPLL_EINVAL, "options.select is EPLL_SELECT_PROPOSAL but no proposal network is attached");
     return EPLL_OK;
 }
 
@@ -200,9 +210,10 @@ static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
 }
 
 // Bases the tables kernel writes for each arithmetic (bit mask, see launch_tables).
-static int basis_format(int precision)
+static int basis_format(const epll_options &o)
 {
-    switch (precision) {
+    if (o.select == EPLL_SELECT_PROPOSAL) return 4;  // exhaustive fallback: split BF16 pass
+    switch (o.precision) {
     case EPLL_BF16: return 1 | 4;
     case EPLL_FP16: return 2 | 4;
     case EPLL_BF16X3: return 4;
@@ -218,7 +229,7 @@ static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &
 {
     Workspace &ws = g->ws;
     epll_status s;
-    if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o.precision), st))) return s;
+    if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o), st))) return s;
     return launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, st);
 }
 
@@ -240,12 +251,15 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
     float tau_abs, tau_rel;
     thresholds(o, &tau_abs, &tau_rel);
-    if (o.precision != EPLL_FP32) {
+    if (o.select == EPLL_SELECT_PROPOSAL) {
+        if ((s = launch_select_proposal(g, xhat, H, W, anchors, n, tau_abs, st))) return s;
+    } else if (o.precision != EPLL_FP32) {
         if ((s = launch_select_tc(g, xhat, H, W, anchors, n, o.precision, tau_abs, tau_rel, st))) return s;
     } else {
         if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau_abs, tau_rel, st))) return s;
     }
-    if ((s = launch_rescore(g, xhat, H, W, anchors, n, o.precision != EPLL_FP32, tau_abs, st))) return s;
+    const bool split_scores = o.select == EPLL_SELECT_PROPOSAL || o.precision != EPLL_FP32;
+    if ((s = launch_rescore(g, xhat, H, W, anchors, n, split_scores, tau_abs, st))) return s;
     if (forced_k)
         EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
@@ -319,6 +333,7 @@ epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
         if (!(beta_mult[t] > 0.0) || !std::isfinite(beta_mult[t]))
             return fail(EPLL_EINVAL, "beta multipliers must be positive");
     if ((s = check_options(o, H, W))) return s;
+    if ((s = check_select(g, o))) return s;
     if (deg) {
         if (deg->kind == EPLL_PIXELWISE) {
             if (!deg->a) return fail(EPLL_EINVAL, "PIXELWISE degradation needs gains a");
@@ -356,6 +371,7 @@ void epll_options_default(epll_options *o)
     o->subset_param = 0.0;
     o->seed = 0;
     o->cg_iters = 100;
+    o->select = EPLL_SELECT_EXHAUSTIVE;
 }
 
 epll_status epll_gmm_load(int K, int P, const double *weights, const double *eigvecs,
@@ -551,6 +567,7 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     epll_status s;
     if ((s = check_image(H, W))) return s;
     if ((s = check_options(o, H, W))) return s;
+    if ((s = check_select(g, o))) return s;
     if ((s = ensure_workspace(g, (size_t)H * W))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace &ws = g->ws;

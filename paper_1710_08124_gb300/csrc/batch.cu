@@ -87,10 +87,13 @@ static void put(std::vector<unsigned char> &k, const T &v)
     k.insert(k.end(), p, p + sizeof(T));
 }
 
-static std::vector<unsigned char> job_key(int n, const epll_job *jobs, const double *beta, int T,
-                                          const epll_options &o)
+static std::vector<unsigned char> job_key(const epll_gmm *g, int n, const epll_job *jobs, const double *beta,
+                                          int T, const epll_options &o)
 {
     std::vector<unsigned char> k;
+    put(k, g->prop);
+    put(k, g->prop_topm);
+    put(k, g->prop_pmin);
     put(k, n);
     for (int i = 0; i < n; ++i) put(k, jobs[i]);
     put(k, T);
@@ -155,6 +158,9 @@ static epll_status prepare_lanes(epll_gmm *g, BatchState *b, const std::vector<s
         for (int j : part[l]) maxN = std::max(maxN, (size_t)jobs[j].H * jobs[j].W);
         epll_status s;
         if ((s = ensure_workspace(b->lanes[l], maxN))) return s;
+        b->lanes[l]->prop = g->prop;
+        b->lanes[l]->prop_topm = g->prop_topm;
+        b->lanes[l]->prop_pmin = g->prop_pmin;
     }
     return EPLL_OK;
 }
@@ -241,7 +247,7 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
     }
     if (!g->batch) g->batch = new BatchState();
     BatchState *b = g->batch;
-    const std::vector<unsigned char> jk = job_key(n, jobs, beta_mult, T, o);
+    const std::vector<unsigned char> jk = job_key(g, n, jobs, beta_mult, T, o);
     int L = lanes;
     if (L == 0) {
         if (b->tuned_key == jk && b->tuned_lanes > 0) {

@@ -35,6 +35,7 @@ struct Tables {
     float *q_hi = nullptr, *q_lo = nullptr;      // [Rtot]
     float *gw = nullptr;                         // [Rtot]
     float *tmax = nullptr;                       // [1]: max_k 1/min_j nu_kj (error scale)
+    float *ibeta = nullptr;                      // [1]: 1/beta of this iteration
     uint16_t *B1 = nullptr;                      // [Rtot][64]: 16-bit Ubar * sqrt|q| (BF16 or FP16), K-major
     uint16_t *Bs = nullptr;                      // [Rtot][64]: BF16 hi part of Ubar * sqrt|q| (split form)
     uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
@@ -55,6 +56,7 @@ __host__ __device__ inline Tables slot_tables(Tables t, int slot, int K, int Rp,
     t.gp += (size_t)slot * K; t.sgn += (size_t)slot * K;
     t.q_hi += (size_t)slot * Rp; t.q_lo += (size_t)slot * Rp; t.gw += (size_t)slot * Rp;
     t.tmax += slot;
+    t.ibeta += slot;
     t.B1 += (size_t)slot * Rtot * 64; t.Bs += (size_t)slot * Rtot * 64; t.Bs_lo += (size_t)slot * Rtot * 64;
     t.B8 += (size_t)slot * Rtot * 64; t.k8s2 += (size_t)slot * K;
     return t;
@@ -97,6 +99,14 @@ struct Workspace {
     float *kern = nullptr;                    // [H][W] wrapped blur kernel
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     int planH = 0, planW = 0;
+    // learned proposal (allocated on first use)
+    size_t prop_cap = 0;
+    uint16_t *H1b = nullptr, *H2b = nullptr;  // [zrows][256] BF16 hidden activations
+    int *cand = nullptr;                      // [N][topm] proposed components
+    float *pmass = nullptr;                   // [N] softmax mass of the proposals
+    int *pperm = nullptr;                     // [N * topm] pairs grouped by component
+    int4 *pitems = nullptr;                   // pair work items
+    float *pscore = nullptr;                  // [N * topm] FP32 scores of the pairs
 };
 
 struct BatchState;  // lanes, streams and the captured graph of epll_restore_batch
@@ -133,6 +143,10 @@ struct epll_gmm {
     // arrays and owns its own tables and workspace
     bool lane = false;
     epll::BatchState *batch = nullptr;
+    // learned top-m proposal (not owned)
+    const epll_proposal *prop = nullptr;
+    int prop_topm = 0;
+    float prop_pmin = 0.0f;
 };
 
 namespace epll {
@@ -184,6 +198,22 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
                            int n, bool split_scores, float tau_abs, cudaStream_t st);
 epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                               cudaStream_t st);
+epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                              const int *flag1, const int *nflag1, float tau_abs, cudaStream_t st);
+// Learned top-m proposal + exact FP32 rescoring of the proposals; undecided
+// patches go through launch_split_pass.  Leaves kstar/gap of every row and the
+// near-tie list of the split pass for launch_rescore.
+epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                   float tau_abs, cudaStream_t st);
+// Proposal network alone: top-m components and their softmax mass per patch
+// (1/beta read from the device scalar ibeta).
+epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                 const float *ibeta, cudaStream_t st);
+// BF16 DC-free patches into ws.Zb (rows padded to 128 with zeros) and |z|^2 into ws.zz.
+epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                cudaStream_t st);
+// Counting sort of n keys (components) into perm and estimation work items.
+epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st);
 inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; }
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);

@@ -1,0 +1,916 @@
+// Learned top-m proposal for the Gaussian selection.
+//
+// A small network, 64 -> 256 -> 256 -> K with GELU, maps a DC-free patch
+// (scaled by sqrt(beta), with log(1/beta) entering the first layer through a
+// learned per-unit coefficient, so that the selection label of Eq. 14 is a
+// function of the input) to logits over the K components.  Inference runs on
+// the tensor cores (one tcgen05 kernel per layer, BF16 operands, FP32
+// accumulation in TMEM, bias + GELU or bias + top-m fused in the epilogue).
+// The m proposed components of every patch are rescored exactly in FP32 --
+// the (patch, candidate) pairs grouped by component, each group's basis in
+// shared memory -- and a patch whose proposals carry too little softmax mass
+// or whose rescored top-2 gap is within the FP32 error bound goes to the
+// exhaustive split-BF16 pass (and, if still undecided, to the compensated
+// rescoring): exhaustive scoring is both the fallback and the judge.
+//
+// Training (BF16-rounded weights, FP32 activations and accumulation, FP32
+// master weights, AdamW) uses plain register-tiled SIMT kernels; it runs
+// offline on (patch, exact selection) pairs produced by the exhaustive path.
+#include "epll_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace epll {
+
+constexpr int HID = 256;
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + HID * PD;
+constexpr int OFF_WB = OFF_B1 + HID;
+constexpr int OFF_W2 = OFF_WB + HID;
+constexpr int OFF_B2 = OFF_W2 + HID * HID;
+constexpr int OFF_W3 = OFF_B2 + HID;
+__host__ __device__ inline size_t off_b3(int K) { return (size_t)OFF_W3 + (size_t)HID * K; }
+__host__ __device__ inline size_t prop_size(int K) { return off_b3(K) + (size_t)K; }
+
+}  // namespace epll
+
+struct epll_proposal {
+    int K = 0;
+    size_t np = 0;
+    float *theta = nullptr, *mom1 = nullptr, *mom2 = nullptr, *grad = nullptr;
+    float *wr = nullptr;  // theta with W1, W2, W3 rounded to BF16 (the weights every forward uses)
+    uint16_t *W1b = nullptr, *W2b = nullptr, *W3b = nullptr;  // BF16 [256][64], [256][256], [256][256]
+    long long step = 0;
+    int Bmax = 0;
+    float *X = nullptr, *cond = nullptr, *A1 = nullptr, *H1 = nullptr, *A2 = nullptr, *H2 = nullptr;
+    float *L = nullptr, *dH = nullptr, *dA = nullptr, *loss = nullptr;
+};
+
+namespace epll {
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// ============================================================================
+// Training kernels (SIMT FP32)
+// ============================================================================
+// C[m][n] (+)= sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+constexpr int GT = 64, GKC = 16;
+__global__ void __launch_bounds__(256)
+k_gemm(int M, int N, int Kd, const float *__restrict__ A, long sam, long sak, const float *__restrict__ Bm,
+       long sbk, long sbn, float *__restrict__ C, int ldc, int accumulate)
+{
+    __shared__ float As[GKC][GT + 1], Bs[GKC][GT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < Kd; k0 += GKC) {
+        for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
+            const int kk = idx / GT, mm = idx % GT;
+            As[kk][mm] = (m0 + mm < M && k0 + kk < Kd) ? A[(long)(m0 + mm) * sam + (long)(k0 + kk) * sak] : 0.0f;
+            Bs[kk][mm] = (n0 + mm < N && k0 + kk < Kd) ? Bm[(long)(k0 + kk) * sbk + (long)(n0 + mm) * sbn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GKC; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m < M && n < N) C[(long)m * ldc + n] = accumulate ? C[(long)m * ldc + n] + acc[i][j] : acc[i][j];
+        }
+}
+
+// X[b] = (patch - mean) * exp(-log_ib/2), cond[b] = log_ib; one warp per sample
+__global__ void k_mlp_gather(const float *__restrict__ images, int n_img, int H, int W,
+                             const int *__restrict__ img_idx, const int *__restrict__ anchors,
+                             const float *__restrict__ log_ib, const int *__restrict__ sel, int n_all, int B,
+                             float *__restrict__ X, float *__restrict__ cond, int *__restrict__ bad)
+{
+    const int b = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const int s = sel ? sel[b] : b;
+    const bool ok_s = s >= 0 && s < n_all;
+    const int im_i = ok_s ? img_idx[s] : -1;
+    const int a = ok_s ? anchors[s] : -1;
+    const float lib = ok_s ? log_ib[s] : 0.0f;
+    if (!ok_s || im_i < 0 || im_i >= n_img || a < 0 || a >= H * W || !isfinite(lib)) {
+        if (lane == 0) {
+            atomicExch(bad, 1);
+            cond[b] = 0.0f;
+        }
+        X[(size_t)b * PD + lane] = 0.0f;
+        X[(size_t)b * PD + lane + 32] = 0.0f;
+        return;
+    }
+    const float *im = images + (size_t)im_i * H * W;
+    const int ai = a / W, aj = a % W;
+    int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
+    if (r0 >= H) r0 -= H;
+    if (r1 >= H) r1 -= H;
+    if (c >= W) c -= W;
+    const float x0 = im[(size_t)r0 * W + c], x1 = im[(size_t)r1 * W + c];
+    float sum = x0 + x1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const float mu = sum * (1.0f / PD), sc = expf(-0.5f * lib);
+    X[(size_t)b * PD + lane] = (x0 - mu) * sc;
+    X[(size_t)b * PD + lane + 32] = (x1 - mu) * sc;
+    if (lane == 0) cond[b] = lib;
+}
+
+// A += bias (+ cond * wb) in place; Hout = gelu(A)
+__global__ void k_bias_gelu(float *__restrict__ A, const float *__restrict__ bias, const float *__restrict__ wb,
+                            const float *__restrict__ cond, int B, float *__restrict__ Hout)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)B * HID) return;
+    const int j = (int)(i % HID), b = (int)(i / HID);
+    const float v = A[i] + bias[j] + (wb ? cond[b] * wb[j] : 0.0f);
+    A[i] = v;
+    Hout[i] = gelu_f(v);
+}
+
+// logits += b3; dL = (softmax - onehot) / B; loss += mean cross-entropy
+__global__ void k_softmax_ce(float *__restrict__ Lg, const float *__restrict__ b3, const int *__restrict__ labels,
+                             const int *__restrict__ sel, int n_all, int B, int K, float *__restrict__ loss,
+                             int *__restrict__ bad)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int s = sel ? sel[b] : b;
+    const int lab = (s >= 0 && s < n_all) ? labels[s] : -1;
+    if (lab < 0 || lab >= K) {  // invalid label: no gradient from this sample
+        atomicExch(bad, 1);
+        for (int k = 0; k < K; ++k) Lg[(size_t)b * K + k] = 0.0f;
+        return;
+    }
+    float *l = Lg + (size_t)b * K;
+    float mx = -FLT_MAX;
+    for (int k = 0; k < K; ++k) {
+        l[k] += b3[k];
+        mx = fmaxf(mx, l[k]);
+    }
+    float se = 0.0f;
+    for (int k = 0; k < K; ++k) se += expf(l[k] - mx);
+    const float lse = mx + logf(se);
+    atomicAdd(loss, (lse - l[lab]) / (float)B);
+    for (int k = 0; k < K; ++k) l[k] = (expf(l[k] - lse) - (k == lab ? 1.0f : 0.0f)) / (float)B;
+}
+
+__global__ void k_gelu_back(float *__restrict__ dH, const float *__restrict__ A, long n)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dH[i] *= gelu_grad_f(A[i]);
+}
+
+// out[n] = sum_b D[b][n] (optionally weighted by cond[b]); rows summed in order
+__global__ void k_colsum(const float *__restrict__ D, int B, int N, const float *__restrict__ cond,
+                         float *__restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s = fmaf(cond ? cond[b] : 1.0f, D[(size_t)b * N + n], s);
+    out[n] = s;
+}
+
+// AdamW (decoupled weight decay on the weight matrices only), then the BF16
+// roundings of the weights (training forward and inference copies).
+__global__ void k_adamw(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m1,
+                        float *__restrict__ m2, long np, int K, float lr, float wd, float c1, float c2)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const bool is_w = i < OFF_B1 || (i >= OFF_W2 && i < OFF_B2) || (i >= OFF_W3 && i < (long)off_b3(K));
+    const float gi = g[i];
+    const float a = 0.9f * m1[i] + 0.1f * gi, b = 0.999f * m2[i] + 0.001f * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    float t = th[i];
+    if (is_w) t -= lr * wd * t;
+    th[i] = t - lr * (a / c1) / (sqrtf(b / c2) + 1e-8f);
+}
+
+__global__ void k_round_weights(const float *__restrict__ th, long np, int K, float *__restrict__ wr,
+                                uint16_t *__restrict__ W1b, uint16_t *__restrict__ W2b, uint16_t *__restrict__ W3b)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const bool is_w = i < OFF_B1 || (i >= OFF_W2 && i < OFF_B2) || (i >= OFF_W3 && i < (long)off_b3(K));
+    const __nv_bfloat16 h = __float2bfloat16_rn(th[i]);
+    wr[i] = is_w ? __bfloat162float(h) : th[i];
+    if (i < OFF_B1) W1b[i] = __bfloat16_as_ushort(h);
+    else if (i >= OFF_W2 && i < OFF_B2) W2b[i - OFF_W2] = __bfloat16_as_ushort(h);
+    else if (i >= OFF_W3 && i < (long)off_b3(K)) W3b[i - OFF_W3] = __bfloat16_as_ushort(h);
+}
+
+static epll_status gemm(const float *A, long sam, long sak, const float *B, long sbk, long sbn, float *C, int ldc,
+                        int M, int N, int Kd, cudaStream_t st)
+{
+    const dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
+    k_gemm<<<grid, 256, 0, st>>>(M, N, Kd, A, sam, sak, B, sbk, sbn, C, ldc, 0);
+    EPLL_CU(cudaGetLastError());
+    return EPLL_OK;
+}
+
+static epll_status ensure_train(epll_proposal *p, int B)
+{
+    if (B <= p->Bmax) return EPLL_OK;
+    float *ptrs[] = {p->X, p->cond, p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA};
+    for (float *q : ptrs)
+        if (q) cudaFree(q);
+    const size_t HB = (size_t)B * HID;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](float **q, size_t n) { if (e == cudaSuccess) e = cudaMalloc(q, sizeof(float) * n); };
+    A(&p->X, (size_t)B * PD); A(&p->cond, B); A(&p->A1, HB); A(&p->H1, HB); A(&p->A2, HB); A(&p->H2, HB);
+    A(&p->L, (size_t)B * p->K); A(&p->dH, HB > (size_t)B * p->K ? HB : (size_t)B * p->K); A(&p->dA, HB);
+    if (e != cudaSuccess) {
+        p->Bmax = 0;
+        return fail(EPLL_ENOMEM, std::string("proposal training buffers: ") + cudaGetErrorString(e));
+    }
+    p->Bmax = B;
+    return EPLL_OK;
+}
+
+// Forward + backward of the mean cross-entropy on one batch; gradient in p->grad.
+struct Batch {
+    const float *images;
+    int n_img, H, W;
+    const int *img_idx, *anchors;
+    const float *log_ib;
+    const int *labels, *sel;
+    int n_all, B;
+};
+
+static epll_status forward_backward(epll_proposal *p, const Batch &d, cudaStream_t st)
+{
+    epll_status s;
+    const int B = d.B;
+    if ((s = ensure_train(p, B))) return s;
+    const int K = p->K;
+    int *bad = reinterpret_cast<int *>(p->loss + 1);
+    const float *w = p->wr;
+    float *g = p->grad;
+    EPLL_CU(cudaMemsetAsync(p->loss, 0, 2 * sizeof(float), st));
+    k_mlp_gather<<<(B + 3) / 4, 128, 0, st>>>(d.images, d.n_img, d.H, d.W, d.img_idx, d.anchors, d.log_ib, d.sel,
+                                              d.n_all, B, p->X, p->cond, bad);
+    EPLL_CU(cudaGetLastError());
+    const long HB = (long)B * HID;
+    const int eb = (int)((HB + 255) / 256);
+    // forward
+    if ((s = gemm(p->X, PD, 1, w + OFF_W1, 1, PD, p->A1, HID, B, HID, PD, st))) return s;
+    k_bias_gelu<<<eb, 256, 0, st>>>(p->A1, w + OFF_B1, w + OFF_WB, p->cond, B, p->H1);
+    if ((s = gemm(p->H1, HID, 1, w + OFF_W2, 1, HID, p->A2, HID, B, HID, HID, st))) return s;
+    k_bias_gelu<<<eb, 256, 0, st>>>(p->A2, w + OFF_B2, nullptr, nullptr, B, p->H2);
+    if ((s = gemm(p->H2, HID, 1, w + OFF_W3, 1, HID, p->L, K, B, K, HID, st))) return s;
+    k_softmax_ce<<<(B + 127) / 128, 128, 0, st>>>(p->L, w + off_b3(K), d.labels, d.sel, d.n_all, B, K, p->loss,
+                                                  bad);
+    EPLL_CU(cudaGetLastError());
+    // backward (p->L now holds dL)
+    if ((s = gemm(p->L, 1, K, p->H2, HID, 1, g + OFF_W3, HID, K, HID, B, st))) return s;    // dW3 = dL^T H2
+    k_colsum<<<(K + 127) / 128, 128, 0, st>>>(p->L, B, K, nullptr, g + off_b3(K));
+    if ((s = gemm(p->L, K, 1, w + OFF_W3, HID, 1, p->dH, HID, B, HID, K, st))) return s;    // dH2 = dL W3
+    k_gelu_back<<<eb, 256, 0, st>>>(p->dH, p->A2, HB);                                      // dA2
+    if ((s = gemm(p->dH, 1, HID, p->H1, HID, 1, g + OFF_W2, HID, HID, HID, B, st))) return s;  // dW2
+    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dH, B, HID, nullptr, g + OFF_B2);
+    if ((s = gemm(p->dH, HID, 1, w + OFF_W2, HID, 1, p->dA, HID, B, HID, HID, st))) return s;  // dH1
+    k_gelu_back<<<eb, 256, 0, st>>>(p->dA, p->A1, HB);                                         // dA1
+    if ((s = gemm(p->dA, 1, HID, p->X, PD, 1, g + OFF_W1, PD, HID, PD, B, st))) return s;     // dW1
+    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dA, B, HID, nullptr, g + OFF_B1);
+    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dA, B, HID, p->cond, g + OFF_WB);
+    EPLL_CU(cudaGetLastError());
+    return EPLL_OK;
+}
+
+static epll_status refresh(epll_proposal *p, cudaStream_t st)
+{
+    k_round_weights<<<(int)((p->np + 255) / 256), 256, 0, st>>>(p->theta, (long)p->np, p->K, p->wr, p->W1b,
+                                                                 p->W2b, p->W3b);
+    EPLL_CU(cudaGetLastError());
+    return EPLL_OK;
+}
+
+// ============================================================================
+// Inference: one tcgen05 kernel per layer.  A CTA takes 128 rows; the layer's
+// whole weight matrix (N = 256 outputs, K = 64 * KC inputs) and the rows' tile
+// are loaded by TMA, KC * 4 MMAs accumulate 128 x 256 in TMEM, and the four
+// warps (one per TMEM lane quarter, one thread per row) run the epilogue:
+//   EPI 1: v = in_scale * acc + bias + cond * wb; out = BF16(gelu(v)) (row of 256),
+//          with in_scale = sqrt(beta), cond = log(1/beta) when ibeta is given;
+//   EPI 2: v = acc + bias over the first nout columns; the top-m (m <= 8)
+//          indices and their softmax mass.
+// ============================================================================
+constexpr int MT = 128;
+constexpr int TOPM_MAX = 8;
+
+template <int KC>
+struct MlpCfg {
+    static constexpr int A_SUB = MT * 128;     // 16 KB per 64-wide K chunk
+    static constexpr int B_SUB = HID * 128;    // 32 KB per 64-wide K chunk
+    static constexpr int SMEM = 1024 + KC * (A_SUB + B_SUB) + 256;
+    // at most two CTAs per SM, so that their 256-column TMEM allocations fit in 512
+    static constexpr int LAUNCH_SMEM = SMEM > 80 * 1024 ? SMEM : 80 * 1024;
+};
+
+template <int KC, int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_mlp_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int rows,
+         const float *__restrict__ bias, const float *__restrict__ wb, const float *__restrict__ ibeta, int nout,
+         int topm, uint16_t *__restrict__ out_h, int *__restrict__ cand, float *__restrict__ pmass,
+         int *__restrict__ err)
+{
+    using C = MlpCfg<KC>;
+    const int m0 = blockIdx.x * MT;
+    if (m0 >= rows) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = smem, *sB = smem + KC * C::A_SUB;
+    unsigned long long *bars = (unsigned long long *)(sB + KC * C::B_SUB);  // [0] loads, [1] mma
+    uint32_t *tslot = (uint32_t *)(bars + 2);
+    volatile int *abort_flag = (volatile int *)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (threadIdx.x == 0) {
+        const uint32_t lb = smem_u32(&bars[0]);
+        mbar_expect_tx(lb, KC * (C::A_SUB + C::B_SUB));
+        for (int c = 0; c < KC; ++c) {
+            tma_load_2d(smem_u32(sA + c * C::A_SUB), &mapA, 64 * c, m0, lb);
+            tma_load_2d(smem_u32(sB + c * C::B_SUB), &mapB, 64 * c, 0, lb);
+        }
+        if (mbar_wait(lb, 0, abort_flag)) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_f16(MT, HID, 1);
+            for (int c = 0; c < KC; ++c)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t off = (uint32_t)(k * 32);
+                    mma_f16(tbase, sdesc_sw128(smem_u32(sA + c * C::A_SUB) + off),
+                            sdesc_sw128(smem_u32(sB + c * C::B_SUB) + off), idesc, (c | k) ? 1u : 0u);
+                }
+            mma_commit(smem_u32(&bars[1]));
+        }
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(smem_u32(&bars[1]), 0, abort_flag);
+    tc_fence_after();
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    if (ok) {
+        if constexpr (EPI == 1) {
+            // first layer: W1 (sqrt(beta) z) = sqrt(beta) (W1 z), log(1/beta) through wb
+            const float ib = ibeta ? *ibeta : 1.0f;
+            const float in_scale = ibeta ? 1.0f / sqrtf(ib) : 1.0f, cond = ibeta ? logf(ib) : 0.0f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < HID; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(taddr + (uint32_t)c0, r);
+                tmem_wait(r);
+                uint32_t packed[16];
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    float v0 = __uint_as_float(r[j]) * in_scale + bias[c0 + j];
+                    float v1 = __uint_as_float(r[j + 1]) * in_scale + bias[c0 + j + 1];
+                    if (wb) {
+                        v0 = fmaf(cond, wb[c0 + j], v0);
+                        v1 = fmaf(cond, wb[c0 + j + 1], v1);
+                    }
+                    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(gelu_f(v0)));
+                    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(gelu_f(v1)));
+                    packed[j / 2] = lo | (hi << 16);
+                }
+                if (row < rows) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(out_h + (size_t)row * HID + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                }
+            }
+        } else {
+            float tv[TOPM_MAX];
+            int ti[TOPM_MAX];
+#pragma unroll
+            for (int q = 0; q < TOPM_MAX; ++q) {
+                tv[q] = -FLT_MAX;
+                ti[q] = 0;
+            }
+            float mx = -FLT_MAX, se = 0.0f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < nout; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(taddr + (uint32_t)c0, r);
+                tmem_wait(r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    if (col >= nout) break;
+                    const float v = __uint_as_float(r[j]) + bias[col];
+                    if (v > mx) {
+                        se = se * expf(mx - v) + 1.0f;
+                        mx = v;
+                    } else {
+                        se += expf(v - mx);
+                    }
+                    if (v > tv[TOPM_MAX - 1]) {  // insertion into the sorted list
+                        float cv = v;
+                        int ci = col;
+#pragma unroll
+                        for (int q = 0; q < TOPM_MAX; ++q) {
+                            if (cv > tv[q]) {
+                                const float t1 = tv[q];
+                                const int t2 = ti[q];
+                                tv[q] = cv;
+                                ti[q] = ci;
+                                cv = t1;
+                                ci = t2;
+                            }
+                        }
+                    }
+                }
+            }
+            if (row < rows) {
+                float mass = 0.0f;
+#pragma unroll
+                for (int q = 0; q < TOPM_MAX; ++q)
+                    if (q < topm) {
+                        mass += expf(tv[q] - mx);
+                        cand[(size_t)row * topm + q] = ti[q];
+                    }
+                pmass[row] = mass / se;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase) : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+// ============================================================================
+// Exact FP32 scores of (patch, candidate) pairs, grouped by component: a block
+// takes one work item (up to 128 pairs of one component), stages Ubar_k, and
+// computes C = Z Ubar_k register-tiled (8 x 8 per thread); the score of Eq. 14
+// sums the eight column groups of a row with lane shuffles.
+// ============================================================================
+constexpr int PS_T = 128;
+// relative FP32 error bound of a proposal's score (64-term dot products, as
+// the SIMT selection, with a factor 2 of margin for the different order)
+constexpr float PROP_REL = 2e-5f;
+constexpr int PS_LDZ = PS_T + 4;
+
+struct PropSmem {
+    float Zt[PD][PS_LDZ];
+    float Us[PD][PD];
+    float qs[PD];
+    float zzs[PS_T];
+    int anchor[PS_T];
+};
+
+__global__ void __launch_bounds__(PS_T)
+k_prop_score(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+             const int *__restrict__ perm, const int4 *__restrict__ items, int topm, int Rtot,
+             const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B, Tables tab,
+             float *__restrict__ pscore)
+{
+    extern __shared__ __align__(16) unsigned char ps_raw[];
+    PropSmem &sm = *reinterpret_cast<PropSmem *>(ps_raw);
+    if ((int)blockIdx.x >= items[0].w) return;
+    const int4 it = items[1 + blockIdx.x];
+    const int k = it.x, first = it.y, cnt_p = it.z;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int o = roff[k], r = rk_[k];
+    if (tid < cnt_p) {
+        const int i = perm[first + tid] / topm;
+        sm.anchor[tid] = anchors ? anchors[i] : i;
+    }
+    for (int idx = tid; idx < PD * PD; idx += PS_T) {
+        const int e = idx >> 6, j = idx & 63;
+        sm.Us[e][j] = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
+    }
+    if (tid < PD) sm.qs[tid] = tid < r ? tab.q_hi[o + tid] : 0.0f;
+    __syncthreads();
+    for (int p0 = w * 32; p0 < w * 32 + 32; p0 += 4) {
+        float x0[4], x1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x0[u] = x1[u] = 0.0f;
+            if (p0 + u < cnt_p) {
+                const int a = sm.anchor[p0 + u];
+                const int ai = a / W, aj = a % W;
+                int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
+                if (r0 >= H) r0 -= H;
+                if (r1 >= H) r1 -= H;
+                if (c >= W) c -= W;
+                x0[u] = xhat[(size_t)r0 * W + c];
+                x1[u] = xhat[(size_t)r1 * W + c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u;
+            float s = x0[u] + x1[u];
+#pragma unroll
+            for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
+            const float m = s * (1.0f / PD);
+            const float z0 = x0[u] - m, z1 = x1[u] - m;
+            float zz = fmaf(z0, z0, z1 * z1);
+#pragma unroll
+            for (int q = 16; q > 0; q >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, q);
+            sm.Zt[lane][p] = p < cnt_p ? z0 : 0.0f;
+            sm.Zt[lane + 32][p] = p < cnt_p ? z1 : 0.0f;
+            if (lane == 0) sm.zzs[p] = zz;
+        }
+    }
+    __syncthreads();
+    const int pg = tid >> 3, cg = tid & 7;
+    float part[8] = {};
+    if (8 * cg < r) {
+        float acc[8][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+        for (int e = 0; e < PD; ++e) {
+            const float4 z0 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg]);
+            const float4 z1 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg + 4]);
+            const float4 u0 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg]);
+            const float4 u1 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg + 4]);
+            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(zv[a], uv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) part[a] = fmaf(sm.qs[8 * cg + b] * acc[a][b], acc[a][b], part[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        float v = part[a];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        const int p = 8 * pg + a;
+        if (cg == 0 && p < cnt_p)
+            pscore[perm[first + p]] = tab.cst_hi[k] + tab.t_hi[k] * sm.zzs[p] + v;
+    }
+}
+
+// Per patch: best and second-best rescored candidate (lowest index on ties);
+// undecided patches (little proposal mass or an FP32 near-tie) are listed for
+// the exhaustive pass.
+__global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, const float *__restrict__ pscore,
+                               const float *__restrict__ pmass, float pmin, const float *__restrict__ zz,
+                               const float *__restrict__ tmax, float tau_abs, float tau_rel,
+                               int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
+                               int *__restrict__ nflag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s1 = FLT_MAX, s2 = FLT_MAX;
+    int k1 = 0x7fffffff;
+    for (int q = 0; q < topm; ++q) {
+        const int k = cand[(size_t)i * topm + q];
+        const float s = pscore[(size_t)i * topm + q];
+        if (s < s1 || (s == s1 && k < k1)) {
+            s2 = s1;
+            s1 = s;
+            k1 = k;
+        } else if (s < s2) {
+            s2 = s;
+        }
+    }
+    kstar[i] = k1;
+    const float gp = s2 - s1;
+    gap[i] = gp;
+    const bool unsure = !(pmass[i] >= pmin) || !(gp >= tau_abs + tau_rel * zz[i] * tmax[0]);
+    if (unsure) flag[atomicAdd(nflag, 1)] = i;
+}
+
+template <int KC, int EPI>
+static epll_status launch_layer(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &b, int rows,
+                                const float *bias, const float *wb, const float *ibeta, int nout, int topm,
+                                uint16_t *out_h, int *cand, float *pmass, cudaStream_t st)
+{
+    using C = MlpCfg<KC>;
+    auto kern = k_mlp_tc<KC, EPI>;
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::LAUNCH_SMEM));
+        attr = true;
+    }
+    kern<<<(rows + MT - 1) / MT, 128, C::LAUNCH_SMEM, st>>>(a, b, rows, bias, wb, ibeta, nout, topm, out_h, cand,
+                                                           pmass, cnt(g, CNT_ERR));
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+static epll_status ensure_prop_ws(epll_gmm *g, int n)
+{
+    Workspace &ws = g->ws;
+    const size_t N = ws.capN;
+    if (ws.H1b && ws.prop_cap >= N) return EPLL_OK;
+    void *ptrs[] = {ws.H1b, ws.H2b, ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    const size_t rows = ws.zrows;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **q, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(q, bytes); };
+    A((void **)&ws.H1b, rows * HID * 2); A((void **)&ws.H2b, rows * HID * 2);
+    A((void **)&ws.cand, N * TOPM_MAX * 4); A((void **)&ws.pmass, N * 4); A((void **)&ws.pperm, N * TOPM_MAX * 4);
+    A((void **)&ws.pitems, (2 + N * TOPM_MAX / 128 + (size_t)g->K) * sizeof(int4));
+    A((void **)&ws.pscore, N * TOPM_MAX * 4);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EPLL_ENOMEM, std::string("proposal workspace: ") + cudaGetErrorString(e));
+    }
+    ws.prop_cap = N;
+    (void)n;
+    return EPLL_OK;
+}
+
+epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                 const float *ibeta, cudaStream_t st)
+{
+    const epll_proposal *p = g->prop;
+    Workspace &ws = g->ws;
+    epll_status s;
+    if ((s = ensure_prop_ws(g, n))) return s;
+    const int rows = (n + MT - 1) / MT * MT;
+    // DC-free patches as BF16 operands (and |z|^2)
+    if ((s = launch_extract_bf16(g, xhat, H, W, anchors, n, st))) return s;
+    CUtensorMap a1, w1, a2, w2, a3, w3;
+    if ((s = make_map(&a1, ws.Zb, rows, MT))) return s;
+    if ((s = make_map(&w1, p->W1b, HID, HID))) return s;
+    if ((s = make_map_wide(&a2, ws.H1b, rows, MT, HID))) return s;
+    if ((s = make_map_wide(&w2, p->W2b, HID, HID, HID))) return s;
+    if ((s = make_map_wide(&a3, ws.H2b, rows, MT, HID))) return s;
+    if ((s = make_map_wide(&w3, p->W3b, HID, HID, HID))) return s;
+    if ((s = launch_layer<1, 1>(g, a1, w1, n, p->wr + OFF_B1, p->wr + OFF_WB, ibeta, HID, 0, ws.H1b, nullptr,
+                                nullptr, st)))
+        return s;
+    if ((s = launch_layer<4, 1>(g, a2, w2, n, p->wr + OFF_B2, nullptr, nullptr, HID, 0, ws.H2b, nullptr, nullptr,
+                                st)))
+        return s;
+    return launch_layer<4, 2>(g, a3, w3, n, p->wr + off_b3(p->K), nullptr, nullptr, p->K, g->prop_topm, nullptr,
+                              ws.cand, ws.pmass, st);
+}
+
+epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                   float tau_abs, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int topm = g->prop_topm;
+    epll_status s;
+    if ((s = launch_proposal_topm(g, xhat, H, W, anchors, n, g->tab.ibeta, st))) return s;
+    // exact FP32 scores of the proposed (patch, component) pairs
+    const int npairs = n * topm;
+    if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st))) return s;
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(k_prop_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(PropSmem)));
+        attr = true;
+    }
+    const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
+    k_prop_score<<<max_items, PS_T, sizeof(PropSmem), st>>>(xhat, H, W, anchors, ws.pperm, ws.pitems, topm, g->Rtot,
+                                                            g->d_roff, g->d_r, g->d_B, g->tab, ws.pscore);
+    EPLL_LAUNCHED(g);
+    int *nflag1 = cnt(g, CNT_NFLAG1);
+    EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
+    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, ws.pscore, ws.pmass, g->prop_pmin, ws.zz,
+                                                   g->tab.tmax, tau_abs, PROP_REL, ws.kstar, ws.gap, ws.flag1,
+                                                   nflag1);
+    EPLL_LAUNCHED(g);
+    // exhaustive split-BF16 pass over the undecided patches
+    return launch_split_pass(g, xhat, H, W, anchors, n, ws.flag1, nflag1, tau_abs, st);
+}
+
+}  // namespace epll
+
+using namespace epll;
+
+extern "C" {
+
+size_t epll_proposal_size(int K) { return K >= 1 ? prop_size(K) : 0; }
+
+void epll_proposal_free(epll_proposal *p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {p->theta, p->mom1, p->mom2, p->grad, p->wr, p->W1b, p->W2b, p->W3b, p->X, p->cond,
+                    p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA, p->loss};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+epll_status epll_proposal_create(int K, uint64_t seed, epll_proposal **out)
+{
+    if (!out) return fail(EPLL_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (K < 2 || K > HID) return fail(EPLL_EINVAL, "proposal networks serve 2..256 components");
+    epll_proposal *p = new epll_proposal();
+    p->K = K;
+    p->np = prop_size(K);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **q, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(q, bytes); };
+    A((void **)&p->theta, p->np * 4); A((void **)&p->mom1, p->np * 4); A((void **)&p->mom2, p->np * 4);
+    A((void **)&p->grad, p->np * 4); A((void **)&p->wr, p->np * 4);
+    A((void **)&p->W1b, HID * PD * 2); A((void **)&p->W2b, HID * HID * 2); A((void **)&p->W3b, HID * HID * 2);
+    A((void **)&p->loss, 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        epll_proposal_free(p);
+        return fail(EPLL_ENOMEM, "proposal allocation failed");
+    }
+    // He-style initialisation from counter-based draws (splitmix64 + Box-Muller)
+    std::vector<float> th(p->np, 0.0f);
+    auto mix = [](uint64_t z) {
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        return z ^ (z >> 31);
+    };
+    auto normal = [&](uint64_t i) {
+        const double u1 = ((mix(seed + 2 * i + 1) >> 11) + 0.5) * 0x1.0p-53;
+        const double u2 = ((mix(seed + 2 * i + 2) >> 11) + 0.5) * 0x1.0p-53;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    for (size_t i = OFF_W1; i < OFF_B1; ++i) th[i] = (float)(normal(i) * std::sqrt(2.0 / PD));
+    for (size_t i = OFF_W2; i < OFF_B2; ++i) th[i] = (float)(normal(i) * std::sqrt(2.0 / HID));
+    for (size_t i = OFF_W3; i < off_b3(K); ++i) th[i] = (float)(normal(i) * std::sqrt(1.0 / HID));
+    auto C = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    C(cudaMemcpy(p->theta, th.data(), p->np * 4, cudaMemcpyHostToDevice));
+    C(cudaMemset(p->mom1, 0, p->np * 4)); C(cudaMemset(p->mom2, 0, p->np * 4));
+    C(cudaMemset(p->W3b, 0, HID * HID * 2));
+    if (e != cudaSuccess || refresh(p, 0) != EPLL_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        epll_proposal_free(p);
+        return fail(EPLL_ECUDA, "proposal initialisation failed");
+    }
+    *out = p;
+    return EPLL_OK;
+}
+
+epll_status epll_proposal_get(const epll_proposal *p, float *params)
+{
+    if (!p || !params) return fail(EPLL_EINVAL, "null argument");
+    EPLL_CU(cudaMemcpy(params, p->theta, p->np * 4, cudaMemcpyDeviceToHost));
+    return EPLL_OK;
+}
+
+epll_status epll_proposal_set(epll_proposal *p, const float *params)
+{
+    if (!p || !params) return fail(EPLL_EINVAL, "null argument");
+    for (size_t i = 0; i < p->np; ++i)
+        if (!std::isfinite(params[i])) return fail(EPLL_EINVAL, "parameters must be finite");
+    EPLL_CU(cudaMemcpy(p->theta, params, p->np * 4, cudaMemcpyHostToDevice));
+    EPLL_CU(cudaMemset(p->mom1, 0, p->np * 4));
+    EPLL_CU(cudaMemset(p->mom2, 0, p->np * 4));
+    p->step = 0;
+    epll_status s = refresh(p, 0);
+    if (s) return s;
+    EPLL_CU(cudaDeviceSynchronize());
+    return EPLL_OK;
+}
+
+static epll_status check_batch(const epll_proposal *p, const Batch &d)
+{
+    if (!p || !d.images || !d.img_idx || !d.anchors || !d.log_ib || !d.labels)
+        return fail(EPLL_EINVAL, "null argument");
+    if (d.n_img < 1 || d.H < PS || d.W < PS || (long long)d.H * d.W > (1LL << 26))
+        return fail(EPLL_EINVAL, "images must be n_img >= 1 of 8 x 8 .. 2^26 pixels");
+    if (d.B < 1 || d.B > (1 << 20)) return fail(EPLL_EINVAL, "batch size must be in 1..2^20");
+    if (d.n_all < d.B || (!d.sel && d.n_all != d.B)) return fail(EPLL_EINVAL, "n_all must be >= B (== B without sel)");
+    return EPLL_OK;
+}
+
+// Reads the loss and the invalid-sample flag (synchronises st).
+static epll_status read_loss(epll_proposal *p, float *loss, cudaStream_t st)
+{
+    float h[2];
+    EPLL_CU(cudaMemcpyAsync(h, p->loss, sizeof(h), cudaMemcpyDeviceToHost, st));
+    EPLL_CU(cudaStreamSynchronize(st));
+    int bad;
+    std::memcpy(&bad, &h[1], sizeof(int));
+    if (bad) return fail(EPLL_EINVAL, "a sample had an out-of-range image index, anchor, label or log(1/beta)");
+    *loss = h[0];
+    return EPLL_OK;
+}
+
+epll_status epll_proposal_grad(epll_proposal *p, const float *images, int n_img, int H, int W, const int *img_idx,
+                               const int *anchors, const float *log_ib, const int *labels, const int *sel,
+                               int n_all, int B, float *grad, float *loss, void *stream)
+{
+    const Batch d{images, n_img, H, W, img_idx, anchors, log_ib, labels, sel, n_all, B};
+    epll_status s;
+    if ((s = check_batch(p, d))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = forward_backward(p, d, st))) return s;
+    if (grad) EPLL_CU(cudaMemcpyAsync(grad, p->grad, p->np * 4, cudaMemcpyDeviceToDevice, st));
+    return loss ? read_loss(p, loss, st) : EPLL_OK;
+}
+
+epll_status epll_proposal_train(epll_proposal *p, const float *images, int n_img, int H, int W,
+                                const int *img_idx, const int *anchors, const float *log_ib, const int *labels,
+                                const int *sel, int n_all, int B, float lr, float weight_decay, float *loss,
+                                void *stream)
+{
+    const Batch d{images, n_img, H, W, img_idx, anchors, log_ib, labels, sel, n_all, B};
+    epll_status s;
+    if ((s = check_batch(p, d))) return s;
+    if (!(lr > 0.0f) || !std::isfinite(lr) || !(weight_decay >= 0.0f) || !std::isfinite(weight_decay))
+        return fail(EPLL_EINVAL, "bad learning rate or weight decay");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = forward_backward(p, d, st))) return s;
+    ++p->step;
+    const float c1 = 1.0f - (float)std::pow(0.9, (double)p->step), c2 = 1.0f - (float)std::pow(0.999, (double)p->step);
+    k_adamw<<<(int)((p->np + 255) / 256), 256, 0, st>>>(p->theta, p->grad, p->mom1, p->mom2, (long)p->np, p->K, lr,
+                                                         weight_decay, c1, c2);
+    EPLL_CU(cudaGetLastError());
+    if ((s = refresh(p, st))) return s;
+    return loss ? read_loss(p, loss, st) : EPLL_OK;
+}
+
+__global__ void k_set_f32(float *p, float v) { *p = v; }
+
+epll_status epll_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                               double beta, int *cand, float *pmass, void *stream)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (!g->prop) return fail(EPLL_EINVAL, "no proposal network attached");
+    if (!xhat || !cand) return fail(EPLL_EINVAL, "null pointer");
+    if (H < PS || W < PS || (long long)H * W > (1LL << 26)) return fail(EPLL_EINVAL, "bad image size");
+    if (!anchors) n = H * W;
+    if (n < 1 || (long long)n > (long long)H * W) return fail(EPLL_EINVAL, "n must be in 1..H*W");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(EPLL_EINVAL, "beta must be positive");
+    epll_status s;
+    if ((s = ensure_workspace(g, (size_t)H * W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &ws = g->ws;
+    EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
+    float *ib = ws.red;  // scratch scalar
+    k_set_f32<<<1, 1, 0, st>>>(ib, (float)(1.0 / beta));
+    EPLL_LAUNCHED(g);
+    if ((s = launch_proposal_topm(g, xhat, H, W, anchors, n, ib, st))) return s;
+    const int topm = g->prop_topm;
+    EPLL_CU(cudaMemcpyAsync(cand, ws.cand, sizeof(int) * (size_t)n * topm, cudaMemcpyDeviceToDevice, st));
+    if (pmass) EPLL_CU(cudaMemcpyAsync(pmass, ws.pmass, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    return EPLL_OK;
+}
+
+epll_status epll_gmm_attach_proposal(epll_gmm *g, const epll_proposal *p, int topm, float pmin)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (p && p->K != g->K) return fail(EPLL_EINVAL, "proposal and model have different K");
+    if (p && (topm < 1 || topm > TOPM_MAX || topm > p->K)) return fail(EPLL_EINVAL, "topm must be in 1..min(8, K)");
+    if (!(pmin >= 0.0f && pmin <= 1.0f)) return fail(EPLL_EINVAL, "pmin must be in [0, 1]");
+    g->prop = p;
+    g->prop_topm = topm;
+    g->prop_pmin = pmin;
+    return EPLL_OK;
+}
+
+}  // extern "C"

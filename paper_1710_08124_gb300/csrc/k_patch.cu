@@ -575,8 +575,7 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
     }
 }
 
-epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
-                            int n, cudaStream_t st)
+epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     const int K = g->K;
@@ -584,12 +583,22 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
     EPLL_CU(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)K, st));
     int hb = (n + 255) / 256;
     if (hb > 152 * 2) hb = 152 * 2;
-    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(ws.kstar, n, K, counts);
+    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(keys, n, K, counts);
     EPLL_LAUNCHED(g);
-    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, ws.items);
+    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, items);
     EPLL_LAUNCHED(g);
-    k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(ws.kstar, n, K, counts, ws.perm);
+    k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(keys, n, K, counts, perm);
     EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
+                            int n, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int K = g->K;
+    epll_status gs = group_by_component(g, ws.kstar, n, ws.perm, ws.items, st);
+    if (gs) return gs;
     static bool attr = false;
     if (!attr) {
         EPLL_CU(cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize,

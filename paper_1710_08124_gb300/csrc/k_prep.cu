@@ -74,6 +74,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
         tab.t_lo[k] = (float)(t - (double)th);
         tab.gp[k] = (float)gP;
         tab.sgn[k] = rk < PD ? -1.0f : 1.0f;
+        if (k == 0) tab.ibeta[0] = (float)ib;
         // error scale of the score: largest 1/nu of this component
         const double numin = rk < PD ? nuP : S[(size_t)k * PD + PD - 1] + ib;
         atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int((float)(1.0 / numin)));

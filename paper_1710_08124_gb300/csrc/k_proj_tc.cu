@@ -19,6 +19,7 @@
 // Patches whose top-2 gap is below tau_abs + tau_rel |z|^2 max_k(1/nu_min)
 // (the error bound of the arithmetic) go to the compensated rescoring.
 #include "epll_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -29,203 +30,6 @@
 #include <mutex>
 
 namespace epll {
-
-// ---------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Every wait is bounded: after ~2 s (clock64 at <= 2.1 GHz) the waiter raises
-// the CTA's abort flag; every other wait polls the flag and gives up too, so
-// the CTA reaches its teardown (TMEM release) and the host sees the error.
-constexpr long long WAIT_CYCLES = 4000000000LL;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
-{
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_CYCLES) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
-{
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-#define EPLL_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
-                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
-#define EPLL_W8(i) "+r"(r[i + 0]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), \
-                   "+r"(r[i + 4]), "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7])
-
-// 32 consecutive accumulator columns of this thread's TMEM lane (row).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : EPLL_R8(0), EPLL_R8(8), EPLL_R8(16), EPLL_R8(24)
-        : "r"(taddr));
-}
-// Waits for this thread's outstanding tcgen05.ld; the registers are tied to
-// the wait so no use of them is scheduled before it.
-__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_W8(0), EPLL_W8(8), EPLL_W8(16), EPLL_W8(24)::"memory");
-}
-
-// 64 / 128 consecutive accumulator columns in one instruction (one round trip).
-#define EPLL_OPS64(M) M(0), M(8), M(16), M(24), M(32), M(40), M(48), M(56)
-#define EPLL_OPS128(M) EPLL_OPS64(M), M(64), M(72), M(80), M(88), M(96), M(104), M(112), M(120)
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : EPLL_OPS64(EPLL_R8)
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait64(uint32_t (&r)[64])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_OPS64(EPLL_W8)::"memory");
-}
-__device__ __forceinline__ void tmem_ld128(uint32_t taddr, uint32_t (&r)[128])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x128.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,"
-        "%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,"
-        "%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,"
-        "%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,"
-        "%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, [%128];"
-        : EPLL_OPS128(EPLL_R8)
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait128(uint32_t (&r)[128])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_OPS128(EPLL_W8)::"memory");
-}
-template <int NC>
-__device__ __forceinline__ void tmem_ld_all(uint32_t taddr, uint32_t (&r)[NC])
-{
-    if constexpr (NC == 64) {
-        tmem_ld64(taddr, r);
-        tmem_wait64(r);
-    } else {
-        static_assert(NC == 128, "64 or 128 columns");
-        tmem_ld128(taddr, r);
-        tmem_wait128(r);
-    }
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile written by TMA
-// with the 128-byte swizzle: rows of 64 16-bit elements (128 B), 8-row
-// groups 1024 B apart (stride byte offset), leading byte offset unused for
-// this layout (encoded 1), descriptor version 1, layout type 2 = SWIZZLE_128B.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-// Same for 8-bit operands: rows of 64 bytes with the 64-byte swizzle, 8-row
-// groups 512 B apart, layout type 4 = SWIZZLE_64B.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
-    return d;
-}
-__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (D format
-// 1 at bit 4), A/B format (0 = F16, 1 = BF16) at bits 7 and 10, both
-// operands K-major, N/8 at bit 17, M/16 at bit 24.  For kind::f8f6f4 the same
-// fields hold the 8-bit formats (0 = E4M3).
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int fmt)
-{
-    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
 
 // ---------------------------------------------------------------- extraction
 // DC-free patches as 16-bit operands (hi, and lo for the split variant) and
@@ -627,46 +431,6 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
-// ---------------------------------------------------------------- host side
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
-// Row-major [rows][64] 16-bit matrix (8-bit when eb = 1), box of box_rows rows x
-// 64 elements, 128-byte swizzle (64-byte for 8-bit rows).
-static epll_status make_map(CUtensorMap *m, const void *base, int rows, int box_rows, int eb = 2)
-{
-    auto fn = encode_fn();
-    if (!fn) {
-        set_error("cuTensorMapEncodeTiled entry point unavailable");
-        return EPLL_ECUDA;
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)PD, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)PD * eb};
-    cuuint32_t box[2] = {(cuuint32_t)PD, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, eb == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
-                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    eb == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-        return EPLL_ECUDA;
-    }
-    return EPLL_OK;
-}
-
 template <int BN, int NT, int RR, bool DUMP = false>
 static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                              const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
@@ -804,7 +568,28 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
                                      st)))
             return s;
     }
-    // ---- split-BF16 pass over the rows the first pass could not decide
+    return launch_split_pass(g, xhat, H, W, anchors, n, flag1, nflag1, tau_abs, st);
+}
+
+// Split-BF16 pass over the rows listed in flag1 (device count nflag1): their
+// kstar / gap are overwritten and the rows it cannot decide go to ws.flag.
+epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int rows = (n + TC_M - 1) / TC_M * TC_M;
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, 1, 0, ws.Zb, nullptr,
+                                                 ws.zz, nullptr);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                              const int *flag1, const int *nflag1, float tau_abs, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int rows = (n + TC_M - 1) / TC_M * TC_M;
+    epll_status s;
     uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
     k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, flag1, nflag1, 1, 1, Z2hi, Z2lo,
                                                  ws.zz2, nullptr);

@@ -65,3 +65,23 @@ def test_options_default(L):
     o = ep._Options()
     L.epll_options_default(C.byref(o))
     assert o.precision == ep.FP32 and o.subset == ep.SUBSET_ALL and o.cg_iters == 100 and o.tie_gap < 0
+    assert o.select == ep.SELECT_EXHAUSTIVE
+
+
+def test_proposal_layout_and_validation(L):
+    from oracle import mlp
+    for K in (2, 20, 200, 256):
+        assert L.epll_proposal_size(K) == mlp.n_params(K)
+    assert L.epll_proposal_size(0) == 0
+    h = C.c_void_p()
+    assert L.epll_proposal_create(1, 0, C.byref(h)) == ep.EINVAL and not h.value
+    assert L.epll_proposal_create(257, 0, C.byref(h)) == ep.EINVAL and not h.value
+    assert L.epll_proposal_create(4, 0, None) == ep.EINVAL
+    assert L.epll_gmm_attach_proposal(None, None, 4, C.c_float(0.0)) == ep.EINVAL
+    assert L.epll_proposal_topm(None, None, 64, 64, None, 0, 1.0, None, None, None) == ep.EINVAL
+    assert L.epll_proposal_grad(None, None, 1, 64, 64, None, None, None, None, None, 10, 10, None, None,
+                                None) == ep.EINVAL
+    assert L.epll_proposal_train(None, None, 1, 64, 64, None, None, None, None, None, 10, 10, C.c_float(1e-3),
+                                 C.c_float(0.0), None, None) == ep.EINVAL
+    assert L.epll_proposal_get(None, None) == ep.EINVAL
+    L.epll_proposal_free(None)
