@@ -47,7 +47,7 @@ static void free_workspace(Workspace &ws)
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
                     ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
-                    ws.H1b, ws.H2b, ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
+                    ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);

@@ -101,7 +101,6 @@ struct Workspace {
     int planH = 0, planW = 0;
     // learned proposal (allocated on first use)
     size_t prop_cap = 0;
-    uint16_t *H1b = nullptr, *H2b = nullptr;  // [zrows][256] BF16 hidden activations
     int *cand = nullptr;                      // [N][topm] proposed components
     float *pmass = nullptr;                   // [N] softmax mass of the proposals
     int *pperm = nullptr;                     // [N * topm] pairs grouped by component

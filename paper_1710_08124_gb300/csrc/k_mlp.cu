@@ -54,10 +54,29 @@ struct epll_proposal {
 
 namespace epll {
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU in its tanh form: 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).
+constexpr float GELU_A = 0.7978845608028654f, GELU_B = 0.044715f;
+__device__ __forceinline__ float gelu_f(float x)
+{
+    return 0.5f * x * (1.0f + tanhf(GELU_A * fmaf(GELU_B * x, x * x, x)));
+}
 __device__ __forceinline__ float gelu_grad_f(float x)
 {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+    const float t = tanhf(GELU_A * fmaf(GELU_B * x, x * x, x));
+    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * GELU_A * fmaf(3.0f * GELU_B, x * x, 1.0f);
+}
+// Inference form: the hardware tanh approximation (about 11 correct bits,
+// below the BF16 rounding that follows).
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_fast(float x)
+{
+    const float hx = 0.5f * x;
+    return fmaf(hx, tanh_fast(GELU_A * fmaf(GELU_B * x, x * x, x)), hx);
 }
 
 // ============================================================================
@@ -314,52 +333,163 @@ static epll_status refresh(epll_proposal *p, cudaStream_t st)
 }
 
 // ============================================================================
-// Inference: one tcgen05 kernel per layer.  A CTA takes 128 rows; the layer's
-// whole weight matrix (N = 256 outputs, K = 64 * KC inputs) and the rows' tile
-// are loaded by TMA, KC * 4 MMAs accumulate 128 x 256 in TMEM, and the four
-// warps (one per TMEM lane quarter, one thread per row) run the epilogue:
-//   EPI 1: v = in_scale * acc + bias + cond * wb; out = BF16(gelu(v)) (row of 256),
-//          with in_scale = sqrt(beta), cond = log(1/beta) when ibeta is given;
-//   EPI 2: v = acc + bias over the first nout columns; the top-m (m <= 8)
-//          indices and their softmax mass.
+// Inference: the three layers fused in one persistent tcgen05 kernel.  A CTA
+// takes 128-patch tiles in turn; the hidden activations never leave the SM:
+//   warp 0      TMA: the tile's BF16 patches (double buffer) and the weight
+//               matrices as nine 64-wide K chunks (W1; W2 x4; W3 x4) through a
+//               three-slot ring (the weights stay in L2 across tiles);
+//   warp 1      MMA: layer l accumulates 128 x 256 FP32 in TMEM (layers 1, 3 at
+//               columns 0..255, layer 2 at 256..511), K chunk by K chunk as the
+//               epilogue releases the operand chunks;
+//   warps 2..   epilogue, one thread per row and a slice of columns per warp:
+//               layer 1: v = sqrt(beta) acc + b1 + log(1/beta) wb, layer 2:
+//               v = acc + b2, both GELU'd, rounded to BF16 and written to shared
+//               memory in the 128-byte-swizzled K-major layout of the next MMA's
+//               A operand (chunk c is released to the MMA as soon as it is
+//               written, so layer 2's products overlap layer 1's epilogue);
+//               layer 3: logits + b3, each warp's top-m and online softmax
+//               sums, merged across the warps of a row.
+// Every wait is bounded (an abort flag ends all roles; err is raised).
 // ============================================================================
 constexpr int MT = 128;
 constexpr int TOPM_MAX = 8;
+constexpr int FM_S = 3;               // weight ring slots
+constexpr int FM_SLOT = HID * 128;    // 32 KB: [256 rows][64] BF16
+constexpr int FM_ZT = MT * 128;       // 16 KB: [128 rows][64] BF16
+constexpr int FM_H = 4 * FM_ZT;       // 64 KB: [128][256] BF16 as four K chunks
 
-template <int KC>
-struct MlpCfg {
-    static constexpr int A_SUB = MT * 128;     // 16 KB per 64-wide K chunk
-    static constexpr int B_SUB = HID * 128;    // 32 KB per 64-wide K chunk
-    static constexpr int SMEM = 1024 + KC * (A_SUB + B_SUB) + 256;
-    // at most two CTAs per SM, so that their 256-column TMEM allocations fit in 512
-    static constexpr int LAUNCH_SMEM = SMEM > 80 * 1024 ? SMEM : 80 * 1024;
+template <int EW>
+struct FmCfg {
+    static constexpr int THREADS = 32 * (2 + EW);
+    static constexpr int CG = EW / 4;   // column groups per TMEM lane quarter
+    static constexpr int CW = 64 / CG;  // columns per warp and chunk
+    static constexpr int OFF_H = FM_S * FM_SLOT;
+    static constexpr int OFF_Z = OFF_H + FM_H;
+    static constexpr int OFF_BIAS = OFF_Z + 2 * FM_ZT;
+    static constexpr int OFF_BAR = OFF_BIAS + 4 * HID * 4;
+    // full[S], empty[S], zfull[2], zempty[2], hready[4], accfull[3], accfree, mready, mdone
+    static constexpr int NBAR = 2 * FM_S + 4 + 4 + 3 + 3;
+    static constexpr int SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
+    static_assert(CG * MT * (2 * TOPM_MAX + 2) * 4 <= FM_H, "merge scratch must fit in the activation buffer");
 };
 
-template <int KC, int EPI>
-__global__ void __launch_bounds__(128, 1)
-k_mlp_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int rows,
-         const float *__restrict__ bias, const float *__restrict__ wb, const float *__restrict__ ibeta, int nout,
-         int topm, uint16_t *__restrict__ out_h, int *__restrict__ cand, float *__restrict__ pmass,
-         int *__restrict__ err)
+template <int CW>
+static __device__ __forceinline__ void tmem_ld_cw(uint32_t taddr, uint32_t (&r)[CW])
 {
-    using C = MlpCfg<KC>;
-    const int m0 = blockIdx.x * MT;
-    if (m0 >= rows) return;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = smem, *sB = smem + KC * C::A_SUB;
-    unsigned long long *bars = (unsigned long long *)(sB + KC * C::B_SUB);  // [0] loads, [1] mma
-    uint32_t *tslot = (uint32_t *)(bars + 2);
-    volatile int *abort_flag = (volatile int *)(tslot + 1);
+    if constexpr (CW == 32) {
+        tmem_ld32(taddr, r);
+        tmem_wait(r);
+    } else {
+        static_assert(CW == 16, "16 or 32 columns");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : EPLL_R8(0), EPLL_R8(8)
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_W8(0), EPLL_W8(8)::"memory");
+    }
+}
+
+static __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// (v, i) ranks before (w, j): larger logit first, lower index on equal logits
+static __device__ __forceinline__ bool before(float v, int i, float w, int j) { return v > w || (v == w && i < j); }
+
+template <int TM>
+static __device__ __forceinline__ void topm_insert(float (&tv)[TM], int (&ti)[TM], float v, int i)
+{
+    if (!before(v, i, tv[TM - 1], ti[TM - 1])) return;
+#pragma unroll
+    for (int q = 0; q < TM; ++q) {
+        if (before(v, i, tv[q], ti[q])) {
+            const float t1 = tv[q];
+            const int t2 = ti[q];
+            tv[q] = v;
+            ti[q] = i;
+            v = t1;
+            i = t2;
+        }
+    }
+}
+
+// One layer's epilogue for hidden layers: v = scale * acc + bias, GELU,
+// BF16, into chunk c of the activation buffer (swizzled like a TMA
+// SWIZZLE_128B load, so the next layer's MMA reads it as its A operand).
+template <int CW>
+static __device__ __forceinline__ void epi_hidden(uint32_t taddr, int c, int j, int rit, float scale,
+                                                  const float *__restrict__ bias, unsigned char *H)
+{
+    uint32_t r[CW];
+    tmem_ld_cw<CW>(taddr, r);
+    const int col0 = 64 * c + j * CW;
+    uint32_t packed[CW / 2];
+#pragma unroll
+    for (int q = 0; q < CW; q += 4) {
+        const float4 b = *reinterpret_cast<const float4 *>(bias + col0 + q);
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(r[q]), scale, b.x)),
+                                                        gelu_fast(fmaf(__uint_as_float(r[q + 1]), scale, b.y)));
+        const __nv_bfloat162 p1 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(r[q + 2]), scale, b.z)),
+                                                        gelu_fast(fmaf(__uint_as_float(r[q + 3]), scale, b.w)));
+        packed[q / 2] = *reinterpret_cast<const uint32_t *>(&p0);
+        packed[q / 2 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
+    }
+    unsigned char *rowp = H + c * FM_ZT + rit * 128;
+#pragma unroll
+    for (int q = 0; q < CW / 8; ++q) {
+        const int lc = (j * CW * 2) / 16 + q;  // logical 16-byte chunk of the 128-byte row
+        *reinterpret_cast<uint4 *>(rowp + ((lc ^ (rit & 7)) << 4)) =
+            make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+    }
+}
+
+template <int EW, int TM>
+__global__ void __launch_bounds__(32 * (2 + EW), 1)
+k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CUtensorMap mapW1,
+            const __grid_constant__ CUtensorMap mapW2, const __grid_constant__ CUtensorMap mapW3, int n, int K,
+            int n3, const float *__restrict__ wr, const float *__restrict__ ibeta, int topm,
+            int *__restrict__ cand, float *__restrict__ pmass, int *__restrict__ err)
+{
+    using C = FmCfg<EW>;
+    extern __shared__ __align__(1024) unsigned char fm_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)fm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *ring = smem, *Hb = smem + C::OFF_H, *Zb = smem + C::OFF_Z;
+    float *sb1 = reinterpret_cast<float *>(smem + C::OFF_BIAS), *sb2 = sb1 + HID, *sb3 = sb2 + HID;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + C::OFF_BAR);
+    unsigned long long *full = bars, *empty = bars + FM_S, *zfull = bars + 2 * FM_S, *zempty = zfull + 2,
+                       *hready = zempty + 2, *accfull = hready + 4, *accfree = accfull + 3,
+                       *mready = accfree + 1, *mdone = mready + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + C::NBAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (n + MT - 1) / MT;
+
+    // first layer: W1 (sqrt(beta) z) + b1 + log(1/beta) wb = sqrt(beta) (W1 z) + b1'
+    const float ib = ibeta ? *ibeta : 1.0f;
+    const float in_scale = ibeta ? 1.0f / sqrtf(ib) : 1.0f, cond = ibeta ? logf(ib) : 0.0f;
+    for (int i = threadIdx.x; i < HID; i += blockDim.x) {
+        sb1[i] = fmaf(cond, wr[OFF_WB + i], wr[OFF_B1 + i]);
+        sb2[i] = wr[OFF_B2 + i];
+        sb3[i] = i < K ? wr[off_b3(K) + i] : 0.0f;
+    }
     if (threadIdx.x == 0) {
         *abort_flag = 0;
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
+        for (int s = 0; s < FM_S; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&zfull[s]), 1);
+            mbar_init(smem_u32(&zempty[s]), 1);
+        }
+        for (int c = 0; c < 4; ++c) mbar_init(smem_u32(&hready[c]), EW);
+        for (int a = 0; a < 3; ++a) mbar_init(smem_u32(&accfull[a]), 1);
+        mbar_init(smem_u32(accfree), EW);
+        mbar_init(smem_u32(mready), EW);  // every epilogue warp wrote its partial top-m
+        mbar_init(smem_u32(mdone), 4);    // the merging warps (one per lane quarter) read them
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tslot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -367,120 +497,175 @@ k_mlp_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    if (threadIdx.x == 0) {
-        const uint32_t lb = smem_u32(&bars[0]);
-        mbar_expect_tx(lb, KC * (C::A_SUB + C::B_SUB));
-        for (int c = 0; c < KC; ++c) {
-            tma_load_2d(smem_u32(sA + c * C::A_SUB), &mapA, 64 * c, m0, lb);
-            tma_load_2d(smem_u32(sB + c * C::B_SUB), &mapB, 64 * c, 0, lb);
-        }
-        if (mbar_wait(lb, 0, abort_flag)) {
-            tc_fence_after();
-            const uint32_t idesc = idesc_f16(MT, HID, 1);
-            for (int c = 0; c < KC; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t off = (uint32_t)(k * 32);
-                    mma_f16(tbase, sdesc_sw128(smem_u32(sA + c * C::A_SUB) + off),
-                            sdesc_sw128(smem_u32(sB + c * C::B_SUB) + off), idesc, (c | k) ? 1u : 0u);
-                }
-            mma_commit(smem_u32(&bars[1]));
-        }
-    }
-    __syncwarp();
-    const bool ok = mbar_wait(smem_u32(&bars[1]), 0, abort_flag);
-    tc_fence_after();
-    const int row = m0 + 32 * warp + lane;
-    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
-    if (ok) {
-        if constexpr (EPI == 1) {
-            // first layer: W1 (sqrt(beta) z) = sqrt(beta) (W1 z), log(1/beta) through wb
-            const float ib = ibeta ? *ibeta : 1.0f;
-            const float in_scale = ibeta ? 1.0f / sqrtf(ib) : 1.0f, cond = ibeta ? logf(ib) : 0.0f;
-#pragma unroll 1
-            for (int c0 = 0; c0 < HID; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(taddr + (uint32_t)c0, r);
-                tmem_wait(r);
-                uint32_t packed[16];
-#pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    float v0 = __uint_as_float(r[j]) * in_scale + bias[c0 + j];
-                    float v1 = __uint_as_float(r[j + 1]) * in_scale + bias[c0 + j + 1];
-                    if (wb) {
-                        v0 = fmaf(cond, wb[c0 + j], v0);
-                        v1 = fmaf(cond, wb[c0 + j + 1], v1);
-                    }
-                    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(gelu_f(v0)));
-                    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(gelu_f(v1)));
-                    packed[j / 2] = lo | (hi << 16);
-                }
-                if (row < rows) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(out_h + (size_t)row * HID + c0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            tma_prefetch_desc(&mapZ);
+            tma_prefetch_desc(&mapW1);
+            tma_prefetch_desc(&mapW2);
+            tma_prefetch_desc(&mapW3);
+            int L = 0, it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+                const int zb = it & 1, zph = (it >> 1) & 1;
+                if (!mbar_wait(smem_u32(&zempty[zb]), zph ^ 1, abort_flag)) break;
+                mbar_expect_tx(smem_u32(&zfull[zb]), FM_ZT);
+                tma_load_2d(smem_u32(Zb + zb * FM_ZT), &mapZ, 0, tile * MT, smem_u32(&zfull[zb]));
+                for (int q = 0; q < 9; ++q, ++L) {
+                    const int slot = L % FM_S, ph = (L / FM_S) & 1;
+                    if (!mbar_wait(smem_u32(&empty[slot]), ph ^ 1, abort_flag)) break;
+                    const CUtensorMap *m = q == 0 ? &mapW1 : (q < 5 ? &mapW2 : &mapW3);
+                    const int x = q == 0 ? 0 : 64 * ((q - 1) & 3);
+                    mbar_expect_tx(smem_u32(&full[slot]), (q < 5 ? HID : n3) * 128);
+                    tma_load_2d(smem_u32(ring + slot * FM_SLOT), m, x, 0, smem_u32(&full[slot]));
                 }
             }
-        } else {
-            float tv[TOPM_MAX];
-            int ti[TOPM_MAX];
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id256 = idesc_f16(MT, HID, 1), id3 = idesc_f16(MT, n3, 1);
+            int L = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+                const int zb = it & 1, zph = (it >> 1) & 1;
+                if (it > 0) ok = mbar_wait(smem_u32(accfree), (it - 1) & 1, abort_flag);
+                ok = ok && mbar_wait(smem_u32(&zfull[zb]), zph, abort_flag);
+                for (int layer = 0; layer < 3 && ok; ++layer) {
+                    const uint32_t dcol = layer == 1 ? 256u : 0u;
+                    const uint32_t idesc = layer == 2 ? id3 : id256;
+                    const int nchunks = layer == 0 ? 1 : 4;
+                    for (int c = 0; c < nchunks && ok; ++c, ++L) {
+                        const int slot = L % FM_S, ph = (L / FM_S) & 1;
+                        ok = mbar_wait(smem_u32(&full[slot]), ph, abort_flag);
+                        if (ok && layer > 0) ok = mbar_wait(smem_u32(&hready[c]), layer - 1, abort_flag);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a0 = layer == 0 ? smem_u32(Zb + zb * FM_ZT) : smem_u32(Hb + c * FM_ZT);
+                        const uint32_t b0 = smem_u32(ring + slot * FM_SLOT);
 #pragma unroll
-            for (int q = 0; q < TOPM_MAX; ++q) {
+                        for (int k = 0; k < 4; ++k)
+                            mma_f16(tbase + dcol, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
+                                    (c | k) ? 1u : 0u);
+                        mma_commit(smem_u32(&empty[slot]));
+                    }
+                    if (!ok) break;
+                    if (layer == 0) mma_commit(smem_u32(&zempty[zb]));
+                    mma_commit(smem_u32(&accfull[layer]));
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        constexpr int CW = C::CW;
+        const int e = warp - 2, qd = warp & 3, j = e >> 2;
+        const int rit = 32 * qd + lane;
+        const uint32_t tl = tbase + ((uint32_t)(32 * qd) << 16);
+        float *scratch = reinterpret_cast<float *>(Hb);  // [CG][2 TM + 2][128]
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int row = tile * MT + rit;
+            // hidden layers
+            bool ok = true;
+            for (int layer = 0; layer < 2 && ok; ++layer) {
+                ok = mbar_wait(smem_u32(&accfull[layer]), it & 1, abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t ta = tl + (layer ? 256u : 0u) + (uint32_t)(64 * c + j * CW);
+                    epi_hidden<CW>(ta, c, j, rit, layer ? 1.0f : in_scale, layer ? sb2 : sb1, Hb);
+                    fence_proxy_async();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&hready[c]));
+                }
+            }
+            if (ok) ok = mbar_wait(smem_u32(&accfull[2]), it & 1, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            // output layer: this warp's top-m and softmax sums over its columns
+            float tv[TM];
+            int ti[TM];
+#pragma unroll
+            for (int q = 0; q < TM; ++q) {
                 tv[q] = -FLT_MAX;
-                ti[q] = 0;
+                ti[q] = 0x7fffffff;
             }
             float mx = -FLT_MAX, se = 0.0f;
-#pragma unroll 1
-            for (int c0 = 0; c0 < nout; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(taddr + (uint32_t)c0, r);
-                tmem_wait(r);
+            for (int c = 0; c < 4; ++c) {
+                const int col0 = 64 * c + j * CW;
+                if (col0 >= K) break;
+                uint32_t r[CW];
+                tmem_ld_cw<CW>(tl + (uint32_t)col0, r);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
-                    if (col >= nout) break;
-                    const float v = __uint_as_float(r[j]) + bias[col];
-                    if (v > mx) {
-                        se = se * expf(mx - v) + 1.0f;
-                        mx = v;
-                    } else {
-                        se += expf(v - mx);
-                    }
-                    if (v > tv[TOPM_MAX - 1]) {  // insertion into the sorted list
-                        float cv = v;
-                        int ci = col;
-#pragma unroll
-                        for (int q = 0; q < TOPM_MAX; ++q) {
-                            if (cv > tv[q]) {
-                                const float t1 = tv[q];
-                                const int t2 = ti[q];
-                                tv[q] = cv;
-                                ti[q] = ci;
-                                cv = t1;
-                                ci = t2;
-                            }
+                for (int q = 0; q < CW; ++q) {
+                    const int col = col0 + q;
+                    if (col < K) {
+                        const float v = __uint_as_float(r[q]) + sb3[col];
+                        if (v > mx) {
+                            se = fmaf(se, __expf(mx - v), 1.0f);
+                            mx = v;
+                        } else {
+                            se += __expf(v - mx);
                         }
+                        // columns arrive in increasing order: a tie never displaces
+                        if (v > tv[TM - 1]) topm_insert<TM>(tv, ti, v, col);
                     }
                 }
             }
-            if (row < rows) {
-                float mass = 0.0f;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(accfree));
+            // merge the column groups of each row (scratch in the activation
+            // buffer: the last layer's products have read it)
+            constexpr int SW = 2 * TM + 2;
+            if (C::CG > 1) {
+                float *my = scratch + (size_t)j * SW * MT + rit;
 #pragma unroll
-                for (int q = 0; q < TOPM_MAX; ++q)
-                    if (q < topm) {
-                        mass += expf(tv[q] - mx);
-                        cand[(size_t)row * topm + q] = ti[q];
-                    }
-                pmass[row] = mass / se;
+                for (int q = 0; q < TM; ++q) {
+                    my[q * MT] = tv[q];
+                    my[(TM + q) * MT] = __int_as_float(ti[q]);
+                }
+                my[2 * TM * MT] = mx;
+                my[(2 * TM + 1) * MT] = se;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(mready));
             }
+            if (j == 0) {
+                if (C::CG > 1 && !mbar_wait(smem_u32(mready), it & 1, abort_flag)) break;
+                for (int jj = 1; jj < C::CG; ++jj) {
+                    const float *o = scratch + (size_t)jj * SW * MT + rit;
+                    const float omx = o[2 * TM * MT], ose = o[(2 * TM + 1) * MT];
+                    const float M = fmaxf(mx, omx);
+                    se = se * __expf(mx - M) + ose * __expf(omx - M);
+                    mx = M;
+#pragma unroll
+                    for (int q = 0; q < TM; ++q) topm_insert<TM>(tv, ti, o[q * MT], __float_as_int(o[(TM + q) * MT]));
+                }
+                if (row < n) {
+                    float mass = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < TM; ++q)
+                        if (q < topm) {
+                            mass += __expf(tv[q] - mx);
+                            cand[(size_t)row * topm + q] = ti[q];
+                        }
+                    pmass[row] = mass / se;
+                }
+                if (C::CG > 1) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(mdone));
+                }
+            }
+            // the next tile's activations overwrite the scratch
+            if (C::CG > 1 && !mbar_wait(smem_u32(mdone), it & 1, abort_flag)) break;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
 }
@@ -614,7 +799,7 @@ __global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, co
     int k1 = 0x7fffffff;
     for (int q = 0; q < topm; ++q) {
         const int k = cand[(size_t)i * topm + q];
-        const float s = pscore[(size_t)i * topm + q];
+        const float s = pscore ? pscore[(size_t)i * topm + q] : 0.0f;
         if (s < s1 || (s == s1 && k < k1)) {
             s2 = s1;
             s1 = s;
@@ -630,36 +815,16 @@ __global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, co
     if (unsure) flag[atomicAdd(nflag, 1)] = i;
 }
 
-template <int KC, int EPI>
-static epll_status launch_layer(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &b, int rows,
-                                const float *bias, const float *wb, const float *ibeta, int nout, int topm,
-                                uint16_t *out_h, int *cand, float *pmass, cudaStream_t st)
-{
-    using C = MlpCfg<KC>;
-    auto kern = k_mlp_tc<KC, EPI>;
-    static bool attr = false;
-    if (!attr) {
-        EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::LAUNCH_SMEM));
-        attr = true;
-    }
-    kern<<<(rows + MT - 1) / MT, 128, C::LAUNCH_SMEM, st>>>(a, b, rows, bias, wb, ibeta, nout, topm, out_h, cand,
-                                                           pmass, cnt(g, CNT_ERR));
-    EPLL_LAUNCHED(g);
-    return EPLL_OK;
-}
-
 static epll_status ensure_prop_ws(epll_gmm *g, int n)
 {
     Workspace &ws = g->ws;
     const size_t N = ws.capN;
-    if (ws.H1b && ws.prop_cap >= N) return EPLL_OK;
-    void *ptrs[] = {ws.H1b, ws.H2b, ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
+    if (ws.cand && ws.prop_cap >= N) return EPLL_OK;
+    void *ptrs[] = {ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    const size_t rows = ws.zrows;
     cudaError_t e = cudaSuccess;
     auto A = [&](void **q, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(q, bytes); };
-    A((void **)&ws.H1b, rows * HID * 2); A((void **)&ws.H2b, rows * HID * 2);
     A((void **)&ws.cand, N * TOPM_MAX * 4); A((void **)&ws.pmass, N * 4); A((void **)&ws.pperm, N * TOPM_MAX * 4);
     A((void **)&ws.pitems, (2 + N * TOPM_MAX / 128 + (size_t)g->K) * sizeof(int4));
     A((void **)&ws.pscore, N * TOPM_MAX * 4);
@@ -672,6 +837,8 @@ static epll_status ensure_prop_ws(epll_gmm *g, int n)
     return EPLL_OK;
 }
 
+constexpr int FM_EW = 16;  // epilogue warps of the fused kernel
+
 epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  const float *ibeta, cudaStream_t st)
 {
@@ -682,21 +849,32 @@ epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, c
     const int rows = (n + MT - 1) / MT * MT;
     // DC-free patches as BF16 operands (and |z|^2)
     if ((s = launch_extract_bf16(g, xhat, H, W, anchors, n, st))) return s;
-    CUtensorMap a1, w1, a2, w2, a3, w3;
-    if ((s = make_map(&a1, ws.Zb, rows, MT))) return s;
+    const int n3 = (p->K + 15) / 16 * 16;
+    CUtensorMap mz, w1, w2, w3;
+    if ((s = make_map(&mz, ws.Zb, rows, MT))) return s;
     if ((s = make_map(&w1, p->W1b, HID, HID))) return s;
-    if ((s = make_map_wide(&a2, ws.H1b, rows, MT, HID))) return s;
     if ((s = make_map_wide(&w2, p->W2b, HID, HID, HID))) return s;
-    if ((s = make_map_wide(&a3, ws.H2b, rows, MT, HID))) return s;
-    if ((s = make_map_wide(&w3, p->W3b, HID, HID, HID))) return s;
-    if ((s = launch_layer<1, 1>(g, a1, w1, n, p->wr + OFF_B1, p->wr + OFF_WB, ibeta, HID, 0, ws.H1b, nullptr,
-                                nullptr, st)))
-        return s;
-    if ((s = launch_layer<4, 1>(g, a2, w2, n, p->wr + OFF_B2, nullptr, nullptr, HID, 0, ws.H2b, nullptr, nullptr,
-                                st)))
-        return s;
-    return launch_layer<4, 2>(g, a3, w3, n, p->wr + off_b3(p->K), nullptr, nullptr, p->K, g->prop_topm, nullptr,
-                              ws.cand, ws.pmass, st);
+    if ((s = make_map_wide(&w3, p->W3b, HID, n3, HID))) return s;
+    using Cf = FmCfg<FM_EW>;
+    const int topm = g->prop_topm;
+    auto kern = topm == 1 ? k_mlp_fused<FM_EW, 1>
+                          : (topm == 2 ? k_mlp_fused<FM_EW, 2> : (topm <= 4 ? k_mlp_fused<FM_EW, 4> : k_mlp_fused<FM_EW, 8>));
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        EPLL_CU(cudaGetDevice(&dev));
+        EPLL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        EPLL_CU(cudaFuncSetAttribute(k_mlp_fused<FM_EW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+        EPLL_CU(cudaFuncSetAttribute(k_mlp_fused<FM_EW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+        EPLL_CU(cudaFuncSetAttribute(k_mlp_fused<FM_EW, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+        EPLL_CU(cudaFuncSetAttribute(k_mlp_fused<FM_EW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+    }
+    const int ntiles = rows / MT;
+    const int grid = ntiles < sms ? ntiles : sms;
+    kern<<<grid, Cf::THREADS, Cf::SMEM, st>>>(mz, w1, w2, w3, n, p->K, n3, p->wr, ibeta, topm, ws.cand, ws.pmass,
+                                              cnt(g, CNT_ERR));
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
 }
 
 epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
@@ -706,22 +884,26 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
     const int topm = g->prop_topm;
     epll_status s;
     if ((s = launch_proposal_topm(g, xhat, H, W, anchors, n, g->tab.ibeta, st))) return s;
-    // exact FP32 scores of the proposed (patch, component) pairs
-    const int npairs = n * topm;
-    if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st))) return s;
-    static bool attr = false;
-    if (!attr) {
-        EPLL_CU(cudaFuncSetAttribute(k_prop_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(PropSmem)));
-        attr = true;
+    // exact FP32 scores of the proposed (patch, component) pairs; a single
+    // proposal is the selection (its gap is reported as FLT_MAX)
+    if (topm > 1) {
+        const int npairs = n * topm;
+        if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st))) return s;
+        static bool attr = false;
+        if (!attr) {
+            EPLL_CU(cudaFuncSetAttribute(k_prop_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PropSmem)));
+            attr = true;
+        }
+        const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
+        k_prop_score<<<max_items, PS_T, sizeof(PropSmem), st>>>(xhat, H, W, anchors, ws.pperm, ws.pitems, topm,
+                                                                g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab, ws.pscore);
+        EPLL_LAUNCHED(g);
     }
-    const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
-    k_prop_score<<<max_items, PS_T, sizeof(PropSmem), st>>>(xhat, H, W, anchors, ws.pperm, ws.pitems, topm, g->Rtot,
-                                                            g->d_roff, g->d_r, g->d_B, g->tab, ws.pscore);
-    EPLL_LAUNCHED(g);
     int *nflag1 = cnt(g, CNT_NFLAG1);
     EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
-    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, ws.pscore, ws.pmass, g->prop_pmin, ws.zz,
+    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
+                                                   g->prop_pmin, ws.zz,
                                                    g->tab.tmax, tau_abs, PROP_REL, ws.kstar, ws.gap, ws.flag1,
                                                    nflag1);
     EPLL_LAUNCHED(g);
