@@ -43,6 +43,10 @@ struct Tables {
     float *k8s2 = nullptr;                       // [K]: s_k^2 of the E4M3 basis
 };
 
+// Relative score error bound of the split BF16 form (hi*hi + lo*hi + hi*lo):
+// a top-2 gap below tau_abs + SPLIT_REL |z|^2 tmax is a near-tie.
+constexpr float SPLIT_REL = 4e-5f;
+
 // Iterations prepared together (tables of every beta, patch subsets).
 constexpr int TB_MAX = 8;
 

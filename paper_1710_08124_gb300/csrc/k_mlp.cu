@@ -361,8 +361,8 @@ constexpr int FM_H = 4 * FM_ZT;       // 64 KB: [128][256] BF16 as four K chunks
 template <int EW>
 struct FmCfg {
     static constexpr int THREADS = 32 * (2 + EW);
-    static constexpr int CG = EW / 4;   // column groups per TMEM lane quarter
-    static constexpr int CW = 64 / CG;  // columns per warp and chunk
+    static constexpr int CG = EW / 4;   // column groups per TMEM lane quarter (16 columns of each chunk)
+    static_assert(EW == 16, "the epilogue slices every 64-column chunk into four 16-column groups");
     static constexpr int OFF_H = FM_S * FM_SLOT;
     static constexpr int OFF_Z = OFF_H + FM_H;
     static constexpr int OFF_BIAS = OFF_Z + 2 * FM_ZT;
@@ -373,21 +373,19 @@ struct FmCfg {
     static_assert(CG * MT * (2 * TOPM_MAX + 2) * 4 <= FM_H, "merge scratch must fit in the activation buffer");
 };
 
-template <int CW>
-static __device__ __forceinline__ void tmem_ld_cw(uint32_t taddr, uint32_t (&r)[CW])
+// 16 accumulator columns at taddr and at taddr + 64 (this warp's slices of
+// two consecutive 64-column K chunks), one wait for both loads.
+static __device__ __forceinline__ void tmem_ld_2x16(uint32_t taddr, uint32_t (&r)[32])
 {
-    if constexpr (CW == 32) {
-        tmem_ld32(taddr, r);
-        tmem_wait(r);
-    } else {
-        static_assert(CW == 16, "16 or 32 columns");
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : EPLL_R8(0), EPLL_R8(8)
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" : EPLL_W8(0), EPLL_W8(8)::"memory");
-    }
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : EPLL_R8(0), EPLL_R8(8)
+                 : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : EPLL_R8(16), EPLL_R8(24)
+                 : "r"(taddr + 64u));
+    tmem_wait(r);
 }
 
 static __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -412,31 +410,29 @@ static __device__ __forceinline__ void topm_insert(float (&tv)[TM], int (&ti)[TM
     }
 }
 
-// One layer's epilogue for hidden layers: v = scale * acc + bias, GELU,
-// BF16, into chunk c of the activation buffer (swizzled like a TMA
-// SWIZZLE_128B load, so the next layer's MMA reads it as its A operand).
-template <int CW>
-static __device__ __forceinline__ void epi_hidden(uint32_t taddr, int c, int j, int rit, float scale,
+// One chunk of a hidden layer's epilogue: v = scale * acc + bias, GELU, BF16,
+// into chunk c of the activation buffer (swizzled like a TMA SWIZZLE_128B
+// load, so the next layer's MMA reads it as its A operand).  acc holds this
+// warp's 16 columns 64 c + 16 j .. of its row.
+static __device__ __forceinline__ void epi_hidden(const uint32_t *acc, int c, int j, int rit, float scale,
                                                   const float *__restrict__ bias, unsigned char *H)
 {
-    uint32_t r[CW];
-    tmem_ld_cw<CW>(taddr, r);
-    const int col0 = 64 * c + j * CW;
-    uint32_t packed[CW / 2];
+    const int col0 = 64 * c + 16 * j;
+    uint32_t packed[8];
 #pragma unroll
-    for (int q = 0; q < CW; q += 4) {
+    for (int q = 0; q < 16; q += 4) {
         const float4 b = *reinterpret_cast<const float4 *>(bias + col0 + q);
-        const __nv_bfloat162 p0 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(r[q]), scale, b.x)),
-                                                        gelu_fast(fmaf(__uint_as_float(r[q + 1]), scale, b.y)));
-        const __nv_bfloat162 p1 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(r[q + 2]), scale, b.z)),
-                                                        gelu_fast(fmaf(__uint_as_float(r[q + 3]), scale, b.w)));
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(acc[q]), scale, b.x)),
+                                                        gelu_fast(fmaf(__uint_as_float(acc[q + 1]), scale, b.y)));
+        const __nv_bfloat162 p1 = __floats2bfloat162_rn(gelu_fast(fmaf(__uint_as_float(acc[q + 2]), scale, b.z)),
+                                                        gelu_fast(fmaf(__uint_as_float(acc[q + 3]), scale, b.w)));
         packed[q / 2] = *reinterpret_cast<const uint32_t *>(&p0);
         packed[q / 2 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
     }
     unsigned char *rowp = H + c * FM_ZT + rit * 128;
 #pragma unroll
-    for (int q = 0; q < CW / 8; ++q) {
-        const int lc = (j * CW * 2) / 16 + q;  // logical 16-byte chunk of the 128-byte row
+    for (int q = 0; q < 2; ++q) {
+        const int lc = 2 * j + q;  // logical 16-byte chunk of the 128-byte row
         *reinterpret_cast<uint4 *>(rowp + ((lc ^ (rit & 7)) << 4)) =
             make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
     }
@@ -557,33 +553,41 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        constexpr int CW = C::CW;
         const int e = warp - 2, qd = warp & 3, j = e >> 2;
         const int rit = 32 * qd + lane;
-        const uint32_t tl = tbase + ((uint32_t)(32 * qd) << 16);
+        const uint32_t tl = tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * j);
         float *scratch = reinterpret_cast<float *>(Hb);  // [CG][2 TM + 2][128]
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int row = tile * MT + rit;
-            // hidden layers
+            // hidden layers: one TMEM round trip for the warp's four slices,
+            // then chunk by chunk into the activation buffer
             bool ok = true;
             for (int layer = 0; layer < 2 && ok; ++layer) {
                 ok = mbar_wait(smem_u32(&accfull[layer]), it & 1, abort_flag);
                 if (!ok) break;
                 tc_fence_after();
-                for (int c = 0; c < 4; ++c) {
-                    const uint32_t ta = tl + (layer ? 256u : 0u) + (uint32_t)(64 * c + j * CW);
-                    epi_hidden<CW>(ta, c, j, rit, layer ? 1.0f : in_scale, layer ? sb2 : sb1, Hb);
-                    fence_proxy_async();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&hready[c]));
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t acc[32];
+                    tmem_ld_2x16(tl + (layer ? 256u : 0u) + 128u * h, acc);
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int c = 2 * h + cc;
+                        epi_hidden(acc + 16 * cc, c, j, rit, layer ? 1.0f : in_scale, layer ? sb2 : sb1, Hb);
+                        fence_proxy_async();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&hready[c]));
+                    }
                 }
             }
             if (ok) ok = mbar_wait(smem_u32(&accfull[2]), it & 1, abort_flag);
             if (!ok) break;
             tc_fence_after();
-            // output layer: this warp's top-m and softmax sums over its columns
+            // output layer: this warp's columns 64 c + 16 j + q (increasing in
+            // (c, q)), two chunks per TMEM round trip; online softmax sums and
+            // top-m without data-dependent branches
             float tv[TM];
             int ti[TM];
 #pragma unroll
@@ -591,25 +595,42 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
                 tv[q] = -FLT_MAX;
                 ti[q] = 0x7fffffff;
             }
-            float mx = -FLT_MAX, se = 0.0f;
-            for (int c = 0; c < 4; ++c) {
-                const int col0 = 64 * c + j * CW;
-                if (col0 >= K) break;
-                uint32_t r[CW];
-                tmem_ld_cw<CW>(tl + (uint32_t)col0, r);
+            float mx = -INFINITY, se = 0.0f;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                if (128 * h + 16 * j >= K) break;
+                uint32_t acc[32];
+                tmem_ld_2x16(tl + 128u * h, acc);
+                float hm = -INFINITY;
 #pragma unroll
-                for (int q = 0; q < CW; ++q) {
-                    const int col = col0 + q;
-                    if (col < K) {
-                        const float v = __uint_as_float(r[q]) + sb3[col];
-                        if (v > mx) {
-                            se = fmaf(se, __expf(mx - v), 1.0f);
-                            mx = v;
-                        } else {
-                            se += __expf(v - mx);
-                        }
-                        // columns arrive in increasing order: a tie never displaces
-                        if (v > tv[TM - 1]) topm_insert<TM>(tv, ti, v, col);
+                for (int q = 0; q < 32; ++q) {
+                    const int col = 128 * h + 64 * (q >> 4) + 16 * j + (q & 15);
+                    const float v = col < K ? __uint_as_float(acc[q]) + sb3[col] : -INFINITY;
+                    acc[q] = __float_as_uint(v);
+                    hm = fmaxf(hm, v);
+                }
+                const float nm = fmaxf(mx, hm);
+                float hs = 0.0f;
+                if (nm > -INFINITY) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) hs += __expf(__uint_as_float(acc[q]) - nm);
+                }
+                se = (mx > -INFINITY ? se * __expf(mx - nm) : 0.0f) + hs;
+                mx = nm;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    // insertion by selects; a tie never displaces (columns ascend)
+                    float v = __uint_as_float(acc[q]);
+                    int ix = 128 * h + 64 * (q >> 4) + 16 * j + (q & 15);
+#pragma unroll
+                    for (int u = 0; u < TM; ++u) {
+                        const bool sw = v > tv[u];
+                        const float tvu = tv[u];
+                        const int tiu = ti[u];
+                        tv[u] = sw ? v : tvu;
+                        ti[u] = sw ? ix : tiu;
+                        v = sw ? tvu : v;
+                        ix = sw ? tiu : ix;
                     }
                 }
             }
@@ -671,117 +692,146 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
 }
 
 // ============================================================================
-// Exact FP32 scores of (patch, candidate) pairs, grouped by component: a block
-// takes one work item (up to 128 pairs of one component), stages Ubar_k, and
-// computes C = Z Ubar_k register-tiled (8 x 8 per thread); the score of Eq. 14
-// sums the eight column groups of a row with lane shuffles.
+// Scores of (patch, candidate) pairs on the tensor cores, grouped by
+// component: a CTA takes one work item (up to 128 pairs proposing component
+// k), gathers their DC-free patches from the image into shared memory as
+// split BF16 operands (hi + lo, written in the 128-byte-swizzled K-major
+// layout), loads the component's split scaled basis Ubar_k sqrt|q_k| (64 rows,
+// hi + lo) by TMA, and accumulates hi*hi + lo*hi + hi*lo (the split form of
+// the exhaustive pass, with the same error bound) into 64 TMEM columns.  Each
+// epilogue thread finishes its pair's score of Eq. 14:
+//   cst_k + t_k |z|^2 + sgn_k sum_{j < r_k} c_j^2.
 // ============================================================================
 constexpr int PS_T = 128;
-// relative FP32 error bound of a proposal's score (64-term dot products, as
-// the SIMT selection, with a factor 2 of margin for the different order)
-constexpr float PROP_REL = 2e-5f;
-constexpr int PS_LDZ = PS_T + 4;
-
-struct PropSmem {
-    float Zt[PD][PS_LDZ];
-    float Us[PD][PD];
-    float qs[PD];
-    float zzs[PS_T];
-    int anchor[PS_T];
-};
+constexpr int PS_TILE = PS_T * 128;   // 16 KB: [128 rows][64] BF16
+constexpr int PS_B = 64 * 128;        // 8 KB: [64 rows][64] BF16
+constexpr int PS_SMEM = 1024 + 2 * PS_TILE + 2 * PS_B + 32 + 2 * PS_T * 4;
 
 __global__ void __launch_bounds__(PS_T)
-k_prop_score(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
-             const int *__restrict__ perm, const int4 *__restrict__ items, int topm, int Rtot,
-             const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B, Tables tab,
-             float *__restrict__ pscore)
+k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant__ CUtensorMap mapBlo,
+                const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+                const int *__restrict__ perm, const int4 *__restrict__ items, int topm,
+                const int *__restrict__ roff, const int *__restrict__ rk_, Tables tab, const float *__restrict__ zz,
+                float *__restrict__ pscore, int *__restrict__ err)
 {
-    extern __shared__ __align__(16) unsigned char ps_raw[];
-    PropSmem &sm = *reinterpret_cast<PropSmem *>(ps_raw);
     if ((int)blockIdx.x >= items[0].w) return;
+    extern __shared__ __align__(1024) unsigned char ps_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)ps_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Ahi = smem, *Alo = smem + PS_TILE, *Bhi = smem + 2 * PS_TILE, *Blo = Bhi + PS_B;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(Blo + PS_B);  // [0] B loaded, [1] MMA done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int4 it = items[1 + blockIdx.x];
     const int k = it.x, first = it.y, cnt_p = it.z;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int o = roff[k], r = rk_[k];
-    if (tid < cnt_p) {
-        const int i = perm[first + tid] / topm;
-        sm.anchor[tid] = anchors ? anchors[i] : i;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int idx = tid; idx < PD * PD; idx += PS_T) {
-        const int e = idx >> 6, j = idx & 63;
-        sm.Us[e][j] = j < r ? B[(size_t)e * Rtot + o + j] : 0.0f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid < PD) sm.qs[tid] = tid < r ? tab.q_hi[o + tid] : 0.0f;
+    tc_fence_before();
     __syncthreads();
-    for (int p0 = w * 32; p0 < w * 32 + 32; p0 += 4) {
-        float x0[4], x1[4];
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (threadIdx.x == 0) {
+        const uint32_t b = smem_u32(&bars[0]);
+        mbar_expect_tx(b, 2 * PS_B);
+        tma_load_2d(smem_u32(Bhi), &mapBs, 0, roff[k], b);
+        tma_load_2d(smem_u32(Blo), &mapBlo, 0, roff[k], b);
+    }
+    // gather: every thread first resolves one row's pair -> patch -> anchor;
+    // then warp w fills rows 32w .. 32w+31, eight rows' loads in flight at a
+    // time, lane l holding patch elements 2l and 2l + 1 (patch row l / 4)
+    int *s_anchor = reinterpret_cast<int *>(tslot + 2), *s_pair = s_anchor + PS_T;
+    if (threadIdx.x < cnt_p) {
+        const int pr = perm[first + threadIdx.x];
+        const int i = pr / topm;
+        s_pair[threadIdx.x] = pr;
+        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+    }
+    __syncthreads();
+    const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
+    for (int rr = 0; rr < 32; rr += 8) {
+        float xa[8], xb[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            x0[u] = x1[u] = 0.0f;
-            if (p0 + u < cnt_p) {
-                const int a = sm.anchor[p0 + u];
+        for (int u = 0; u < 8; ++u) {
+            const int t = 32 * warp + rr + u;
+            xa[u] = xb[u] = 0.0f;
+            if (t < cnt_p) {
+                const int a = s_anchor[t];
                 const int ai = a / W, aj = a % W;
-                int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
-                if (r0 >= H) r0 -= H;
-                if (r1 >= H) r1 -= H;
-                if (c >= W) c -= W;
-                x0[u] = xhat[(size_t)r0 * W + c];
-                x1[u] = xhat[(size_t)r1 * W + c];
+                int r = ai + pr_, c0 = aj + pc_, c1 = c0 + 1;
+                if (r >= H) r -= H;
+                if (c0 >= W) c0 -= W;
+                if (c1 >= W) c1 -= W;
+                xa[u] = xhat[(size_t)r * W + c0];
+                xb[u] = xhat[(size_t)r * W + c1];
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int p = p0 + u;
-            float s = x0[u] + x1[u];
+        for (int u = 0; u < 8; ++u) {
+            const int t = 32 * warp + rr + u;
+            float sum = xa[u] + xb[u];
 #pragma unroll
-            for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
-            const float m = s * (1.0f / PD);
-            const float z0 = x0[u] - m, z1 = x1[u] - m;
-            float zz = fmaf(z0, z0, z1 * z1);
-#pragma unroll
-            for (int q = 16; q > 0; q >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, q);
-            sm.Zt[lane][p] = p < cnt_p ? z0 : 0.0f;
-            sm.Zt[lane + 32][p] = p < cnt_p ? z1 : 0.0f;
-            if (lane == 0) sm.zzs[p] = zz;
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
+            const float z0 = xa[u] - mu, z1 = xb[u] - mu;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
+            // elements 2l, 2l+1: bytes 4l..4l+3 of the row, 16-byte chunk l / 4 swizzled by t mod 8
+            const uint32_t o = t * 128 + ((((uint32_t)lane >> 2) ^ (t & 7)) << 4) + 4 * (lane & 3);
+            *reinterpret_cast<__nv_bfloat162 *>(Ahi + o) = h;
+            *reinterpret_cast<__nv_bfloat162 *>(Alo + o) = l;
         }
     }
+    fence_proxy_async();
     __syncthreads();
-    const int pg = tid >> 3, cg = tid & 7;
-    float part[8] = {};
-    if (8 * cg < r) {
-        float acc[8][8];
+    if (threadIdx.x == 0) {
+        if (mbar_wait(smem_u32(&bars[0]), 0, abort_flag)) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_f16(PS_T, 64, 1);
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
-#pragma unroll 4
-        for (int e = 0; e < PD; ++e) {
-            const float4 z0 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg]);
-            const float4 z1 = *reinterpret_cast<const float4 *>(&sm.Zt[e][8 * pg + 4]);
-            const float4 u0 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg]);
-            const float4 u1 = *reinterpret_cast<const float4 *>(&sm.Us[e][8 * cg + 4]);
-            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-            const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(zv[a], uv[b], acc[a][b]);
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t o = 32 * kk;
+                mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, kk ? 1u : 0u);
+                mma_f16(tbase, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+                mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+            }
+            mma_commit(smem_u32(&bars[1]));
         }
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int b = 0; b < 8; ++b) part[a] = fmaf(sm.qs[8 * cg + b] * acc[a][b], acc[a][b], part[a]);
     }
+    __syncwarp();
+    const bool ok = mbar_wait(smem_u32(&bars[1]), 0, abort_flag);
+    tc_fence_after();
+    if (ok) {
+        uint32_t r[64];
+        tmem_ld_all<64>(tbase + ((uint32_t)(32 * warp) << 16), r);
+        const int t = 32 * warp + lane, rk = rk_[k];
+        float sq = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        float v = part[a];
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        const int p = 8 * pg + a;
-        if (cg == 0 && p < cnt_p)
-            pscore[perm[first + p]] = tab.cst_hi[k] + tab.t_hi[k] * sm.zzs[p] + v;
+        for (int j = 0; j < 64; ++j) {
+            const float c = __uint_as_float(r[j]);
+            if (j < rk) sq = fmaf(c, c, sq);
+        }
+        if (t < cnt_p) {
+            const int pr = s_pair[t];
+            pscore[pr] = tab.cst_hi[k] + tab.t_hi[k] * zz[pr / topm] + tab.sgn[k] * sq;
+        }
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
 }
 
 // Per patch: best and second-best rescored candidate (lowest index on ties);
@@ -891,20 +941,23 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
         if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st))) return s;
         static bool attr = false;
         if (!attr) {
-            EPLL_CU(cudaFuncSetAttribute(k_prop_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PropSmem)));
+            EPLL_CU(cudaFuncSetAttribute(k_pair_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM));
             attr = true;
         }
+        CUtensorMap bs, bslo;
+        if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 64))) return s;
+        if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 64))) return s;
         const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
-        k_prop_score<<<max_items, PS_T, sizeof(PropSmem), st>>>(xhat, H, W, anchors, ws.pperm, ws.pitems, topm,
-                                                                g->Rtot, g->d_roff, g->d_r, g->d_B, g->tab, ws.pscore);
+        k_pair_score_tc<<<max_items, PS_T, PS_SMEM, st>>>(bs, bslo, xhat, H, W, anchors, ws.pperm, ws.pitems, topm,
+                                                          g->d_roff, g->d_r, g->tab, ws.zz, ws.pscore,
+                                                          cnt(g, CNT_ERR));
         EPLL_LAUNCHED(g);
     }
     int *nflag1 = cnt(g, CNT_NFLAG1);
     EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
     k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
                                                    g->prop_pmin, ws.zz,
-                                                   g->tab.tmax, tau_abs, PROP_REL, ws.kstar, ws.gap, ws.flag1,
+                                                   g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, ws.flag1,
                                                    nflag1);
     EPLL_LAUNCHED(g);
     // exhaustive split-BF16 pass over the undecided patches

@@ -484,9 +484,6 @@ static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensor
 #undef EPLL_TC_ARGS
 }
 
-// Relative error bound of the split form (see thresholds() in api.cu).
-constexpr float SPLIT_REL = 4e-5f;
-
 // Split-BF16 scores of every component for the rows of the near-tie list
 // (ws.flag, device count): the candidates of the compensated rescoring are the
 // components within the split form's error band of the best.  Returns
