@@ -60,8 +60,13 @@ def parse():
     ap.add_argument("--precision", choices=list(PREC_NAMES), default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain-FP32 comparison leg")
-    ap.add_argument("--workload", choices=["fepll", "uneven"], default="fepll",
-                    help="fepll: the 512x512 FEPLL denoising workload (default line); uneven: 64 images of "
+    ap.add_argument("--topm", type=int, default=4, help="proposal workload: proposals per patch of the value")
+    ap.add_argument("--pmin", type=float, default=0.0, help="proposal workload: softmax mass below which a "
+                    "patch is scored exhaustively")
+    ap.add_argument("--train-steps", type=int, default=3000, help="proposal workload: AdamW steps")
+    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal"], default="fepll",
+                    help="fepll: the 512x512 FEPLL denoising workload (default line); proposal: the learned "
+                         "top-m proposal at 512x512, sigma 25/255, K=200, r=64; uneven: 64 images of "
                          "uneven size, noise and degradation in one captured batch vs per-image launches")
     return ap.parse_args()
 
@@ -291,6 +296,183 @@ def run_uneven(args):
     return 0
 
 
+# ---------------------------------------------------------------- proposal workload
+PROP_RANK = 64
+PROP_SIGMA = 25 / 255
+PROP_TRAIN = 24       # 128x128 training observations -> 24 * 5 * 16384 = 1,966,080 pairs
+PROP_WORKLOAD = ("learned top-m proposal: network 64-256-256-200 trained on 1,966,080 (patch, exact selection) "
+                 "pairs from 24 dead-leaves 128x128 denoising trajectories (sigma U[5,50]/255, K=200, r=64, "
+                 "5 iterations, exhaustive BF16X3 labels); timed on a 512x512 dead-leaves image at sigma "
+                 "25/255, K=200, r=64, random 1/3 patch subset, 5 HQS iterations")
+
+
+def run_proposal(args):
+    """Trains the proposal network (setup, not timed), then times 512x512
+    restorations with the proposal selection for m in {1, 4, 8} next to the
+    exhaustive split-BF16 and plain FP32 forms on the same image; reports the
+    selection agreement with the exhaustive path along the trajectory, the
+    fallback fraction and the PSNR of each form (against the FP64 oracle's
+    restoration of the same image in the cpu_baseline leg)."""
+    import torch
+
+    import paper_1710_08124_gb300 as ep
+    from paper_1710_08124_gb300 import proposal as pr
+
+    ep.build()
+    dev = torch.device("cuda", 0)
+    g = synth.synthetic_gmm(K)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, PROP_RANK)
+    rng = np.random.default_rng(4)
+    sig = rng.uniform(5, 50, PROP_TRAIN) / 255
+    obs = [torch.as_tensor((synth.image(500 + i, 128) + synth.noise(500 + i, 128, 128, s)).astype(np.float32),
+                           device=dev) for i, s in enumerate(sig)]
+    t0 = time.perf_counter()
+    data = pr.make_pairs(gm, obs, sig)
+    torch.cuda.synchronize()
+    pairs_s = time.perf_counter() - t0
+    net = ep.Proposal(K, seed=11)
+    t0 = time.perf_counter()
+    losses = pr.train(net, data, steps=args.train_steps, batch=4096, lr=2e-3, seed=1,
+                      log_every=max(1, args.train_steps // 6))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del data
+
+    x, y = synth.denoise_problem(301, H, PROP_SIGMA)
+    yd = torch.as_tensor(y.astype(np.float32), device=dev)
+    out = torch.empty_like(yd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    common = dict(subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=2)
+    o_ex = ep.Options(precision=ep.BF16X3, **common)
+    o_32 = ep.Options(precision=ep.FP32, **common)
+    o_pr = ep.Options(select=ep.SELECT_PROPOSAL, **common)
+
+    def timed(options, steps):
+        for _ in range(max(args.warmup, 3)):
+            ep.restore(gm, yd, PROP_SIGMA, BETA, options=options, out=out)
+        _, _, launches = ep.last_counters(gm)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ep.restore(gm, yd, PROP_SIGMA, BETA, options=options, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        return steps / tot, out.cpu().numpy(), launches, tot
+
+    steps = max(5, min(args.steps, 60))
+    ex_rate, x_ex, _, _ = timed(o_ex, steps)
+    r32, x_32, _, _ = timed(o_32, max(3, steps // 10))
+
+    # selection agreement with the exhaustive path along its own trajectory
+    lam = pr.denoise_lambda(PROP_SIGMA)
+    traj = [yd] + [ep.restore(gm, yd, PROP_SIGMA, BETA[:t], options=o_ex) for t in range(1, len(BETA))]
+    per_m = {}
+    sel_ms = sel_n = sel_flops = 0.0
+    clk = None
+    for m in (1, 4, 8):
+        ep.attach_proposal(gm, net, topm=m, pmin=args.pmin)
+        agree, hit, nsel = 0, 0, 0
+        for t, xt in enumerate(traj):
+            beta = lam * BETA[t] / PROP_SIGMA ** 2
+            _, an, k_ex, _ = ep.patch_step(gm, xt, beta, o_ex, t)
+            _, _, k_pr, _ = ep.patch_step(gm, xt, beta, o_pr, t)
+            cand, _ = ep.proposal_topm(gm, xt, beta, anchors=an)
+            agree += int((k_pr == k_ex).sum().item())
+            hit += int((cand == k_ex[:, None]).any(dim=1).sum().item())
+            nsel += int(k_ex.numel())
+        ep.restore(gm, yd, PROP_SIGMA, BETA, options=o_pr, out=out)
+        fb = ep.last_fallbacks(gm)
+        if m == args.topm:
+            ep.profile_enable(gm, True)
+            ep.profile_read(gm)
+            clocks = ClockSampler(0)
+            clocks.start()
+        rate, x_pr, launches, tot = timed(o_pr, steps)
+        if m == args.topm:
+            clk = clocks.stop()
+            sel_ms, sel_n, sel_flops = ep.profile_read(gm)
+            ep.profile_enable(gm, False)
+        per_m[m] = {"restores_per_s": rate, "ms_per_restore": 1e3 / rate,
+                    "selection_agreement": agree / nsel, "topm_hit_rate": hit / nsel,
+                    "fallback_fraction": fb / (len(BETA) * M_PATCH),
+                    "psnr_db": psnr(x_pr, x), "psnr_delta_vs_exhaustive_db": psnr(x_pr, x) - psnr(x_ex, x),
+                    "gpu_launches_per_restore": launches, "_x": x_pr, "_steps": steps, "_tot": tot}
+    ep.attach_proposal(gm, net, topm=args.topm, pmin=args.pmin)
+    sel = per_m[args.topm]
+
+    # end to end through the host-buffer C ABI call
+    hy = torch.from_numpy(y.astype(np.float32)).pin_memory()
+    hx = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    n_e2e = max(3, steps // 2)
+    ep.restore_host(gm, hy, PROP_SIGMA, BETA, options=o_pr, out=hx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ep.restore_host(gm, hy, PROP_SIGMA, BETA, options=o_pr, out=hx)
+    e2e_rate = n_e2e / (time.perf_counter() - t0)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_note = "measured (sustained, cuBLAS bf16)"
+    if peak is None:
+        peak, peak_note = 1700.0, "fallback"
+    achieved = (sel_flops / (sel_ms / 1e3) / 1e12) if sel_ms > 0 else None
+    line = {
+        "metric": "512x512 restores/s with the learned top-m proposal (K=200, r=64, 1/3 subset, sigma 25/255)",
+        "value": sel["restores_per_s"], "unit": "restores/s", "n_gpus": 1, "steps": sel["_steps"],
+        "warmup": args.warmup, "ms_per_step": sel["ms_per_restore"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": PROP_WORKLOAD, "topm": args.topm, "pmin": args.pmin,
+                   "train_steps": args.train_steps, "batch": 4096, "pairs_generation_s": pairs_s,
+                   "train_s": train_s, "train_loss": [[int(a), float(b)] for a, b in losses],
+                   "l2": "256 MB buffer written before each restore, outside the timed events"},
+        "mpatch_evals_per_s": sel["restores_per_s"] * len(BETA) * M_PATCH / 1e6,
+        "e2e": {"value": e2e_rate, "unit": "restores/s", "h2d_bytes_per_step": N_PIX * 4,
+                "d2h_bytes_per_step": N_PIX * 4},
+        "gpu_launches": sel["gpu_launches_per_restore"] * sel["_steps"],
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "fused proposal network (3 tcgen05 layers, GELU and top-m epilogues)",
+                     "launches": int(sel_n), "kernel_ms": sel_ms,
+                     "share_of_step": sel_ms / 1e3 / sel["_tot"] if sel["_tot"] else None,
+                     "peak_source": peak_note},
+        "proposal": {str(m): {k: v for k, v in d.items() if not k.startswith("_")} for m, d in per_m.items()},
+        "exhaustive_bf16x3": {"restores_per_s": ex_rate, "psnr_db": psnr(x_ex, x)},
+        "plain_fp32": {"restores_per_s": r32, "psnr_db": psnr(x_32, x),
+                       "speedup_of_value": sel["restores_per_s"] / r32},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        # the FP64 oracle restores the same image (timed: the CPU baseline;
+        # its output also gives each GPU form's PSNR distance to the oracle)
+        import oracle
+        om = oracle.Model(g.w, g.U, g.S, "fixed", PROP_RANK)
+        t0 = time.perf_counter()
+        xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), PROP_SIGMA, BETA,
+                            subset=oracle.FRACTION, subset_param=FRACTION, seed=2)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "restores/s", "cores": os.cpu_count() or 1,
+                                "kind": "oracle", "sample": "one full 512x512 restoration of the timed image "
+                                "(FP64, exhaustive, OpenMP over patches)"}
+        po = psnr(xo, x)
+        line["oracle_psnr_db"] = po
+        for m, d in per_m.items():
+            line["proposal"][str(m)]["psnr_delta_vs_oracle_db"] = psnr(d["_x"], x) - po
+        line["exhaustive_bf16x3"]["psnr_delta_vs_oracle_db"] = psnr(x_ex, x) - po
+        line["plain_fp32"]["psnr_delta_vs_oracle_db"] = psnr(x_32, x) - po
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 def traffic_record(kernel_src_hash: str, precision: str):
     """DRAM bytes per selection-kernel launch from the committed ncu summary,
@@ -314,6 +496,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "uneven":
         return run_uneven(args) if rank == 0 else 0
+    if args.workload == "proposal":
+        return run_proposal(args) if rank == 0 else 0
 
     import torch
 

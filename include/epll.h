@@ -249,8 +249,16 @@ epll_status epll_sample_noalloc(int H, int W, const epll_options *opt, int t, in
 epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *rescored,
                                long long *launches);
 
+/* Patches that the last epll_restore / epll_patch_step with the proposal
+ * selection sent to the exhaustive pass (too little proposal mass or a
+ * near-tie among the proposals), summed over its iterations; host out;
+ * synchronises the device. */
+epll_status epll_last_fallbacks(epll_gmm *g, long long *fallbacks);
+
 /* Instrumentation of the selection kernel (the projection + score contraction,
- * the step that dominates the restoration's arithmetic).  While enabled, the
+ * the step that dominates the restoration's arithmetic; with the proposal
+ * selection, the fused network kernel instead, whose algorithmic FLOPs are
+ * 2 (64*256 + 256*256 + 256*K) per patch).  While enabled, the
  * library records a pair of CUDA events on the call's stream around every
  * launch of that kernel (at most 8192 launches between reads; later launches
  * are not recorded).  epll_profile_read synchronises the device, returns the

@@ -117,6 +117,7 @@ def lib():
                                           vp, vp]
         L.epll_gmm_attach_proposal.argtypes = [vp, vp, i, C.c_float]
         L.epll_proposal_topm.argtypes = [vp, vp, i, i, vp, i, d, vp, vp, vp]
+        L.epll_last_fallbacks.argtypes = [vp, C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
 
@@ -299,6 +300,13 @@ def last_counters(g: GMM):
     a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
     _check(lib().epll_last_counters(g.handle, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def last_fallbacks(g: GMM) -> int:
+    """Patches the last proposal-selection call sent to the exhaustive pass."""
+    v = C.c_longlong()
+    _check(lib().epll_last_fallbacks(g.handle, C.byref(v)))
+    return v.value
 
 
 def profile_enable(g: GMM, enable: bool = True):

@@ -15,11 +15,11 @@ void prof_begin(epll_gmm *g, cudaStream_t st)
 {
     if (g->prof_on && g->prof_n < PROF_MAX) cudaEventRecord(g->prof_ev[2 * g->prof_n], st);
 }
-void prof_end(epll_gmm *g, cudaStream_t st, int n)
+void prof_end(epll_gmm *g, cudaStream_t st, int n, double flops_per_row)
 {
     if (g->prof_on && g->prof_n < PROF_MAX) {
         cudaEventRecord(g->prof_ev[2 * g->prof_n + 1], st);
-        g->prof_flops += 2.0 * PD * (double)g->rank_sum * (double)n;
+        g->prof_flops += (flops_per_row >= 0.0 ? flops_per_row : 2.0 * PD * (double)g->rank_sum) * (double)n;
         ++g->prof_n;
     }
 }
@@ -682,6 +682,16 @@ epll_status epll_last_counters(epll_gmm *g, long long *patch_evals, long long *r
     if (rescored) *rescored = c[0];
     if (launches) *launches = g->last_launches;
     if (timed_out) return fail(EPLL_ETIMEOUT, "a tensor-core selection kernel gave up on a bounded wait");
+    return EPLL_OK;
+}
+
+epll_status epll_last_fallbacks(epll_gmm *g, long long *fallbacks)
+{
+    if (!g || !fallbacks) return fail(EPLL_EINVAL, "null argument");
+    EPLL_CU(cudaDeviceSynchronize());
+    long long c[4] = {0, 0, 0, 0};
+    if (g->ws.ctr) EPLL_CU(cudaMemcpy(c, g->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    *fallbacks = c[1];
     return EPLL_OK;
 }
 

@@ -252,6 +252,7 @@ epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W, const 
 // Selection-kernel instrumentation (no-ops unless enabled).
 constexpr int PROF_MAX = 8192;
 void prof_begin(epll_gmm *g, cudaStream_t st);
-void prof_end(epll_gmm *g, cudaStream_t st, int n);
+// flops_per_row < 0: the selection GEMM's 2 * 64 * sum_k r_k
+void prof_end(epll_gmm *g, cudaStream_t st, int n, double flops_per_row = -1.0);
 
 }  // namespace epll

@@ -835,34 +835,38 @@ k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant
 }
 
 // Per patch: best and second-best rescored candidate (lowest index on ties);
-// undecided patches (little proposal mass or an FP32 near-tie) are listed for
-// the exhaustive pass.
+// undecided patches (proposal mass below pmin, or a top-2 gap within the
+// split-BF16 error bound) are listed for the exhaustive pass.
 __global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, const float *__restrict__ pscore,
                                const float *__restrict__ pmass, float pmin, const float *__restrict__ zz,
                                const float *__restrict__ tmax, float tau_abs, float tau_rel,
                                int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
-                               int *__restrict__ nflag)
+                               int *__restrict__ nflag, long long *__restrict__ nfallback)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s1 = FLT_MAX, s2 = FLT_MAX;
-    int k1 = 0x7fffffff;
-    for (int q = 0; q < topm; ++q) {
-        const int k = cand[(size_t)i * topm + q];
-        const float s = pscore ? pscore[(size_t)i * topm + q] : 0.0f;
-        if (s < s1 || (s == s1 && k < k1)) {
-            s2 = s1;
-            s1 = s;
-            k1 = k;
-        } else if (s < s2) {
-            s2 = s;
+    bool unsure = false;
+    if (i < n) {
+        float s1 = FLT_MAX, s2 = FLT_MAX;
+        int k1 = 0x7fffffff;
+        for (int q = 0; q < topm; ++q) {
+            const int k = cand[(size_t)i * topm + q];
+            const float s = pscore ? pscore[(size_t)i * topm + q] : 0.0f;
+            if (s < s1 || (s == s1 && k < k1)) {
+                s2 = s1;
+                s1 = s;
+                k1 = k;
+            } else if (s < s2) {
+                s2 = s;
+            }
         }
+        kstar[i] = k1;
+        const float gp = s2 - s1;
+        gap[i] = gp;
+        unsure = !(pmass[i] >= pmin) || !(gp >= tau_abs + tau_rel * zz[i] * tmax[0]);
+        if (unsure) flag[atomicAdd(nflag, 1)] = i;
     }
-    kstar[i] = k1;
-    const float gp = s2 - s1;
-    gap[i] = gp;
-    const bool unsure = !(pmass[i] >= pmin) || !(gp >= tau_abs + tau_rel * zz[i] * tmax[0]);
-    if (unsure) flag[atomicAdd(nflag, 1)] = i;
+    const unsigned b = __ballot_sync(0xffffffffu, unsure);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd((unsigned long long *)nfallback, (unsigned long long)__popc(b));
 }
 
 static epll_status ensure_prop_ws(epll_gmm *g, int n)
@@ -921,8 +925,10 @@ epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, c
     }
     const int ntiles = rows / MT;
     const int grid = ntiles < sms ? ntiles : sms;
+    prof_begin(g, st);
     kern<<<grid, Cf::THREADS, Cf::SMEM, st>>>(mz, w1, w2, w3, n, p->K, n3, p->wr, ibeta, topm, ws.cand, ws.pmass,
                                               cnt(g, CNT_ERR));
+    prof_end(g, st, n, 2.0 * ((double)HID * PD + (double)HID * HID + (double)HID * p->K));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -958,7 +964,7 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
     k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
                                                    g->prop_pmin, ws.zz,
                                                    g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, ws.flag1,
-                                                   nflag1);
+                                                   nflag1, ws.ctr + 1);
     EPLL_LAUNCHED(g);
     // exhaustive split-BF16 pass over the undecided patches
     return launch_split_pass(g, xhat, H, W, anchors, n, ws.flag1, nflag1, tau_abs, st);
