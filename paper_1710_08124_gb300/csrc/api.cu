@@ -24,6 +24,23 @@ void prof_end(epll_gmm *g, cudaStream_t st, int n, double flops_per_row)
     }
 }
 
+// BF16 of a float, rounded to nearest even (NaN kept quiet), and back.
+static uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float bf16_value(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -142,7 +159,7 @@ static void free_model(epll_gmm *g)
     free_batch(g);
     free_tables(g);
     if (g->lane) return;  // lanes share the model arrays of their handle
-    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo};
+    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo, g->d_Ub, g->d_U2b};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
@@ -262,7 +279,13 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     if ((s = launch_rescore(g, xhat, H, W, anchors, n, split_scores, tau_abs, st))) return s;
     if (forced_k)
         EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
+    // the FP32 form keeps the SIMT estimate (FP32 parity with the oracle);
+    // the reduced-precision forms use the split-BF16 tensor-core estimate
+    if (o.precision == EPLL_FP32 && o.select != EPLL_SELECT_PROPOSAL) {
+        if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
+    } else {
+        if ((s = launch_estimate_tc(g, xhat, H, W, anchors, n, st))) return s;
+    }
     g->last_evals += n;
     return EPLL_OK;
 }
@@ -464,6 +487,7 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(dalloc(&g->d_r, K)); A(dalloc(&g->d_roff, K + 1)); A(dalloc(&g->d_colk, R + COL_PAD));
     A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
     A(dalloc(&g->d_B, (size_t)PD * R + COL_PAD)); A(dalloc(&g->d_Blo, (size_t)PD * R + COL_PAD));
+    A(dalloc(&g->d_Ub, 2 * (size_t)PD * R)); A(dalloc(&g->d_U2b, 2 * (size_t)PD * R));
     g->Rp = R + COL_PAD;
     A(alloc_tables(g));
     if (e != cudaSuccess) {
@@ -483,6 +507,23 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_Blo, Blo.data(), sizeof(float) * Blo.size(), cudaMemcpyHostToDevice));
+    {
+        // split BF16 copies of B (hi = BF16(b), lo = BF16(b - hi)) in both
+        // orientations for the tensor-core estimation
+        const size_t PR = (size_t)PD * R;
+        std::vector<uint16_t> ub(2 * PR), u2b(2 * PR);
+        for (int ee = 0; ee < PD; ++ee)
+            for (int j = 0; j < R; ++j) {
+                const float b = B[(size_t)ee * R + j];
+                const uint16_t h = bf16_bits(b), l = bf16_bits(b - bf16_value(h));
+                ub[(size_t)j * PD + ee] = h;
+                ub[PR + (size_t)j * PD + ee] = l;
+                u2b[(size_t)ee * R + j] = h;
+                u2b[PR + (size_t)ee * R + j] = l;
+            }
+        A(cudaMemcpy(g->d_Ub, ub.data(), sizeof(uint16_t) * ub.size(), cudaMemcpyHostToDevice));
+        A(cudaMemcpy(g->d_U2b, u2b.data(), sizeof(uint16_t) * u2b.size(), cudaMemcpyHostToDevice));
+    }
     if (e != cudaSuccess) {
         free_model(g);
         delete g;

@@ -52,6 +52,8 @@ static epll_gmm *make_lane(const epll_gmm *g)
     l->d_lam = g->d_lam;
     l->d_B = g->d_B;
     l->d_Blo = g->d_Blo;
+    l->d_Ub = g->d_Ub;
+    l->d_U2b = g->d_U2b;
     l->Rp = g->Rp;
     l->rank_sum = g->rank_sum;
     l->lane = true;

@@ -130,6 +130,8 @@ struct epll_gmm {
     double *d_S = nullptr, *d_w = nullptr, *d_lam = nullptr;     // [K][64], [K], [K]
     float *d_B = nullptr;         // [64][Rtot] Ubar_k concatenated (FP32 rounding of U)
     float *d_Blo = nullptr;       // [64][Rtot] U - B (the FP32 rounding error)
+    uint16_t *d_Ub = nullptr;     // [2][Rtot][64] BF16 hi, lo of B transposed (estimation, first product)
+    uint16_t *d_U2b = nullptr;    // [2][64][Rtot] BF16 hi, lo of B (estimation, second product)
     epll::Tables tab;             // tables of the current iteration (a slot of tab0)
     epll::Tables tab0;            // storage of TB_MAX iterations' tables
     int Rp = 0;                   // Rtot + column padding
@@ -220,6 +222,9 @@ epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, i
 inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; }
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);
+// Same on the tensor cores in the split BF16 form (csrc/k_estimate_tc.cu).
+epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                               cudaStream_t st);
 // Reprojection.  When y != nullptr the pixelwise image update is fused
 // (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult; a == nullptr means a = 1),
 // otherwise xtilde is written to xout.

@@ -1,0 +1,241 @@
+// Patch estimation (Eqs. 15-16) on the tensor cores, grouped by component.
+//
+// For the patches that selected component k (a work item of up to 128):
+//   c = Ubar_k^T z,  c'_j = (gamma_kj - gamma_kP) c_j,
+//   zhat = Ubar_k c' + gamma_kP z + mu
+// as two chained GEMMs in the split BF16 form (hi*hi + lo*hi + hi*lo, the
+// same arithmetic as the split selection pass): the CTA gathers its patches
+// from the image into shared memory (DC removed, hi + lo, 128-byte-swizzled
+// K-major rows), TMA brings Ubar_k in both orientations (hi + lo), the first
+// product lands in TMEM, the epilogue scales it by the Wiener gains and writes
+// it back to shared memory as the split A operand of the second product, and
+// the second epilogue adds the tail term and the mean and writes the patch's
+// 64 estimates (one FP32 row per anchor) for the reprojection.
+#include "epll_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda_bf16.h>
+
+namespace epll {
+
+constexpr int ET_T = 128;
+constexpr int ET_TILE = ET_T * 128;  // 16 KB: [128 rows][64] BF16
+constexpr int ET_B = 64 * 128;       // 8 KB: [64 rows][64] BF16
+// A hi/lo, C' hi/lo, B1 hi/lo, B2 hi/lo, then barriers and per-row scalars
+constexpr int ET_SMEM = 1024 + 4 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4;
+
+static __device__ __forceinline__ uint32_t swz(int row, int e)
+{
+    // byte offset of element e (16-bit) of row `row` in a 128-byte-swizzled tile
+    return (uint32_t)(row * 128 + ((((e >> 3) ^ (row & 7))) << 4) + (e & 7) * 2);
+}
+
+__global__ void __launch_bounds__(ET_T)
+k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__ CUtensorMap mapU1lo,
+              const __grid_constant__ CUtensorMap mapU2, const __grid_constant__ CUtensorMap mapU2lo,
+              const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+              const int *__restrict__ perm, const int4 *__restrict__ items, const int *__restrict__ roff,
+              const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, int *__restrict__ err)
+{
+    if ((int)blockIdx.x >= items[0].w) return;
+    extern __shared__ __align__(1024) unsigned char et_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)et_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Ahi = smem, *Alo = Ahi + ET_TILE, *Chi = Alo + ET_TILE, *Clo = Chi + ET_TILE;
+    unsigned char *B1hi = Clo + ET_TILE, *B1lo = B1hi + ET_B, *B2hi = B1lo + ET_B, *B2lo = B2hi + ET_B;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(B2lo + ET_B);  // bases, GEMM 1, GEMM 2
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    float *s_mu = reinterpret_cast<float *>(bars + 8);
+    int *s_anchor = reinterpret_cast<int *>(s_mu + ET_T), *s_patch = s_anchor + ET_T;
+    const int4 it = items[1 + blockIdx.x];
+    const int k = it.x, first = it.y, cnt_p = it.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int o = roff[k], r = rk_[k];
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&bars[b]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (threadIdx.x == 0) {
+        // B1: rows o..o+63 of the [Rtot][64] copy (GEMM 1: N = basis column, K = pixel);
+        // B2: columns o..o+63 of the [64][Rtot] copy (GEMM 2: N = pixel, K = basis column)
+        const uint32_t b = smem_u32(&bars[0]);
+        mbar_expect_tx(b, 4 * ET_B);
+        tma_load_2d(smem_u32(B1hi), &mapU1, 0, o, b);
+        tma_load_2d(smem_u32(B1lo), &mapU1lo, 0, o, b);
+        tma_load_2d(smem_u32(B2hi), &mapU2, o, 0, b);
+        tma_load_2d(smem_u32(B2lo), &mapU2lo, o, 0, b);
+    }
+    if (threadIdx.x < cnt_p) {
+        const int i = perm[first + threadIdx.x];
+        s_patch[threadIdx.x] = i;
+        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+    }
+    __syncthreads();
+    // gather: warp w fills rows 32w .. 32w+31, eight rows' loads in flight,
+    // lane l holding patch elements 2l and 2l + 1
+    const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
+    for (int rr = 0; rr < 32; rr += 8) {
+        float xa[8], xb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = 32 * warp + rr + u;
+            xa[u] = xb[u] = 0.0f;
+            if (t < cnt_p) {
+                const int a = s_anchor[t];
+                const int ai = a / W, aj = a % W;
+                int rw = ai + pr_, c0 = aj + pc_, c1 = c0 + 1;
+                if (rw >= H) rw -= H;
+                if (c0 >= W) c0 -= W;
+                if (c1 >= W) c1 -= W;
+                xa[u] = xhat[(size_t)rw * W + c0];
+                xb[u] = xhat[(size_t)rw * W + c1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = 32 * warp + rr + u;
+            float sum = xa[u] + xb[u];
+#pragma unroll
+            for (int q = 16; q > 0; q >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, q);
+            const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
+            const float z0 = xa[u] - mu, z1 = xb[u] - mu;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
+            const uint32_t off = swz(t, 2 * lane);
+            *reinterpret_cast<__nv_bfloat162 *>(Ahi + off) = h;
+            *reinterpret_cast<__nv_bfloat162 *>(Alo + off) = l;
+            if (lane == 0) s_mu[t] = mu;
+        }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    const uint32_t idesc = idesc_f16(ET_T, 64, 1);
+    if (threadIdx.x == 0) {
+        if (mbar_wait(smem_u32(&bars[0]), 0, abort_flag)) {
+            tc_fence_after();
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(B1hi), bl = smem_u32(B1lo);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t q = 32 * kk;
+                mma_f16(tbase, sdesc_sw128(ah + q), sdesc_sw128(bh + q), idesc, kk ? 1u : 0u);
+                mma_f16(tbase, sdesc_sw128(al + q), sdesc_sw128(bh + q), idesc, 1u);
+                mma_f16(tbase, sdesc_sw128(ah + q), sdesc_sw128(bl + q), idesc, 1u);
+            }
+            mma_commit(smem_u32(&bars[1]));
+        }
+    }
+    __syncwarp();
+    // tcgen05.ld is warp-collective: every lane takes the same branch
+    bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), 0, abort_flag));
+    tc_fence_after();
+    const int t = 32 * warp + lane;
+    const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
+    if (ok) {
+        // c'_j = gw_kj c_j (zero beyond the rank), split into the A operand of GEMM 2
+        uint32_t c[64];
+        tmem_ld_all<64>(tl, c);
+#pragma unroll
+        for (int j8 = 0; j8 < 8; ++j8) {
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 8 * j8 + 2 * q;
+                const float v0 = j < r ? tab.gw[o + j] * __uint_as_float(c[j]) : 0.0f;
+                const float v1 = j + 1 < r ? tab.gw[o + j + 1] * __uint_as_float(c[j + 1]) : 0.0f;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+                ph[q] = *reinterpret_cast<const uint32_t *>(&h);
+                pl[q] = *reinterpret_cast<const uint32_t *>(&l);
+            }
+            const uint32_t off = (uint32_t)(t * 128 + ((j8 ^ (t & 7)) << 4));
+            *reinterpret_cast<uint4 *>(Chi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            *reinterpret_cast<uint4 *>(Clo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+        tc_fence_after();
+        const uint32_t ah = smem_u32(Chi), al = smem_u32(Clo), bh = smem_u32(B2hi), bl = smem_u32(B2lo);
+        const int ksteps = (r + 15) >> 4;
+        for (int kk = 0; kk < ksteps; ++kk) {
+            const uint32_t q = 32 * kk;
+            mma_f16(tbase + 64, sdesc_sw128(ah + q), sdesc_sw128(bh + q), idesc, kk ? 1u : 0u);
+            mma_f16(tbase + 64, sdesc_sw128(al + q), sdesc_sw128(bh + q), idesc, 1u);
+            mma_f16(tbase + 64, sdesc_sw128(ah + q), sdesc_sw128(bl + q), idesc, 1u);
+        }
+        mma_commit(smem_u32(&bars[2]));
+    }
+    __syncwarp();
+    ok = __all_sync(0xffffffffu, ok && mbar_wait(smem_u32(&bars[2]), 0, abort_flag));
+    tc_fence_after();
+    uint32_t v[64];
+    if (ok) tmem_ld_all<64>(tl + 64, v);  // whole warp, before the per-row test
+    if (ok && t < cnt_p) {
+        // zhat = Ubar c' + gamma_P z + mu, z = hi + lo of this row
+        const float gp = tab.gp[k], mu = s_mu[t];
+        float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)s_anchor[t] * PD);
+#pragma unroll
+        for (int e8 = 0; e8 < 8; ++e8) {
+            const uint32_t off = (uint32_t)(t * 128 + ((e8 ^ (t & 7)) << 4));
+            const uint4 zh = *reinterpret_cast<const uint4 *>(Ahi + off);
+            const uint4 zl = *reinterpret_cast<const uint4 *>(Alo + off);
+            const uint32_t hw[4] = {zh.x, zh.y, zh.z, zh.w}, lw[4] = {zl.x, zl.y, zl.z, zl.w};
+            float out[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&hw[q]);
+                const __nv_bfloat162 l = *reinterpret_cast<const __nv_bfloat162 *>(&lw[q]);
+                const float z0 = __low2float(h) + __low2float(l), z1 = __high2float(h) + __high2float(l);
+                out[2 * q] = fmaf(gp, z0, __uint_as_float(v[8 * e8 + 2 * q])) + mu;
+                out[2 * q + 1] = fmaf(gp, z1, __uint_as_float(v[8 * e8 + 2 * q + 1])) + mu;
+            }
+            dst[2 * e8] = make_float4(out[0], out[1], out[2], out[3]);
+            dst[2 * e8 + 1] = make_float4(out[4], out[5], out[6], out[7]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tbase) : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                               cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    epll_status s;
+    if ((s = group_by_component(g, ws.kstar, n, ws.perm, ws.items, st))) return s;
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(k_estimate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, ET_SMEM));
+        attr = true;
+    }
+    const size_t R = (size_t)g->Rtot;
+    CUtensorMap u1, u1lo, u2, u2lo;
+    if ((s = make_map(&u1, g->d_Ub, g->Rtot, 64))) return s;
+    if ((s = make_map(&u1lo, g->d_Ub + R * PD, g->Rtot, 64))) return s;
+    if ((s = make_map_wide(&u2, g->d_U2b, PD, 64, g->Rtot))) return s;
+    if ((s = make_map_wide(&u2lo, g->d_U2b + R * PD, PD, 64, g->Rtot))) return s;
+    const int max_items = (n + ET_T - 1) / ET_T + g->K;
+    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, xhat, H, W, anchors, ws.perm, ws.items,
+                                                    g->d_roff, g->d_r, g->tab, ws.zrow, cnt(g, CNT_ERR));
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+}  // namespace epll

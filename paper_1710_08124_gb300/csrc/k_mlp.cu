@@ -388,7 +388,6 @@ static __device__ __forceinline__ void tmem_ld_2x16(uint32_t taddr, uint32_t (&r
     tmem_wait(r);
 }
 
-static __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // (v, i) ranks before (w, j): larger logit first, lower index on equal logits
 static __device__ __forceinline__ bool before(float v, int i, float w, int j) { return v > w || (v == w && i < j); }
@@ -564,7 +563,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
             // then chunk by chunk into the activation buffer
             bool ok = true;
             for (int layer = 0; layer < 2 && ok; ++layer) {
-                ok = mbar_wait(smem_u32(&accfull[layer]), it & 1, abort_flag);
+                // tcgen05.ld is warp-collective: every lane takes the same branch
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accfull[layer]), it & 1, abort_flag));
                 if (!ok) break;
                 tc_fence_after();
 #pragma unroll 1
@@ -582,7 +582,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
                     }
                 }
             }
-            if (ok) ok = mbar_wait(smem_u32(&accfull[2]), it & 1, abort_flag);
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accfull[2]), it & 1, abort_flag));
             if (!ok) break;
             tc_fence_after();
             // output layer: this warp's columns 64 c + 16 j + q (increasing in
@@ -653,7 +653,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
                 if (lane == 0) mbar_arrive(smem_u32(mready));
             }
             if (j == 0) {
-                if (C::CG > 1 && !mbar_wait(smem_u32(mready), it & 1, abort_flag)) break;
+                if (C::CG > 1 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mready), it & 1, abort_flag))) break;
                 for (int jj = 1; jj < C::CG; ++jj) {
                     const float *o = scratch + (size_t)jj * SW * MT + rit;
                     const float omx = o[2 * TM * MT], ose = o[(2 * TM + 1) * MT];
@@ -679,7 +679,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
                 }
             }
             // the next tile's activations overwrite the scratch
-            if (C::CG > 1 && !mbar_wait(smem_u32(mdone), it & 1, abort_flag)) break;
+            if (C::CG > 1 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mdone), it & 1, abort_flag))) break;
         }
     }
     tc_fence_before();
@@ -808,7 +808,7 @@ k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant
         }
     }
     __syncwarp();
-    const bool ok = mbar_wait(smem_u32(&bars[1]), 0, abort_flag);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), 0, abort_flag));
     tc_fence_after();
     if (ok) {
         uint32_t r[64];

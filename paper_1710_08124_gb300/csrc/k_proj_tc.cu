@@ -309,7 +309,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             for (int it = 0; it < ntiles; ++it) {
                 const int gi = mt * ntiles + it;
                 const int b = gi % C::NB, tround = gi / C::NB;
-                if (!mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag)) {
+                // tcgen05.ld is warp-collective: every lane takes the same branch
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag))) {
                     ok = false;
                     break;
                 }
