@@ -497,3 +497,108 @@ def test_mlp_inference_form_scaling_and_topm():
     np.testing.assert_array_equal(idx, [[1, 2], [0, 1]])
     e = np.exp(logits[0] - 2.0)
     np.testing.assert_allclose(mass, [2 / e.sum(), 0.5], rtol=1e-15)
+
+
+def test_tree_kl_closed_forms():
+    """Eq. 17: for diagonal covariances 1/2 sum(a/b + b/a - 2); zero for equal
+    covariances; symmetric; invariant under a common rotation."""
+    from oracle import tree
+    rng = np.random.default_rng(8)
+    a, b = rng.uniform(0.1, 2.0, 64), rng.uniform(0.1, 2.0, 64)
+    assert abs(tree.sym_kl(np.diag(a), np.diag(b)) - 0.5 * np.sum(a / b + b / a - 2)) < 1e-10
+    A = rng.standard_normal((64, 64))
+    A = A @ A.T + 64 * np.eye(64)
+    B = rng.standard_normal((64, 64))
+    B = B @ B.T + 64 * np.eye(64)
+    assert abs(tree.sym_kl(A, A)) < 1e-10
+    assert abs(tree.sym_kl(A, B) - tree.sym_kl(B, A)) < 1e-10
+    Q, _ = np.linalg.qr(rng.standard_normal((64, 64)))
+    assert abs(tree.sym_kl(Q @ A @ Q.T, Q @ B @ Q.T) - tree.sym_kl(A, B)) < 1e-8 * tree.sym_kl(A, B)
+
+
+def test_tree_collapse_is_the_mixture_second_moment():
+    """Eq. 19: the collapsed covariance is the second moment of samples drawn
+    from the cluster's zero-mean mixture (Monte Carlo, 400k samples)."""
+    from oracle import tree
+    rng = np.random.default_rng(9)
+    P = 4
+    covs = []
+    for _ in range(3):
+        M = rng.standard_normal((P, P))
+        covs.append(M @ M.T + 0.5 * np.eye(P))
+    w = np.array([0.2, 0.5, 0.3])
+    wl, cl = tree.collapse(w, covs, [[0, 1, 2]])
+    assert abs(wl[0] - 1.0) < 1e-15
+    n = 400_000
+    comp = rng.choice(3, n, p=w)
+    x = np.empty((n, P))
+    for k in range(3):
+        sel = comp == k
+        x[sel] = rng.multivariate_normal(np.zeros(P), covs[k], sel.sum())
+    emp = x.T @ x / n
+    assert np.abs(emp - cl[0]).max() < 0.03 * np.abs(cl[0]).max()
+
+
+def test_tree_partition_balanced_and_swap_optimal():
+    """Clusters partition the components with sizes floor(n/L) or ceil(n/L),
+    no single swap lowers Eq. 18, and the cost beats random balanced partitions;
+    on 8 components in 2 clusters it is compared with brute force."""
+    import itertools
+    from oracle import tree
+    import synth
+    g = synth.synthetic_gmm(23)
+    covs = [g.U[k] @ np.diag(g.S[k]) @ g.U[k].T for k in range(23)]
+    D = tree.kl_matrix(covs)
+    parts = tree.partition(D, g.w, 8)
+    assert sorted(sum(parts, [])) == list(range(23))
+    assert sorted(len(p) for p in parts) == [2] + [3] * 7
+    c = tree.cost(D, parts)
+    for a, b in itertools.combinations(range(23), 2):
+        la = next(i for i, p in enumerate(parts) if a in p)
+        lb = next(i for i, p in enumerate(parts) if b in p)
+        if la == lb:
+            continue
+        q = [list(p) for p in parts]
+        q[la][q[la].index(a)] = b
+        q[lb][q[lb].index(b)] = a
+        assert tree.cost(D, q) >= c - 1e-9
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        perm = rng.permutation(23)
+        sizes = [len(p) for p in parts]
+        q, o = [], 0
+        for s_ in sizes:
+            q.append(perm[o:o + s_].tolist())
+            o += s_
+        assert tree.cost(D, q) >= c
+    D8 = D[:8, :8]
+    p8 = tree.partition(D8, g.w[:8], 2)
+    best = min(tree.cost(D8, [list(s_), [x for x in range(8) if x not in s_]])
+               for s_ in itertools.combinations(range(8), 4))
+    assert tree.cost(D8, p8) <= best * 1.10
+
+
+def test_tree_descent_special_cases():
+    """A root with every component as a child is the exhaustive argmin (lowest
+    index on ties); a hand-built two-level tree follows the cheaper branch even
+    when a leaf of the other branch is cheaper."""
+    from oracle import tree
+    rng = np.random.default_rng(4)
+    sc = rng.standard_normal((50, 6))
+    sc[3, 2] = sc[3, 4] = sc[3].min() - 1.0
+    cb = np.array([1, 7, 7, 7, 7, 7, 7, 7])   # root 0 -> nodes 1..6 (leaves)
+    leaf, gap = tree.descend(np.concatenate([np.zeros((50, 1)), sc], axis=1), cb)
+    assert np.array_equal(leaf - 1, np.argmin(sc, axis=1))
+    assert leaf[3] == 3 and gap[3] == 0.0
+    # root 0 -> {1, 2}; 1 -> {3, 4}; 2 -> {5, 6}
+    cb2 = np.array([1, 3, 5, 7, 7, 7, 7, 7])
+    s2 = np.array([[0, 1.0, 2.0, 5.0, 4.0, 0.5, 3.0]])
+    leaf2, gap2 = tree.descend(s2, cb2)
+    assert leaf2[0] == 4 and abs(gap2[0] - 1.0) < 1e-15
+
+
+def test_tree_level_sizes_follow_the_paper():
+    """K = 200 collapses to 64, 32, 16, 8, 4, 2 and 1 components (327 nodes)."""
+    from oracle import tree
+    s = tree.level_sizes(200)
+    assert s == [64, 32, 16, 8, 4, 2, 1] and 200 + sum(s) == 327
