@@ -69,7 +69,13 @@ enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3, EPLL_FP8 = 
  *            best rescored proposals are within the FP32 error bound of each
  *            other, is scored exhaustively (BF16X3, then compensated FP32
  *            rescoring of its near-ties).  `precision` is ignored. */
-enum { EPLL_SELECT_EXHAUSTIVE = 0, EPLL_SELECT_PROPOSAL = 1 };
+/* TREE       the balanced search tree attached to the model
+ *            (epll_gmm_attach_tree): every patch descends from the root to a
+ *            leaf, taking at each level the child with the lowest score of
+ *            Eq. 14 on the node's flat-tailed Gaussian (split BF16 on the
+ *            tensor cores; ties to the lowest child).  An approximation of the
+ *            exhaustive argmin, as in the paper.  `precision` is ignored. */
+enum { EPLL_SELECT_EXHAUSTIVE = 0, EPLL_SELECT_PROPOSAL = 1, EPLL_SELECT_TREE = 2 };
 
 typedef struct epll_gmm epll_gmm; /* opaque, library-owned */
 typedef struct epll_proposal epll_proposal; /* opaque, library-owned */
@@ -96,7 +102,7 @@ typedef struct {
     double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */
     uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
     int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
-    int select;         /* EPLL_SELECT_EXHAUSTIVE or EPLL_SELECT_PROPOSAL */
+    int select;         /* EPLL_SELECT_EXHAUSTIVE, EPLL_SELECT_PROPOSAL or EPLL_SELECT_TREE */
 } epll_options;
 
 /* Fills *o with the defaults: FP32, default tie gap, all patches, seed 0, 100 CG
@@ -127,6 +133,24 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
 
 /* Frees the handle and its workspace (synchronises the device). NULL is a no-op. */
 void epll_gmm_free(epll_gmm *g);
+
+/*
+ * Attaches the balanced search tree of Sec. "Speed-up via a balanced search
+ * tree" (built offline, e.g. by collapsing the GMM with Eqs. 17-19) to a
+ * model; the handle keeps its own copy.  Nodes are given in breadth-first
+ * order, node 0 the root, the children of node v being the consecutive nodes
+ * child_begin[v] .. child_begin[v+1]-1 (child_begin[0] = 1, child_begin[n_nodes]
+ * = n_nodes); each node is a zero-mean Gaussian in the layout of
+ * epll_gmm_load (host weights [n], eigvecs [n][64][64], eigvals [n][64],
+ * flat-tailed with the model's rank rule); leaf_component[v] is the model
+ * component of a leaf, -1 for an internal node.  Every component must be
+ * exactly one leaf, every leaf at the same depth (1..32), no node may have
+ * more than 4 children nor children with more than 256 basis columns in all.
+ * n_nodes = 0 detaches.  Synchronous.  Errors: EPLL_EINVAL, EPLL_ENOMEM,
+ * EPLL_ECUDA.
+ */
+epll_status epll_gmm_attach_tree(epll_gmm *g, int n_nodes, const double *weights, const double *eigvecs,
+                                 const double *eigvals, const int *child_begin, const int *leaf_component);
 
 /* Copies the chosen ranks r_k (host int[K]) and tail eigenvalues lambda_k
  * (host double[K], 0 where r_k = P) out of the handle; either may be NULL. */

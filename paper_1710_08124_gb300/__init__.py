@@ -24,7 +24,7 @@ RANK_FIXED, RANK_RHO = 0, 1
 DENOISE, PIXELWISE, CONV_PERIODIC = 0, 1, 2
 SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER = 0, 1, 2
 FP32, BF16, FP16, BF16X3, FP8 = 0, 1, 2, 3, 4
-SELECT_EXHAUSTIVE, SELECT_PROPOSAL = 0, 1
+SELECT_EXHAUSTIVE, SELECT_PROPOSAL, SELECT_TREE = 0, 1, 2
 PAPER_BETA = (1.0, 4.0, 8.0, 16.0, 32.0)
 
 
@@ -118,6 +118,7 @@ def lib():
         L.epll_gmm_attach_proposal.argtypes = [vp, vp, i, C.c_float]
         L.epll_proposal_topm.argtypes = [vp, vp, i, i, vp, i, d, vp, vp, vp]
         L.epll_last_fallbacks.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.epll_gmm_attach_tree.argtypes = [vp, i, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -407,3 +408,20 @@ def proposal_topm(g: GMM, xhat, beta: float, anchors=None, stream=None):
     _check(lib().epll_proposal_topm(g.handle, _dptr(xhat, torch.float32), H, W, _dptr(anchors, torch.int32), n,
                                     float(beta), _dptr(cand), _dptr(pmass), _stream(stream)))
     return cand, pmass
+
+
+def attach_tree(g: GMM, tree):
+    """Attaches a search tree (``tree.build_tree``'s result) to a model, or
+    detaches it with None."""
+    if tree is None:
+        _check(lib().epll_gmm_attach_tree(g.handle, 0, None, None, None, None, None))
+        g._tree = None
+        return
+    w = np.ascontiguousarray(tree.weights, np.float64)
+    U = np.ascontiguousarray(tree.eigvecs, np.float64)
+    S = np.ascontiguousarray(tree.eigvals, np.float64)
+    cb = np.ascontiguousarray(tree.child_begin, np.int32)
+    lf = np.ascontiguousarray(tree.leaf_component, np.int32)
+    _check(lib().epll_gmm_attach_tree(g.handle, int(w.shape[0]), w.ctypes.data, U.ctypes.data, S.ctypes.data,
+                                      cb.ctypes.data, lf.ctypes.data))
+    g._tree = tree

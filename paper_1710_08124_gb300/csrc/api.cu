@@ -64,7 +64,7 @@ static void free_workspace(Workspace &ws)
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
                     ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
-                    ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore};
+                    ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore, ws.tnode, ws.tcounts, ws.titems};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
@@ -154,9 +154,23 @@ static void free_tables(epll_gmm *g)
 }
 
 
+void free_tree(epll_gmm *g)
+{
+    TreeState *tr = g->tree;
+    if (!tr) return;
+    if (tr->tm) epll_gmm_free(tr->tm);
+    if (tr->owns_arrays) {
+        if (tr->d_child) cudaFree(tr->d_child);
+        if (tr->d_leaf) cudaFree(tr->d_leaf);
+    }
+    delete tr;
+    g->tree = nullptr;
+}
+
 static void free_model(epll_gmm *g)
 {
     free_batch(g);
+    free_tree(g);
     free_tables(g);
     if (g->lane) return;  // lanes share the model arrays of their handle
     void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo, g->d_Ub, g->d_U2b};
@@ -189,8 +203,8 @@ static epll_status check_options(const epll_options &o, int H, int W)
         return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION or _JITTER");
     }
     if (o.cg_iters < 0 || o.cg_iters > 100000) return fail(EPLL_EINVAL, "options.cg_iters out of range");
-    if (o.select != EPLL_SELECT_EXHAUSTIVE && o.select != EPLL_SELECT_PROPOSAL)
-        return fail(EPLL_EINVAL, "options.select must be EPLL_SELECT_EXHAUSTIVE or _PROPOSAL");
+    if (o.select != EPLL_SELECT_EXHAUSTIVE && o.select != EPLL_SELECT_PROPOSAL && o.select != EPLL_SELECT_TREE)
+        return fail(EPLL_EINVAL, "options.select must be EPLL_SELECT_EXHAUSTIVE, _PROPOSAL or _TREE");
     return EPLL_OK;
 }
 
@@ -198,6 +212,8 @@ static epll_status check_select(const epll_gmm *g, const epll_options &o)
 {
     if (o.select == EPLL_SELECT_PROPOSAL && !g->prop)
         return fail(EPLL_EINVAL, "options.select is EPLL_SELECT_PROPOSAL but no proposal network is attached");
+    if (o.select == EPLL_SELECT_TREE && !g->tree)
+        return fail(EPLL_EINVAL, "options.select is EPLL_SELECT_TREE but no search tree is attached");
     return EPLL_OK;
 }
 
@@ -230,6 +246,7 @@ static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
 static int basis_format(const epll_options &o)
 {
     if (o.select == EPLL_SELECT_PROPOSAL) return 4;  // exhaustive fallback: split BF16 pass
+    if (o.select == EPLL_SELECT_TREE) return 0;      // the node model carries the bases
     switch (o.precision) {
     case EPLL_BF16: return 1 | 4;
     case EPLL_FP16: return 2 | 4;
@@ -247,6 +264,9 @@ static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &
     Workspace &ws = g->ws;
     epll_status s;
     if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o), st))) return s;
+    if (o.select == EPLL_SELECT_TREE &&
+        (s = launch_tables(g->tree->tm, d_lambda, mult, nb, sigma2, beta_direct, 4, st)))
+        return s;
     return launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, st);
 }
 
@@ -254,6 +274,10 @@ static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &
 static void use_slot(epll_gmm *g, int b, size_t N)
 {
     g->tab = slot_tables(g->tab0, b, g->K, g->Rp, g->Rtot);
+    if (g->tree) {
+        epll_gmm *tm = g->tree->tm;
+        tm->tab = slot_tables(tm->tab0, b, tm->K, tm->Rp, tm->Rtot);
+    }
     g->ws.anchors = g->ws.anchors_all + (size_t)b * N;
     g->ws.mult = g->ws.mult_all + (size_t)b * N;
 }
@@ -268,7 +292,9 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
     float tau_abs, tau_rel;
     thresholds(o, &tau_abs, &tau_rel);
-    if (o.select == EPLL_SELECT_PROPOSAL) {
+    if (o.select == EPLL_SELECT_TREE) {
+        if ((s = launch_select_tree(g, xhat, H, W, anchors, n, st))) return s;
+    } else if (o.select == EPLL_SELECT_PROPOSAL) {
         if ((s = launch_select_proposal(g, xhat, H, W, anchors, n, tau_abs, st))) return s;
     } else if (o.precision != EPLL_FP32) {
         if ((s = launch_select_tc(g, xhat, H, W, anchors, n, o.precision, tau_abs, tau_rel, st))) return s;
@@ -276,12 +302,14 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
         if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau_abs, tau_rel, st))) return s;
     }
     const bool split_scores = o.select == EPLL_SELECT_PROPOSAL || o.precision != EPLL_FP32;
-    if ((s = launch_rescore(g, xhat, H, W, anchors, n, split_scores, tau_abs, st))) return s;
+    if (o.select != EPLL_SELECT_TREE &&
+        (s = launch_rescore(g, xhat, H, W, anchors, n, split_scores, tau_abs, st)))
+        return s;
     if (forced_k)
         EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     // the FP32 form keeps the SIMT estimate (FP32 parity with the oracle);
     // the reduced-precision forms use the split-BF16 tensor-core estimate
-    if (o.precision == EPLL_FP32 && o.select != EPLL_SELECT_PROPOSAL) {
+    if (o.precision == EPLL_FP32 && o.select == EPLL_SELECT_EXHAUSTIVE) {
         if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
     } else {
         if ((s = launch_estimate_tc(g, xhat, H, W, anchors, n, st))) return s;
@@ -540,6 +568,87 @@ void epll_gmm_free(epll_gmm *g)
     free_workspace(g->ws);
     free_model(g);
     delete g;
+}
+
+epll_status epll_gmm_attach_tree(epll_gmm *g, int n_nodes, const double *weights, const double *eigvecs,
+                                 const double *eigvals, const int *child_begin, const int *leaf_component)
+{
+    if (!g || g->lane) return fail(EPLL_EINVAL, "null model handle");
+    if (n_nodes == 0) {
+        EPLL_CU(cudaDeviceSynchronize());
+        free_batch(g);
+        free_tree(g);
+        return EPLL_OK;
+    }
+    if (n_nodes < 2 || n_nodes > 65536) return fail(EPLL_EINVAL, "n_nodes must be in 2..65536 (0 detaches)");
+    if (!weights || !eigvecs || !eigvals || !child_begin || !leaf_component)
+        return fail(EPLL_EINVAL, "null tree array");
+    if (child_begin[0] != 1 || child_begin[n_nodes] != n_nodes)
+        return fail(EPLL_EINVAL, "child_begin must start at 1 (the root's children) and end at n_nodes");
+    std::vector<int> parent(n_nodes, -1), depth(n_nodes, 0);
+    std::vector<char> seen(g->K, 0);
+    int leaves = 0, leaf_depth = -1;
+    for (int v = 0; v < n_nodes; ++v) {
+        const int b = child_begin[v], e = child_begin[v + 1];
+        if (e < b) return fail(EPLL_EINVAL, "child_begin must be non-decreasing");
+        if (e > b) {
+            if (b <= v) return fail(EPLL_EINVAL, "nodes must be in breadth-first order (children after their parent)");
+            if (e - b > 4) return fail(EPLL_EINVAL, "a node has more than 4 children");
+            if (leaf_component[v] != -1) return fail(EPLL_EINVAL, "an internal node has a leaf component");
+            for (int c = b; c < e; ++c) parent[c] = v;
+        } else {
+            const int k = leaf_component[v];
+            if (k < 0 || k >= g->K || seen[k]) return fail(EPLL_EINVAL, "leaves must map to distinct components");
+            seen[k] = 1;
+            ++leaves;
+        }
+    }
+    if (leaves != g->K) return fail(EPLL_EINVAL, "every component must be a leaf");
+    for (int v = 1; v < n_nodes; ++v) depth[v] = depth[parent[v]] + 1;
+    for (int v = 0; v < n_nodes; ++v)
+        if (child_begin[v] == child_begin[v + 1]) {
+            if (leaf_depth < 0) leaf_depth = depth[v];
+            if (depth[v] != leaf_depth) return fail(EPLL_EINVAL, "every leaf must be at the same depth");
+        }
+    if (leaf_depth < 1 || leaf_depth > 32) return fail(EPLL_EINVAL, "tree depth must be in 1..32");
+    epll_gmm *tm = nullptr;
+    epll_status s = epll_gmm_load(n_nodes, PD, weights, eigvecs, eigvals, g->rank_mode, g->rank_param, &tm);
+    if (s) return s;
+    double cols = 0.0;
+    int internal = 0;
+    for (int v = 0; v < n_nodes; ++v)
+        if (child_begin[v + 1] > child_begin[v]) {
+            const int last = child_begin[v + 1] - 1;
+            const int c = tm->h_roff[last] + (tm->h_r[last] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN -
+                          tm->h_roff[child_begin[v]];
+            if (c > 256) {
+                epll_gmm_free(tm);
+                return fail(EPLL_EINVAL, "a node's children have more than 256 basis columns");
+            }
+            cols += c;
+            ++internal;
+        }
+    TreeState *tr = new TreeState();
+    tr->tm = tm;
+    tr->n_nodes = n_nodes;
+    tr->depth = leaf_depth;
+    tr->child_cols_mean = cols / internal;
+    cudaError_t e = cudaMalloc(&tr->d_child, sizeof(int) * (n_nodes + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&tr->d_leaf, sizeof(int) * n_nodes);
+    if (e == cudaSuccess) e = cudaMemcpy(tr->d_child, child_begin, sizeof(int) * (n_nodes + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tr->d_leaf, leaf_component, sizeof(int) * n_nodes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        epll_gmm tmp;
+        tmp.tree = tr;
+        free_tree(&tmp);
+        return fail(EPLL_ENOMEM, std::string("tree upload: ") + cudaGetErrorString(e));
+    }
+    EPLL_CU(cudaDeviceSynchronize());
+    free_batch(g);
+    free_tree(g);
+    g->tree = tr;
+    return EPLL_OK;
 }
 
 epll_status epll_gmm_ranks(const epll_gmm *g, int *ranks, double *lambdas)

@@ -33,7 +33,7 @@ struct BatchState {
     int tuned_lanes = 0;
 };
 
-static epll_gmm *make_lane(const epll_gmm *g)
+epll_gmm *make_lane(const epll_gmm *g)
 {
     epll_gmm *l = new epll_gmm();
     l->K = g->K;
@@ -94,6 +94,7 @@ static std::vector<unsigned char> job_key(const epll_gmm *g, int n, const epll_j
 {
     std::vector<unsigned char> k;
     put(k, g->prop);
+    put(k, g->tree);
     put(k, g->prop_topm);
     put(k, g->prop_pmin);
     put(k, n);
@@ -163,6 +164,22 @@ static epll_status prepare_lanes(epll_gmm *g, BatchState *b, const std::vector<s
         b->lanes[l]->prop = g->prop;
         b->lanes[l]->prop_topm = g->prop_topm;
         b->lanes[l]->prop_pmin = g->prop_pmin;
+        // the tree: a lane of the node model (own tables), the handle's arrays
+        epll_gmm *ln = b->lanes[l];
+        if (!(ln->tree && ln->tree->src == g->tree)) {
+            free_tree(ln);
+            if (g->tree) {
+                TreeState *tr = new TreeState(*g->tree);
+                tr->owns_arrays = false;
+                tr->src = g->tree;
+                tr->tm = make_lane(g->tree->tm);
+                if (!tr->tm) {
+                    delete tr;
+                    return fail(EPLL_ENOMEM, "batch lane tree allocation failed");
+                }
+                ln->tree = tr;
+            }
+        }
     }
     return EPLL_OK;
 }

@@ -103,6 +103,12 @@ struct Workspace {
     float *kern = nullptr;                    // [H][W] wrapped blur kernel
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     int planH = 0, planW = 0;
+    // search tree (allocated on first use)
+    int *tnode = nullptr;                     // [N] current node of each patch
+    int *tcounts = nullptr;                   // [nodes] bucket counters
+    int4 *titems = nullptr;                   // work items of a level
+    size_t tree_cap = 0;
+    int tree_nodes = 0;
     // learned proposal (allocated on first use)
     size_t prop_cap = 0;
     int *cand = nullptr;                      // [N][topm] proposed components
@@ -113,6 +119,19 @@ struct Workspace {
 };
 
 struct BatchState;  // lanes, streams and the captured graph of epll_restore_batch
+
+// Search tree attached to a model: its nodes form a model of their own (the
+// node Gaussians, flat-tailed with the model's rank rule; tables per beta),
+// in breadth-first order with every node's children consecutive.
+struct TreeState {
+    epll_gmm *tm = nullptr;       // node model (owned)
+    int n_nodes = 0, depth = 0;
+    int *d_child = nullptr;       // [n_nodes + 1] child ranges
+    int *d_leaf = nullptr;        // [n_nodes] component of a leaf, -1 otherwise
+    bool owns_arrays = true;      // batch lanes share their handle's child / leaf arrays
+    const TreeState *src = nullptr;  // for a lane: the handle's tree it mirrors
+    double child_cols_mean = 0;   // mean basis columns of a node's children (instrumentation)
+};
 
 }  // namespace epll
 
@@ -148,6 +167,8 @@ struct epll_gmm {
     // arrays and owns its own tables and workspace
     bool lane = false;
     epll::BatchState *batch = nullptr;
+    // search tree (owned; see TreeState)
+    epll::TreeState *tree = nullptr;
     // learned top-m proposal (not owned)
     const epll_proposal *prop = nullptr;
     int prop_topm = 0;
@@ -219,6 +240,16 @@ epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, co
                                 cudaStream_t st);
 // Counting sort of n keys (components) into perm and estimation work items.
 epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st);
+// Same for keys in 0..K-1 with an explicit [K] counter array.
+epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts, int *perm, int4 *items,
+                         cudaStream_t st);
+// Selection down the search tree (csrc/k_tree.cu): writes kstar and the
+// smallest sibling gap on each patch's path.
+epll_status launch_select_tree(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                               cudaStream_t st);
+// A context sharing g's model arrays with its own tables (csrc/batch.cu).
+epll_gmm *make_lane(const epll_gmm *g);
+void free_tree(epll_gmm *g);
 inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; }
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);

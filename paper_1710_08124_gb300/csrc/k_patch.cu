@@ -577,9 +577,13 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
 
 epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st)
 {
-    Workspace &ws = g->ws;
-    const int K = g->K;
-    int *counts = ws.counts;  // [K] counts -> cursors
+    return group_by_key(g, keys, n, g->K, g->ws.counts, perm, items, st);
+}
+
+epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts, int *perm, int4 *items,
+                         cudaStream_t st)
+{
+    // counts: [K] counts -> cursors
     EPLL_CU(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)K, st));
     int hb = (n + 255) / 256;
     if (hb > 152 * 2) hb = 152 * 2;

@@ -85,3 +85,7 @@ def test_proposal_layout_and_validation(L):
                                  C.c_float(0.0), None, None) == ep.EINVAL
     assert L.epll_proposal_get(None, None) == ep.EINVAL
     L.epll_proposal_free(None)
+
+
+def test_attach_tree_rejects_null_handle(L):
+    assert L.epll_gmm_attach_tree(None, 0, None, None, None, None, None) == ep.EINVAL
