@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--pmin", type=float, default=0.0, help="proposal workload: softmax mass below which a "
                     "patch is scored exhaustively")
     ap.add_argument("--train-steps", type=int, default=3000, help="proposal workload: AdamW steps")
-    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal"], default="fepll",
+    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal", "tree"], default="fepll",
                     help="fepll: the 512x512 FEPLL denoising workload (default line); proposal: the learned "
-                         "top-m proposal at 512x512, sigma 25/255, K=200, r=64; uneven: 64 images of "
+                         "top-m proposal at 512x512, sigma 25/255, K=200, r=64; tree: the balanced search "
+                         "tree at 512x512, sigma 25/255, K=200, r in {64,8}; uneven: 64 images of "
                          "uneven size, noise and degradation in one captured batch vs per-image launches")
     return ap.parse_args()
 
@@ -473,6 +474,150 @@ def run_proposal(args):
     return 0
 
 
+# ---------------------------------------------------------------- tree workload
+TREE_WORKLOAD = ("balanced search tree (327 nodes: 200 -> 64 -> 32 -> 16 -> 8 -> 4 -> 2 -> 1, built by "
+                 "Eqs. 17-19) vs exhaustive selection: 512x512 dead-leaves image, sigma 25/255, K=200, flat-tail "
+                 "rank r in {64, 8}, random 1/3 patch subset, 5 HQS iterations")
+
+
+def run_tree(args):
+    """Restorations with the selection down the search tree against the
+    exhaustive split-BF16 and plain FP32 forms on the same image, per rank;
+    selection agreement with the exhaustive path along its trajectory; the
+    FP64 oracle's descent timed on a sample of patches (cpu_baseline)."""
+    import torch
+
+    import paper_1710_08124_gb300 as ep
+    from paper_1710_08124_gb300 import proposal as pr
+    from paper_1710_08124_gb300 import tree as ptree
+
+    ep.build()
+    dev = torch.device("cuda", 0)
+    g = synth.synthetic_gmm(K)
+    t0 = time.perf_counter()
+    T = ptree.build_tree(g.w, g.U, g.S)
+    build_s = time.perf_counter() - t0
+    sigma = PROP_SIGMA
+    x, y = synth.denoise_problem(301, H, sigma)
+    yd = torch.as_tensor(y.astype(np.float32), device=dev)
+    out = torch.empty_like(yd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    common = dict(subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=2)
+    o_ex = ep.Options(precision=ep.BF16X3, **common)
+    o_32 = ep.Options(precision=ep.FP32, **common)
+    o_tr = ep.Options(select=ep.SELECT_TREE, **common)
+    steps = max(5, min(args.steps, 60))
+    lam = pr.denoise_lambda(sigma)
+
+    def timed(gm, options, n):
+        for _ in range(max(args.warmup, 3)):
+            ep.restore(gm, yd, sigma, BETA, options=options, out=out)
+        _, _, launches = ep.last_counters(gm)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ep.restore(gm, yd, sigma, BETA, options=options, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        return n / tot, out.cpu().numpy(), launches, tot
+
+    per_rank = {}
+    clk = None
+    sel = {}
+    for r in RANKS:
+        gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r)
+        ep.attach_tree(gm, T)
+        ex_rate, x_ex, _, _ = timed(gm, o_ex, steps)
+        r32, x_32, _, _ = timed(gm, o_32, max(3, steps // 10))
+        traj = [yd] + [ep.restore(gm, yd, sigma, BETA[:t], options=o_ex) for t in range(1, len(BETA))]
+        agree = nsel = 0
+        for t, xt in enumerate(traj):
+            beta = lam * BETA[t] / sigma ** 2
+            _, _, k_ex, _ = ep.patch_step(gm, xt, beta, o_ex, t)
+            _, _, k_tr, _ = ep.patch_step(gm, xt, beta, o_tr, t)
+            agree += int((k_tr == k_ex).sum().item())
+            nsel += int(k_ex.numel())
+        if r == RANKS[0]:
+            ep.profile_enable(gm, True)
+            ep.profile_read(gm)
+            clocks = ClockSampler(0)
+            clocks.start()
+        rate, x_tr, launches, tot = timed(gm, o_tr, steps)
+        if r == RANKS[0]:
+            clk = clocks.stop()
+            sel = dict(zip(("ms", "launches", "flops"), ep.profile_read(gm)))
+            sel["tot"] = tot
+            ep.profile_enable(gm, False)
+        per_rank[r] = {"tree_restores_per_s": rate, "exhaustive_bf16x3_restores_per_s": ex_rate,
+                       "plain_fp32_restores_per_s": r32, "speedup_vs_exhaustive": rate / ex_rate,
+                       "speedup_vs_plain_fp32": rate / r32, "selection_agreement_with_exhaustive": agree / nsel,
+                       "psnr_db": {"tree": psnr(x_tr, x), "exhaustive_bf16x3": psnr(x_ex, x),
+                                   "plain_fp32": psnr(x_32, x)},
+                       "gpu_launches_per_restore": launches, "_steps": steps}
+        if r == RANKS[0]:
+            hy = torch.from_numpy(y.astype(np.float32)).pin_memory()
+            hx = torch.empty((H, W), dtype=torch.float32).pin_memory()
+            ep.restore_host(gm, hy, sigma, BETA, options=o_tr, out=hx)
+            torch.cuda.synchronize()
+            n_e2e = max(3, steps // 2)
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                ep.restore_host(gm, hy, sigma, BETA, options=o_tr, out=hx)
+            e2e_rate = n_e2e / (time.perf_counter() - t0)
+    main = per_rank[RANKS[0]]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    achieved = sel["flops"] / (sel["ms"] / 1e3) / 1e12 if sel.get("ms") else None
+    line = {
+        "metric": "512x512 restores/s with the search-tree selection (K=200, r=64, 1/3 subset, sigma 25/255)",
+        "value": main["tree_restores_per_s"], "unit": "restores/s", "n_gpus": 1, "steps": main["_steps"],
+        "warmup": args.warmup, "ms_per_step": 1e3 / main["tree_restores_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": TREE_WORKLOAD, "tree_nodes": T.n_nodes, "tree_depth": T.depth,
+                   "tree_build_s": build_s,
+                   "l2": "256 MB buffer written before each restore, outside the timed events"},
+        "mpatch_evals_per_s": main["tree_restores_per_s"] * len(BETA) * M_PATCH / 1e6,
+        "e2e": {"value": e2e_rate, "unit": "restores/s", "h2d_bytes_per_step": N_PIX * 4,
+                "d2h_bytes_per_step": N_PIX * 4},
+        "gpu_launches": main["gpu_launches_per_restore"] * main["_steps"],
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "tree level (gather + split-BF16 children scores)",
+                     "launches": int(sel.get("launches", 0)), "kernel_ms": sel.get("ms"),
+                     "share_of_step": sel["ms"] / 1e3 / sel["tot"] if sel.get("ms") else None,
+                     "peak_source": "measured (sustained, cuBLAS bf16)" if peaks else "fallback"},
+        "per_rank": {str(r): {k: v for k, v in d.items() if not k.startswith("_")} for r, d in per_rank.items()},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import tree as otree
+        om_nodes = oracle.Model(T.weights, T.eigvecs, T.eigvals, "fixed", RANKS[0])
+        an = oracle.sample(H, W, oracle.FRACTION, FRACTION, seed=1, t=0)
+        nsamp = 2048
+        t0 = time.perf_counter()
+        sc = oracle.scores(om_nodes, 8 / sigma ** 2, x.astype(np.float64), an[:nsamp])
+        otree.descend(sc, T.child_begin)
+        dt = time.perf_counter() - t0
+        per_patch = dt / nsamp
+        line["cpu_baseline"] = {"value": 1.0 / (per_patch * len(BETA) * M_PATCH), "unit": "restores/s",
+                                "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": f"FP64 oracle tree selection (all node scores, then the descent) of "
+                                          f"{nsamp} patches at r={RANKS[0]}, scaled to {len(BETA)} iterations x "
+                                          f"{M_PATCH} patches (selection only)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 def traffic_record(kernel_src_hash: str, precision: str):
     """DRAM bytes per selection-kernel launch from the committed ncu summary,
@@ -498,6 +643,8 @@ def main():
         return run_uneven(args) if rank == 0 else 0
     if args.workload == "proposal":
         return run_proposal(args) if rank == 0 else 0
+    if args.workload == "tree":
+        return run_tree(args) if rank == 0 else 0
 
     import torch
 

@@ -235,6 +235,9 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
 // (1/beta read from the device scalar ibeta).
 epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  const float *ibeta, cudaStream_t st);
+// Split BF16 (hi, lo) DC-free patches into ws.Zb's two halves and |z|^2 into ws.zz.
+epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                 cudaStream_t st);
 // BF16 DC-free patches into ws.Zb (rows padded to 128 with zeros) and |z|^2 into ws.zz.
 epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                 cudaStream_t st);

@@ -418,21 +418,30 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ c
     if (threadIdx.x == 0) items[0] = make_int4(0, 0, 0, icarry);
 }
 
-__global__ void k_bucket_scatter(const int *__restrict__ kstar, int n, int K, int *__restrict__ cursor,
-                                 int *__restrict__ perm)
+// A block places 1024 keys: per-key ranks from shared-memory counters, one
+// global reservation per key present in the block, then the writes.
+constexpr int SCAT_T = 256, SCAT_PER = 4;
+__global__ void __launch_bounds__(SCAT_T)
+k_bucket_scatter(const int *__restrict__ keys, int n, int K, int *__restrict__ cursor, int *__restrict__ perm)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = i < n ? clamp_k(kstar[i], K) : -1;
-    // lanes with the same component share one atomic: the lowest such lane
-    // reserves the group's slots, the others take consecutive ones
-    const unsigned peers = __match_any_sync(0xffffffffu, k);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    int base = 0;
-    if (lane == leader && k >= 0) base = atomicAdd(&cursor[k], __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (k >= 0) perm[base + rank] = i;
+    extern __shared__ int sh[];  // [K]: block counts, then the block's base in each bucket
+    for (int k = threadIdx.x; k < K; k += SCAT_T) sh[k] = 0;
+    __syncthreads();
+    const int i0 = blockIdx.x * SCAT_T * SCAT_PER + threadIdx.x;
+    int key[SCAT_PER], loc[SCAT_PER];
+#pragma unroll
+    for (int u = 0; u < SCAT_PER; ++u) {
+        const int i = i0 + u * SCAT_T;
+        key[u] = i < n ? clamp_k(keys[i], K) : -1;
+        loc[u] = key[u] >= 0 ? atomicAdd(&sh[key[u]], 1) : 0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += SCAT_T)
+        if (sh[k]) sh[k] = atomicAdd(&cursor[k], sh[k]);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SCAT_PER; ++u)
+        if (key[u] >= 0) perm[sh[key[u]] + loc[u]] = i0 + u * SCAT_T;
 }
 
 // ============================================================================
@@ -591,7 +600,8 @@ epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts
     EPLL_LAUNCHED(g);
     k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, items);
     EPLL_LAUNCHED(g);
-    k_bucket_scatter<<<(n + 255) / 256, 256, 0, st>>>(keys, n, K, counts, perm);
+    k_bucket_scatter<<<(n + SCAT_T * SCAT_PER - 1) / (SCAT_T * SCAT_PER), SCAT_T, sizeof(int) * (size_t)K, st>>>(
+        keys, n, K, counts, perm);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

@@ -582,6 +582,17 @@ epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, co
     return EPLL_OK;
 }
 
+epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                                 cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int rows = (n + TC_M - 1) / TC_M * TC_M;
+    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, 1, 1, ws.Zb,
+                                                 ws.Zb + ws.zrows * PD, ws.zz, nullptr);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
 epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                               const int *flag1, const int *nflag1, float tau_abs, cudaStream_t st)
 {

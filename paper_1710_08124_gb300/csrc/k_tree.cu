@@ -4,11 +4,12 @@
 // Eq. 14, on the node's own tables) is cheapest, until it reaches a leaf,
 // i.e. a component of the model.
 //
-// One launch per level.  The patches are grouped by their current node (the
-// counting sort of the estimation step, keyed by node), and a CTA takes one
-// group of up to 128 patches of one node: it gathers them from the image
-// into shared memory as split BF16 operands (hi + lo, 128-byte-swizzled
-// K-major rows) with their |z|^2, loads the children's concatenated scaled
+// The DC-free patches are extracted once per iteration as split BF16
+// operands (hi + lo) with their |z|^2; then one launch per level.  The
+// patches are grouped by their current node (the counting sort of the
+// estimation step, keyed by node), and a CTA takes one group of up to 128
+// patches of one node: it copies their operand rows into shared memory
+// (128-byte-swizzled K-major rows), loads the children's concatenated scaled
 // bases (consecutive in the node model's column order, at most 256 columns)
 // by TMA, accumulates hi*hi + lo*hi + hi*lo into TMEM and scores each child
 // in the epilogue.  Ties go to the lowest child.  The smallest top-2 gap met
@@ -27,11 +28,11 @@ constexpr int TL_TILE = TL_T * 128;  // 16 KB: [128 rows][64] BF16
 constexpr int TL_BMAX = 256;         // basis columns of one node's children
 constexpr int TL_B = TL_BMAX * 128;  // 32 KB
 constexpr int TL_CH = 4;             // children of one node
-constexpr int TL_SMEM = 1024 + 2 * TL_TILE + 2 * TL_B + 64 + 3 * TL_T * 4;
+constexpr int TL_SMEM = 1024 + 2 * TL_TILE + 2 * TL_B + 64 + 2 * TL_T * 4;
 
 __global__ void __launch_bounds__(TL_T)
 k_tree_level(const __grid_constant__ CUtensorMap mapBs, const __grid_constant__ CUtensorMap mapBlo,
-             const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+             const uint4 *__restrict__ Zhi, const uint4 *__restrict__ Zlo, const float *__restrict__ zz,
              const int *__restrict__ perm, const int4 *__restrict__ items, const int *__restrict__ child,
              const int *__restrict__ leaf, const int *__restrict__ roff, const int *__restrict__ rk_, Tables tab,
              int first_level, int last_level,
@@ -45,7 +46,7 @@ k_tree_level(const __grid_constant__ CUtensorMap mapBs, const __grid_constant__ 
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     float *s_zz = reinterpret_cast<float *>(bars + 8);
-    int *s_anchor = reinterpret_cast<int *>(s_zz + TL_T), *s_patch = s_anchor + TL_T;
+    int *s_patch = reinterpret_cast<int *>(s_zz + TL_T);
     const int4 it = items[1 + blockIdx.x];
     const int v = it.x, first = it.y, cnt_p = it.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -80,47 +81,22 @@ k_tree_level(const __grid_constant__ CUtensorMap mapBs, const __grid_constant__ 
     if (threadIdx.x < cnt_p) {
         const int i = perm[first + threadIdx.x];
         s_patch[threadIdx.x] = i;
-        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+        s_zz[threadIdx.x] = zz[i];
     }
     __syncthreads();
-    // gather: warp w fills rows 32w .. 32w+31, eight rows' loads in flight,
-    // lane l holding patch elements 2l and 2l + 1 (patch row l / 4)
-    const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
-    for (int rr = 0; rr < 32; rr += 8) {
-        float xa[8], xb[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            xa[u] = xb[u] = 0.0f;
-            if (t < cnt_p) {
-                const int a = s_anchor[t];
-                const int ai = a / W, aj = a % W;
-                int rw = ai + pr_, cc0 = aj + pc_, cc1 = cc0 + 1;
-                if (rw >= H) rw -= H;
-                if (cc0 >= W) cc0 -= W;
-                if (cc1 >= W) cc1 -= W;
-                xa[u] = xhat[(size_t)rw * W + cc0];
-                xb[u] = xhat[(size_t)rw * W + cc1];
-            }
+    // the group's rows of the split operands extracted once per iteration:
+    // eight threads per 128-byte row, 16-byte chunks to their swizzled place
+    for (int q = threadIdx.x; q < TL_T * 8; q += TL_T) {
+        const int t = q >> 3, c = q & 7;
+        uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+        if (t < cnt_p) {
+            const size_t src = (size_t)s_patch[t] * 8 + c;
+            h = Zhi[src];
+            l = Zlo[src];
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            float sum = xa[u] + xb[u];
-#pragma unroll
-            for (int q = 16; q > 0; q >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, q);
-            const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
-            const float z0 = xa[u] - mu, z1 = xb[u] - mu;
-            float q2 = fmaf(z0, z0, z1 * z1);
-#pragma unroll
-            for (int q = 16; q > 0; q >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, q);
-            const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
-            const uint32_t o = t * 128 + ((((uint32_t)lane >> 2) ^ (t & 7)) << 4) + 4 * (lane & 3);
-            *reinterpret_cast<__nv_bfloat162 *>(Ahi + o) = h;
-            *reinterpret_cast<__nv_bfloat162 *>(Alo + o) = l;
-            if (lane == 0) s_zz[t] = q2;
-        }
+        const uint32_t o = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
+        *reinterpret_cast<uint4 *>(Ahi + o) = h;
+        *reinterpret_cast<uint4 *>(Alo + o) = l;
     }
     fence_proxy_async();
     __syncthreads();
@@ -242,6 +218,8 @@ epll_status launch_select_tree(epll_gmm *g, const float *xhat, int H, int W, con
     CUtensorMap bs, bslo;
     if ((s = make_map(&bs, tm->tab.Bs, tm->Rtot, 64))) return s;
     if ((s = make_map(&bslo, tm->tab.Bs_lo, tm->Rtot, 64))) return s;
+    // split BF16 DC-free patches and |z|^2, once for every level
+    if ((s = launch_extract_split(g, xhat, H, W, anchors, n, st))) return s;
     EPLL_CU(cudaMemsetAsync(ws.tnode, 0, sizeof(int) * (size_t)n, st));  // every patch at the root
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));     // no near-tie list
     const int max_items = (n + TL_T - 1) / TL_T + tr->n_nodes;
@@ -249,7 +227,9 @@ epll_status launch_select_tree(epll_gmm *g, const float *xhat, int H, int W, con
         if ((s = group_by_key(g, ws.tnode, n, tr->n_nodes, ws.tcounts, ws.perm, ws.titems, st))) return s;
         const int last = lev == tr->depth - 1;
         prof_begin(g, st);
-        k_tree_level<<<max_items, TL_T, TL_SMEM, st>>>(bs, bslo, xhat, H, W, anchors, ws.perm, ws.titems,
+        k_tree_level<<<max_items, TL_T, TL_SMEM, st>>>(bs, bslo, reinterpret_cast<const uint4 *>(ws.Zb),
+                                                       reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD),
+                                                       ws.zz, ws.perm, ws.titems,
                                                        tr->d_child, tr->d_leaf, tm->d_roff, tm->d_r, tm->tab, lev == 0,
                                                        last, ws.tnode, ws.kstar, ws.gap, cnt(g, CNT_ERR));
         prof_end(g, st, n, 2.0 * PD * (double)tr->child_cols_mean);
