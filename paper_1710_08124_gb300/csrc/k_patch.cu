@@ -232,10 +232,15 @@ __device__ __forceinline__ bool df_less(df x, df y)
 // FP32 pass-1 band: absolute + relative to |z|^2 max 1/nu (the FP32 error scale)
 constexpr float RESCORE_ABS = 1e-3f;
 constexpr float RESCORE_REL = 2e-5f;
-constexpr int RS_WARPS = 4;
+constexpr int RS_WARPS = 8;
 
 // Entries [f0, f0 + fcap) of the near-tie list; scores[(f - f0) * K + k] holds
-// each component's FP32 score (written by the FP32 kernel in list mode).
+// each component's FP32 score (written by the FP32 kernel in list mode).  A
+// block takes one listed patch: warp 0 forms the compensated DC-free patch and
+// |z|^2, every warp lists the components within the band of the best dumped
+// score, the candidates are dealt to the warps in turn, and the warps' best
+// and second best (compensated; the lower component on equal scores) are
+// merged at the end.
 __global__ void __launch_bounds__(32 * RS_WARPS)
 k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
           const int *__restrict__ flag, const int *__restrict__ nflag, int f0, int fcap, int K,
@@ -244,36 +249,49 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
           const float *__restrict__ scores, float band_abs, float band_rel, int *__restrict__ kstar,
           float *__restrict__ gap, long long *__restrict__ ctr)
 {
-    __shared__ float zh[RS_WARPS][PD], zl[RS_WARPS][PD];
+    __shared__ float zh[PD], zl[PD];
+    __shared__ df s_zz;
+    __shared__ float s_best;
+    __shared__ df r_b1[RS_WARPS], r_b2[RS_WARPS];
+    __shared__ int r_kb[RS_WARPS];
+    __shared__ float r_out[RS_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = min(*nflag - f0, fcap);
-    const int gw = blockIdx.x * RS_WARPS + w, nw = gridDim.x * RS_WARPS;
-    if (gw == 0 && lane == 0 && total > 0) atomicAdd((unsigned long long *)ctr, (unsigned long long)total);
-    for (int f = gw; f < total; f += nw) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && total > 0)
+        atomicAdd((unsigned long long *)ctr, (unsigned long long)total);
+    for (int f = blockIdx.x; f < total; f += gridDim.x) {
         const int i = flag[f0 + f];
-        const int a = anchors ? anchors[i] : i;
-        const int ai = a / W, aj = a % W;
-        const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
-        const float x1 = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
-        // mean and DC-free patch, compensated
-        df sx = df_warp_sum(two_sum(x0, x1));
-        df mu = {sx.hi * (1.0f / PD), sx.lo * (1.0f / PD)};
-        df z0 = df_add({x0, 0.0f}, {-mu.hi, -mu.lo});
-        df z1 = df_add({x1, 0.0f}, {-mu.hi, -mu.lo});
-        df zz = df_warp_sum(df_add(df_mul(z0, z0), df_mul(z1, z1)));
-        zh[w][lane] = z0.hi; zl[w][lane] = z0.lo;
-        zh[w][lane + 32] = z1.hi; zl[w][lane + 32] = z1.lo;
-        __syncwarp();
         const float *sc = scores + (size_t)f * K;
-        float best = FLT_MAX;
-        for (int k = lane; k < K; k += 32) best = fminf(best, sc[k]);
+        if (w == 0) {
+            const int a = anchors ? anchors[i] : i;
+            const int ai = a / W, aj = a % W;
+            const float x0 = xhat[pix(ai, aj, lane >> 3, lane & 7, H, W)];
+            const float x1 = xhat[pix(ai, aj, (lane >> 3) + 4, lane & 7, H, W)];
+            // mean and DC-free patch, compensated
+            df sx = df_warp_sum(two_sum(x0, x1));
+            df mu = {sx.hi * (1.0f / PD), sx.lo * (1.0f / PD)};
+            df z0 = df_add({x0, 0.0f}, {-mu.hi, -mu.lo});
+            df z1 = df_add({x1, 0.0f}, {-mu.hi, -mu.lo});
+            df zz = df_warp_sum(df_add(df_mul(z0, z0), df_mul(z1, z1)));
+            zh[lane] = z0.hi; zl[lane] = z0.lo;
+            zh[lane + 32] = z1.hi; zl[lane + 32] = z1.lo;
+            float best = FLT_MAX;
+            for (int k = lane; k < K; k += 32) best = fminf(best, sc[k]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+            for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (lane == 0) {
+                s_zz = zz;
+                s_best = best;
+            }
+        }
+        __syncthreads();
+        const df zz = s_zz;
+        const float best = s_best;
         const float band = band_abs + band_rel * (zz.hi + zz.lo) * tab.tmax[0];
         // compensated scores of the components within the band of the best;
-        // lanes scan 32 components at a time, a ballot lists the candidates
+        // candidate number c (in component order) goes to warp c mod RS_WARPS
         df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
-        int kb = -1;
+        int kb = -1, ncand = 0;
         float outside = FLT_MAX;
         for (int k0 = 0; k0 < K; k0 += 32) {
             const float sk = k0 + lane < K ? sc[k0 + lane] : FLT_MAX;
@@ -283,6 +301,7 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
             while (m) {
                 const int k = k0 + __ffs(m) - 1;
                 m &= m - 1;
+                if ((ncand++ % RS_WARPS) != w) continue;
                 const int o = roff[k], r = rk_[k];
                 df part = {0.0f, 0.0f};
                 for (int j = lane; j < r; j += 32) {
@@ -290,7 +309,7 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
 #pragma unroll 16
                     for (int e = 0; e < PD; ++e) {
                         df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
-                        c = df_add(c, df_mul(u, {zh[w][e], zl[w][e]}));
+                        c = df_add(c, df_mul(u, {zh[e], zl[e]}));
                     }
                     df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
                     part = df_add(part, df_mul(q, df_mul(c, c)));
@@ -304,13 +323,36 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) outside = fminf(outside, __shfl_xor_sync(0xffffffffu, outside, o));
-        if (lane == 0 && kb >= 0) {  // kb < 0 only if every score was NaN
-            kstar[i] = kb;
-            float g2 = (b2.hi == FLT_MAX) ? outside - (b1.hi + b1.lo)
-                                          : (b2.hi - b1.hi) + (b2.lo - b1.lo);
-            gap[i] = fminf(g2, outside - (b1.hi + b1.lo));
+        if (lane == 0) {
+            r_b1[w] = b1;
+            r_b2[w] = b2;
+            r_kb[w] = kb;
+            r_out[w] = outside;
         }
-        __syncwarp();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            df m1 = {FLT_MAX, 0.0f}, m2 = {FLT_MAX, 0.0f};
+            int mk = -1;
+            for (int q = 0; q < RS_WARPS; ++q) {
+                if (r_kb[q] < 0) continue;
+                // merge warp q's best and second best (its best carries r_kb[q])
+                const bool first = df_less(r_b1[q], m1) || (!df_less(m1, r_b1[q]) && mk >= 0 && r_kb[q] < mk);
+                if (first) {
+                    m2 = df_less(r_b2[q], m1) ? r_b2[q] : m1;
+                    m1 = r_b1[q];
+                    mk = r_kb[q];
+                } else {
+                    if (df_less(r_b1[q], m2)) m2 = r_b1[q];
+                }
+            }
+            if (mk >= 0) {  // mk < 0 only if every score was NaN
+                kstar[i] = mk;
+                const float out = r_out[0];
+                float g2 = (m2.hi == FLT_MAX) ? out - (m1.hi + m1.lo) : (m2.hi - m1.hi) + (m2.lo - m1.lo);
+                gap[i] = fminf(g2, out - (m1.hi + m1.lo));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -323,8 +365,8 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
         epll_status s = launch_dump_split(g, xhat, H, W, anchors, n, st);
         if (s == EPLL_OK) {
             // band: twice the split form's near-tie threshold (its error bound is half of it)
-            int blocks = (n + RS_WARPS - 1) / RS_WARPS;
-            if (blocks > 152 * 4) blocks = 152 * 4;
+            int blocks = n < 152 * 8 ? n : 152 * 8;
+            if (blocks < 1) blocks = 1;
             k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), 0,
                                                         fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
                                                         g->d_Blo, g->tab, ws.fscore, 2.0f * tau_abs, 8e-5f,
@@ -341,8 +383,8 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
             xhat, H, W, anchors, 0, g->d_B, g->Rtot, g->d_colk, g->tab, 0.0f, 0.0f, nullptr, nullptr,
             nullptr, nullptr, ws.flag, cnt(g, CNT_NFLAG), f0, fcap, g->K, g->d_roff, ws.fscore);
         EPLL_LAUNCHED(g);
-        int blocks = (rows + RS_WARPS - 1) / RS_WARPS;
-        if (blocks > 152 * 4) blocks = 152 * 4;
+        int blocks = rows < 152 * 8 ? rows : 152 * 8;
+        if (blocks < 1) blocks = 1;
         k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
                                                     fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
                                                     g->d_Blo, g->tab, ws.fscore, RESCORE_ABS, RESCORE_REL,
