@@ -62,7 +62,7 @@ static void free_workspace(Workspace &ws)
 {
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
-                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.cg, ws.red, ws.scal,
+                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.mu, ws.cg, ws.red, ws.scal,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
                     ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore, ws.tnode, ws.tcounts, ws.titems};
     for (void *p : ptrs)
@@ -86,7 +86,7 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     A(dalloc(&ws.flag, N)); A(dalloc(&ws.flag1, N)); A(dalloc(&ws.perm, N)); A(dalloc(&ws.zrow, N * PD));
     A(dalloc(&ws.items, 2 + N / 128 + (size_t)g->K));
     const size_t zrows = (N + 127) / 128 * 128;
-    A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N));
+    A(dalloc(&ws.Zb, 2 * zrows * PD)); A(dalloc(&ws.zz, N)); A(dalloc(&ws.mu, N));
     A(dalloc(&ws.Z2, 2 * zrows * PD)); A(dalloc(&ws.zz2, N)); A(dalloc(&ws.zsc2, N));
     // FP32 scores of near-tie rows: at most this many rows per rescoring pass
     size_t fcap = (size_t)1 << 26;
@@ -312,7 +312,10 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     if (o.precision == EPLL_FP32 && o.select == EPLL_SELECT_EXHAUSTIVE) {
         if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
     } else {
-        if ((s = launch_estimate_tc(g, xhat, H, W, anchors, n, st))) return s;
+        // the split first pass, the proposal and the tree leave every patch's
+        // split operands and mean in ws.Zb / ws.mu
+        const bool reuse = o.select != EPLL_SELECT_EXHAUSTIVE || o.precision == EPLL_BF16X3;
+        if ((s = launch_estimate_tc(g, xhat, H, W, anchors, n, reuse, st))) return s;
     }
     g->last_evals += n;
     return EPLL_OK;

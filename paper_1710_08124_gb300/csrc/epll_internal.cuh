@@ -93,6 +93,7 @@ struct Workspace {
     uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
     size_t zrows = 0;                         // N rounded up to the 128-row tile
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)
+    float *mu = nullptr;                      // [N] patch means (split extraction)
     float *cg = nullptr;                      // [4N] CG vectors r, d, q, spare
     float *red = nullptr;                     // reduction partials
     double *scal = nullptr;                   // device scalars (lambda, CG state)
@@ -235,12 +236,10 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
 // (1/beta read from the device scalar ibeta).
 epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  const float *ibeta, cudaStream_t st);
-// Split BF16 (hi, lo) DC-free patches into ws.Zb's two halves and |z|^2 into ws.zz.
+// Split BF16 (hi, lo) DC-free patches into ws.Zb's two halves (rows padded
+// to 128 with zeros), |z|^2 into ws.zz and the patch means into ws.mu.
 epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  cudaStream_t st);
-// BF16 DC-free patches into ws.Zb (rows padded to 128 with zeros) and |z|^2 into ws.zz.
-epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
-                                cudaStream_t st);
 // Counting sort of n keys (components) into perm and estimation work items.
 epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st);
 // Same for keys in 0..K-1 with an explicit [K] counter array.
@@ -257,8 +256,10 @@ inline int *cnt(epll_gmm *g, int slot) { return g->ws.counts + 2 * g->K + slot; 
 epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
                             int n, cudaStream_t st);
 // Same on the tensor cores in the split BF16 form (csrc/k_estimate_tc.cu).
+// With reuse, the split operands and means the selection extracted (ws.Zb,
+// ws.mu) are copied instead of gathering the patches from the image again.
 epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
-                               cudaStream_t st);
+                               bool reuse, cudaStream_t st);
 // Reprojection.  When y != nullptr the pixelwise image update is fused
 // (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult; a == nullptr means a = 1),
 // otherwise xtilde is written to xout.

@@ -10,7 +10,9 @@
 // product lands in TMEM, the epilogue scales it by the Wiener gains and writes
 // it back to shared memory as the split A operand of the second product, and
 // the second epilogue adds the tail term and the mean and writes the patch's
-// 64 estimates (one FP32 row per anchor) for the reprojection.
+// 64 estimates (one FP32 row per anchor) for the reprojection.  When the
+// selection already extracted every patch's split operands and mean, the
+// CTA copies those rows instead of gathering from the image.
 #include "epll_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,6 +36,7 @@ __global__ void __launch_bounds__(ET_T)
 k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__ CUtensorMap mapU1lo,
               const __grid_constant__ CUtensorMap mapU2, const __grid_constant__ CUtensorMap mapU2lo,
               const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
+              const uint4 *__restrict__ Zhi_g, const uint4 *__restrict__ Zlo_g, const float *__restrict__ mu_g,
               const int *__restrict__ perm, const int4 *__restrict__ items, const int *__restrict__ roff,
               const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, int *__restrict__ err)
 {
@@ -79,12 +82,29 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         const int i = perm[first + threadIdx.x];
         s_patch[threadIdx.x] = i;
         s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+        if (Zhi_g) s_mu[threadIdx.x] = mu_g[i];
     }
     __syncthreads();
+    if (Zhi_g) {
+        // the selection's split operand rows: eight threads per 128-byte row,
+        // 16-byte chunks to their swizzled place
+        for (int q = threadIdx.x; q < ET_T * 8; q += ET_T) {
+            const int t = q >> 3, c = q & 7;
+            uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+            if (t < cnt_p) {
+                const size_t src = (size_t)s_patch[t] * 8 + c;
+                h = Zhi_g[src];
+                l = Zlo_g[src];
+            }
+            const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
+            *reinterpret_cast<uint4 *>(Ahi + o2) = h;
+            *reinterpret_cast<uint4 *>(Alo + o2) = l;
+        }
+    }
     // gather: warp w fills rows 32w .. 32w+31, eight rows' loads in flight,
     // lane l holding patch elements 2l and 2l + 1
     const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
-    for (int rr = 0; rr < 32; rr += 8) {
+    for (int rr = 0; rr < 32 && !Zhi_g; rr += 8) {
         float xa[8], xb[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -215,7 +235,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
 }
 
 epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
-                               cudaStream_t st)
+                               bool reuse, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     epll_status s;
@@ -232,7 +252,10 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
     if ((s = make_map_wide(&u2, g->d_U2b, PD, 64, g->Rtot))) return s;
     if ((s = make_map_wide(&u2lo, g->d_U2b + R * PD, PD, 64, g->Rtot))) return s;
     const int max_items = (n + ET_T - 1) / ET_T + g->K;
-    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, xhat, H, W, anchors, ws.perm, ws.items,
+    const uint4 *zh = reuse ? reinterpret_cast<const uint4 *>(ws.Zb) : nullptr;
+    const uint4 *zl = reuse ? reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD) : nullptr;
+    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, xhat, H, W, anchors, zh, zl,
+                                                    reuse ? ws.mu : nullptr, ws.perm, ws.items,
                                                     g->d_roff, g->d_r, g->tab, ws.zrow, cnt(g, CNT_ERR));
     EPLL_LAUNCHED(g);
     return EPLL_OK;

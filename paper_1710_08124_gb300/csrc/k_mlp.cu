@@ -901,8 +901,9 @@ epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, c
     epll_status s;
     if ((s = ensure_prop_ws(g, n))) return s;
     const int rows = (n + MT - 1) / MT * MT;
-    // DC-free patches as BF16 operands (and |z|^2)
-    if ((s = launch_extract_bf16(g, xhat, H, W, anchors, n, st))) return s;
+    // DC-free patches as split BF16 operands (the network reads the hi part;
+    // the estimation reuses both), |z|^2 and the means
+    if ((s = launch_extract_split(g, xhat, H, W, anchors, n, st))) return s;
     const int n3 = (p->K + 15) / 16 * 16;
     CUtensorMap mz, w1, w2, w3;
     if ((s = make_map(&mz, ws.Zb, rows, MT))) return s;

@@ -61,54 +61,60 @@ __device__ __forceinline__ float from16(uint16_t v, int fmt)
 }
 
 // Row i of the operand is sampled patch i, or patch rowmap[i] when a row map
-// (a device list with device count *n_dev) is given.
+// (a device list with device count *n_dev) is given.  mu_out (nullable)
+// receives each row's patch mean.
 // fmt 3: 8-bit E4M3 operands scaled per row (max |z| -> 448), the square of
 // the scale in zsc2; Zhi is then read as bytes.
 __global__ void __launch_bounds__(128)
 k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
              const int *__restrict__ rowmap, const int *__restrict__ n_dev, int fmt, int split,
              uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz,
-             float *__restrict__ zsc2)
+             float *__restrict__ zsc2, float *__restrict__ mu_out)
 {
-    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     if (n_dev) n = *n_dev;
     const int rows = (n + 127) / 128 * 128;
-    if (i >= rows) return;
-    float z0 = 0.0f, z1 = 0.0f, q = 0.0f;
-    if (i < n) {
-        const int p = rowmap ? rowmap[i] : i;
-        const int a = anchors ? anchors[p] : p;
-        const int ai = a / W, aj = a % W;
-        int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
-        if (r0 >= H) r0 -= H;
-        if (r1 >= H) r1 -= H;
-        if (c >= W) c -= W;
-        const float x0 = xhat[(size_t)r0 * W + c], x1 = xhat[(size_t)r1 * W + c];
-        const float mu = warp_sum_tc(x0 + x1) * (1.0f / PD);
-        z0 = x0 - mu;
-        z1 = x1 - mu;
-        q = warp_sum_tc(z0 * z0 + z1 * z1);
-    }
-    if (fmt == 3) {
-        const float m = warp_max_tc(fmaxf(fabsf(z0), fabsf(z1)));
-        const float sc = m > 0.0f ? m / 448.0f : 1.0f;
-        uint8_t *Z8 = reinterpret_cast<uint8_t *>(Zhi);
-        Z8[(size_t)i * PD + lane] = to_e4m3(z0 / sc);
-        Z8[(size_t)i * PD + lane + 32] = to_e4m3(z1 / sc);
+    // grid-stride over rows (a listed subset launches a capped grid)
+    for (int i = blockIdx.x * 4 + (threadIdx.x >> 5); i < rows; i += gridDim.x * 4) {
+        float z0 = 0.0f, z1 = 0.0f, q = 0.0f, mu = 0.0f;
+        if (i < n) {
+            const int p = rowmap ? rowmap[i] : i;
+            const int a = anchors ? anchors[p] : p;
+            const int ai = a / W, aj = a % W;
+            int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
+            if (r0 >= H) r0 -= H;
+            if (r1 >= H) r1 -= H;
+            if (c >= W) c -= W;
+            const float x0 = xhat[(size_t)r0 * W + c], x1 = xhat[(size_t)r1 * W + c];
+            mu = warp_sum_tc(x0 + x1) * (1.0f / PD);
+            z0 = x0 - mu;
+            z1 = x1 - mu;
+            q = warp_sum_tc(z0 * z0 + z1 * z1);
+        }
+        if (fmt == 3) {
+            const float m = warp_max_tc(fmaxf(fabsf(z0), fabsf(z1)));
+            const float sc = m > 0.0f ? m / 448.0f : 1.0f;
+            uint8_t *Z8 = reinterpret_cast<uint8_t *>(Zhi);
+            Z8[(size_t)i * PD + lane] = to_e4m3(z0 / sc);
+            Z8[(size_t)i * PD + lane + 32] = to_e4m3(z1 / sc);
+            if (lane == 0 && i < n) {
+                zz[i] = q;
+                zsc2[i] = sc * sc;
+            }
+            continue;
+        }
+        const uint16_t h0 = to16(z0, fmt), h1 = to16(z1, fmt);
+        Zhi[(size_t)i * PD + lane] = h0;
+        Zhi[(size_t)i * PD + lane + 32] = h1;
+        if (split) {
+            Zlo[(size_t)i * PD + lane] = to16(z0 - from16(h0, fmt), fmt);
+            Zlo[(size_t)i * PD + lane + 32] = to16(z1 - from16(h1, fmt), fmt);
+        }
         if (lane == 0 && i < n) {
             zz[i] = q;
-            zsc2[i] = sc * sc;
+            if (mu_out) mu_out[i] = mu;
         }
-        return;
     }
-    const uint16_t h0 = to16(z0, fmt), h1 = to16(z1, fmt);
-    Zhi[(size_t)i * PD + lane] = h0;
-    Zhi[(size_t)i * PD + lane + 32] = h1;
-    if (split) {
-        Zlo[(size_t)i * PD + lane] = to16(z0 - from16(h0, fmt), fmt);
-        Zlo[(size_t)i * PD + lane + 32] = to16(z1 - from16(h1, fmt), fmt);
-    }
-    if (lane == 0 && i < n) zz[i] = q;
 }
 
 // ---------------------------------------------------------------- main kernel
@@ -498,8 +504,8 @@ epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, cons
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
     int *nf = cnt(g, CNT_NFLAG);
-    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, ws.flag, nf, 1, 1, Z2hi, Z2lo, ws.zz2,
-                                                 nullptr);
+    k_extract_tc<<<min((rows + 3) / 4, 152 * 16), 128, 0, st>>>(xhat, H, W, anchors, n, ws.flag, nf, 1, 1, Z2hi,
+                                                                 Z2lo, ws.zz2, nullptr, nullptr);
     EPLL_LAUNCHED(g);
     CUtensorMap a2, a2lo, bs, bslo;
     epll_status s;
@@ -536,7 +542,8 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     epll_status s;
     // ---- first pass over every sampled patch
     k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, fmt,
-                                                 split_first ? 1 : 0, Zhi, Zlo, ws.zz, ws.zsc2);
+                                                 split_first ? 1 : 0, Zhi, Zlo, ws.zz, ws.zsc2,
+                                                 split_first ? ws.mu : nullptr);
     EPLL_LAUNCHED(g);
     int *flag1 = split_first ? ws.flag : ws.flag1;
     int *nflag1 = cnt(g, split_first ? CNT_NFLAG : CNT_NFLAG1);
@@ -571,24 +578,13 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
 
 // Split-BF16 pass over the rows listed in flag1 (device count nflag1): their
 // kstar / gap are overwritten and the rows it cannot decide go to ws.flag.
-epll_status launch_extract_bf16(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
-                                cudaStream_t st)
-{
-    Workspace &ws = g->ws;
-    const int rows = (n + TC_M - 1) / TC_M * TC_M;
-    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, 1, 0, ws.Zb, nullptr,
-                                                 ws.zz, nullptr);
-    EPLL_LAUNCHED(g);
-    return EPLL_OK;
-}
-
 epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  cudaStream_t st)
 {
     Workspace &ws = g->ws;
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, nullptr, nullptr, 1, 1, ws.Zb,
-                                                 ws.Zb + ws.zrows * PD, ws.zz, nullptr);
+                                                 ws.Zb + ws.zrows * PD, ws.zz, nullptr, ws.mu);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -600,8 +596,8 @@ epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, cons
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     epll_status s;
     uint16_t *Z2hi = ws.Z2, *Z2lo = ws.Z2 + ws.zrows * PD;
-    k_extract_tc<<<(rows + 3) / 4, 128, 0, st>>>(xhat, H, W, anchors, n, flag1, nflag1, 1, 1, Z2hi, Z2lo,
-                                                 ws.zz2, nullptr);
+    k_extract_tc<<<min((rows + 3) / 4, 152 * 16), 128, 0, st>>>(xhat, H, W, anchors, n, flag1, nflag1, 1, 1,
+                                                                 Z2hi, Z2lo, ws.zz2, nullptr, nullptr);
     EPLL_LAUNCHED(g);
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
     CUtensorMap a2, a2lo, bs, bslo;
