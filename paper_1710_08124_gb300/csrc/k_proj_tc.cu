@@ -552,9 +552,9 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     if ((s = make_map(&a, Zhi, rows, TC_M))) return s;
     if ((s = make_map(&alo, Zlo, rows, TC_M))) return s;
     if (split_first) {
-        if ((s = make_map(&b, g->tab.Bs, g->Rtot, 128))) return s;
-        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, 128))) return s;
-        return dispatch_rr<128, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 1),
+        if ((s = make_map(&b, g->tab.Bs, g->Rtot, 256))) return s;
+        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, 256))) return s;
+        return dispatch_rr<256, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1),
                                    tau_abs, tau_rel, flag1, nflag1, st);
     }
     if (fp8) {
@@ -603,9 +603,9 @@ epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, cons
     CUtensorMap a2, a2lo, bs, bslo;
     if ((s = make_map(&a2, Z2hi, rows, TC_M))) return s;
     if ((s = make_map(&a2lo, Z2lo, rows, TC_M))) return s;
-    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 128))) return s;
-    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 128))) return s;
-    return dispatch_rr<128, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 128, 1),
+    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 256))) return s;
+    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 256))) return s;
+    return dispatch_rr<256, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 256, 1),
                                tau_abs, SPLIT_REL, ws.flag, cnt(g, CNT_NFLAG), st);
 }
 
