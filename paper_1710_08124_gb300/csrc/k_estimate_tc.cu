@@ -4,15 +4,14 @@
 //   c = Ubar_k^T z,  c'_j = (gamma_kj - gamma_kP) c_j,
 //   zhat = Ubar_k c' + gamma_kP z + mu
 // as two chained GEMMs in the split BF16 form (hi*hi + lo*hi + hi*lo, the
-// same arithmetic as the split selection pass): the CTA gathers its patches
-// from the image into shared memory (DC removed, hi + lo, 128-byte-swizzled
-// K-major rows), TMA brings Ubar_k in both orientations (hi + lo), the first
-// product lands in TMEM, the epilogue scales it by the Wiener gains and writes
-// it back to shared memory as the split A operand of the second product, and
-// the second epilogue adds the tail term and the mean and writes the patch's
-// 64 estimates (one FP32 row per anchor) for the reprojection.  When the
-// selection already extracted every patch's split operands and mean, the
-// CTA copies those rows instead of gathering from the image.
+// same arithmetic as the split selection pass): the CTA copies its patches'
+// split operand rows (extracted once per iteration, with the means) into
+// shared memory in the 128-byte-swizzled K-major layout, TMA brings Ubar_k
+// in both orientations (hi + lo), the first product lands in TMEM, the
+// epilogue scales it by the Wiener gains and writes it back over the patch
+// rows as the split A operand of the second product, and the second epilogue
+// adds the tail term (z from the extracted rows) and the mean and writes the
+// patch's 64 estimates (one FP32 row per anchor) for the reprojection.
 #include "epll_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -23,28 +22,22 @@ namespace epll {
 constexpr int ET_T = 128;
 constexpr int ET_TILE = ET_T * 128;  // 16 KB: [128 rows][64] BF16
 constexpr int ET_B = 64 * 128;       // 8 KB: [64 rows][64] BF16
-// A hi/lo, C' hi/lo, B1 hi/lo, B2 hi/lo, then barriers and per-row scalars
-constexpr int ET_SMEM = 1024 + 4 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4;
-
-static __device__ __forceinline__ uint32_t swz(int row, int e)
-{
-    // byte offset of element e (16-bit) of row `row` in a 128-byte-swizzled tile
-    return (uint32_t)(row * 128 + ((((e >> 3) ^ (row & 7))) << 4) + (e & 7) * 2);
-}
+// A hi/lo (overwritten by C' hi/lo), B1 hi/lo, B2 hi/lo, then barriers and per-row scalars
+constexpr int ET_SMEM = 1024 + 2 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4;
 
 __global__ void __launch_bounds__(ET_T)
 k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__ CUtensorMap mapU1lo,
               const __grid_constant__ CUtensorMap mapU2, const __grid_constant__ CUtensorMap mapU2lo,
-              const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
-              const uint4 *__restrict__ Zhi_g, const uint4 *__restrict__ Zlo_g, const float *__restrict__ mu_g,
+              const int *__restrict__ anchors, const uint4 *__restrict__ Zhi_g, const uint4 *__restrict__ Zlo_g,
+              const float *__restrict__ mu_g,
               const int *__restrict__ perm, const int4 *__restrict__ items, const int *__restrict__ roff,
               const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, int *__restrict__ err)
 {
     if ((int)blockIdx.x >= items[0].w) return;
     extern __shared__ __align__(1024) unsigned char et_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)et_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *Ahi = smem, *Alo = Ahi + ET_TILE, *Chi = Alo + ET_TILE, *Clo = Chi + ET_TILE;
-    unsigned char *B1hi = Clo + ET_TILE, *B1lo = B1hi + ET_B, *B2hi = B1lo + ET_B, *B2lo = B2hi + ET_B;
+    unsigned char *Ahi = smem, *Alo = Ahi + ET_TILE, *Chi = Ahi, *Clo = Alo;  // C' over A after GEMM 1
+    unsigned char *B1hi = Alo + ET_TILE, *B1lo = B1hi + ET_B, *B2hi = B1lo + ET_B, *B2lo = B2hi + ET_B;
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(B2lo + ET_B);  // bases, GEMM 1, GEMM 2
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
@@ -82,60 +75,22 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         const int i = perm[first + threadIdx.x];
         s_patch[threadIdx.x] = i;
         s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
-        if (Zhi_g) s_mu[threadIdx.x] = mu_g[i];
+        s_mu[threadIdx.x] = mu_g[i];
     }
     __syncthreads();
-    if (Zhi_g) {
-        // the selection's split operand rows: eight threads per 128-byte row,
-        // 16-byte chunks to their swizzled place
-        for (int q = threadIdx.x; q < ET_T * 8; q += ET_T) {
-            const int t = q >> 3, c = q & 7;
-            uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
-            if (t < cnt_p) {
-                const size_t src = (size_t)s_patch[t] * 8 + c;
-                h = Zhi_g[src];
-                l = Zlo_g[src];
-            }
-            const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
-            *reinterpret_cast<uint4 *>(Ahi + o2) = h;
-            *reinterpret_cast<uint4 *>(Alo + o2) = l;
+    // the patches' split operand rows: eight threads per 128-byte row,
+    // 16-byte chunks to their swizzled place
+    for (int q = threadIdx.x; q < ET_T * 8; q += ET_T) {
+        const int t = q >> 3, c = q & 7;
+        uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+        if (t < cnt_p) {
+            const size_t src = (size_t)s_patch[t] * 8 + c;
+            h = Zhi_g[src];
+            l = Zlo_g[src];
         }
-    }
-    // gather: warp w fills rows 32w .. 32w+31, eight rows' loads in flight,
-    // lane l holding patch elements 2l and 2l + 1
-    const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
-    for (int rr = 0; rr < 32 && !Zhi_g; rr += 8) {
-        float xa[8], xb[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            xa[u] = xb[u] = 0.0f;
-            if (t < cnt_p) {
-                const int a = s_anchor[t];
-                const int ai = a / W, aj = a % W;
-                int rw = ai + pr_, c0 = aj + pc_, c1 = c0 + 1;
-                if (rw >= H) rw -= H;
-                if (c0 >= W) c0 -= W;
-                if (c1 >= W) c1 -= W;
-                xa[u] = xhat[(size_t)rw * W + c0];
-                xb[u] = xhat[(size_t)rw * W + c1];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            float sum = xa[u] + xb[u];
-#pragma unroll
-            for (int q = 16; q > 0; q >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, q);
-            const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
-            const float z0 = xa[u] - mu, z1 = xb[u] - mu;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
-            const uint32_t off = swz(t, 2 * lane);
-            *reinterpret_cast<__nv_bfloat162 *>(Ahi + off) = h;
-            *reinterpret_cast<__nv_bfloat162 *>(Alo + off) = l;
-            if (lane == 0) s_mu[t] = mu;
-        }
+        const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
+        *reinterpret_cast<uint4 *>(Ahi + o2) = h;
+        *reinterpret_cast<uint4 *>(Alo + o2) = l;
     }
     fence_proxy_async();
     __syncthreads();
@@ -206,11 +161,11 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         // zhat = Ubar c' + gamma_P z + mu, z = hi + lo of this row
         const float gp = tab.gp[k], mu = s_mu[t];
         float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)s_anchor[t] * PD);
+        const size_t zr = (size_t)s_patch[t] * 8;
 #pragma unroll
         for (int e8 = 0; e8 < 8; ++e8) {
-            const uint32_t off = (uint32_t)(t * 128 + ((e8 ^ (t & 7)) << 4));
-            const uint4 zh = *reinterpret_cast<const uint4 *>(Ahi + off);
-            const uint4 zl = *reinterpret_cast<const uint4 *>(Alo + off);
+            const uint4 zh = Zhi_g[zr + e8];
+            const uint4 zl = Zlo_g[zr + e8];
             const uint32_t hw[4] = {zh.x, zh.y, zh.z, zh.w}, lw[4] = {zl.x, zl.y, zl.z, zl.w};
             float out[8];
 #pragma unroll
@@ -239,6 +194,8 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
 {
     Workspace &ws = g->ws;
     epll_status s;
+    // split operands and means of every patch (unless the selection left them)
+    if (!reuse && (s = launch_extract_split(g, xhat, H, W, anchors, n, st))) return s;
     if ((s = group_by_component(g, ws.kstar, n, ws.perm, ws.items, st))) return s;
     static bool attr = false;
     if (!attr) {
@@ -252,10 +209,9 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
     if ((s = make_map_wide(&u2, g->d_U2b, PD, 64, g->Rtot))) return s;
     if ((s = make_map_wide(&u2lo, g->d_U2b + R * PD, PD, 64, g->Rtot))) return s;
     const int max_items = (n + ET_T - 1) / ET_T + g->K;
-    const uint4 *zh = reuse ? reinterpret_cast<const uint4 *>(ws.Zb) : nullptr;
-    const uint4 *zl = reuse ? reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD) : nullptr;
-    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, xhat, H, W, anchors, zh, zl,
-                                                    reuse ? ws.mu : nullptr, ws.perm, ws.items,
+    const uint4 *zh = reinterpret_cast<const uint4 *>(ws.Zb);
+    const uint4 *zl = reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD);
+    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, anchors, zh, zl, ws.mu, ws.perm, ws.items,
                                                     g->d_roff, g->d_r, g->tab, ws.zrow, cnt(g, CNT_ERR));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
