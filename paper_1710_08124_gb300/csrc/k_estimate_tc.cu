@@ -23,7 +23,7 @@ constexpr int ET_T = 128;
 constexpr int ET_TILE = ET_T * 128;  // 16 KB: [128 rows][64] BF16
 constexpr int ET_B = 64 * 128;       // 8 KB: [64 rows][64] BF16
 // A hi/lo (overwritten by C' hi/lo), B1 hi/lo, B2 hi/lo, then barriers and per-row scalars
-constexpr int ET_SMEM = 1024 + 2 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4;
+constexpr int ET_SMEM = 1024 + 2 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4 + 64 * 4;
 
 __global__ void __launch_bounds__(ET_T)
 k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__ CUtensorMap mapU1lo,
@@ -43,6 +43,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     float *s_mu = reinterpret_cast<float *>(bars + 8);
     int *s_anchor = reinterpret_cast<int *>(s_mu + ET_T), *s_patch = s_anchor + ET_T;
+    float *s_gw = reinterpret_cast<float *>(s_patch + ET_T);  // Wiener gains of the component (0 beyond r)
     const int4 it = items[1 + blockIdx.x];
     const int k = it.x, first = it.y, cnt_p = it.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -78,19 +79,28 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         s_mu[threadIdx.x] = mu_g[i];
     }
     __syncthreads();
+    if (threadIdx.x < 64) s_gw[threadIdx.x] = threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
     // the patches' split operand rows: eight threads per 128-byte row,
-    // 16-byte chunks to their swizzled place
-    for (int q = threadIdx.x; q < ET_T * 8; q += ET_T) {
-        const int t = q >> 3, c = q & 7;
-        uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
-        if (t < cnt_p) {
-            const size_t src = (size_t)s_patch[t] * 8 + c;
-            h = Zhi_g[src];
-            l = Zlo_g[src];
+    // 16-byte chunks to their swizzled place (all sixteen loads in flight)
+    {
+        uint4 h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = threadIdx.x + u * ET_T, t = q >> 3, c = q & 7;
+            h[u] = l[u] = make_uint4(0, 0, 0, 0);
+            if (t < cnt_p) {
+                const size_t src = (size_t)s_patch[t] * 8 + c;
+                h[u] = Zhi_g[src];
+                l[u] = Zlo_g[src];
+            }
         }
-        const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
-        *reinterpret_cast<uint4 *>(Ahi + o2) = h;
-        *reinterpret_cast<uint4 *>(Alo + o2) = l;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = threadIdx.x + u * ET_T, t = q >> 3, c = q & 7;
+            const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
+            *reinterpret_cast<uint4 *>(Ahi + o2) = h[u];
+            *reinterpret_cast<uint4 *>(Alo + o2) = l[u];
+        }
     }
     fence_proxy_async();
     __syncthreads();
@@ -125,8 +135,8 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int j = 8 * j8 + 2 * q;
-                const float v0 = j < r ? tab.gw[o + j] * __uint_as_float(c[j]) : 0.0f;
-                const float v1 = j + 1 < r ? tab.gw[o + j + 1] * __uint_as_float(c[j + 1]) : 0.0f;
+                const float v0 = s_gw[j] * __uint_as_float(c[j]);
+                const float v1 = s_gw[j + 1] * __uint_as_float(c[j + 1]);
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
                 ph[q] = *reinterpret_cast<const uint32_t *>(&h);
@@ -162,10 +172,16 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         const float gp = tab.gp[k], mu = s_mu[t];
         float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)s_anchor[t] * PD);
         const size_t zr = (size_t)s_patch[t] * 8;
+        uint4 zhs[8], zls[8];
 #pragma unroll
         for (int e8 = 0; e8 < 8; ++e8) {
-            const uint4 zh = Zhi_g[zr + e8];
-            const uint4 zl = Zlo_g[zr + e8];
+            zhs[e8] = Zhi_g[zr + e8];
+            zls[e8] = Zlo_g[zr + e8];
+        }
+#pragma unroll
+        for (int e8 = 0; e8 < 8; ++e8) {
+            const uint4 zh = zhs[e8];
+            const uint4 zl = zls[e8];
             const uint32_t hw[4] = {zh.x, zh.y, zh.z, zh.w}, lw[4] = {zl.x, zl.y, zl.z, zl.w};
             float out[8];
 #pragma unroll

@@ -696,11 +696,11 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             int aj = j - v;
             if (aj < 0) aj += W;
             const size_t an = (size_t)ai * W + aj;
+            // both loads issued together; an unsampled anchor's row is never used
             const unsigned m = mult ? mult[an] : 1u;
-            if (m) {
-                sum = fmaf((float)m, zrow[an * PD + u * PS + v], sum);
-                cnt += m;
-            }
+            const float z = zrow[an * PD + u * PS + v];
+            sum = m ? fmaf((float)m, z, sum) : sum;
+            cnt += m;
         }
     }
     const float xt = cnt ? sum / (float)cnt : xhat[p];
