@@ -246,3 +246,48 @@ def test_trained_network_gains():
     ep.last_counters(gm)
     ps = lambda a: -10 * math.log10(np.mean((a - x) ** 2))
     assert abs(ps(xp) - ps(xe)) <= 0.05, (ps(xp), ps(xe))
+
+
+def test_proposal_small_k_edge_cases():
+    """K = 2 with one and two proposals, an 8x8 image (one patch row), and
+    topm larger than K rejected."""
+    g = synth.tiny_gmm(2, seed=3)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, 64)
+    om = oracle.Model(g.w, g.U, g.S, "fixed", 64)
+    p = ep.Proposal(2, seed=2)
+    with pytest.raises(ep.EpllError):
+        ep.attach_proposal(gm, p, topm=3)
+    x = (synth.image(60, 8) + synth.noise(60, 8, 8, 0.05)).astype(np.float32)
+    beta = 1 / 0.05 ** 2
+    for m in (1, 2):
+        ep.attach_proposal(gm, p, topm=m, pmin=0.0)
+        _, an, ks, _ = ep.patch_step(gm, dev(x), beta, ep.Options(select=ep.SELECT_PROPOSAL))
+        cand, pm = ep.proposal_topm(gm, dev(x), beta)
+        ks, cand, an = ks.cpu().numpy(), cand.cpu().numpy(), an.cpu().numpy()
+        assert np.all(np.isin(ks, [0, 1])) and cand.shape == (64, m)
+        if m == 2:
+            # both components proposed: the selection is the exhaustive one
+            _, oks, ogap, _ = oracle.patch_step(om, beta, x.astype(np.float64), an)
+            assert np.all((ks == oks) | (ogap < TIE))
+            np.testing.assert_allclose(pm.cpu().numpy(), 1.0, atol=1e-6)
+
+
+def test_proposal_batch_graph_equals_sequential():
+    K = 200
+    g = synth.synthetic_gmm(K)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, 8)
+    p = ep.Proposal(K, seed=8)
+    ep.attach_proposal(gm, p, topm=4, pmin=0.3)
+    jobs = []
+    for i, side in enumerate((64, 48, 96)):
+        _, y = synth.denoise_problem(70 + i, side, 25 / 255)
+        yd = dev(y)
+        jobs.append((yd, torch.empty_like(yd), None, ep.DENOISE, 25 / 255))
+    opts = ep.Options(select=ep.SELECT_PROPOSAL, subset=ep.SUBSET_FRACTION, subset_param=1 / 3, seed=4)
+    ep.restore_batch(gm, jobs, options=opts, mode=ep.BATCH_GRAPH, lanes=2)
+    torch.cuda.synchronize()
+    a = [j[1].cpu().numpy().copy() for j in jobs]
+    ep.restore_batch(gm, jobs, options=opts, mode=ep.BATCH_SEQUENTIAL)
+    torch.cuda.synchronize()
+    for u, j in zip(a, jobs):
+        np.testing.assert_array_equal(u, j[1].cpu().numpy())

@@ -164,3 +164,33 @@ def test_invalid_trees_are_rejected():
     ep.attach_tree(gm, None)
     with pytest.raises(ep.EpllError):
         ep.patch_step(gm, dev(synth.image(0, 16)), 100.0, ep.Options(select=ep.SELECT_TREE))
+
+
+@pytest.mark.parametrize("K", [5, 7])
+def test_small_trees_and_ragged_ranks(K):
+    """Small models (two levels, clusters of 2-3) with rho-mode ragged ranks
+    (children with different column counts) on a jittered subset."""
+    g = synth.tiny_gmm(K, seed=50 + K)
+    T = ptree.build_tree(g.w, g.U, g.S)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_RHO, 0.9)
+    ep.attach_tree(gm, T)
+    om = oracle.Model(g.w, g.U, g.S, "rho", 0.9)
+    om_nodes = oracle.Model(T.weights, T.eigvecs, T.eigvals, "rho", 0.9)
+    sigma = 15 / 255
+    x = (synth.image(40 + K, 33, 35) + synth.noise(40 + K, 33, 35, sigma)).astype(np.float32)
+    opts = ep.Options(select=ep.SELECT_TREE, subset=ep.SUBSET_JITTER, subset_param=4, seed=9)
+    check_descent(gm, om, om_nodes, T, x, 4 / sigma ** 2, opts)
+
+
+def test_tree_deblur_restore_runs_and_matches_forced_oracle_step():
+    """Periodic deblurring with the tree selection: the run is error-free and its
+    first patch step equals the oracle's descent on the same estimate."""
+    g, T, gm, om, om_nodes = setup(40, 8)
+    sigma = 2 / 255
+    x, k, y = synth.deblur_problem(24, 64, sigma)
+    xg = ep.restore(gm, dev(y), sigma, kind=ep.CONV_PERIODIC, kernel=k,
+                    options=ep.Options(select=ep.SELECT_TREE)).cpu().numpy()
+    ep.last_counters(gm)
+    assert np.all(np.isfinite(xg))
+    check_descent(gm, om, om_nodes, T, xg, 16 * oracle.lam(oracle.CONV, 64, 64, sigma, kernel=k) / sigma ** 2,
+                  ep.Options(select=ep.SELECT_TREE))
