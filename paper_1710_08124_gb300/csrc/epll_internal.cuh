@@ -236,6 +236,13 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
 // (1/beta read from the device scalar ibeta).
 epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  const float *ibeta, cudaStream_t st);
+// Operand rows of n sampled patches (csrc/k_extract.cu): row i is patch i, or
+// patch rowmap[i] of a device list with device count *n_dev; fmt 1 BF16,
+// 2 FP16 (split: hi into Zhi, lo into Zlo), 3 E4M3 with the squared row scale
+// in zsc2; |z|^2 into zz, the means into mu (nullable).
+epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
+                           const int *rowmap, const int *n_dev, int fmt, int split, uint16_t *Zhi, uint16_t *Zlo,
+                           float *zz, float *zsc2, float *mu, cudaStream_t st);
 // Split BF16 (hi, lo) DC-free patches into ws.Zb's two halves (rows padded
 // to 128 with zeros), |z|^2 into ws.zz and the patch means into ws.mu.
 epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
