@@ -16,7 +16,7 @@
  * Eqs. 11-12 flat-tail identities, Eqs. 13-16 flat-tail form, Eq. 17
  * symmetric KL, Eq. 18 clustering cost, Eq. 19 GMM collapse, Eq. 20 jitter.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *  - periodic boundaries; patch anchor = top-left pixel; element e = 8u+v;
  *  - the DC (patch mean) is removed before selection and estimation and
  *    added back unshrunk;
