@@ -47,8 +47,8 @@ RESTORES_PER_STEP = len(RANKS) * len(SIGMAS)
 WORKLOAD = ("FEPLL denoise 512x512 dead leaves, sigma {10,25,50}/255, synthetic GMM K=200, "
             "flat-tail rank r in {64,8}, random 1/3 patch subset per iteration, 5 HQS iterations")
 METRIC = "512x512 restores/s (FEPLL denoise, K=200, r in {64,8}, 1/3 subset)"
-PREC_NAMES = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp8": 4}
-DTYPE = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "bf16x3": "bf16", "fp8": "e4m3"}
+PREC_NAMES = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp8": 4, "auto": 5}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "bf16x3": "bf16", "fp8": "e4m3", "auto": "f16+bf16"}
 
 
 def parse():

@@ -56,11 +56,16 @@ enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
  * BF16X3 tcgen05 tensor cores, operands split into hi + lo BF16 parts
  *        (three products: hi*hi + lo*hi + hi*lo), FP32 accumulation;
  * FP8    tcgen05 tensor cores (kind::f8f6f4), E4M3 operands with one scale per
- *        component and one per patch, FP32 accumulation.
- * The one-term forms (BF16, FP16, FP8) hand the patches they cannot decide to
- * a BF16X3 pass; every form rescores its remaining near-ties in compensated
- * FP32 (see tie_gap). */
-enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3, EPLL_FP8 = 4 };
+ *        component and one per patch, FP32 accumulation;
+ * AUTO   FP16 for models of uniform rank >= 32, BF16X3 otherwise.
+ * FP16 keeps each patch's four best components; a patch it cannot decide has
+ * the components within its error bound of the best rescored in the BF16X3
+ * form (grouped by component on the tensor cores).  BF16 and FP8 hand the
+ * patches they cannot decide to a BF16X3 pass over every component.  Every
+ * form rescores its remaining near-ties (and FP16 every patch with more than
+ * four components in its band) in compensated FP32 (see tie_gap).  All forms
+ * select the exact argmin of Eq. 14 up to that rescoring's resolution. */
+enum { EPLL_FP32 = 0, EPLL_BF16 = 1, EPLL_FP16 = 2, EPLL_BF16X3 = 3, EPLL_FP8 = 4, EPLL_AUTO = 5 };
 /* how the Gaussian selection finds its candidates:
  * EXHAUSTIVE every component is scored (Algorithm 1, step 2);
  * PROPOSAL   a learned network attached to the model (epll_gmm_attach_proposal)
@@ -91,7 +96,7 @@ typedef struct {
 } epll_degradation;
 
 typedef struct {
-    int precision;      /* EPLL_FP32, EPLL_BF16, EPLL_FP16, EPLL_BF16X3 or EPLL_FP8 */
+    int precision;      /* EPLL_FP32, EPLL_BF16, EPLL_FP16, EPLL_BF16X3, EPLL_FP8 or EPLL_AUTO */
     float tie_gap;      /* absolute part of the near-tie threshold: a patch whose top-2
                            score gap is below tie_gap + rho * |z|^2 * max_kj 1/nu_kj is
                            rescored in compensated FP32 (rho is the relative error bound of

@@ -187,8 +187,8 @@ static void free_model(epll_gmm *g)
 
 static epll_status check_options(const epll_options &o, int H, int W)
 {
-    if (o.precision < EPLL_FP32 || o.precision > EPLL_FP8)
-        return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32, _BF16, _FP16, _BF16X3 or _FP8");
+    if (o.precision < EPLL_FP32 || o.precision > EPLL_AUTO)
+        return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32, _BF16, _FP16, _BF16X3, _FP8 or _AUTO");
     if (!(std::isfinite(o.tie_gap)))
         return fail(EPLL_EINVAL, "options.tie_gap must be finite");
     if (o.subset == EPLL_SUBSET_FRACTION) {
@@ -224,30 +224,40 @@ static epll_status check_image(int H, int W)
     return EPLL_OK;
 }
 
+// The arithmetic EPLL_AUTO stands for: the FP16 one-term pass with FP32
+// candidate rescoring where the projection is long enough for the pass to
+// save more than its candidates cost (uniform ranks of 32 and more), the
+// split BF16 pass otherwise.
+static int eff_precision(const epll_gmm *g, const epll_options &o)
+{
+    if (o.precision != EPLL_AUTO) return o.precision;
+    return g->uniform_rank >= 32 ? EPLL_FP16 : EPLL_BF16X3;
+}
+
 // Near-tie threshold tau_abs + tau_rel |z|^2 max 1/nu.  tau_rel bounds the
 // relative score error of each arithmetic (twice the largest error observed
 // on the synthetic prior, rounded up): FP32 dot products of 64 terms; FP16 /
 // BF16 operand rounding (2^-11 / 2^-8 per operand); E4M3 operands with
 // per-component / per-patch scales (2^-4 per operand; 4.4e-2 measured); the split BF16 form
 // (residual error of order 2^-16; at most 8e-6 relative measured).
-static void thresholds(const epll_options &o, float *tau_abs, float *tau_rel)
+static void thresholds(const epll_options &o, int precision, float *tau_abs, float *tau_rel)
 {
     *tau_abs = o.tie_gap >= 0.0f ? o.tie_gap : 1e-3f;
-    switch (o.precision) {
+    switch (precision) {
     case EPLL_BF16: *tau_rel = 1e-2f; break;
     case EPLL_FP16: *tau_rel = 1.5e-3f; break;
     case EPLL_BF16X3: *tau_rel = 4e-5f; break;
     case EPLL_FP8: *tau_rel = 1e-1f; break;
-    default: *tau_rel = 1e-5f; break;
+    default: *tau_rel = F32_REL; break;
     }
 }
 
 // Bases the tables kernel writes for each arithmetic (bit mask, see launch_tables).
-static int basis_format(const epll_options &o)
+static int basis_format(const epll_options &o, int precision)
 {
     if (o.select == EPLL_SELECT_PROPOSAL) return 4;  // exhaustive fallback: split BF16 pass
     if (o.select == EPLL_SELECT_TREE) return 0;      // the node model carries the bases
-    switch (o.precision) {
+    switch (precision) {
     case EPLL_BF16: return 1 | 4;
     case EPLL_FP16: return 2 | 4;
     case EPLL_BF16X3: return 4;
@@ -263,7 +273,8 @@ static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &
 {
     Workspace &ws = g->ws;
     epll_status s;
-    if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o), st))) return s;
+    if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o, eff_precision(g, o)), st)))
+        return s;
     if (o.select == EPLL_SELECT_TREE &&
         (s = launch_tables(g->tree->tm, d_lambda, mult, nb, sigma2, beta_direct, 4, st)))
         return s;
@@ -290,18 +301,19 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
     Workspace &ws = g->ws;
     epll_status s;
     const int *anchors = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.anchors;
+    const int prec = eff_precision(g, o);
     float tau_abs, tau_rel;
-    thresholds(o, &tau_abs, &tau_rel);
+    thresholds(o, prec, &tau_abs, &tau_rel);
     if (o.select == EPLL_SELECT_TREE) {
         if ((s = launch_select_tree(g, xhat, H, W, anchors, n, st))) return s;
     } else if (o.select == EPLL_SELECT_PROPOSAL) {
         if ((s = launch_select_proposal(g, xhat, H, W, anchors, n, tau_abs, st))) return s;
-    } else if (o.precision != EPLL_FP32) {
-        if ((s = launch_select_tc(g, xhat, H, W, anchors, n, o.precision, tau_abs, tau_rel, st))) return s;
+    } else if (prec != EPLL_FP32) {
+        if ((s = launch_select_tc(g, xhat, H, W, anchors, n, prec, tau_abs, tau_rel, st))) return s;
     } else {
         if ((s = launch_select_fp32(g, xhat, H, W, anchors, n, tau_abs, tau_rel, st))) return s;
     }
-    const bool split_scores = o.select == EPLL_SELECT_PROPOSAL || o.precision != EPLL_FP32;
+    const bool split_scores = o.select == EPLL_SELECT_PROPOSAL || prec != EPLL_FP32;
     if (o.select != EPLL_SELECT_TREE &&
         (s = launch_rescore(g, xhat, H, W, anchors, n, split_scores, tau_abs, st)))
         return s;
@@ -309,12 +321,12 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
         EPLL_CU(cudaMemcpyAsync(ws.kstar, forced_k, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     // the FP32 form keeps the SIMT estimate (FP32 parity with the oracle);
     // the reduced-precision forms use the split-BF16 tensor-core estimate
-    if (o.precision == EPLL_FP32 && o.select == EPLL_SELECT_EXHAUSTIVE) {
+    if (prec == EPLL_FP32 && o.select == EPLL_SELECT_EXHAUSTIVE) {
         if ((s = launch_estimate(g, xhat, H, W, anchors, n, st))) return s;
     } else {
-        // the split first pass, the proposal and the tree leave every patch's
-        // split operands and mean in ws.Zb / ws.mu
-        const bool reuse = o.select != EPLL_SELECT_EXHAUSTIVE || o.precision == EPLL_BF16X3;
+        // the split and FP16 passes, the proposal and the tree leave every
+        // patch's split operands and mean in ws.Zb / ws.mu
+        const bool reuse = o.select != EPLL_SELECT_EXHAUSTIVE || prec == EPLL_BF16X3 || prec == EPLL_FP16;
         if ((s = launch_estimate_tc(g, xhat, H, W, anchors, n, reuse, st))) return s;
     }
     g->last_evals += n;

@@ -46,6 +46,8 @@ struct Tables {
 // Relative score error bound of the split BF16 form (hi*hi + lo*hi + hi*lo):
 // a top-2 gap below tau_abs + SPLIT_REL |z|^2 tmax is a near-tie.
 constexpr float SPLIT_REL = 4e-5f;
+// The same for FP32 dot products of 64 terms.
+constexpr float F32_REL = 1e-5f;
 
 // Iterations prepared together (tables of every beta, patch subsets).
 constexpr int TB_MAX = 8;
@@ -239,19 +241,34 @@ epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, c
 // Operand rows of n sampled patches (csrc/k_extract.cu): row i is patch i, or
 // patch rowmap[i] of a device list with device count *n_dev; fmt 1 BF16,
 // 2 FP16 (split: hi into Zhi, lo into Zlo), 3 E4M3 with the squared row scale
-// in zsc2; |z|^2 into zz, the means into mu (nullable).
+// in zsc2; |z|^2 into zz, the means into mu (nullable); Zf (nullable) an
+// FP16 copy of the rows beside the fmt rows.
 epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                            const int *rowmap, const int *n_dev, int fmt, int split, uint16_t *Zhi, uint16_t *Zlo,
-                           float *zz, float *zsc2, float *mu, cudaStream_t st);
+                           float *zz, float *zsc2, float *mu, cudaStream_t st, uint16_t *Zf = nullptr);
 // Split BF16 (hi, lo) DC-free patches into ws.Zb's two halves (rows padded
 // to 128 with zeros), |z|^2 into ws.zz and the patch means into ws.mu.
 epll_status launch_extract_split(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                  cudaStream_t st);
-// Counting sort of n keys (components) into perm and estimation work items.
-epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st);
+// Candidate pairs (csrc/k_mlp.cu): ws.cand holds m candidate components per
+// entry (negative: absent); entry f is patch f, or patch list[f] of a device
+// list with device count *nlist.  launch_pair_scores groups the pairs by
+// component and writes their split-BF16 scores of Eq. 14 to ws.pscore;
+// launch_cand_combine writes each listed patch's best rescored candidate to
+// kstar / gap and appends the patch to flag (count nflag) when its top-2 gap
+// is within the split form's error bound or its first candidate is absent.
+epll_status ensure_prop_ws(epll_gmm *g, int n);
+epll_status launch_pair_scores(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n, int m,
+                               const int *list, const int *nlist, cudaStream_t st);
+epll_status launch_cand_combine(epll_gmm *g, int n, int m, const int *list, const int *nlist, float tau_abs,
+                                int *flag, int *nflag, cudaStream_t st);
+// Counting sort of n keys (components; negative keys are left out) into perm
+// and estimation work items; with n_dev the key count is min(n, mult * *n_dev).
+epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st,
+                               const int *n_dev = nullptr, int mult = 1);
 // Same for keys in 0..K-1 with an explicit [K] counter array.
 epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts, int *perm, int4 *items,
-                         cudaStream_t st);
+                         cudaStream_t st, const int *n_dev = nullptr, int mult = 1);
 // Selection down the search tree (csrc/k_tree.cu): writes kstar and the
 // smallest sibling gap on each patch's path.
 epll_status launch_select_tree(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,

@@ -38,7 +38,8 @@ __device__ __forceinline__ float from16(uint16_t v, int fmt)
 
 // Row i of the operand is sampled patch i, or patch rowmap[i] when a row map
 // (a device list with device count *n_dev) is given.  mu_out (nullable)
-// receives each row's patch mean.
+// receives each row's patch mean; Zf (nullable) an FP16 copy of the rows
+// (written beside BF16 split rows for an FP16 first pass).
 // fmt 3: 8-bit E4M3 operands scaled per row (max |z| -> 448), the square of
 // the scale in zsc2; Zhi is then read as bytes.
 constexpr int EX_ROWS = 4;  // rows per warp and pass: their loads are issued together
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(128)
 k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
              const int *__restrict__ rowmap, const int *__restrict__ n_dev, int fmt, int split,
              uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz,
-             float *__restrict__ zsc2, float *__restrict__ mu_out)
+             float *__restrict__ zsc2, float *__restrict__ mu_out, uint16_t *__restrict__ Zf)
 {
     const int lane = threadIdx.x & 31;
     if (n_dev) n = *n_dev;
@@ -99,6 +100,10 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
                     Zlo[(size_t)i * PD + lane] = to16(z0 - from16(h0, fmt), fmt);
                     Zlo[(size_t)i * PD + lane + 32] = to16(z1 - from16(h1, fmt), fmt);
                 }
+                if (Zf) {
+                    Zf[(size_t)i * PD + lane] = to16(z0, 2);
+                    Zf[(size_t)i * PD + lane + 32] = to16(z1, 2);
+                }
                 if (lane == 0 && i < n) {
                     zz[i] = q;
                     if (mu_out) mu_out[i] = mu;
@@ -117,11 +122,11 @@ static inline int ex_grid(int rows, bool listed)
 
 epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                            const int *rowmap, const int *n_dev, int fmt, int split, uint16_t *Zhi, uint16_t *Zlo,
-                           float *zz, float *zsc2, float *mu, cudaStream_t st)
+                           float *zz, float *zsc2, float *mu, cudaStream_t st, uint16_t *Zf)
 {
     const int rows = (n + 127) / 128 * 128;
     k_extract_tc<<<ex_grid(rows, n_dev != nullptr), 128, 0, st>>>(xhat, H, W, anchors, n, rowmap, n_dev, fmt, split,
-                                                                  Zhi, Zlo, zz, zsc2, mu);
+                                                                  Zhi, Zlo, zz, zsc2, mu, Zf);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

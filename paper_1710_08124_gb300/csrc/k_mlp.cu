@@ -705,24 +705,24 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CU
 constexpr int PS_T = 128;
 constexpr int PS_TILE = PS_T * 128;   // 16 KB: [128 rows][64] BF16
 constexpr int PS_B = 64 * 128;        // 8 KB: [64 rows][64] BF16
-constexpr int PS_SMEM = 1024 + 2 * PS_TILE + 2 * PS_B + 32 + 2 * PS_T * 4;
+constexpr int PS_SMEM = 1024 + 2 * PS_TILE + 2 * PS_B + 32 + 3 * PS_T * 4;
 
 __global__ void __launch_bounds__(PS_T)
 k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant__ CUtensorMap mapBlo,
                 const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
                 const int *__restrict__ perm, const int4 *__restrict__ items, int topm,
-                const int *__restrict__ roff, const int *__restrict__ rk_, Tables tab, const float *__restrict__ zz,
-                float *__restrict__ pscore, int *__restrict__ err)
+                const int *__restrict__ rowlist, const int *__restrict__ roff, const int *__restrict__ rk_,
+                Tables tab, const float *__restrict__ zz, float *__restrict__ pscore, int *__restrict__ err)
 {
-    if ((int)blockIdx.x >= items[0].w) return;
+    const int nitems = items[0].w;
+    if ((int)blockIdx.x >= nitems) return;
     extern __shared__ __align__(1024) unsigned char ps_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)ps_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Ahi = smem, *Alo = smem + PS_TILE, *Bhi = smem + 2 * PS_TILE, *Blo = Bhi + PS_B;
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(Blo + PS_B);  // [0] B loaded, [1] MMA done
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-    const int4 it = items[1 + blockIdx.x];
-    const int k = it.x, first = it.y, cnt_p = it.z;
+    int *s_anchor = reinterpret_cast<int *>(tslot + 2), *s_pair = s_anchor + PS_T, *s_row = s_pair + PS_T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -739,91 +739,97 @@ k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    if (threadIdx.x == 0) {
-        const uint32_t b = smem_u32(&bars[0]);
-        mbar_expect_tx(b, 2 * PS_B);
-        tma_load_2d(smem_u32(Bhi), &mapBs, 0, roff[k], b);
-        tma_load_2d(smem_u32(Blo), &mapBlo, 0, roff[k], b);
-    }
-    // gather: every thread first resolves one row's pair -> patch -> anchor;
-    // then warp w fills rows 32w .. 32w+31, eight rows' loads in flight at a
-    // time, lane l holding patch elements 2l and 2l + 1 (patch row l / 4)
-    int *s_anchor = reinterpret_cast<int *>(tslot + 2), *s_pair = s_anchor + PS_T;
-    if (threadIdx.x < cnt_p) {
-        const int pr = perm[first + threadIdx.x];
-        const int i = pr / topm;
-        s_pair[threadIdx.x] = pr;
-        s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
-    }
-    __syncthreads();
     const int pr_ = lane >> 2, pc_ = 2 * (lane & 3);
-    for (int rr = 0; rr < 32; rr += 8) {
-        float xa[8], xb[8];
+    // work items b, b + gridDim.x, ...; the barriers' phase is the local iteration's parity
+    for (int item = blockIdx.x, iter = 0; item < nitems; item += gridDim.x, ++iter) {
+        const int4 it = items[1 + item];
+        const int k = it.x, first = it.y, cnt_p = it.z;
+        const uint32_t ph = (uint32_t)(iter & 1);
+        if (threadIdx.x == 0) {
+            const uint32_t b = smem_u32(&bars[0]);
+            mbar_expect_tx(b, 2 * PS_B);
+            tma_load_2d(smem_u32(Bhi), &mapBs, 0, roff[k], b);
+            tma_load_2d(smem_u32(Blo), &mapBlo, 0, roff[k], b);
+        }
+        // gather: every thread first resolves one row's pair -> patch -> anchor;
+        // then warp w fills rows 32w .. 32w+31, eight rows' loads in flight at a
+        // time, lane l holding patch elements 2l and 2l + 1 (patch row l / 4)
+        if (threadIdx.x < cnt_p) {
+            const int pr = perm[first + threadIdx.x];
+            const int i = rowlist ? rowlist[pr / topm] : pr / topm;
+            s_pair[threadIdx.x] = pr;
+            s_row[threadIdx.x] = i;
+            s_anchor[threadIdx.x] = anchors ? anchors[i] : i;
+        }
+        __syncthreads();
+        for (int rr = 0; rr < 32; rr += 8) {
+            float xa[8], xb[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            xa[u] = xb[u] = 0.0f;
-            if (t < cnt_p) {
-                const int a = s_anchor[t];
-                const int ai = a / W, aj = a % W;
-                int r = ai + pr_, c0 = aj + pc_, c1 = c0 + 1;
-                if (r >= H) r -= H;
-                if (c0 >= W) c0 -= W;
-                if (c1 >= W) c1 -= W;
-                xa[u] = xhat[(size_t)r * W + c0];
-                xb[u] = xhat[(size_t)r * W + c1];
+            for (int u = 0; u < 8; ++u) {
+                const int t = 32 * warp + rr + u;
+                xa[u] = xb[u] = 0.0f;
+                if (t < cnt_p) {
+                    const int a = s_anchor[t];
+                    const int ai = a / W, aj = a % W;
+                    int r = ai + pr_, c0 = aj + pc_, c1 = c0 + 1;
+                    if (r >= H) r -= H;
+                    if (c0 >= W) c0 -= W;
+                    if (c1 >= W) c1 -= W;
+                    xa[u] = xhat[(size_t)r * W + c0];
+                    xb[u] = xhat[(size_t)r * W + c1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = 32 * warp + rr + u;
+                float sum = xa[u] + xb[u];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
+                const float z0 = xa[u] - mu, z1 = xb[u] - mu;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
+                // elements 2l, 2l+1: bytes 4l..4l+3 of the row, 16-byte chunk l / 4 swizzled by t mod 8
+                const uint32_t o = t * 128 + ((((uint32_t)lane >> 2) ^ (t & 7)) << 4) + 4 * (lane & 3);
+                *reinterpret_cast<__nv_bfloat162 *>(Ahi + o) = h;
+                *reinterpret_cast<__nv_bfloat162 *>(Alo + o) = l;
             }
         }
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (mbar_wait(smem_u32(&bars[0]), ph, abort_flag)) {
+                tc_fence_after();
+                const uint32_t idesc = idesc_f16(PS_T, 64, 1);
+                const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int t = 32 * warp + rr + u;
-            float sum = xa[u] + xb[u];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            const float mu = t < cnt_p ? sum * (1.0f / PD) : 0.0f;
-            const float z0 = xa[u] - mu, z1 = xb[u] - mu;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - __low2float(h), z1 - __high2float(h));
-            // elements 2l, 2l+1: bytes 4l..4l+3 of the row, 16-byte chunk l / 4 swizzled by t mod 8
-            const uint32_t o = t * 128 + ((((uint32_t)lane >> 2) ^ (t & 7)) << 4) + 4 * (lane & 3);
-            *reinterpret_cast<__nv_bfloat162 *>(Ahi + o) = h;
-            *reinterpret_cast<__nv_bfloat162 *>(Alo + o) = l;
-        }
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (mbar_wait(smem_u32(&bars[0]), 0, abort_flag)) {
-            tc_fence_after();
-            const uint32_t idesc = idesc_f16(PS_T, 64, 1);
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t o = 32 * kk;
-                mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, kk ? 1u : 0u);
-                mma_f16(tbase, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
-                mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t o = 32 * kk;
+                    mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, kk ? 1u : 0u);
+                    mma_f16(tbase, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+                    mma_f16(tbase, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+                }
+                mma_commit(smem_u32(&bars[1]));
             }
-            mma_commit(smem_u32(&bars[1]));
         }
-    }
-    __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), 0, abort_flag));
-    tc_fence_after();
-    if (ok) {
-        uint32_t r[64];
-        tmem_ld_all<64>(tbase + ((uint32_t)(32 * warp) << 16), r);
-        const int t = 32 * warp + lane, rk = rk_[k];
-        float sq = 0.0f;
+        __syncwarp();
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), ph, abort_flag));
+        tc_fence_after();
+        if (ok) {
+            uint32_t r[64];
+            tmem_ld_all<64>(tbase + ((uint32_t)(32 * warp) << 16), r);
+            const int t = 32 * warp + lane, rk = rk_[k];
+            float sq = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            const float c = __uint_as_float(r[j]);
-            if (j < rk) sq = fmaf(c, c, sq);
+            for (int j = 0; j < 64; ++j) {
+                const float c = __uint_as_float(r[j]);
+                if (j < rk) sq = fmaf(c, c, sq);
+            }
+            if (t < cnt_p) pscore[s_pair[t]] = tab.cst_hi[k] + tab.t_hi[k] * zz[s_row[t]] + tab.sgn[k] * sq;
         }
-        if (t < cnt_p) {
-            const int pr = s_pair[t];
-            pscore[pr] = tab.cst_hi[k] + tab.t_hi[k] * zz[pr / topm] + tab.sgn[k] * sq;
-        }
+        tc_fence_before();
+        // the next item overwrites the operands and the accumulator
+        if (__syncthreads_or(!ok)) break;
     }
     tc_fence_before();
     __syncthreads();
@@ -834,23 +840,29 @@ k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
 }
 
-// Per patch: best and second-best rescored candidate (lowest index on ties);
+// Per entry: best and second-best rescored candidate (lowest index on ties);
 // undecided patches (proposal mass below pmin, or a top-2 gap within the
-// split-BF16 error bound) are listed for the exhaustive pass.
-__global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, const float *__restrict__ pscore,
+// split-BF16 error bound, or an absent first candidate) are listed for the
+// next pass.  Entry f is patch f, or patch list[f] of a device list (count
+// *nlist); a negative candidate is absent; pmass and nfallback are nullable.
+__global__ void k_prop_combine(int n, const int *__restrict__ list, const int *__restrict__ nlist, int topm,
+                               const int *__restrict__ cand, const float *__restrict__ pscore,
                                const float *__restrict__ pmass, float pmin, const float *__restrict__ zz,
                                const float *__restrict__ tmax, float tau_abs, float tau_rel,
                                int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
                                int *__restrict__ nflag, long long *__restrict__ nfallback)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = list ? min(n, *nlist) : n;
     bool unsure = false;
-    if (i < n) {
+    if (f < total) {
+        const int i = list ? list[f] : f;
         float s1 = FLT_MAX, s2 = FLT_MAX;
         int k1 = 0x7fffffff;
         for (int q = 0; q < topm; ++q) {
-            const int k = cand[(size_t)i * topm + q];
-            const float s = pscore ? pscore[(size_t)i * topm + q] : 0.0f;
+            const int k = cand[(size_t)f * topm + q];
+            if (k < 0) continue;
+            const float s = pscore ? pscore[(size_t)f * topm + q] : 0.0f;
             if (s < s1 || (s == s1 && k < k1)) {
                 s2 = s1;
                 s1 = s;
@@ -859,17 +871,21 @@ __global__ void k_prop_combine(int n, int topm, const int *__restrict__ cand, co
                 s2 = s;
             }
         }
-        kstar[i] = k1;
         const float gp = s2 - s1;
-        gap[i] = gp;
-        unsure = !(pmass[i] >= pmin) || !(gp >= tau_abs + tau_rel * zz[i] * tmax[0]);
+        if (k1 != 0x7fffffff) {
+            kstar[i] = k1;
+            gap[i] = gp;
+        }
+        unsure = k1 == 0x7fffffff || (pmass && !(pmass[i] >= pmin)) ||
+                 !(gp >= tau_abs + tau_rel * zz[i] * tmax[0]);
         if (unsure) flag[atomicAdd(nflag, 1)] = i;
     }
     const unsigned b = __ballot_sync(0xffffffffu, unsure);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd((unsigned long long *)nfallback, (unsigned long long)__popc(b));
+    if (nfallback && (threadIdx.x & 31) == 0 && b)
+        atomicAdd((unsigned long long *)nfallback, (unsigned long long)__popc(b));
 }
 
-static epll_status ensure_prop_ws(epll_gmm *g, int n)
+epll_status ensure_prop_ws(epll_gmm *g, int n)
 {
     Workspace &ws = g->ws;
     const size_t N = ws.capN;
@@ -934,6 +950,41 @@ epll_status launch_proposal_topm(epll_gmm *g, const float *xhat, int H, int W, c
     return EPLL_OK;
 }
 
+epll_status launch_pair_scores(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n, int m,
+                               const int *list, const int *nlist, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int npairs = n * m;
+    epll_status s;
+    if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st, list ? nlist : nullptr, m))) return s;
+    static bool attr = false;
+    if (!attr) {
+        EPLL_CU(cudaFuncSetAttribute(k_pair_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM));
+        attr = true;
+    }
+    CUtensorMap bs, bslo;
+    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 64))) return s;
+    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 64))) return s;
+    // persistent over the work items (their count is known on the device only)
+    const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
+    const int grid = max_items < 152 * 4 ? max_items : 152 * 4;
+    k_pair_score_tc<<<grid, PS_T, PS_SMEM, st>>>(bs, bslo, xhat, H, W, anchors, ws.pperm, ws.pitems, m, list,
+                                                 g->d_roff, g->d_r, g->tab, ws.zz, ws.pscore, cnt(g, CNT_ERR));
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+epll_status launch_cand_combine(epll_gmm *g, int n, int m, const int *list, const int *nlist, float tau_abs,
+                                int *flag, int *nflag, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, list, nlist, m, ws.cand, ws.pscore, nullptr, 0.0f, ws.zz,
+                                                   g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, flag, nflag,
+                                                   nullptr);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
 epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                    float tau_abs, cudaStream_t st)
 {
@@ -943,26 +994,10 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
     if ((s = launch_proposal_topm(g, xhat, H, W, anchors, n, g->tab.ibeta, st))) return s;
     // exact FP32 scores of the proposed (patch, component) pairs; a single
     // proposal is the selection (its gap is reported as FLT_MAX)
-    if (topm > 1) {
-        const int npairs = n * topm;
-        if ((s = group_by_component(g, ws.cand, npairs, ws.pperm, ws.pitems, st))) return s;
-        static bool attr = false;
-        if (!attr) {
-            EPLL_CU(cudaFuncSetAttribute(k_pair_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM));
-            attr = true;
-        }
-        CUtensorMap bs, bslo;
-        if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 64))) return s;
-        if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 64))) return s;
-        const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
-        k_pair_score_tc<<<max_items, PS_T, PS_SMEM, st>>>(bs, bslo, xhat, H, W, anchors, ws.pperm, ws.pitems, topm,
-                                                          g->d_roff, g->d_r, g->tab, ws.zz, ws.pscore,
-                                                          cnt(g, CNT_ERR));
-        EPLL_LAUNCHED(g);
-    }
+    if (topm > 1 && (s = launch_pair_scores(g, xhat, H, W, anchors, n, topm, nullptr, nullptr, st))) return s;
     int *nflag1 = cnt(g, CNT_NFLAG1);
     EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
-    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
+    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, nullptr, nullptr, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
                                                    g->prop_pmin, ws.zz,
                                                    g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, ws.flag1,
                                                    nflag1, ws.ctr + 1);

@@ -5,6 +5,7 @@
 #include "epll_internal.cuh"
 
 #include <cfloat>
+#include <climits>
 
 namespace epll {
 
@@ -396,20 +397,26 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
 
 // Component indices handed in by the caller (teacher forcing) are clamped
 // into range before they index anything.
-__device__ __forceinline__ int clamp_k(int k, int K) { return k < 0 ? 0 : (k >= K ? K - 1 : k); }
+// Bucket of a key: negative keys are absent (-1); keys past the range are clamped.
+__device__ __forceinline__ int clamp_k(int k, int K) { return k < 0 ? -1 : (k >= K ? K - 1 : k); }
 
 // ============================================================================
 // Grouping by component (counting sort): histogram, exclusive scan, scatter.
 // The order inside a group does not matter: every patch's estimate depends
 // only on the patch and its component.
 // ============================================================================
-__global__ void k_bucket_hist(const int *__restrict__ kstar, int n, int K, int *__restrict__ counts)
+// n_dev (nullable): the key count is min(n, mult * *n_dev).
+__global__ void k_bucket_hist(const int *__restrict__ kstar, int n, int K, int *__restrict__ counts,
+                              const int *__restrict__ n_dev, int mult)
 {
     extern __shared__ int h[];
+    if (n_dev) n = min(n, mult * *n_dev);
     for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&h[clamp_k(kstar[i], K)], 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k = clamp_k(kstar[i], K);
+        if (k >= 0) atomicAdd(&h[k], 1);
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x)
         if (h[k]) atomicAdd(&counts[k], h[k]);
@@ -464,9 +471,12 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ c
 // global reservation per key present in the block, then the writes.
 constexpr int SCAT_T = 256, SCAT_PER = 4;
 __global__ void __launch_bounds__(SCAT_T)
-k_bucket_scatter(const int *__restrict__ keys, int n, int K, int *__restrict__ cursor, int *__restrict__ perm)
+k_bucket_scatter(const int *__restrict__ keys, int n, int K, int *__restrict__ cursor, int *__restrict__ perm,
+                 const int *__restrict__ n_dev, int mult)
 {
     extern __shared__ int sh[];  // [K]: block counts, then the block's base in each bucket
+    if (n_dev) n = min(n, mult * *n_dev);
+    if ((int)blockIdx.x * SCAT_T * SCAT_PER >= n) return;  // whole block past the keys
     for (int k = threadIdx.x; k < K; k += SCAT_T) sh[k] = 0;
     __syncthreads();
     const int i0 = blockIdx.x * SCAT_T * SCAT_PER + threadIdx.x;
@@ -626,24 +636,25 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
     }
 }
 
-epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st)
+epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, int4 *items, cudaStream_t st,
+                               const int *n_dev, int mult)
 {
-    return group_by_key(g, keys, n, g->K, g->ws.counts, perm, items, st);
+    return group_by_key(g, keys, n, g->K, g->ws.counts, perm, items, st, n_dev, mult);
 }
 
 epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts, int *perm, int4 *items,
-                         cudaStream_t st)
+                         cudaStream_t st, const int *n_dev, int mult)
 {
     // counts: [K] counts -> cursors
     EPLL_CU(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)K, st));
     int hb = (n + 255) / 256;
     if (hb > 152 * 2) hb = 152 * 2;
-    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(keys, n, K, counts);
+    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(keys, n, K, counts, n_dev, mult);
     EPLL_LAUNCHED(g);
     k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, items);
     EPLL_LAUNCHED(g);
     k_bucket_scatter<<<(n + SCAT_T * SCAT_PER - 1) / (SCAT_T * SCAT_PER), SCAT_T, sizeof(int) * (size_t)K, st>>>(
-        keys, n, K, counts, perm);
+        keys, n, K, counts, perm, n_dev, mult);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

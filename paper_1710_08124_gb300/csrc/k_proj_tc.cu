@@ -5,8 +5,9 @@
 // 64.  Each CTA owns 128 patches: their 16-bit tile is loaded once by TMA
 // (128-byte swizzle) and stays in shared memory while the basis streams
 // through a multi-stage TMA ring.  One thread issues tcgen05.mma into FP32
-// accumulators in tensor memory (2-4 buffers, 512 columns); eight epilogue
-// warps read the accumulators back with tcgen05.ld and fold them straight
+// accumulators in tensor memory (2-4 buffers, 512 columns); up to sixteen
+// epilogue warps (four per TMEM lane quarter, each owning a quarter of the
+// columns) read the accumulators back with tcgen05.ld and fold them straight
 // into the scores of Eq. 14, keeping the best and second-best component per
 // patch, so the K x N score matrix never exists anywhere.
 //
@@ -25,16 +26,16 @@
 #include <cudaTypedefs.h>
 
 #include <cfloat>
+#include <climits>
 #include <mutex>
 
 namespace epll {
 
 // ---------------------------------------------------------------- main kernel
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
 
-template <int BN, int NT>
+template <int BN, int NT, int RR, bool CAND = false>
 struct TcCfg {
     // NT: 1 one 16-bit product, 3 split BF16 (three products), 8 one E4M3 product
     static constexpr int ROWB = NT == 8 ? 64 : 128;            // bytes per 64-element row
@@ -45,8 +46,14 @@ struct TcCfg {
     static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - 2 * A_BYTES) / B_STAGE;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int NB = 512 / BN;                        // TMEM accumulator buffers
-    static constexpr int HALF = BN / 2;                        // columns per epilogue warp
-    static constexpr int CTRL = 2048;
+    // epilogue column groups: each group (one warp per TMEM lane quarter)
+    // owns whole components of BN / NG columns; ragged ranks use one group
+    static constexpr int NG = RR == 0 ? 1 : (BN / RR >= 4 ? 4 : BN / RR);
+    static constexpr int EW = 4 * NG;                          // epilogue warps
+    static constexpr int THREADS = 64 + 32 * EW;               // warp 0 TMA, warp 1 MMA, then the epilogue
+    static constexpr int COLS = BN / NG;                       // columns per epilogue warp
+    static constexpr int MW = CAND ? 8 : 3;                    // merge words per row and group
+    static constexpr int CTRL = 1024 + (NG - 1) * TC_M * MW * 4; // barriers + the [NG-1][128][MW] merge buffer
     static constexpr int SMEM = 1024 + 2 * A_BYTES + STAGES * B_STAGE + CTRL;
 };
 
@@ -70,6 +77,25 @@ __device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &
     }
 }
 
+// (score, component) order: the lower component first among equal scores
+__device__ __forceinline__ bool sk_less(float a, int ka, float b, int kb) { return a < b || (a == b && ka < kb); }
+
+// The four lowest (score, component) pairs, ascending; empty slots hold (FLT_MAX, INT_MAX).
+__device__ __forceinline__ void top4(float s, int k, float (&cs)[4], int (&ck)[4])
+{
+    if (sk_less(s, k, cs[3], ck[3])) {
+        cs[3] = s;
+        ck[3] = k;
+#pragma unroll
+        for (int j = 3; j > 0; --j) {
+            if (sk_less(cs[j], ck[j], cs[j - 1], ck[j - 1])) {
+                const float ts = cs[j]; cs[j] = cs[j - 1]; cs[j - 1] = ts;
+                const int tk = ck[j]; ck[j] = ck[j - 1]; ck[j - 1] = tk;
+            }
+        }
+    }
+}
+
 // Persistent: CTA b takes the 128-row tiles b, b + gridDim.x, ... of the n
 // rows (n read from the device when n_dev is given).  Two A buffers let the
 // next tile's patches load while the current tile is multiplied; the basis
@@ -78,18 +104,25 @@ __device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &
 // DUMP = true: instead of the top-2 selection every component's score is
 // written to scores[row * K + k]; blockIdx.y then takes a slice of the basis
 // tiles (uniform ranks only, so no component straddles two slices).
-template <int BN, int NT, int RR, bool DUMP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// CAND = true (one-term first pass): the four best components are kept; a
+// patch whose top-2 gap is within the error bound is listed (flag[f] = row)
+// with its candidates, the components within that bound of the best, in
+// cand[f] (-1: absent); a first candidate of -1 means the band may hold more
+// than four components.
+template <int BN, int NT, int RR, bool DUMP, bool CAND>
+__global__ void __launch_bounds__(TcCfg<BN, NT, RR, CAND>::THREADS, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
           const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
           int n, const int *__restrict__ rowmap, const int *__restrict__ n_dev, int K, int Rtot,
           uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk, Tables tab,
           float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
           int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err,
-          float *__restrict__ scores, const float *__restrict__ zsc2)
+          float *__restrict__ scores, const float *__restrict__ zsc2, int4 *__restrict__ cand)
 {
-    using C = TcCfg<BN, NT>;
+    using C = TcCfg<BN, NT, RR, CAND>;
+    static_assert(!(DUMP && CAND), "one output form");
     static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
+    static_assert(RR == 0 || C::COLS % RR == 0, "an epilogue warp owns whole components");
     if (n_dev) n = *n_dev;                       // rows listed on the device
     const int mtiles = (n + TC_M - 1) / TC_M;
     if ((int)blockIdx.x >= mtiles) return;       // whole CTA idle, before any setup
@@ -105,7 +138,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     unsigned char *sA = smem;                      // 2 x A_BYTES
     unsigned char *sB = smem + 2 * C::A_BYTES;
     TcCtrl *ctl = (TcCtrl *)(sB + C::STAGES * C::B_STAGE);
-    float *mrg = (float *)(ctl + 1);  // [128][3] merge buffer of the two epilogue halves
+    float *mrg = (float *)((unsigned char *)ctl + 1024);  // [NG-1][128][MW] merge buffer of the column groups
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &ctl->abort_flag;
@@ -122,7 +155,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
         for (int b = 0; b < C::NB; ++b) {
             mbar_init(smem_u32(&ctl->t_full[b]), 1);
-            mbar_init(smem_u32(&ctl->t_empty[b]), 8);
+            mbar_init(smem_u32(&ctl->t_empty[b]), C::EW);
         }
         mbar_init(smem_u32(&ctl->drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -212,9 +245,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             mbar_wait(smem_u32(&ctl->drain), 0, abort_flag);
         }
     } else {
-        // ------------------------------------------------ epilogue (8 warps)
+        // ------------------------------------------------ epilogue (EW warps)
         const int q = warp & 3;        // TMEM lane quarter this warp may access
-        const int h = (warp - 2) >> 2; // column half of each accumulator tile
+        const int h = (warp - 2) >> 2; // column group of each accumulator tile
         const int row = 32 * q + lane;
         bool ok = true;
         for (int mt = 0; ok && mt < my_m; ++mt) {
@@ -224,6 +257,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const float rs2 = (NT == 8 && grow < n) ? zsc2[grow] : 1.0f;  // 8-bit: row scale squared
             float s1 = FLT_MAX, s2 = FLT_MAX, acc = 0.0f;
             int k1 = 0, curk = -1;
+            float cs[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+            int ck[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
             for (int it = 0; it < ntiles; ++it) {
                 const int gi = mt * ntiles + it;
                 const int b = gi % C::NB, tround = gi / C::NB;
@@ -233,23 +268,23 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     break;
                 }
                 tc_fence_after();
-                // uniform ranks: each half-warp-group owns whole components of its half;
-                // ragged ranks: the h = 0 warps take the whole tile (components may
-                // straddle the halves), the h = 1 warps only keep the handshake.
-                const int cbeg = RR ? h * C::HALF : 0;
-                const int ncol = RR ? C::HALF : (h == 0 ? BN : 0);
+                // uniform ranks: each column group owns whole components of its
+                // BN / NG columns; ragged ranks: one group takes the whole tile
+                // (components may straddle any split of it).
+                const int cbeg = RR ? h * C::COLS : 0;
+                const int ncol = RR ? C::COLS : BN;
                 const int col0 = (tile0 + it) * BN + cbeg;
                 const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbeg);
                 if constexpr (RR > 0) {
-                    // the whole half-tile in one TMEM round trip; the buffer is
+                    // the warp's columns in one TMEM round trip; the buffer is
                     // handed back to the MMA warp before the arithmetic
-                    uint32_t r[C::HALF];
-                    tmem_ld_all<C::HALF>(taddr, r);
+                    uint32_t r[C::COLS];
+                    tmem_ld_all<C::COLS>(taddr, r);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
 #pragma unroll
-                    for (int p = 0; p < C::HALF / RR; ++p) {
+                    for (int p = 0; p < C::COLS / RR; ++p) {
                         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
                         for (int j = 0; j < RR; j += 4) {
@@ -268,6 +303,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                                              (RR == 64 ? sq : -sq);
                             if (DUMP) {
                                 if (grow < n) scores[(size_t)grow * K + k] = sc;
+                            } else if (CAND) {
+                                top4(sc, k, cs, ck);
                             } else {
                                 top2(sc, k, s1, s2, k1);
                             }
@@ -289,7 +326,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                                     const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                                     const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
                                                      __ldg(&tab.sgn[curk]) * a8;
-                                    top2(sc, curk, s1, s2, k1);
+                                    if (CAND) top4(sc, curk, cs, ck);
+                                    else top2(sc, curk, s1, s2, k1);
                                 }
                                 curk = k;
                                 acc = 0.0f;
@@ -309,26 +347,64 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                 const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
                                  __ldg(&tab.sgn[curk]) * a8;
-                top2(sc, curk, s1, s2, k1);
+                if (CAND) top4(sc, curk, cs, ck);
+                else top2(sc, curk, s1, s2, k1);
             }
-            if (!DUMP) {
-                // merge the two halves: components of half 1 interleave with half 0's
-                if (h == 1) {
-                    mrg[row * 3 + 0] = s1;
-                    mrg[row * 3 + 1] = s2;
-                    mrg[row * 3 + 2] = __int_as_float(k1);
+            if (CAND) {
+                // merge the column groups' four best, then list the undecided patch
+                if (C::NG > 1 && h > 0) {
+                    float *m = mrg + ((h - 1) * TC_M + row) * 8;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        m[j] = cs[j];
+                        m[4 + j] = __int_as_float(ck[j]);
+                    }
                 }
-                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
+                if (h == 0 && grow < n && ok) {
+#pragma unroll
+                    for (int o = 1; o < C::NG; ++o) {
+                        const float *m = mrg + ((o - 1) * TC_M + row) * 8;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) top4(m[j], __float_as_int(m[4 + j]), cs, ck);
+                    }
+                    kstar[grow] = ck[0];
+                    const float gp = cs[1] - cs[0];
+                    gap[grow] = gp;
+                    const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
+                    if (!(gp >= thr)) {
+                        const float lim = cs[0] + thr;
+                        const int f = atomicAdd(nflag, 1);
+                        flag[f] = grow;
+                        cand[f] = cs[3] < lim ? make_int4(-1, -1, -1, -1)
+                                              : make_int4(ck[0], ck[1], cs[2] < lim ? ck[2] : -1, -1);
+                    }
+                }
+                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");  // mrg is reused
+            } else if (!DUMP) {
+                // merge the column groups (their components interleave); among
+                // equal scores the lowest component index wins
+                if (C::NG > 1 && h > 0) {
+                    float *m = mrg + ((h - 1) * TC_M + row) * 3;
+                    m[0] = s1;
+                    m[1] = s2;
+                    m[2] = __int_as_float(k1);
+                }
+                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
                 if (h == 0 && grow < n && ok) {
                     const int out = rowmap ? rowmap[grow] : grow;
-                    const float t1 = mrg[row * 3 + 0], t2 = mrg[row * 3 + 1];
-                    const int tk = __float_as_int(mrg[row * 3 + 2]);
-                    float b1, b2;
-                    int bk;
-                    if (t1 < s1 || (t1 == s1 && tk < k1)) {
-                        b1 = t1; bk = tk; b2 = fminf(s1, t2);
-                    } else {
-                        b1 = s1; bk = k1; b2 = fminf(t1, s2);
+                    float b1 = s1, b2 = s2;
+                    int bk = k1;
+#pragma unroll
+                    for (int o = 1; o < C::NG; ++o) {
+                        const float *m = mrg + ((o - 1) * TC_M + row) * 3;
+                        const float t1 = m[0], t2 = m[1];
+                        const int tk = __float_as_int(m[2]);
+                        if (t1 < b1 || (t1 == b1 && tk < bk)) {
+                            b2 = fminf(b1, t2); b1 = t1; bk = tk;
+                        } else {
+                            b2 = fminf(b2, t1);
+                        }
                     }
                     kstar[out] = bk;
                     const float gp = b2 - b1;
@@ -336,7 +412,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
                     if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = out;
                 }
-                asm volatile("bar.sync 1, 256;" ::: "memory");  // mrg is reused by the next tile
+                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");  // mrg is reused
             }
         }
     }
@@ -350,15 +426,15 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
-template <int BN, int NT, int RR, bool DUMP = false>
+template <int BN, int NT, int RR, bool DUMP = false, bool CAND = false>
 static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                              const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                              const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
                              float tau_rel, int *flag, int *nflag, cudaStream_t st,
                              float *scores = nullptr, int slices = 1, const float *zsc2 = nullptr)
 {
-    using Cfg = TcCfg<BN, NT>;
-    auto kern = k_proj_tc<BN, NT, RR, DUMP>;
+    using Cfg = TcCfg<BN, NT, RR, CAND>;
+    auto kern = k_proj_tc<BN, NT, RR, DUMP, CAND>;
     static bool attr = false;
     if (!attr) {
         EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
@@ -378,15 +454,16 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     const dim3 grid(gx, slices);
     // the instrumentation covers the pass over every sampled patch only
     if (!n_dev) prof_begin(g, st);
-    kern<<<grid, TC_THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
                                              g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
-                                             nflag, cnt(g, CNT_ERR), scores, zsc2);
+                                             nflag, cnt(g, CNT_ERR), scores, zsc2,
+                                             reinterpret_cast<int4 *>(ws.cand));
     if (!n_dev) prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
 
-template <int BN, int NT>
+template <int BN, int NT, bool CAND = false>
 static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                                const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                                const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
@@ -395,10 +472,10 @@ static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensor
 {
 #define EPLL_TC_ARGS g, a, alo, b, blo, n, rowmap, n_dev, zz, idesc, tau_abs, tau_rel, flag, nflag, st, nullptr, 1, zsc2
     switch (g->uniform_rank) {
-    case 64: return launch_tc<BN, NT, 64>(EPLL_TC_ARGS);
-    case 16: return launch_tc<BN, NT, 16>(EPLL_TC_ARGS);
-    case 8: return launch_tc<BN, NT, 8>(EPLL_TC_ARGS);
-    default: return launch_tc<BN, NT, 0>(EPLL_TC_ARGS);
+    case 64: return launch_tc<BN, NT, 64, false, CAND>(EPLL_TC_ARGS);
+    case 16: return launch_tc<BN, NT, 16, false, CAND>(EPLL_TC_ARGS);
+    case 8: return launch_tc<BN, NT, 8, false, CAND>(EPLL_TC_ARGS);
+    default: return launch_tc<BN, NT, 0, false, CAND>(EPLL_TC_ARGS);
     }
 #undef EPLL_TC_ARGS
 }
@@ -436,11 +513,20 @@ epll_status launch_dump_split(epll_gmm *g, const float *xhat, int H, int W, cons
 #undef EPLL_DUMP_ARGS
 }
 
-// Gaussian selection on the tensor cores.  A one-term pass (BF16 or FP16)
-// scores every sampled patch; the rows it cannot decide (top-2 gap within its
-// error bound) are rescored by the split-BF16 pass; what that pass cannot
-// decide goes to the compensated FP32 rescoring (ws.flag).  With the split
-// form as the first pass the second is skipped.
+// Gaussian selection on the tensor cores.
+// BF16X3: the split pass scores every sampled patch; its near-ties go to the
+// compensated FP32 rescoring (ws.flag).
+// FP16: a one-term pass scores every sampled patch and keeps each patch's
+// four best components; a patch it cannot decide is listed with the
+// components within its error bound of the best, and these (patch,
+// component) pairs are grouped by component and rescored in the split form
+// (launch_pair_scores); what that cannot decide, and every patch whose band
+// may hold more than four components, goes to the compensated rescoring.
+// The split rows and means of every patch are extracted beside the FP16
+// operand, for the estimation step.
+// BF16 / FP8: a one-term pass; the rows it cannot decide (a third or more of
+// them for BF16) are rescored by the split pass over every component, whose
+// near-ties go to the compensated rescoring.
 epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                              int precision, float tau_abs, float tau_rel, cudaStream_t st)
 {
@@ -451,6 +537,25 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Zhi = ws.Zb, *Zlo = ws.Zb + ws.zrows * PD;
     epll_status s;
+    if (fmt == 2) {
+        if ((s = ensure_prop_ws(g, n))) return s;  // ws.cand, the pair buffers
+        // FP16 operand rows in ws.Z2 (free until the rescoring's score dump)
+        uint16_t *Zf = ws.Z2;
+        if ((s = launch_extract(g, xhat, H, W, anchors, n, nullptr, nullptr, 1, 1, Zhi, Zlo, ws.zz, nullptr, ws.mu,
+                                st, Zf)))
+            return s;
+        int *nflag1 = cnt(g, CNT_NFLAG1);
+        EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
+        EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
+        CUtensorMap a, b;
+        if ((s = make_map(&a, Zf, rows, TC_M))) return s;
+        if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
+        if ((s = dispatch_rr<256, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 0),
+                                           tau_abs, tau_rel, ws.flag1, nflag1, st)))
+            return s;
+        if ((s = launch_pair_scores(g, xhat, H, W, anchors, n, 4, ws.flag1, nflag1, st))) return s;
+        return launch_cand_combine(g, n, 4, ws.flag1, nflag1, tau_abs, ws.flag, cnt(g, CNT_NFLAG), st);
+    }
     // ---- first pass over every sampled patch
     if ((s = launch_extract(g, xhat, H, W, anchors, n, nullptr, nullptr, fmt, split_first ? 1 : 0, Zhi, Zlo, ws.zz,
                             ws.zsc2, split_first ? ws.mu : nullptr, st)))
@@ -477,10 +582,9 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
             return s;
     } else {
         if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
-        // one-term pass: no lo operands (the lo map arguments are unused)
-        if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz,
-                                     idesc_f16(TC_M, 256, fmt == 2 ? 0 : 1), tau_abs, tau_rel, flag1, nflag1,
-                                     st)))
+        // one-term BF16 pass: no lo operands (the lo map arguments are unused)
+        if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1), tau_abs,
+                                     tau_rel, flag1, nflag1, st)))
             return s;
     }
     return launch_split_pass(g, xhat, H, W, anchors, n, flag1, nflag1, tau_abs, st);

@@ -159,11 +159,14 @@ static __device__ __forceinline__ void tmem_wait128(uint32_t (&r)[128])
 template <int NC>
 static __device__ __forceinline__ void tmem_ld_all(uint32_t taddr, uint32_t (&r)[NC])
 {
-    if constexpr (NC == 64) {
+    if constexpr (NC == 32) {
+        tmem_ld32(taddr, r);
+        tmem_wait(r);
+    } else if constexpr (NC == 64) {
         tmem_ld64(taddr, r);
         tmem_wait64(r);
     } else {
-        static_assert(NC == 128, "64 or 128 columns");
+        static_assert(NC == 128, "32, 64 or 128 columns");
         tmem_ld128(taddr, r);
         tmem_wait128(r);
     }

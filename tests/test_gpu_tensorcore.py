@@ -23,8 +23,8 @@ if not torch.cuda.is_available():
 import paper_1710_08124_gb300 as ep  # noqa: E402
 
 TIE = 1e-4
-REL = {ep.BF16: 1e-2, ep.FP16: 1.5e-3, ep.BF16X3: 1e-4, ep.FP8: 1e-1}
-PRECS = [ep.BF16X3, ep.FP16, ep.BF16, ep.FP8]
+REL = {ep.BF16: 1e-2, ep.FP16: 1.5e-3, ep.BF16X3: 1e-4, ep.FP8: 1e-1, ep.AUTO: 1.5e-3}
+PRECS = [ep.BF16X3, ep.FP16, ep.BF16, ep.FP8, ep.AUTO]
 
 
 @pytest.fixture(scope="module", autouse=True)
