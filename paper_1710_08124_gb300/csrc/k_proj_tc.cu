@@ -122,7 +122,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     using C = TcCfg<BN, NT, RR, CAND>;
     static_assert(!(DUMP && CAND), "one output form");
     static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
-    static_assert(RR == 0 || C::COLS % RR == 0, "an epilogue warp owns whole components");
+    static_assert(RR == 0 || C::COLS % (RR ? RR : 1) == 0, "an epilogue warp owns whole components");
     if (n_dev) n = *n_dev;                       // rows listed on the device
     const int mtiles = (n + TC_M - 1) / TC_M;
     if ((int)blockIdx.x >= mtiles) return;       // whole CTA idle, before any setup

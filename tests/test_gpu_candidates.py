@@ -116,3 +116,26 @@ def test_one_term_ranks_match_split(r):
     clear = ogap >= TIE
     assert np.array_equal(out[ep.FP16][1][clear], oks[clear])
     assert np.array_equal(out[ep.BF16X3][1][clear], oks[clear])
+
+
+@pytest.mark.parametrize("prec", [ep.FP16, ep.AUTO])
+def test_many_tiles_per_cta(prec):
+    """Every patch of a 256x256 image: 512 tiles of 128 patches, so each
+    persistent CTA of the FP16 pass takes three or four tiles; the selection
+    must match the oracle's."""
+    g = synth.synthetic_gmm(12, seed=5)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, 64)
+    om = oracle.Model(g.w, g.U, g.S, "fixed", 64)
+    sigma = 15 / 255
+    x = synth.image(25, 256) + synth.noise(25, 256, 256, sigma)
+    beta = 4 / sigma ** 2
+    xt, an, ks, gp = ep.patch_step(gm, dev(x), beta, ep.Options(precision=prec), 0)
+    ep.last_counters(gm)
+    an, ks = an.cpu().numpy(), ks.cpu().numpy()
+    assert len(an) == 256 * 256
+    x64 = x.astype(np.float32).astype(np.float64)
+    oxt, oks, ogap, _ = oracle.patch_step(om, beta, x64, an)
+    bad = (ks != oks) & (ogap >= TIE)
+    assert not bad.any(), f"{bad.sum()} disagreements"
+    if np.array_equal(ks, oks):
+        np.testing.assert_allclose(xt.cpu().numpy(), oxt, atol=1e-5, rtol=0)
