@@ -234,14 +234,21 @@ __device__ __forceinline__ bool df_less(df x, df y)
 constexpr float RESCORE_ABS = 1e-3f;
 constexpr float RESCORE_REL = 2e-5f;
 constexpr int RS_WARPS = 8;
+constexpr int RS_QW = 4;                  // warps per candidate: each sums 16 of the 64 terms
+constexpr int RS_CPR = RS_WARPS / RS_QW;  // candidates per round
+constexpr int RS_KMAX = 4096;             // candidate list capacity (the model's K at most)
 
 // Entries [f0, f0 + fcap) of the near-tie list; scores[(f - f0) * K + k] holds
-// each component's FP32 score (written by the FP32 kernel in list mode).  A
-// block takes one listed patch: warp 0 forms the compensated DC-free patch and
-// |z|^2, every warp lists the components within the band of the best dumped
-// score, the candidates are dealt to the warps in turn, and the warps' best
-// and second best (compensated; the lower component on equal scores) are
-// merged at the end.
+// each component's dumped score.  A block takes one listed patch: warp 0
+// forms the compensated DC-free patch and |z|^2 while the block finds the
+// best dumped score and lists the components within the band of it (all
+// their loads issued at once).  The candidates are then rescored two at a
+// time, four warps each: warp quarter qq forms, for coefficients j = lane
+// and lane + 32, the compensated partial sum of c_j = u_j . z over the terms
+// 16 qq .. 16 qq + 15 (its 64 basis loads independent of each other); the
+// candidate's first warp adds the four partials in order and forms the
+// score.  The best and second best (compensated; the lower component on
+// equal scores) are merged at the end.
 __global__ void __launch_bounds__(32 * RS_WARPS)
 k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
           const int *__restrict__ flag, const int *__restrict__ nflag, int f0, int fcap, int K,
@@ -252,10 +259,12 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
 {
     __shared__ float zh[PD], zl[PD];
     __shared__ df s_zz;
-    __shared__ float s_best;
+    __shared__ float s_red[RS_WARPS];
+    __shared__ int s_cand[RS_KMAX];
+    __shared__ int s_nc;
+    __shared__ df s_part[RS_CPR][RS_QW][PD];
     __shared__ df r_b1[RS_WARPS], r_b2[RS_WARPS];
     __shared__ int r_kb[RS_WARPS];
-    __shared__ float r_out[RS_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = min(*nflag - f0, fcap);
     if (blockIdx.x == 0 && threadIdx.x == 0 && total > 0)
@@ -276,59 +285,91 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
             df zz = df_warp_sum(df_add(df_mul(z0, z0), df_mul(z1, z1)));
             zh[lane] = z0.hi; zl[lane] = z0.lo;
             zh[lane + 32] = z1.hi; zl[lane + 32] = z1.lo;
-            float best = FLT_MAX;
-            for (int k = lane; k < K; k += 32) best = fminf(best, sc[k]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
             if (lane == 0) {
                 s_zz = zz;
-                s_best = best;
+                s_nc = 0;
             }
         }
+        // best dumped score (block-wide)
+        float best = FLT_MAX;
+        for (int k = threadIdx.x; k < K; k += 32 * RS_WARPS) best = fminf(best, sc[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) s_red[w] = best;
         __syncthreads();
+        best = s_red[0];
+#pragma unroll
+        for (int q = 1; q < RS_WARPS; ++q) best = fminf(best, s_red[q]);
         const df zz = s_zz;
-        const float best = s_best;
         const float band = band_abs + band_rel * (zz.hi + zz.lo) * tab.tmax[0];
-        // compensated scores of the components within the band of the best;
-        // candidate number c (in component order) goes to warp c mod RS_WARPS
-        df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
-        int kb = -1, ncand = 0;
+        // the components within the band (any order: the merge is order-free)
         float outside = FLT_MAX;
-        for (int k0 = 0; k0 < K; k0 += 32) {
-            const float sk = k0 + lane < K ? sc[k0 + lane] : FLT_MAX;
-            const bool cand = k0 + lane < K && !(sk > best + band);
-            if (!cand) outside = fminf(outside, sk);
-            unsigned m = __ballot_sync(0xffffffffu, cand);
-            while (m) {
-                const int k = k0 + __ffs(m) - 1;
-                m &= m - 1;
-                if ((ncand++ % RS_WARPS) != w) continue;
-                const int o = roff[k], r = rk_[k];
+        for (int k = threadIdx.x; k < K; k += 32 * RS_WARPS) {
+            const float sk = sc[k];
+            if (!(sk > best + band)) s_cand[atomicAdd(&s_nc, 1)] = k;
+            else outside = fminf(outside, sk);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) outside = fminf(outside, __shfl_xor_sync(0xffffffffu, outside, o));
+        __syncthreads();  // s_red is rewritten below; s_cand / s_nc complete
+        if (lane == 0) s_red[w] = outside;
+        const int nc = s_nc;
+        const int slot = w / RS_QW, qq = w % RS_QW;
+        df b1 = {FLT_MAX, 0.0f}, b2 = {FLT_MAX, 0.0f};
+        int kb = -1;
+        for (int c0 = 0; c0 < nc; c0 += RS_CPR) {
+            const int ci = c0 + slot;
+            const bool mine = ci < nc;  // warp-uniform
+            int k = 0, o = 0, r = 0;
+            if (mine) {
+                k = s_cand[ci];
+                o = roff[k];
+                r = rk_[k];
+                const int j0 = lane, j1 = lane + 32;
+                const float *b0 = B + o + j0, *bl0 = Blo + o + j0;
+                df c0s = {0.0f, 0.0f}, c1s = {0.0f, 0.0f};
+#pragma unroll
+                for (int e = 16 * qq; e < 16 * qq + 16; ++e) {
+                    const size_t off = (size_t)e * Rtot;
+                    const df z = {zh[e], zl[e]};
+                    const df u0 = j0 < r ? df{b0[off], bl0[off]} : df{0.0f, 0.0f};
+                    const df u1 = j1 < r ? df{b0[off + 32], bl0[off + 32]} : df{0.0f, 0.0f};
+                    c0s = df_add(c0s, df_mul(u0, z));
+                    c1s = df_add(c1s, df_mul(u1, z));
+                }
+                s_part[slot][qq][j0] = c0s;
+                s_part[slot][qq][j1] = c1s;
+            }
+            __syncthreads();
+            if (mine && qq == 0) {
                 df part = {0.0f, 0.0f};
-                for (int j = lane; j < r; j += 32) {
-                    df c = {0.0f, 0.0f};
-#pragma unroll 16
-                    for (int e = 0; e < PD; ++e) {
-                        df u = {B[(size_t)e * Rtot + o + j], Blo[(size_t)e * Rtot + o + j]};
-                        c = df_add(c, df_mul(u, {zh[e], zl[e]}));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = lane + 32 * h;
+                    if (j < r) {
+                        df c = s_part[slot][0][j];
+                        c = df_add(c, s_part[slot][1][j]);
+                        c = df_add(c, s_part[slot][2][j]);
+                        c = df_add(c, s_part[slot][3][j]);
+                        df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
+                        part = df_add(part, df_mul(q, df_mul(c, c)));
                     }
-                    df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
-                    part = df_add(part, df_mul(q, df_mul(c, c)));
                 }
                 df sv = df_warp_sum(part);
                 sv = df_add(sv, df_mul({tab.t_hi[k], tab.t_lo[k]}, zz));
                 sv = df_add(sv, {tab.cst_hi[k], tab.cst_lo[k]});
-                if (df_less(sv, b1)) { b2 = b1; b1 = sv; kb = k; }
-                else if (df_less(sv, b2)) { b2 = sv; }
+                if (df_less(sv, b1) || (!df_less(b1, sv) && kb >= 0 && k < kb)) {
+                    b2 = b1; b1 = sv; kb = k;
+                } else if (df_less(sv, b2)) {
+                    b2 = sv;
+                }
             }
+            __syncthreads();  // s_part is rewritten by the next round
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) outside = fminf(outside, __shfl_xor_sync(0xffffffffu, outside, o));
         if (lane == 0) {
             r_b1[w] = b1;
             r_b2[w] = b2;
             r_kb[w] = kb;
-            r_out[w] = outside;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -348,7 +389,8 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
             }
             if (mk >= 0) {  // mk < 0 only if every score was NaN
                 kstar[i] = mk;
-                const float out = r_out[0];
+                float out = s_red[0];
+                for (int q = 1; q < RS_WARPS; ++q) out = fminf(out, s_red[q]);
                 float g2 = (m2.hi == FLT_MAX) ? out - (m1.hi + m1.lo) : (m2.hi - m1.hi) + (m2.lo - m1.lo);
                 gap[i] = fminf(g2, out - (m1.hi + m1.lo));
             }
