@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=list(PREC_NAMES), default="bf16x3")
+    ap.add_argument("--precision", choices=list(PREC_NAMES), default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain-FP32 comparison leg")
     ap.add_argument("--topm", type=int, default=4, help="proposal workload: proposals per patch of the value")

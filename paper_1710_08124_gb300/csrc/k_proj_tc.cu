@@ -290,10 +290,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         for (int j = 0; j < RR; j += 4) {
                             const float v0 = __uint_as_float(r[p * RR + j]), v1 = __uint_as_float(r[p * RR + j + 1]);
                             const float v2 = __uint_as_float(r[p * RR + j + 2]), v3 = __uint_as_float(r[p * RR + j + 3]);
-                            a0 = fmaf(v0, v0, a0);
-                            a1 = fmaf(v1, v1, a1);
-                            a2 = fmaf(v2, v2, a2);
-                            a3 = fmaf(v3, v3, a3);
+                            sq_acc2(a0, a1, v0, v1);
+                            sq_acc2(a2, a3, v2, v3);
                         }
                         float sq = (a0 + a1) + (a2 + a3);
                         const int k = col0 / RR + p;

@@ -172,6 +172,19 @@ static __device__ __forceinline__ void tmem_ld_all(uint32_t taddr, uint32_t (&r)
     }
 }
 
+// (d0, d1) += (a0 * a0, a1 * a1) as one packed FP32x2 FMA (round to nearest,
+// the same result as two fmaf calls)
+static __device__ __forceinline__ void sq_acc2(float &d0, float &d1, float a0, float a1)
+{
+    asm("{\n.reg .b64 x, d;\n"
+        "mov.b64 x, {%2, %3};\n"
+        "mov.b64 d, {%0, %1};\n"
+        "fma.rn.f32x2 d, x, x, d;\n"
+        "mov.b64 {%0, %1}, d;\n}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1));
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
 // with the 128-byte swizzle: rows of 64 16-bit elements (128 B), 8-row
 // groups 1024 B apart (stride byte offset), leading byte offset unused for
