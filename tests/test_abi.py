@@ -89,3 +89,20 @@ def test_proposal_layout_and_validation(L):
 
 def test_attach_tree_rejects_null_handle(L):
     assert L.epll_gmm_attach_tree(None, 0, None, None, None, None, None) == ep.EINVAL
+
+
+def test_header_enums_match_binding():
+    """Every EPLL_* enum constant of include/epll.h has the value the Python
+    binding passes for it (precision forms including EPLL_AUTO, selection
+    variants, rank rules, degradations, samplers, status codes)."""
+    src = open(os.path.join(ROOT, "include", "epll.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for name, v in re.findall(r"\bEPLL_(\w+)\s*=\s*(-?\d+)", body):
+            vals[name] = int(v)
+    assert vals["AUTO"] == 5 and vals["BF16X3"] == 3
+    for name, v in vals.items():
+        py = getattr(ep, name, None)
+        assert py is not None, name
+        assert py == v, (name, py, v)
