@@ -346,6 +346,7 @@ def run_proposal(args):
     stream = torch.cuda.current_stream(dev)
     common = dict(subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=2)
     o_ex = ep.Options(precision=ep.BF16X3, **common)
+    o_auto = ep.Options(precision=ep.AUTO, **common)
     o_32 = ep.Options(precision=ep.FP32, **common)
     o_pr = ep.Options(select=ep.SELECT_PROPOSAL, **common)
 
@@ -367,6 +368,7 @@ def run_proposal(args):
 
     steps = max(5, min(args.steps, 60))
     ex_rate, x_ex, _, _ = timed(o_ex, steps)
+    auto_rate, x_auto, _, _ = timed(o_auto, steps)
     r32, x_32, _, _ = timed(o_32, max(3, steps // 10))
 
     # selection agreement with the exhaustive path along its own trajectory
@@ -448,6 +450,7 @@ def run_proposal(args):
                      "peak_source": peak_note},
         "proposal": {str(m): {k: v for k, v in d.items() if not k.startswith("_")} for m, d in per_m.items()},
         "exhaustive_bf16x3": {"restores_per_s": ex_rate, "psnr_db": psnr(x_ex, x)},
+        "exhaustive_auto": {"restores_per_s": auto_rate, "psnr_db": psnr(x_auto, x)},
         "plain_fp32": {"restores_per_s": r32, "psnr_db": psnr(x_32, x),
                        "speedup_of_value": sel["restores_per_s"] / r32},
         "clocks": clk,
@@ -505,6 +508,7 @@ def run_tree(args):
     stream = torch.cuda.current_stream(dev)
     common = dict(subset=ep.SUBSET_FRACTION, subset_param=FRACTION, seed=2)
     o_ex = ep.Options(precision=ep.BF16X3, **common)
+    o_auto = ep.Options(precision=ep.AUTO, **common)
     o_32 = ep.Options(precision=ep.FP32, **common)
     o_tr = ep.Options(select=ep.SELECT_TREE, **common)
     steps = max(5, min(args.steps, 60))
@@ -533,6 +537,7 @@ def run_tree(args):
         gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r)
         ep.attach_tree(gm, T)
         ex_rate, x_ex, _, _ = timed(gm, o_ex, steps)
+        auto_rate, _, _, _ = timed(gm, o_auto, steps)
         r32, x_32, _, _ = timed(gm, o_32, max(3, steps // 10))
         traj = [yd] + [ep.restore(gm, yd, sigma, BETA[:t], options=o_ex) for t in range(1, len(BETA))]
         agree = nsel = 0
@@ -554,6 +559,7 @@ def run_tree(args):
             sel["tot"] = tot
             ep.profile_enable(gm, False)
         per_rank[r] = {"tree_restores_per_s": rate, "exhaustive_bf16x3_restores_per_s": ex_rate,
+                       "exhaustive_auto_restores_per_s": auto_rate,
                        "plain_fp32_restores_per_s": r32, "speedup_vs_exhaustive": rate / ex_rate,
                        "speedup_vs_plain_fp32": rate / r32, "selection_agreement_with_exhaustive": agree / nsel,
                        "psnr_db": {"tree": psnr(x_tr, x), "exhaustive_bf16x3": psnr(x_ex, x),
