@@ -80,7 +80,32 @@ __device__ __forceinline__ void top2(float s, int k, float &s1, float &s2, int &
 // (score, component) order: the lower component first among equal scores
 __device__ __forceinline__ bool sk_less(float a, int ka, float b, int kb) { return a < b || (a == b && ka < kb); }
 
-// The four lowest (score, component) pairs, ascending; empty slots hold (FLT_MAX, INT_MAX).
+// Running four lowest scores of one thread's row, ascending, for components
+// that arrive in increasing index order: strict comparisons then keep the
+// lower index first among equal scores.  Empty slots hold (FLT_MAX, INT_MAX).
+__device__ __forceinline__ void top4_inc(float s, int k, float (&cs)[4], int (&ck)[4])
+{
+    if (s < cs[3]) {
+        if (s < cs[1]) {
+            cs[3] = cs[2]; ck[3] = ck[2];
+            cs[2] = cs[1]; ck[2] = ck[1];
+            if (s < cs[0]) {
+                cs[1] = cs[0]; ck[1] = ck[0];
+                cs[0] = s; ck[0] = k;
+            } else {
+                cs[1] = s; ck[1] = k;
+            }
+        } else if (s < cs[2]) {
+            cs[3] = cs[2]; ck[3] = ck[2];
+            cs[2] = s; ck[2] = k;
+        } else {
+            cs[3] = s; ck[3] = k;
+        }
+    }
+}
+
+// The four lowest (score, component) pairs, ascending, for pairs in any
+// order (merging the column groups); empty slots hold (FLT_MAX, INT_MAX).
 __device__ __forceinline__ void top4(float s, int k, float (&cs)[4], int (&ck)[4])
 {
     if (sk_less(s, k, cs[3], ck[3])) {
@@ -302,7 +327,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                             if (DUMP) {
                                 if (grow < n) scores[(size_t)grow * K + k] = sc;
                             } else if (CAND) {
-                                top4(sc, k, cs, ck);
+                                top4_inc(sc, k, cs, ck);
                             } else {
                                 top2(sc, k, s1, s2, k1);
                             }
@@ -324,7 +349,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                                     const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                                     const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
                                                      __ldg(&tab.sgn[curk]) * a8;
-                                    if (CAND) top4(sc, curk, cs, ck);
+                                    if (CAND) top4_inc(sc, curk, cs, ck);
                                     else top2(sc, curk, s1, s2, k1);
                                 }
                                 curk = k;
@@ -345,7 +370,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
                 const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
                                  __ldg(&tab.sgn[curk]) * a8;
-                if (CAND) top4(sc, curk, cs, ck);
+                if (CAND) top4_inc(sc, curk, cs, ck);
                 else top2(sc, curk, s1, s2, k1);
             }
             if (CAND) {

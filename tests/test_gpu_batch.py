@@ -43,10 +43,11 @@ def make_jobs():
     return jobs, refs
 
 
-@pytest.mark.parametrize("prec", [ep.BF16X3, ep.FP32])
-def test_batch_modes_match_per_image(prec):
+@pytest.mark.parametrize("prec,r", [(ep.BF16X3, 8), (ep.FP32, 8), (ep.AUTO, 64)])
+def test_batch_modes_match_per_image(prec, r):
+    """AUTO at rank 64 runs the FP16 pass with its candidate step in every lane."""
     g = synth.synthetic_gmm(37)
-    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, 8)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r)
     o = ep.Options(precision=prec, subset=ep.SUBSET_FRACTION, subset_param=1 / 3, seed=4, cg_iters=50)
     jobs, _ = make_jobs()
     singles = [ep.restore(gm, y, s, kind=k, a=a, options=o).cpu().numpy() for y, _, a, k, s in jobs]
