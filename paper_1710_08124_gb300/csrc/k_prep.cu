@@ -53,6 +53,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
 {
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
+    __shared__ float tile[PD][PD + 1];  // one 64-column chunk of the basis, padded rows
     const int k = blockIdx.x, j = threadIdx.x;
     const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
     const double mult = mults.m[blockIdx.y];
@@ -110,18 +111,31 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
         if (j == 0) tab.k8s2[k] = s8 * s8;
     }
     // scaled basis, K-major: B[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
-    // split form stores the BF16 value and the BF16 remainder.
-    for (int jj = 0; jj < rp; ++jj) {
-        const float v = (jj < rk) ? B[(size_t)j * Rtot + o + jj] * sq[jj] : 0.0f;
-        const size_t dst = (size_t)(o + jj) * PD + j;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        if (fmt & 1) tab.B1[dst] = __bfloat16_as_ushort(h);
-        if (fmt & 2) tab.B1[dst] = __half_as_ushort(__float2half_rn(v));
-        if (fmt & 4) {
-            tab.Bs[dst] = __bfloat16_as_ushort(h);
-            tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    // split form stores the BF16 value and the BF16 remainder.  B is e-major,
+    // so 64-column chunks go through shared memory: read along the columns
+    // (coalesced), written along e (coalesced).
+    for (int c0 = 0; c0 < rp; c0 += PD) {
+        __syncthreads();  // the previous chunk's reads of tile are done
+#pragma unroll 8
+        for (int e = 0; e < PD; ++e) {
+            const int jj = c0 + j;
+            tile[e][j] = (jj < rk) ? B[(size_t)e * Rtot + o + jj] : 0.0f;
         }
-        if (fmt & 8) tab.B8[dst] = (uint8_t)__nv_cvt_float_to_fp8(v / s8, __NV_SATFINITE, __NV_E4M3);
+        __syncthreads();
+        const int nc = min(PD, rp - c0);
+        for (int jl = 0; jl < nc; ++jl) {
+            const int jj = c0 + jl;
+            const float v = (jj < rk) ? tile[j][jl] * sq[jj] : 0.0f;
+            const size_t dst = (size_t)(o + jj) * PD + j;
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            if (fmt & 1) tab.B1[dst] = __bfloat16_as_ushort(h);
+            if (fmt & 2) tab.B1[dst] = __half_as_ushort(__float2half_rn(v));
+            if (fmt & 4) {
+                tab.Bs[dst] = __bfloat16_as_ushort(h);
+                tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+            }
+            if (fmt & 8) tab.B8[dst] = (uint8_t)__nv_cvt_float_to_fp8(v / s8, __NV_SATFINITE, __NV_E4M3);
+        }
     }
 }
 
