@@ -101,7 +101,7 @@ typedef struct {
                            score gap is below tie_gap + rho * |z|^2 * max_kj 1/nu_kj is
                            rescored in compensated FP32 (rho is the relative error bound of
                            the precision: 1e-5 FP32, 1.5e-3 FP16, 1e-2 BF16, 4e-5 BF16X3,
-                           1e-1 FP8);
+                           1e-1 FP8; AUTO that of the form it stands for);
                            < 0 selects the default 1e-3 */
     int subset;         /* EPLL_SUBSET_* */
     double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */
