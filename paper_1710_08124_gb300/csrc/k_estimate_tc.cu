@@ -19,13 +19,14 @@
 
 namespace epll {
 
-constexpr int ET_T = 128;
+constexpr int ET_T = 128;           // patches per work item (the MMA's M)
+constexpr int ET_THREADS = 256;     // two warps per TMEM lane quarter, each taking 32 of the 64 columns
 constexpr int ET_TILE = ET_T * 128;  // 16 KB: [128 rows][64] BF16
 constexpr int ET_B = 64 * 128;       // 8 KB: [64 rows][64] BF16
 // A hi/lo (overwritten by C' hi/lo), B1 hi/lo, B2 hi/lo, then barriers and per-row scalars
 constexpr int ET_SMEM = 1024 + 2 * ET_TILE + 4 * ET_B + 64 + 3 * ET_T * 4 + 64 * 4;
 
-__global__ void __launch_bounds__(ET_T)
+__global__ void __launch_bounds__(ET_THREADS)
 k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__ CUtensorMap mapU1lo,
               const __grid_constant__ CUtensorMap mapU2, const __grid_constant__ CUtensorMap mapU2lo,
               const int *__restrict__ anchors, const uint4 *__restrict__ Zhi_g, const uint4 *__restrict__ Zlo_g,
@@ -81,12 +82,13 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
     __syncthreads();
     if (threadIdx.x < 64) s_gw[threadIdx.x] = threadIdx.x < r ? tab.gw[o + threadIdx.x] : 0.0f;
     // the patches' split operand rows: eight threads per 128-byte row,
-    // 16-byte chunks to their swizzled place (all sixteen loads in flight)
+    // 16-byte chunks to their swizzled place (all eight loads in flight)
     {
-        uint4 h[8], l[8];
+        constexpr int NU = ET_T * 8 / ET_THREADS;
+        uint4 h[NU], l[NU];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int q = threadIdx.x + u * ET_T, t = q >> 3, c = q & 7;
+        for (int u = 0; u < NU; ++u) {
+            const int q = threadIdx.x + u * ET_THREADS, t = q >> 3, c = q & 7;
             h[u] = l[u] = make_uint4(0, 0, 0, 0);
             if (t < cnt_p) {
                 const size_t src = (size_t)s_patch[t] * 8 + c;
@@ -95,8 +97,8 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
             }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int q = threadIdx.x + u * ET_T, t = q >> 3, c = q & 7;
+        for (int u = 0; u < NU; ++u) {
+            const int q = threadIdx.x + u * ET_THREADS, t = q >> 3, c = q & 7;
             const uint32_t o2 = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
             *reinterpret_cast<uint4 *>(Ahi + o2) = h[u];
             *reinterpret_cast<uint4 *>(Alo + o2) = l[u];
@@ -123,20 +125,23 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
     // tcgen05.ld is warp-collective: every lane takes the same branch
     bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), 0, abort_flag));
     tc_fence_after();
-    const int t = 32 * warp + lane;
-    const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
+    // warp w: TMEM lane quarter w % 4 (rows 32 (w % 4) ..), columns 32 (w / 4) .. + 31
+    const int qd = warp & 3, hh = warp >> 2;
+    const int t = 32 * qd + lane;
+    const uint32_t tl = tbase + ((uint32_t)(32 * qd) << 16);
     if (ok) {
         // c'_j = gw_kj c_j (zero beyond the rank), split into the A operand of GEMM 2
-        uint32_t c[64];
-        tmem_ld_all<64>(tl, c);
+        uint32_t c[32];
+        tmem_ld_all<32>(tl + (uint32_t)(32 * hh), c);
 #pragma unroll
-        for (int j8 = 0; j8 < 8; ++j8) {
+        for (int jl = 0; jl < 4; ++jl) {
+            const int j8 = 4 * hh + jl;
             uint32_t ph[4], pl[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int j = 8 * j8 + 2 * q;
-                const float v0 = s_gw[j] * __uint_as_float(c[j]);
-                const float v1 = s_gw[j + 1] * __uint_as_float(c[j + 1]);
+                const int j = 8 * j8 + 2 * q, jc = 8 * jl + 2 * q;
+                const float v0 = s_gw[j] * __uint_as_float(c[jc]);
+                const float v1 = s_gw[j + 1] * __uint_as_float(c[jc + 1]);
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
                 ph[q] = *reinterpret_cast<const uint32_t *>(&h);
@@ -165,23 +170,24 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
     __syncwarp();
     ok = __all_sync(0xffffffffu, ok && mbar_wait(smem_u32(&bars[2]), 0, abort_flag));
     tc_fence_after();
-    uint32_t v[64];
-    if (ok) tmem_ld_all<64>(tl + 64, v);  // whole warp, before the per-row test
+    uint32_t v[32];
+    if (ok) tmem_ld_all<32>(tl + 64 + (uint32_t)(32 * hh), v);  // whole warp, before the per-row test
     if (ok && t < cnt_p) {
-        // zhat = Ubar c' + gamma_P z + mu, z = hi + lo of this row
+        // zhat = Ubar c' + gamma_P z + mu, z = hi + lo of this row (elements 32 hh .. 32 hh + 31)
         const float gp = tab.gp[k], mu = s_mu[t];
         float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)s_anchor[t] * PD);
         const size_t zr = (size_t)s_patch[t] * 8;
-        uint4 zhs[8], zls[8];
+        uint4 zhs[4], zls[4];
 #pragma unroll
-        for (int e8 = 0; e8 < 8; ++e8) {
-            zhs[e8] = Zhi_g[zr + e8];
-            zls[e8] = Zlo_g[zr + e8];
+        for (int el = 0; el < 4; ++el) {
+            zhs[el] = Zhi_g[zr + 4 * hh + el];
+            zls[el] = Zlo_g[zr + 4 * hh + el];
         }
 #pragma unroll
-        for (int e8 = 0; e8 < 8; ++e8) {
-            const uint4 zh = zhs[e8];
-            const uint4 zl = zls[e8];
+        for (int el = 0; el < 4; ++el) {
+            const int e8 = 4 * hh + el;
+            const uint4 zh = zhs[el];
+            const uint4 zl = zls[el];
             const uint32_t hw[4] = {zh.x, zh.y, zh.z, zh.w}, lw[4] = {zl.x, zl.y, zl.z, zl.w};
             float out[8];
 #pragma unroll
@@ -189,8 +195,8 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
                 const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&hw[q]);
                 const __nv_bfloat162 l = *reinterpret_cast<const __nv_bfloat162 *>(&lw[q]);
                 const float z0 = __low2float(h) + __low2float(l), z1 = __high2float(h) + __high2float(l);
-                out[2 * q] = fmaf(gp, z0, __uint_as_float(v[8 * e8 + 2 * q])) + mu;
-                out[2 * q + 1] = fmaf(gp, z1, __uint_as_float(v[8 * e8 + 2 * q + 1])) + mu;
+                out[2 * q] = fmaf(gp, z0, __uint_as_float(v[8 * el + 2 * q])) + mu;
+                out[2 * q + 1] = fmaf(gp, z1, __uint_as_float(v[8 * el + 2 * q + 1])) + mu;
             }
             dst[2 * e8] = make_float4(out[0], out[1], out[2], out[3]);
             dst[2 * e8 + 1] = make_float4(out[4], out[5], out[6], out[7]);
@@ -227,7 +233,7 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
     const int max_items = (n + ET_T - 1) / ET_T + g->K;
     const uint4 *zh = reinterpret_cast<const uint4 *>(ws.Zb);
     const uint4 *zl = reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD);
-    k_estimate_tc<<<max_items, ET_T, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, anchors, zh, zl, ws.mu, ws.perm, ws.items,
+    k_estimate_tc<<<max_items, ET_THREADS, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, anchors, zh, zl, ws.mu, ws.perm, ws.items,
                                                     g->d_roff, g->d_r, g->tab, ws.zrow, cnt(g, CNT_ERR));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
