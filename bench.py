@@ -64,11 +64,13 @@ def parse():
     ap.add_argument("--pmin", type=float, default=0.0, help="proposal workload: softmax mass below which a "
                     "patch is scored exhaustively")
     ap.add_argument("--train-steps", type=int, default=3000, help="proposal workload: AdamW steps")
-    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal", "tree"], default="fepll",
+    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal", "tree", "subsets"], default="fepll",
                     help="fepll: the 512x512 FEPLL denoising workload (default line); proposal: the learned "
                          "top-m proposal at 512x512, sigma 25/255, K=200, r=64; tree: the balanced search "
                          "tree at 512x512, sigma 25/255, K=200, r in {64,8}; uneven: 64 images of "
-                         "uneven size, noise and degradation in one captured batch vs per-image launches")
+                         "uneven size, noise and degradation in one captured batch vs per-image launches; "
+                         "subsets: the fepll images and models under each patch subset (regular grid s=3, "
+                         "jittered grid s=6, random 1/3, all patches)")
     return ap.parse_args()
 
 
@@ -229,6 +231,73 @@ def _uneven_problem(args):
         return x, y.astype(np.float32), a.astype(np.float32)
     x, y = synth.denoise_problem(100 + i, side, sigma)
     return x, y.astype(np.float32), None
+
+
+def run_subsets(args):
+    """The default workload's images and models (512x512, sigma {10,25,50}/255,
+    K=200, r in {64,8}, AUTO precision, 5 iterations) under each patch subset:
+    the regular grid of spacing 3 (the paper's 9x setting; the line's value),
+    the jittered grid of spacing 6 (its 36x setting), the random 1/3 subset
+    and every patch.  Device-timed like the default line."""
+    import torch
+
+    import paper_1710_08124_gb300 as ep
+
+    ep.build()
+    dev = torch.device("cuda", 0)
+    g = synth.synthetic_gmm(K)
+    models = {r: ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r) for r in RANKS}
+    probs = problems(0)
+    ys = [torch.as_tensor(y, device=dev) for _, y in probs]
+    outs = [torch.empty_like(y) for y in ys]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    kinds = [("regular_s3", ep.SUBSET_REGULAR, 3.0), ("jitter_s6", ep.SUBSET_JITTER, 6.0),
+             ("random_1/3", ep.SUBSET_FRACTION, FRACTION), ("all", ep.SUBSET_ALL, 0.0)]
+    steps = max(3, min(args.steps, 40))
+    res = {}
+    for name, kind, param in kinds:
+        o = ep.Options(precision=PREC_NAMES[args.precision], subset=kind, subset_param=param, seed=7)
+        for _ in range(max(args.warmup, 3)):
+            for r in RANKS:
+                for si in range(len(SIGMAS)):
+                    ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=o, out=outs[si])
+        for m in models.values():
+            ep.last_counters(m)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for r in RANKS:
+                for si in range(len(SIGMAS)):
+                    ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=o, out=outs[si])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        evals, _, _ = ep.last_counters(models[RANKS[-1]])
+        pq = []
+        for r in RANKS:
+            for si in range(len(SIGMAS)):
+                pq.append(psnr(ep.restore(models[r], ys[si], SIGMAS[si], BETA, options=o).cpu().numpy(),
+                               probs[si][0]))
+        res[name] = {"restores_per_s": steps * RESTORES_PER_STEP / tot,
+                     "patches_per_iteration": evals // len(BETA), "mean_psnr_db": float(np.mean(pq))}
+    main = res["regular_s3"]
+    line = {
+        "metric": "512x512 restores/s with regular patch subsampling s=3 (FEPLL denoise, K=200, r in {64,8})",
+        "value": main["restores_per_s"], "unit": "restores/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": RESTORES_PER_STEP / main["restores_per_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "patch subsets on the default images and models: " + WORKLOAD,
+                   "precision": args.precision,
+                   "l2": "256 MB buffer written before each step, outside the timed events"},
+        "by_subset": res,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_uneven(args):
@@ -651,6 +720,8 @@ def main():
         return run_proposal(args) if rank == 0 else 0
     if args.workload == "tree":
         return run_tree(args) if rank == 0 else 0
+    if args.workload == "subsets":
+        return run_subsets(args) if rank == 0 else 0
 
     import torch
 

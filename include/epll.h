@@ -47,8 +47,11 @@ typedef enum {
 enum { EPLL_RANK_FIXED = 0, EPLL_RANK_RHO = 1 };
 /* degradation operator A of y = A x + w (Sec. 2) */
 enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2 };
-/* patch subset (Sec. "Speed-up via the restriction to a random subset of patches") */
-enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2 };
+/* patch subset (Sec. "Speed-up via the restriction to a random subset of patches"):
+ * ALL every pixel's patch; FRACTION ceil(f N) distinct anchors redrawn every
+ * iteration; JITTER the jittered grid of Eq. 20 (spacing s); REGULAR the
+ * regular grid of spacing s, anchors (s n, s m), the same at every iteration */
+enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2, EPLL_SUBSET_REGULAR = 3 };
 /* arithmetic of the projection that drives the Gaussian selection:
  * FP32   SIMT FP32 dot products;
  * BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation;
@@ -104,7 +107,7 @@ typedef struct {
                            1e-1 FP8; AUTO that of the form it stands for);
                            < 0 selects the default 1e-3 */
     int subset;         /* EPLL_SUBSET_* */
-    double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER: grid spacing s in 1..8 */
+    double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER / REGULAR: grid spacing s in 1..8 */
     uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
     int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
     int select;         /* EPLL_SELECT_EXHAUSTIVE, EPLL_SELECT_PROPOSAL or EPLL_SELECT_TREE */

@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 P = 64
-FULL, FRACTION, JITTER = 0, 1, 2
+FULL, FRACTION, JITTER, REGULAR = 0, 1, 2, 3
 DENOISE, PIXELWISE, CONV = 0, 1, 2
 
 
@@ -56,6 +56,7 @@ def _L():
             lib.or_sample_full.argtypes = [i, i, vp]
             lib.or_sample_fraction.argtypes = [i, i, d, u64, i, vp]
             lib.or_sample_jitter.argtypes = [i, i, i, u64, i, vp]
+            lib.or_sample_regular.argtypes = [i, i, i, vp]
             lib.or_scores.argtypes = [i, vp, vp, vp, vp, vp, d, vp, i, i, vp, i, vp]
             lib.or_scores.restype = None
             lib.or_patch_step.argtypes = [i, vp, vp, vp, vp, vp, d, vp, i, i, vp, i, vp,
@@ -118,8 +119,12 @@ def sample(H: int, W: int, kind: int = FULL, param: float = 0.0, seed: int = 0, 
         n = L.or_sample_full(H, W, _p(out))
     elif kind == FRACTION:
         n = L.or_sample_fraction(H, W, float(param), seed, t, _p(out))
-    else:
+    elif kind == JITTER:
         n = L.or_sample_jitter(H, W, int(param), seed, t, _p(out))
+    elif kind == REGULAR:
+        n = L.or_sample_regular(H, W, int(param), _p(out))
+    else:
+        raise ValueError("unknown sampler kind")
     if n < 0:
         raise ValueError("sampler failed")
     return out[:n].copy()

@@ -184,6 +184,20 @@ int or_sample_jitter(int H, int W, int s, uint64_t seed, int t, int *anchors)
     return g;
 }
 
+/* Regular patch subsampling (Sec. "Speed-up via the restriction to a random
+ * subset of patches"): the grid of spacing s in both directions, points
+ * (s n, s m) for n = 0..ceil(H/s)-1, m = 0..ceil(W/s)-1, the same at every
+ * iteration (origin 0: a reading, the paper draws the grid from an arbitrary
+ * (i0, j0)).  Raster order; no point wraps, so there are no duplicates. */
+int or_sample_regular(int H, int W, int s, int *anchors)
+{
+    if (s < 1 || s > PSIDE) return -1;
+    int g = 0;
+    for (int i = 0; i < H; i += s)
+        for (int j = 0; j < W; j += s) anchors[g++] = i * W + j;
+    return g;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-beta quantities (Eqs. 8 and 14): nu_kj = S_kj + 1/beta for j < r_k,   */
 /* nu_kP = lambda_k + 1/beta, gamma = S / nu, iota_k = -2 log w_k.           */
@@ -561,7 +575,8 @@ void or_init_cg(const double *a, const double *y, int H, int W, double c, int it
 /* Whole restoration: Algorithm 1 iterated T times with                       */
 /* beta_t = lambda * beta_mult[t] / sigma^2 (Sec. "Parameter settings").      */
 /* deg_kind 0 denoise, 1 pixelwise a, 2 periodic blur.  subset 0 full set,    */
-/* 1 random fraction subset_param, 2 jitter with spacing (int)subset_param.   */
+/* 1 random fraction subset_param, 2 jitter with spacing (int)subset_param,  */
+/* 3 regular grid with spacing (int)subset_param.                            */
 /* ks_out / gap_out (nullable) receive each iteration's selections, at       */
 /* [t * H * W + i] for the i-th sampled patch; nsel_out[t] their count.       */
 /* ------------------------------------------------------------------------ */
@@ -588,7 +603,8 @@ int or_restore(int K, const double *w, const double *U, const double *S, const i
         int n;
         if (subset == 0) n = or_sample_full(H, W, anchors);
         else if (subset == 1) n = or_sample_fraction(H, W, subset_param, seed, t, anchors);
-        else n = or_sample_jitter(H, W, (int)subset_param, seed, t, anchors);
+        else if (subset == 2) n = or_sample_jitter(H, W, (int)subset_param, seed, t, anchors);
+        else n = or_sample_regular(H, W, (int)subset_param, anchors);
         if (n < 0) { free(anchors); free(xt); return -1; }
         if (nsel_out) nsel_out[t] = n;
         if (or_patch_step(K, w, U, S, r, lam, beta, x, H, W, anchors, n, NULL, xt,

@@ -194,13 +194,13 @@ static epll_status check_options(const epll_options &o, int H, int W)
     if (o.subset == EPLL_SUBSET_FRACTION) {
         if (!(o.subset_param > 0.0 && o.subset_param <= 1.0))
             return fail(EPLL_EINVAL, "options.subset_param: fraction must be in (0, 1]");
-    } else if (o.subset == EPLL_SUBSET_JITTER) {
+    } else if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
         int s = (int)o.subset_param;
         if ((double)s != o.subset_param || s < 1 || s > PS)
-            return fail(EPLL_EINVAL, "options.subset_param: jitter spacing must be an integer in 1..8");
+            return fail(EPLL_EINVAL, "options.subset_param: grid spacing must be an integer in 1..8");
         (void)H; (void)W;
     } else if (o.subset != EPLL_SUBSET_ALL) {
-        return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION or _JITTER");
+        return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION, _JITTER or _REGULAR");
     }
     if (o.cg_iters < 0 || o.cg_iters > 100000) return fail(EPLL_EINVAL, "options.cg_iters out of range");
     if (o.select != EPLL_SELECT_EXHAUSTIVE && o.select != EPLL_SELECT_PROPOSAL && o.select != EPLL_SELECT_TREE)

@@ -180,7 +180,9 @@ __device__ __forceinline__ int uniform_int(uint64_t u, int m)
 // ---------------------------------------------------------------- jitter
 // Jittered grid of Eq. 20: spacing s, global shift from draws 0/1, per-point
 // offsets in [-J, J] from draws 2+2g / 3+2g; raster order of grid points.
-__global__ void k_jitter(int H, int W, int s, uint64_t seed, int t0, int ni, int nj,
+// regular != 0: the regular grid of the same spacing (Sec. "Speed-up via the
+// restriction to a random subset of patches"): no shift, no offsets.
+__global__ void k_jitter(int H, int W, int s, uint64_t seed, int t0, int ni, int nj, int regular,
                          int *__restrict__ anchors_all, unsigned *__restrict__ mult_all)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,11 +191,11 @@ __global__ void k_jitter(int H, int W, int s, uint64_t seed, int t0, int ni, int
     int *anchors = anchors_all + (size_t)blockIdx.y * H * W;
     unsigned *mult = mult_all + (size_t)blockIdx.y * H * W;
     const uint64_t st = stream_state(seed, (uint64_t)t);
-    const int J = (PS - s) / 2;
-    const int gi = uniform_int(draw(st, 0), s), gj = uniform_int(draw(st, 1), s);
+    const int J = regular ? 0 : (PS - s) / 2;
+    const int gi = regular ? 0 : uniform_int(draw(st, 0), s), gj = regular ? 0 : uniform_int(draw(st, 1), s);
     const int n = g / nj, m = g % nj;
-    const int di = uniform_int(draw(st, 2 + 2 * (uint64_t)g), 2 * J + 1) - J;
-    const int dj = uniform_int(draw(st, 3 + 2 * (uint64_t)g), 2 * J + 1) - J;
+    const int di = regular ? 0 : uniform_int(draw(st, 2 + 2 * (uint64_t)g), 2 * J + 1) - J;
+    const int dj = regular ? 0 : uniform_int(draw(st, 3 + 2 * (uint64_t)g), 2 * J + 1) - J;
     const int i = ((gi + s * n + di) % H + H) % H;
     const int j = ((gj + s * m + dj) % W + W) % W;
     const int a = i * W + j;
@@ -382,7 +384,7 @@ int sample_count(int H, int W, const epll_options &o)
         int M = (int)ceil(o.subset_param * (double)N);
         return M > N ? N : (M < 1 ? 1 : M);
     }
-    if (o.subset == EPLL_SUBSET_JITTER) {
+    if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
         int s = (int)o.subset_param;
         return ((H + s - 1) / s) * ((W + s - 1) / s);
     }
@@ -398,11 +400,12 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     const int N = H * W;
     *n = sample_count(H, W, o);
     if (o.subset == EPLL_SUBSET_ALL) return EPLL_OK;
-    if (o.subset == EPLL_SUBSET_JITTER) {
+    if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
         const int s = (int)o.subset_param;
         EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N * nb, st));
         const int ni = (H + s - 1) / s, nj = (W + s - 1) / s;
-        k_jitter<<<dim3((ni * nj + 255) / 256, nb), 256, 0, st>>>(H, W, s, o.seed, t0, ni, nj, anchors, mult);
+        k_jitter<<<dim3((ni * nj + 255) / 256, nb), 256, 0, st>>>(
+            H, W, s, o.seed, t0, ni, nj, o.subset == EPLL_SUBSET_REGULAR ? 1 : 0, anchors, mult);
         EPLL_LAUNCHED(g);
         return EPLL_OK;
     }

@@ -89,10 +89,10 @@ extern "C" epll_status epll_sample_noalloc(int H, int W, const epll_options *opt
             set_error("epll_sample_noalloc: fraction must be in (0, 1]");
             return EPLL_EINVAL;
         }
-    } else if (o.subset == EPLL_SUBSET_JITTER) {
+    } else if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
         const int s = (int)o.subset_param;
         if ((double)s != o.subset_param || s < 1 || s > PS) {
-            set_error("epll_sample_noalloc: jitter spacing must be an integer in 1..8");
+            set_error("epll_sample_noalloc: grid spacing must be an integer in 1..8");
             return EPLL_EINVAL;
         }
     } else if (o.subset != EPLL_SUBSET_ALL) {

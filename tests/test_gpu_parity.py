@@ -52,7 +52,8 @@ def agree(ks_gpu, ks_or, gap_or):
 def test_sampler_bit_identical(H, W):
     for t in range(3):
         for kind, param in [(ep.SUBSET_FRACTION, 1 / 3), (ep.SUBSET_FRACTION, 0.05),
-                            (ep.SUBSET_JITTER, 6), (ep.SUBSET_JITTER, 3)]:
+                            (ep.SUBSET_JITTER, 6), (ep.SUBSET_JITTER, 3),
+                            (ep.SUBSET_REGULAR, 3), (ep.SUBSET_REGULAR, 8)]:
             o = ep.Options(subset=kind, subset_param=param, seed=1234 + t)
             g = ep.sample(H, W, o, t).cpu().numpy()
             r = oracle.sample(H, W, kind, param, seed=1234 + t, t=t)
@@ -149,6 +150,19 @@ def test_restore_subset_jitter():
     o = ep.Options(subset=ep.SUBSET_JITTER, subset_param=6, seed=11)
     xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, subset=oracle.JITTER,
                         subset_param=6, seed=11)
+    xg = ep.restore(gm, dev(y), sigma, options=o).cpu().numpy()
+    assert abs(psnr(xg, x) - psnr(xo, x)) <= 0.05
+    assert np.abs(xg - xo).max() <= 1e-4
+
+
+def test_restore_subset_regular():
+    """Regular patch subsampling with spacing 3 (the paper's 9x setting)."""
+    gm, om = models(30, "fixed", 8)
+    sigma = 25 / 255
+    x, y = synth.denoise_problem(3, 72, sigma, W=56)
+    o = ep.Options(subset=ep.SUBSET_REGULAR, subset_param=3)
+    xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, subset=oracle.REGULAR,
+                        subset_param=3)
     xg = ep.restore(gm, dev(y), sigma, options=o).cpu().numpy()
     assert abs(psnr(xg, x) - psnr(xo, x)) <= 0.05
     assert np.abs(xg - xo).max() <= 1e-4

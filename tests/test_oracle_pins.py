@@ -393,6 +393,34 @@ def test_jitter_covers_every_pixel(H, W, s):
             assert min(di, H - di) <= J and min(dj, W - dj) <= J
 
 
+@pytest.mark.parametrize("H,W,s", [(64, 64, 8), (50, 37, 3), (17, 23, 5), (8, 8, 8), (20, 13, 2)])
+def test_regular_grid_pins(H, W, s):
+    """Regular patch subsampling (Sec. on the random subset of patches): |I| =
+    N / s^2 when s divides both sides (ceil otherwise), every pixel covered for
+    s <= 8, the same list at every iteration; at s = 8 it is the jittered grid
+    (J = 0 there) without its random shift; at s = 1 it is the full set."""
+    an = oracle.sample(H, W, oracle.REGULAR, s)
+    assert an.shape[0] == -(-H // s) * -(-W // s)
+    if H % s == 0 and W % s == 0:
+        assert an.shape[0] * s * s == H * W
+    assert len(set(an.tolist())) == an.shape[0]
+    cov = np.zeros((H, W), int)
+    for a in an:
+        i, j = divmod(int(a), W)
+        cov[np.ix_((np.arange(8) + i) % H, (np.arange(8) + j) % W)] += 1
+    assert cov.min() >= 1
+    assert np.array_equal(an, oracle.sample(H, W, oracle.REGULAR, s, seed=9, t=3))
+    if s == 8:
+        for t in range(3):
+            jit = oracle.sample(H, W, oracle.JITTER, 8, seed=77, t=t)
+            gi = ((oracle.rng_u64(77, t, 0) >> 32) * 8) >> 32
+            gj = ((oracle.rng_u64(77, t, 1) >> 32) * 8) >> 32
+            ji, jj = np.divmod(jit, W)
+            unshifted = ((ji - gi) % H) * W + (jj - gj) % W
+            assert np.array_equal(unshifted, an)
+    assert np.array_equal(oracle.sample(H, W, oracle.REGULAR, 1), oracle.sample(H, W, oracle.FULL))
+
+
 def test_jitter_expected_coverage_is_uniform():
     """The random global shift makes every pixel's expected coverage equal
     (Sec. on the random subset of patches)."""

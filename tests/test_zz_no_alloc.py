@@ -32,6 +32,7 @@ CASES = [
     (512, 512, ep.SUBSET_FRACTION, 1 / 3),
     (50, 37, ep.SUBSET_JITTER, 6),
     (1024, 1024, ep.SUBSET_JITTER, 3),
+    (50, 37, ep.SUBSET_REGULAR, 4),
     (33, 40, ep.SUBSET_ALL, 0.0),
 ]
 
