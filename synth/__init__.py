@@ -221,3 +221,25 @@ def deblur_problem(i: int, H: int, sigma: float, W: int | None = None,
     x = image(i, H, W)
     k = gaussian_kernel(size, sigma_b)
     return x, k, blur_periodic(x, k) + noise(i, H, W, sigma)
+
+
+def clean_patches(n: int, seed: int = 0, side: int = 256) -> np.ndarray:
+    """n DC-free 8x8 patches (rows of 64) at random positions (periodic wrap)
+    of dead-leaves images side x side, the i-th image drawn with seed
+    5000 + 1000 seed + i; training data for an EM-fitted prior."""
+    rng = np.random.default_rng(seed)
+    per_image = side * side // 4
+    out = np.empty((n, P))
+    got, i = 0, 0
+    while got < n:
+        img = dead_leaves(side, side, 5000 + seed * 1000 + i)
+        m = min(per_image, n - got)
+        a = rng.integers(0, side * side, m)
+        r, c = np.divmod(a, side)
+        rows = (r[:, None] + np.arange(8)[None, :]) % side
+        cols = (c[:, None] + np.arange(8)[None, :]) % side
+        p = img[rows[:, :, None], cols[:, None, :]].reshape(m, P)
+        out[got:got + m] = p - p.mean(axis=1, keepdims=True)
+        got += m
+        i += 1
+    return out
