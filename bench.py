@@ -860,6 +860,8 @@ def main():
                    "l2": "256 MB buffer written before each step, outside the timed events",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "mpatch_evals_per_s": restores * len(BETA) * M_PATCH / dev_s / 1e6,
+        # component scorings: every patch evaluation scores all K components
+        "mscores_per_s": restores * len(BETA) * M_PATCH * K / dev_s / 1e6,
         "e2e": {"value": job_rate(n_e2e * RESTORES_PER_STEP, ws, e2e_s), "unit": "restores/s",
                 "h2d_bytes_per_step": RESTORES_PER_STEP * N_PIX * 4,
                 "d2h_bytes_per_step": RESTORES_PER_STEP * N_PIX * 4},
