@@ -16,8 +16,10 @@ M step:
     Sigma_k = sum_i gamma_ik z_i z_i^T / N_k + eps I
 eps (a small multiple of the data's mean variance) keeps every covariance
 positive definite: DC-free patches leave the constant direction empty, and a
-component may hold few patches.  A component whose weight collapses is
-re-seeded from the patch the model explains worst.
+component may hold few patches.  A component whose weight falls below
+min_weight is re-seeded with the covariance of a share of the patches the
+model explains worst (a heuristic step outside EM; min_weight = 0 turns it
+off).
 """
 from __future__ import annotations
 
