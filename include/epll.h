@@ -178,7 +178,9 @@ epll_status epll_gmm_ranks(const epll_gmm *g, int *ranks, double *lambdas);
  *   y, x_out     device [H][W]; x_out may alias y
  *   H, W         8 <= H, W and H*W <= 2^26
  *   sigma        noise standard deviation in image units, > 0
- *   beta_mult    host [T], > 0 (the paper uses {1, 4, 8, 16, 32}); T in 1..64
+ *   beta_mult    host [T], > 0 (the paper uses {1, 4, 8, 16, 32}); T in 0..64;
+ *                T = 0 runs only the initialisation and returns x0 (beta_mult
+ *                may then be NULL)
  *   opt          NULL = defaults
  * Asynchronous on `stream`.  Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA.
  */
@@ -249,6 +251,22 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
                             int *kstar, float *gap, const int *forced_k, int *n_out,
                             void *stream);
 
+/*
+ * The image estimation step alone (last step of Algorithm 1, Eq. 6 with the
+ * constant patch overlap of periodic boundaries), for testing: given the
+ * reprojected patch average xtilde,
+ *   x = (A^T A + bs I)^-1 (A^T y + bs xtilde),  bs = lambda * beta_mult,
+ * with lambda computed from the degradation as in epll_restore.  Pixelwise A
+ * (and denoising, a = 1): x = (a y + bs xtilde) / (a^2 + bs) per pixel;
+ * CONV_PERIODIC: the same division frequency by frequency (cuFFT).
+ *   y, xtilde, x_out  device [H][W]; x_out must not alias y or xtilde
+ *   beta_mult         > 0 (the iteration's multiplier m_t)
+ * Asynchronous on `stream`.  Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA.
+ */
+epll_status epll_image_update(epll_gmm *g, const float *y, const float *xtilde, int H, int W,
+                              const epll_degradation *deg, float sigma, double beta_mult, float *x_out,
+                              void *stream);
+
 /* Patch sampling alone (for tests): writes the anchors of iteration t to the
  * device buffer `anchors` (capacity H*W) and their count to *n_out (host);
  * synchronises `stream`. */
@@ -268,9 +286,11 @@ epll_status epll_sample(int H, int W, const epll_options *opt, int t, int *ancho
  * 2^20 pixels (larger ones return EPLL_EINVAL).  Every call shares the array
  * and the work it enqueues clears what must start at zero, so calls whose
  * device work overlaps (different streams, no ordering between them) race.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  Errors: EPLL_EINVAL, EPLL_ECUDA.
+ * Every call looks up the array's device address (cudaGetSymbolAddress) on
+ * the current device; the first call on a device may load the library's
+ * device code there, so make it before any stream capture.  Arguments are
+ * validated as for epll_sample, plus the 2^20-pixel limit.
+ * Errors: EPLL_EINVAL, EPLL_ECUDA.
  */
 epll_status epll_sample_noalloc(int H, int W, const epll_options *opt, int t, int *anchors,
                                 int *n_out, void *stream);

@@ -162,3 +162,34 @@ def topm(logits, m: int):
     e = np.exp(logits - mx)
     mass = np.take_along_axis(e, order, axis=1).sum(axis=1) / e.sum(axis=1)
     return order, mass
+
+
+# Exponential decay rates and epsilon of the optimiser (Kingma & Ba's defaults).
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+# Parameter blocks whose weight decays (the matrices; biases and wb do not).
+DECAYED = ("W1", "W2", "W3")
+
+
+def adamw_step(p, g, m, v, step: int, lr: float, wd: float):
+    """One AdamW step (Loshchilov & Hutter, "Decoupled weight decay
+    regularization", ICLR 2019, Algorithm 2 with the schedule multiplier
+    eta_t = lr and alpha = 1): first and second moment estimates
+    m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, their bias corrections
+    m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t), and the update
+    theta <- theta - lr (m_hat / (sqrt(v_hat) + eps) + wd theta), where the
+    decay term appears only for the weight matrices and is not part of the
+    gradient that the moments see.  p, g, m, v are dicts of FP64 arrays; returns
+    the new (p, m, v); `step` is t >= 1, the index of this step."""
+    c1 = 1.0 - ADAM_B1 ** step
+    c2 = 1.0 - ADAM_B2 ** step
+    p2, m2, v2 = {}, {}, {}
+    for name in p:
+        mk = ADAM_B1 * m[name] + (1.0 - ADAM_B1) * g[name]
+        vk = ADAM_B2 * v[name] + (1.0 - ADAM_B2) * g[name] * g[name]
+        upd = (mk / c1) / (np.sqrt(vk / c2) + ADAM_EPS)
+        if name in DECAYED:
+            upd = upd + wd * p[name]
+        p2[name] = p[name] - lr * upd
+        m2[name] = mk
+        v2[name] = vk
+    return p2, m2, v2

@@ -93,6 +93,7 @@ def lib():
         L.epll_restore.argtypes = [vp, vp, i, i, C.POINTER(_Degradation), C.c_float, vp, i,
                                    C.POINTER(_Options), vp, vp]
         L.epll_restore_host.argtypes = L.epll_restore.argtypes
+        L.epll_image_update.argtypes = [vp, vp, vp, i, i, C.POINTER(_Degradation), C.c_float, d, vp, vp]
         L.epll_patch_step.argtypes = [vp, vp, i, i, d, C.POINTER(_Options), i, vp, vp, vp, vp,
                                       vp, C.POINTER(C.c_int), vp]
         L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
@@ -213,6 +214,20 @@ def restore(g: GMM, y, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE, 
     return out
 
 
+def image_update(g: GMM, y, xtilde, sigma: float, beta_mult: float, kind: int = DENOISE, a=None,
+                 kernel=None, out=None, stream=None):
+    """The image estimation step alone (``epll_image_update``); float32 CUDA tensors."""
+    import torch
+    H, W = y.shape
+    out = torch.empty_like(y) if out is None else out
+    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel)
+    _check(lib().epll_image_update(g.handle, _dptr(y, torch.float32), _dptr(xtilde, torch.float32), H, W,
+                                   C.byref(deg), float(sigma), float(beta_mult), _dptr(out, torch.float32),
+                                   _stream(stream)))
+    del keep
+    return out
+
+
 def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = None,
                   mode: int = BATCH_GRAPH, lanes: int = 0, stream=None):
     """Batched restoration (``epll_restore_batch``).  ``jobs`` is a list of
@@ -288,7 +303,14 @@ def sample_noalloc(H: int, W: int, options: Options | None = None, t: int = 0, o
     (``epll_sample_noalloc``); ``out`` is a caller-provided int32 CUDA tensor of
     at least H*W entries.  Returns the filled prefix of ``out``."""
     import torch
-    an = torch.empty(H * W, dtype=torch.int32, device="cuda") if out is None else out
+    if out is None:
+        an = torch.empty(H * W, dtype=torch.int32, device="cuda")
+    else:
+        an = out
+        if an.device.type != "cuda" or an.device.index != torch.cuda.current_device():
+            raise ValueError("out must be on the current CUDA device (the static scratch is per device)")
+        if not an.is_contiguous() or an.numel() < H * W:
+            raise ValueError(f"out must be a contiguous int32 tensor of at least H*W = {H * W} entries")
     n = C.c_int(0)
     opt = (options or Options())._c()
     _check(lib().epll_sample_noalloc(H, W, C.byref(opt), int(t), _dptr(an, torch.int32), C.byref(n),

@@ -62,7 +62,7 @@ static void free_workspace(Workspace &ws)
 {
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
-                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.mu, ws.cg, ws.red, ws.scal,
+                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.mu, ws.cg, ws.red, ws.scal, ws.lamf,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
                     ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore, ws.tnode, ws.tcounts, ws.titems};
     for (void *p : ptrs)
@@ -94,7 +94,7 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     if (fcap < 4096) fcap = 4096;
     if (fcap > N) fcap = N;
     A(dalloc(&ws.fscore, fcap * (size_t)g->K)); A(dalloc(&ws.cg, 4 * N));
-    A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16));
+    A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16)); A(dalloc(&ws.lamf, 16));
     const size_t sstride = sampler_stride(N);
     A(dalloc(&ws.sampler, TB_MAX * sstride));
     A(dalloc(&ws.counts, 2 * (size_t)g->K + 8)); A(dalloc(&ws.ctr, 4));
@@ -185,7 +185,7 @@ static void free_model(epll_gmm *g)
     }
 }
 
-static epll_status check_options(const epll_options &o, int H, int W)
+epll_status check_options(const epll_options &o, int H, int W)
 {
     if (o.precision < EPLL_FP32 || o.precision > EPLL_AUTO)
         return fail(EPLL_EINVAL, "options.precision must be EPLL_FP32, _BF16, _FP16, _BF16X3, _FP8 or _AUTO");
@@ -217,7 +217,7 @@ static epll_status check_select(const epll_gmm *g, const epll_options &o)
     return EPLL_OK;
 }
 
-static epll_status check_image(int H, int W)
+epll_status check_image(int H, int W)
 {
     if (H < PS || W < PS) return fail(EPLL_EINVAL, "image must be at least 8 x 8");
     if ((long long)H * W > (1LL << 26)) return fail(EPLL_EINVAL, "image larger than 2^26 pixels");
@@ -371,12 +371,12 @@ epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int 
         if ((s = patch_phase(g, ws.xhat, H, W, o, n, nullptr, st))) return s;
         const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
         if (kind == EPLL_CONV_PERIODIC) {
-            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, ws.xtil, st)))
+            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.lamf, 0.0, ws.xtil, st)))
                 return s;
             if ((s = fft_update(g, H, W, beta_mult[t], st))) return s;
         } else {
             if ((s = launch_aggregate(g, ws.xhat, H, W, mult, y, kind == EPLL_PIXELWISE ? a : nullptr,
-                                      ws.scal, beta_mult[t], ws.xhat, st)))
+                                      ws.lamf, beta_mult[t], ws.xhat, st)))
                 return s;
         }
     }
@@ -394,7 +394,8 @@ epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
     epll_status s;
     if ((s = check_image(H, W))) return s;
     if (!(sigma > 0.0f) || !std::isfinite(sigma)) return fail(EPLL_EINVAL, "sigma must be positive");
-    if (!beta_mult || T < 1 || T > 64) return fail(EPLL_EINVAL, "beta schedule must have 1..64 entries");
+    if (T < 0 || T > 64 || (T > 0 && !beta_mult))
+        return fail(EPLL_EINVAL, "beta schedule must have 0..64 entries");
     for (int t = 0; t < T; ++t)
         if (!(beta_mult[t] > 0.0) || !std::isfinite(beta_mult[t]))
             return fail(EPLL_EINVAL, "beta multipliers must be positive");
@@ -572,6 +573,7 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
         delete g;
         return fail(EPLL_ECUDA, std::string("model upload: ") + cudaGetErrorString(e));
     }
+    cg_setup();
     *out = g;
     return EPLL_OK;
 }
@@ -714,6 +716,37 @@ epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W, const e
     return EPLL_OK;
 }
 
+epll_status epll_image_update(epll_gmm *g, const float *y, const float *xtilde, int H, int W,
+                              const epll_degradation *deg, float sigma, double beta_mult, float *x_out,
+                              void *stream)
+{
+    if (!g) return fail(EPLL_EINVAL, "null model handle");
+    if (!xtilde) return fail(EPLL_EINVAL, "null image pointer");
+    if (!(beta_mult > 0.0) || !std::isfinite(beta_mult)) return fail(EPLL_EINVAL, "beta multiplier must be positive");
+    epll_options o;
+    epll_options_default(&o);
+    epll_status s;
+    if ((s = check_restore_args(g, y, H, W, deg, sigma, nullptr, 0, o, x_out))) return s;
+    if ((s = ensure_workspace(g, (size_t)H * W))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &ws = g->ws;
+    const int kind = deg ? deg->kind : EPLL_DENOISE;
+    const float *a = kind == EPLL_PIXELWISE ? deg->a : nullptr;
+    g->launches = 0;
+    if (kind == EPLL_CONV_PERIODIC) {
+        if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
+        if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;
+        EPLL_CU(cudaMemcpyAsync(ws.xtil, xtilde, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
+        if ((s = fft_update(g, H, W, beta_mult, st))) return s;
+        EPLL_CU(cudaMemcpyAsync(x_out, ws.xhat, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
+    } else {
+        if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;
+        if ((s = launch_pixel_update(g, a, y, xtilde, H, W, beta_mult, x_out, st))) return s;
+    }
+    g->last_launches = g->launches;
+    return EPLL_OK;
+}
+
 __global__ void k_iota(int *out, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -746,7 +779,7 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
     use_slot(g, 0, (size_t)H * W);
     if ((s = patch_phase(g, xhat, H, W, o, n, forced_k, st))) return s;
     const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
-    if ((s = launch_aggregate(g, xhat, H, W, mult, nullptr, nullptr, ws.scal, 0.0, xtilde, st))) return s;
+    if ((s = launch_aggregate(g, xhat, H, W, mult, nullptr, nullptr, ws.lamf, 0.0, xtilde, st))) return s;
     if (anchors) {
         if (o.subset == EPLL_SUBSET_ALL) {
             k_iota<<<(n + 255) / 256, 256, 0, st>>>(anchors, n);

@@ -96,9 +96,10 @@ struct Workspace {
     size_t zrows = 0;                         // N rounded up to the 128-row tile
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)
     float *mu = nullptr;                      // [N] patch means (split extraction)
-    float *cg = nullptr;                      // [4N] CG vectors r, d, q, spare
+    float *cg = nullptr;                      // [4N] CG vectors r, d (two buffers), q
     float *red = nullptr;                     // reduction partials
-    double *scal = nullptr;                   // device scalars (lambda, CG state)
+    double *scal = nullptr;                   // [0]: lambda, input of the FP64 per-beta tables
+    float *lamf = nullptr;                    // [2]: lambda as an unevaluated float pair (hi, lo)
     unsigned *sampler = nullptr;              // radix-select histograms and state
     int *counts = nullptr;                    // [2K+8] bucket counts/cursors + counters
     long long *ctr = nullptr;                 // [4] device counters: rescored patches
@@ -213,8 +214,17 @@ epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mul
 epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb, int *n,
                           int *anchors, unsigned *mult, unsigned *scratch, size_t sstride,
                           cudaStream_t st);
-size_t sampler_stride(size_t N);
+// The random-fraction sampler works on tiles of FRAC_TILE anchors (256
+// threads x FRAC_ITEMS); its scratch per iteration is 1024 histogram words,
+// 16 words of selection state and two words per tile (plus two spare tiles).
+constexpr int FRAC_ITEMS = 8;
+constexpr int FRAC_TILE = 256 * FRAC_ITEMS;
+constexpr size_t sampler_words(size_t N) { return 1040 + 2 * (N / FRAC_TILE + 2); }
+size_t sampler_stride(size_t N);  // = sampler_words(N)
 int sample_count(int H, int W, const epll_options &o);
+// Argument checks shared by the entry points (set the error message).
+epll_status check_options(const epll_options &o, int H, int W);
+epll_status check_image(int H, int W);
 
 // Near-tie threshold: gap < tau_abs + tau_rel * |z|^2 * tmax.
 epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, const int *anchors,
@@ -285,21 +295,25 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
                                bool reuse, cudaStream_t st);
 // Reprojection.  When y != nullptr the pixelwise image update is fused
-// (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult; a == nullptr means a = 1),
-// otherwise xtilde is written to xout.
+// (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult with lambda = lamf[0];
+// a == nullptr means a = 1), otherwise xtilde is written to xout.
 epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
-                             const float *y, const float *a, const double *d_lambda, double bmult,
+                             const float *y, const float *a, const float *lamf, double bmult,
                              float *xout, cudaStream_t st);
 
 // Image-domain steps (k_image.cu)
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
-                          cudaStream_t st);   // writes ws.scal[0]
+                          cudaStream_t st);   // writes ws.scal[0] and ws.lamf
 epll_status fft_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *y,
                         int H, int W, cudaStream_t st);  // plans, Hh, Yh
 epll_status fft_init(epll_gmm *g, int H, int W, double sigma, cudaStream_t st);    // ws.xhat
 epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st);  // ws.xtil -> ws.xhat
 epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, double sigma,
-                    int iters, cudaStream_t st);  // ws.xhat
+                    int iters, cudaStream_t st);  // ws.xhat (one cluster launch)
+void cg_setup();  // picks the CG kernel's cluster size; call outside stream capture
+// x = (a y + bs xt)/(a^2 + bs), bs = lambda * bmult (a == nullptr: a = 1)
+epll_status launch_pixel_update(epll_gmm *g, const float *a, const float *y, const float *xt, int H, int W,
+                                double bmult, float *x, cudaStream_t st);
 
 epll_status ensure_workspace(epll_gmm *g, size_t N);
 epll_status fail(epll_status s, const std::string &msg);

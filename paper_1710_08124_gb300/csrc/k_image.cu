@@ -6,80 +6,156 @@
 // gradients for a pixelwise A).
 #include "epll_internal.cuh"
 
+#include <cooperative_groups.h>
+
 namespace epll {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
 
+// ---------------------------------------------------------------- compensated FP32 sums
+// Sums of many FP32 terms are carried as unevaluated pairs (s, c) of floats:
+// every addition is an exact TwoSum (Knuth) whose rounding error goes into c,
+// and a product's rounding error is recovered exactly with one FMA, as in the
+// Dot2 algorithm of Ogita, Rump & Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 2005).  The result is about as accurate as if the sum
+// had been formed in twice the working precision.  Intrinsics keep the
+// compiler from contracting or reordering these operations.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void csum_add(float &s, float &c, float v)
+{
+    float t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+}
+// s += u * v with the product's rounding error kept
+__device__ __forceinline__ void csum_fma(float &s, float &c, float u, float v)
+{
+    const float p = __fmul_rn(u, v);
+    const float pe = __fmaf_rn(u, v, -p);
+    csum_add(s, c, p);
+    c = __fadd_rn(c, pe);
+}
+__device__ __forceinline__ void csum_merge(float &s, float &c, float s2, float c2)
+{
+    float t, e;
+    two_sum(s, s2, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+// (s, c) / d for a float d > 0: quotient with one correction step
+__device__ __forceinline__ void csum_div(float s, float c, float d, float &q, float &ql)
+{
+    q = __fdiv_rn(s, d);
+    const float rem = __fadd_rn(__fmaf_rn(-q, d, s), c);
+    ql = __fdiv_rn(rem, d);
+}
+
+// Block-wide sum of (s, c) pairs and maximum m, in a fixed order; the result
+// is valid in thread 0.
+template <int NT>
+__device__ void block_csum_max(float &s, float &c, float &m)
+{
+    __shared__ float ws_[NT / 32][3];
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+        const float m2 = __shfl_down_sync(0xffffffffu, m, o);
+        csum_merge(s, c, s2, c2);
+        m = fmaxf(m, m2);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { ws_[wid][0] = s; ws_[wid][1] = c; ws_[wid][2] = m; }
+    __syncthreads();
+    if (wid == 0) {
+        s = lane < NT / 32 ? ws_[lane][0] : 0.0f;
+        c = lane < NT / 32 ? ws_[lane][1] : 0.0f;
+        m = lane < NT / 32 ? ws_[lane][2] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+            const float m2 = __shfl_down_sync(0xffffffffu, m, o);
+            csum_merge(s, c, s2, c2);
+            m = fmaxf(m, m2);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- lambda
 // Partials of (sum of squared operator eigenvalues squared, max squared
 // eigenvalue): mode 1 over the gains a (A = diag(a)); mode 2 over the half
 // spectrum of the blur (weights 2 for the columns that stand for two
-// frequencies of the full spectrum).
+// frequencies of the full spectrum).  Partial b: part[3b..3b+2] = (s, c, max).
 __global__ void __launch_bounds__(RED_THREADS)
 k_lambda_part(int mode, const float *__restrict__ a, const cufftComplex *__restrict__ Hh, int H,
-              int W, double *__restrict__ part)
+              int W, float *__restrict__ part)
 {
-    __shared__ double s4[RED_THREADS], mx[RED_THREADS];
-    double acc = 0.0, m = 0.0;
+    float s = 0.0f, c = 0.0f, m = 0.0f;
     const int Wc = W / 2 + 1;
     const int total = mode == 1 ? H * W : H * Wc;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
-        double e2, wgt = 1.0;
+        float e2, wgt = 1.0f;
         if (mode == 1) {
-            double v = a[p];
-            e2 = v * v;
+            const float v = a[p];
+            e2 = __fmul_rn(v, v);
         } else {
             const int col = p % Wc;
-            const double re = Hh[p].x, im = Hh[p].y;
-            e2 = re * re + im * im;
-            if (col != 0 && !(W % 2 == 0 && col == W / 2)) wgt = 2.0;
+            const float re = Hh[p].x, im = Hh[p].y;
+            e2 = __fmaf_rn(re, re, __fmul_rn(im, im));
+            if (col != 0 && !(W % 2 == 0 && col == W / 2)) wgt = 2.0f;
         }
-        acc += wgt * e2 * e2;
-        m = fmax(m, e2);
+        // e2^2 with its rounding error, times the (exact) weight
+        const float p4 = __fmul_rn(e2, e2), p4e = __fmaf_rn(e2, e2, -p4);
+        csum_add(s, c, wgt * p4);
+        c = __fadd_rn(c, wgt * p4e);
+        m = fmaxf(m, e2);
     }
-    s4[threadIdx.x] = acc;
-    mx[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            s4[threadIdx.x] += s4[threadIdx.x + s];
-            mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
+    block_csum_max<RED_THREADS>(s, c, m);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s4[0];
-        part[2 * blockIdx.x + 1] = mx[0];
+        part[3 * blockIdx.x] = s;
+        part[3 * blockIdx.x + 1] = c;
+        part[3 * blockIdx.x + 2] = m;
     }
 }
 
-// lambda = min{ N^-1 sum / max , 250 sigma_255^2 }; mode 0 = denoising (value 1)
+// lambda = min{ N^-1 sum / max , 250 sigma_255^2 }; mode 0 = denoising (value 1).
+// Writes lamf[0..1] = lambda as an unevaluated float pair and d_lambda[0] =
+// their sum, the input of the (FP64) per-beta tables.
 __global__ void __launch_bounds__(RED_THREADS)
-k_lambda_final(int mode, const double *__restrict__ part, int nparts, double N, double cap,
-               double *__restrict__ out)
+k_lambda_final(int mode, const float *__restrict__ part, int nparts, float N, float cap_hi,
+               float cap_lo, float *__restrict__ lamf, double *__restrict__ d_lambda)
 {
-    __shared__ double s4[RED_THREADS], mx[RED_THREADS];
-    double acc = 0.0, m = 0.0;
+    float s = 0.0f, c = 0.0f, m = 0.0f;
     if (mode != 0)
         for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-            acc += part[2 * b];
-            m = fmax(m, part[2 * b + 1]);
+            csum_merge(s, c, part[3 * b], part[3 * b + 1]);
+            m = fmaxf(m, part[3 * b + 2]);
         }
-    s4[threadIdx.x] = acc;
-    mx[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            s4[threadIdx.x] += s4[threadIdx.x + s];
-            mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
+    block_csum_max<RED_THREADS>(s, c, m);
     if (threadIdx.x == 0) {
-        double v = mode == 0 ? 1.0 : (s4[0] / N) / mx[0];
-        out[0] = v < cap ? v : cap;
+        float v = 1.0f, vl = 0.0f;
+        if (mode != 0) {
+            float q, ql;
+            csum_div(s, c, N, q, ql);
+            two_sum(q, ql, q, ql);
+            csum_div(q, ql, m, v, vl);
+            two_sum(v, vl, v, vl);
+        }
+        if (v > cap_hi || (v == cap_hi && vl > cap_lo)) { v = cap_hi; vl = cap_lo; }
+        lamf[0] = v;
+        lamf[1] = vl;
+        d_lambda[0] = (double)v + (double)vl;
     }
+}
+
+static void split_float(double v, float *hi, float *lo)
+{
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
 }
 
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
@@ -87,17 +163,20 @@ epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, d
 {
     Workspace &ws = g->ws;
     const double s255 = 255.0 * sigma;
-    const double cap = 250.0 * s255 * s255;
-    double *part = reinterpret_cast<double *>(ws.red);
+    float cap_hi, cap_lo;
+    split_float(250.0 * s255 * s255, &cap_hi, &cap_lo);
+    float *part = ws.red;
     if (kind == EPLL_DENOISE) {
-        k_lambda_final<<<1, RED_THREADS, 0, st>>>(0, part, 0, (double)H * W, cap, ws.scal);
+        k_lambda_final<<<1, RED_THREADS, 0, st>>>(0, part, 0, (float)H * (float)W, cap_hi, cap_lo, ws.lamf,
+                                                 ws.scal);
         EPLL_LAUNCHED(g);
         return EPLL_OK;
     }
     const int mode = kind == EPLL_PIXELWISE ? 1 : 2;
     k_lambda_part<<<RED_BLOCKS, RED_THREADS, 0, st>>>(mode, a, ws.Hh, H, W, part);
     EPLL_LAUNCHED(g);
-    k_lambda_final<<<1, RED_THREADS, 0, st>>>(mode, part, RED_BLOCKS, (double)H * W, cap, ws.scal);
+    k_lambda_final<<<1, RED_THREADS, 0, st>>>(mode, part, RED_BLOCKS, (float)((double)H * W), cap_hi, cap_lo,
+                                             ws.lamf, ws.scal);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -115,14 +194,14 @@ __global__ void k_wrap_kernel(const float *__restrict__ kern, int kh, int kw, in
 
 // x0 = conj(H) Y / (|H|^2 + c Lhat), c = 0.2 sigma^2 / lambda; 1/N of the inverse folded in.
 __global__ void k_fft_init(const cufftComplex *__restrict__ Hh, const cufftComplex *__restrict__ Yh,
-                           int H, int W, double sigma2, const double *__restrict__ d_lambda,
+                           int H, int W, float c_num, const float *__restrict__ lamf,
                            cufftComplex *__restrict__ X)
 {
     const int Wc = W / 2 + 1;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= H * Wc) return;
     const int u = p / Wc, v = p % Wc;
-    const float c = (float)(0.2 * sigma2 / d_lambda[0]);
+    const float c = c_num / lamf[0];
     const float Lh = 4.0f - 2.0f * cospif(2.0f * (float)u / (float)H) - 2.0f * cospif(2.0f * (float)v / (float)W);
     const cufftComplex h = Hh[p], y = Yh[p];
     const float h2 = h.x * h.x + h.y * h.y;
@@ -132,13 +211,13 @@ __global__ void k_fft_init(const cufftComplex *__restrict__ Hh, const cufftCompl
 
 // X = (conj(H) Y + bs X) / (|H|^2 + bs), bs = lambda * mult
 __global__ void k_fft_update(const cufftComplex *__restrict__ Hh, const cufftComplex *__restrict__ Yh,
-                             int H, int W, const double *__restrict__ d_lambda, double bmult,
+                             int H, int W, const float *__restrict__ lamf, float bmult,
                              cufftComplex *__restrict__ X)
 {
     const int Wc = W / 2 + 1;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= H * Wc) return;
-    const float bs = (float)(d_lambda[0] * bmult);
+    const float bs = lamf[0] * bmult;
     const cufftComplex h = Hh[p], y = Yh[p], x = X[p];
     const float h2 = h.x * h.x + h.y * h.y;
     const float inv = 1.0f / ((h2 + bs) * (float)H * (float)W);
@@ -186,7 +265,7 @@ epll_status fft_init(epll_gmm *g, int H, int W, double sigma, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     const int M = H * (W / 2 + 1);
-    k_fft_init<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, H, W, sigma * sigma, ws.scal, ws.Xh);
+    k_fft_init<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, H, W, (float)(0.2 * sigma * sigma), ws.lamf, ws.Xh);
     EPLL_LAUNCHED(g);
     EPLL_FFT(cufftExecC2R(ws.plan_c2r, ws.Xh, ws.xhat));
     return EPLL_OK;
@@ -197,7 +276,7 @@ epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st)
     Workspace &ws = g->ws;
     const int M = H * (W / 2 + 1);
     EPLL_FFT(cufftExecR2C(ws.plan_r2c, ws.xtil, ws.Xh));
-    k_fft_update<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, H, W, ws.scal, bmult, ws.Xh);
+    k_fft_update<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, H, W, ws.lamf, (float)bmult, ws.Xh);
     EPLL_LAUNCHED(g);
     EPLL_FFT(cufftExecC2R(ws.plan_c2r, ws.Xh, ws.xhat));
     return EPLL_OK;
@@ -205,155 +284,212 @@ epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st)
 
 // ---------------------------------------------------------------- CG path
 // Conjugate gradients on (diag(a^2) + c L) x = a y from x = a y, a fixed
-// number of iterations; stops (device flag) once d^T q is not positive.
-// Dot products: FP64 per-block partials with a fixed tree, then one block.
-// scal: [0] lambda, [1] rr, [2] alpha, [3] beta, [4] done.
-__device__ __forceinline__ float apply_A(const float *__restrict__ a, float c,
-                                         const float *__restrict__ v, int i, int j, int H, int W)
+// number of iterations; stops early only once r^T r or d^T q is no longer
+// positive.  The whole iteration runs in one launch of one thread-block
+// cluster (16 CTAs where the device allows it, else 8): the CTAs split the
+// pixels, and every dot product is a compensated FP32 sum (Dot2) reduced
+// across the cluster through distributed shared memory, in a fixed order, so
+// that every CTA obtains bit-identical step sizes.  The hardware cluster
+// barrier orders the stencil's neighbour reads after their writes.  The
+// search direction is recomputed on the fly (d = r + beta d_old at the pixel
+// and its four neighbours) into a second buffer, so each iteration needs two
+// barriers: one per dot product.
+constexpr int CG_THREADS = 1024;
+
+__device__ __forceinline__ float cg_dir(const float *__restrict__ r, const float *__restrict__ dold, float beta,
+                                        bool first, size_t p)
 {
-    const size_t p = (size_t)i * W + j;
-    const int im = i ? i - 1 : H - 1, ip = i + 1 < H ? i + 1 : 0;
-    const int jm = j ? j - 1 : W - 1, jp = j + 1 < W ? j + 1 : 0;
-    const float lap = 4.0f * v[p] - v[(size_t)im * W + j] - v[(size_t)ip * W + j] -
-                      v[(size_t)i * W + jm] - v[(size_t)i * W + jp];
-    return a[p] * a[p] * v[p] + c * lap;
+    return first ? r[p] : __fmaf_rn(beta, dold[p], r[p]);
 }
 
-__device__ void block_partial(double v, double *out)
+// Sum of the cluster's (s, c) pairs; every thread of every CTA returns the
+// same float (hi + lo rounded).  `slot` alternates between calls so that a
+// CTA never overwrites a partial that another CTA may still be reading.
+__device__ float cluster_total(cooperative_groups::cluster_group &cl, float (*part)[2], int slot, float s,
+                               float c)
 {
-    __shared__ double s[RED_THREADS];
-    s[threadIdx.x] = v;
+    __shared__ float wsum[CG_THREADS / 32][2];
+    __shared__ float total;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+        csum_merge(s, c, s2, c2);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { wsum[wid][0] = s; wsum[wid][1] = c; }
     __syncthreads();
-    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[blockIdx.x] = s[0];
-}
-
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_x0(const float *__restrict__ a, const float *__restrict__ y, int N, float *__restrict__ x)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x)
-        x[p] = a[p] * y[p];
-}
-
-// r = a y - A x, d = r, partial r.r
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_r0(const float *__restrict__ a, const float *__restrict__ y, const float *__restrict__ x,
-        int H, int W, double sigma2, const double *__restrict__ scal, float *__restrict__ r,
-        float *__restrict__ d, double *__restrict__ part)
-{
-    const float c = (float)(0.2 * sigma2 / scal[0]);
-    double acc = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < H * W; p += gridDim.x * blockDim.x) {
-        const float rv = a[p] * y[p] - apply_A(a, c, x, p / W, p % W, H, W);
-        r[p] = rv;
-        d[p] = rv;
-        acc += (double)rv * rv;
-    }
-    block_partial(acc, part);
-}
-
-// q = A d, partial d.q
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_q(const float *__restrict__ a, const float *__restrict__ d, int H, int W, double sigma2,
-       const double *__restrict__ scal, float *__restrict__ q, double *__restrict__ part)
-{
-    const float c = (float)(0.2 * sigma2 / scal[0]);
-    double acc = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < H * W; p += gridDim.x * blockDim.x) {
-        const float qv = apply_A(a, c, d, p / W, p % W, H, W);
-        q[p] = qv;
-        acc += (double)d[p] * qv;
-    }
-    block_partial(acc, part);
-}
-
-// which: 0 -> rr = sum; 1 -> dq = sum, alpha = rr/dq (done if dq <= 0); 2 -> beta = sum/rr, rr = sum
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_scalar(int which, const double *__restrict__ part, int nparts, double *__restrict__ scal)
-{
-    __shared__ double s[RED_THREADS];
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) acc += part[b];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x) return;
-    const double v = s[0];
-    if (which == 0) {
-        scal[1] = v;
-        scal[4] = v > 0.0 ? 0.0 : 1.0;
-    } else if (which == 1) {
-        if (!(v > 0.0)) scal[4] = 1.0;
-        scal[2] = scal[4] != 0.0 ? 0.0 : scal[1] / v;
-    } else {
-        scal[3] = scal[4] != 0.0 ? 0.0 : v / scal[1];
-        if (scal[4] == 0.0) scal[1] = v;
-    }
-}
-
-// x += alpha d, r -= alpha q, partial r.r
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_xr(const float *__restrict__ d, const float *__restrict__ q, int N,
-        const double *__restrict__ scal, float *__restrict__ x, float *__restrict__ r,
-        double *__restrict__ part)
-{
-    const bool done = scal[4] != 0.0;
-    const float alpha = (float)scal[2];
-    double acc = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-        float rv = r[p];
-        if (!done) {
-            x[p] = fmaf(alpha, d[p], x[p]);
-            rv = fmaf(-alpha, q[p], rv);
-            r[p] = rv;
+    if (wid == 0) {
+        s = wsum[lane][0];
+        c = wsum[lane][1];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+            csum_merge(s, c, s2, c2);
         }
-        acc += (double)rv * rv;
+        if (lane == 0) { part[slot][0] = s; part[slot][1] = c; }
     }
-    block_partial(acc, part);
+    cl.sync();
+    if (wid == 0) {
+        const int nb = (int)cl.num_blocks();
+        s = 0.0f;
+        c = 0.0f;
+        if (lane < nb) {
+            const float *rp = cl.map_shared_rank(&part[slot][0], lane);
+            s = rp[0];
+            c = rp[1];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+            csum_merge(s, c, s2, c2);
+        }
+        if (lane == 0) total = __fadd_rn(s, c);
+    }
+    __syncthreads();
+    return total;
 }
 
-// d = r + beta d
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_d(const float *__restrict__ r, int N, const double *__restrict__ scal, float *__restrict__ d)
+__global__ void __launch_bounds__(CG_THREADS, 1)
+k_cg_cluster(const float *__restrict__ a, const float *__restrict__ y, int H, int W, float c_num,
+             const float *__restrict__ lamf, int iters, float *__restrict__ x, float *__restrict__ r,
+             float *__restrict__ d0, float *__restrict__ d1, float *__restrict__ q)
 {
-    if (scal[4] != 0.0) return;
-    const float b = (float)scal[3];
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x)
-        d[p] = fmaf(b, d[p], r[p]);
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    __shared__ float part[2][2];
+    const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+    const size_t N = (size_t)H * W;
+    const size_t chunk = (N + nb - 1) / nb;
+    const size_t p0 = (size_t)rank * chunk, p1 = p0 + chunk < N ? p0 + chunk : N;
+    const float c = c_num / lamf[0];
+    const float c4 = 4.0f * c;
+    for (size_t p = p0 + threadIdx.x; p < p1; p += CG_THREADS) x[p] = a[p] * y[p];
+    cl.sync();
+    // r = a y - (diag(a^2) + c L) x, rr = r^T r
+    float s = 0.0f, e = 0.0f;
+    for (size_t p = p0 + threadIdx.x; p < p1; p += CG_THREADS) {
+        const int i = (int)(p / W), j = (int)(p % W);
+        const size_t pn = (size_t)(i ? i - 1 : H - 1) * W + j, ps = (size_t)(i + 1 < H ? i + 1 : 0) * W + j;
+        const size_t pw = (size_t)i * W + (j ? j - 1 : W - 1), pe = (size_t)i * W + (j + 1 < W ? j + 1 : 0);
+        const float ap = a[p], xv = x[p];
+        const float lap = c4 * xv - c * (x[pn] + x[ps] + x[pw] + x[pe]);
+        const float rv = ap * y[p] - (ap * ap * xv + lap);
+        r[p] = rv;
+        csum_fma(s, e, rv, rv);
+    }
+    float rr = cluster_total(cl, part, 1, s, e);
+    float beta = 0.0f;
+    float *dold = d1, *dnew = d0;
+    for (int it = 0; it < iters && rr > 0.0f; ++it) {
+        const bool first = it == 0;
+        // d = r + beta d_old (first: d = r), q = A d, dq = d^T q
+        s = 0.0f;
+        e = 0.0f;
+        for (size_t p = p0 + threadIdx.x; p < p1; p += CG_THREADS) {
+            const int i = (int)(p / W), j = (int)(p % W);
+            const size_t pn = (size_t)(i ? i - 1 : H - 1) * W + j, ps = (size_t)(i + 1 < H ? i + 1 : 0) * W + j;
+            const size_t pw = (size_t)i * W + (j ? j - 1 : W - 1), pe = (size_t)i * W + (j + 1 < W ? j + 1 : 0);
+            const float dv = cg_dir(r, dold, beta, first, p);
+            const float nsum = cg_dir(r, dold, beta, first, pn) + cg_dir(r, dold, beta, first, ps) +
+                               cg_dir(r, dold, beta, first, pw) + cg_dir(r, dold, beta, first, pe);
+            const float ap = a[p];
+            const float qv = ap * ap * dv + (c4 * dv - c * nsum);
+            dnew[p] = dv;
+            q[p] = qv;
+            csum_fma(s, e, dv, qv);
+        }
+        const float dq = cluster_total(cl, part, 0, s, e);
+        if (!(dq > 0.0f)) break;
+        const float alpha = rr / dq;
+        // x += alpha d, r -= alpha q, rr' = r^T r
+        s = 0.0f;
+        e = 0.0f;
+        for (size_t p = p0 + threadIdx.x; p < p1; p += CG_THREADS) {
+            const float dv = dnew[p];
+            x[p] = __fmaf_rn(alpha, dv, x[p]);
+            const float rv = __fmaf_rn(-alpha, q[p], r[p]);
+            r[p] = rv;
+            csum_fma(s, e, rv, rv);
+        }
+        const float rr2 = cluster_total(cl, part, 1, s, e);
+        beta = rr2 / rr;
+        rr = rr2;
+        float *t = dold;
+        dold = dnew;
+        dnew = t;
+    }
+    cl.sync();  // no CTA leaves while another may still read its partials
 }
+
+// Cluster size of the CG kernel: 16 CTAs where one such cluster fits, else 8.
+static int cg_cluster_size()
+{
+    static int size = 0;
+    if (size) return size;
+    size = 8;
+    if (cudaFuncSetAttribute(k_cg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(CG_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cg_cluster, &cfg) == cudaSuccess && nclusters > 0)
+            size = 16;
+    }
+    cudaGetLastError();
+    return size;
+}
+
+void cg_setup() { (void)cg_cluster_size(); }
 
 epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, double sigma,
                     int iters, cudaStream_t st)
 {
     Workspace &ws = g->ws;
+    const size_t cap = ws.capN;
+    float *r = ws.cg, *d0 = ws.cg + cap, *d1 = ws.cg + 2 * cap, *q = ws.cg + 3 * cap;
+    const int cl = cg_cluster_size();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(CG_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    EPLL_CU(cudaLaunchKernelEx(&cfg, k_cg_cluster, a, y, H, W, (float)(0.2 * sigma * sigma),
+                               (const float *)ws.lamf, iters, ws.xhat, r, d0, d1, q));
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+// ---------------------------------------------------------------- pixelwise update
+// x = (a y + bs xt) / (a^2 + bs), bs = lambda * mult (a == nullptr: a = 1); the
+// restoration loop fuses this into the reprojection, this standalone form
+// serves epll_image_update.
+__global__ void k_pixel_update(const float *__restrict__ a, const float *__restrict__ y,
+                               const float *__restrict__ xt, int N, const float *__restrict__ lamf, float bmult,
+                               float *__restrict__ x)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const float bs = lamf[0] * bmult;
+    const float ap = a ? a[p] : 1.0f;
+    x[p] = (ap * y[p] + bs * xt[p]) / (ap * ap + bs);
+}
+
+epll_status launch_pixel_update(epll_gmm *g, const float *a, const float *y, const float *xt, int H, int W,
+                                double bmult, float *x, cudaStream_t st)
+{
     const int N = H * W;
-    float *r = ws.cg, *d = ws.cg + ws.capN, *q = ws.cg + 2 * ws.capN;
-    double *part = reinterpret_cast<double *>(ws.red);
-    const double s2 = sigma * sigma;
-    k_cg_x0<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, y, N, ws.xhat);
+    k_pixel_update<<<(N + 255) / 256, 256, 0, st>>>(a, y, xt, N, g->ws.lamf, (float)bmult, x);
     EPLL_LAUNCHED(g);
-    k_cg_r0<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, y, ws.xhat, H, W, s2, ws.scal, r, d, part);
-    EPLL_LAUNCHED(g);
-    k_cg_scalar<<<1, RED_THREADS, 0, st>>>(0, part, RED_BLOCKS, ws.scal);
-    EPLL_LAUNCHED(g);
-    for (int it = 0; it < iters; ++it) {
-        k_cg_q<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, d, H, W, s2, ws.scal, q, part);
-        EPLL_LAUNCHED(g);
-        k_cg_scalar<<<1, RED_THREADS, 0, st>>>(1, part, RED_BLOCKS, ws.scal);
-        EPLL_LAUNCHED(g);
-        k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, st>>>(d, q, N, ws.scal, ws.xhat, r, part);
-        EPLL_LAUNCHED(g);
-        k_cg_scalar<<<1, RED_THREADS, 0, st>>>(2, part, RED_BLOCKS, ws.scal);
-        EPLL_LAUNCHED(g);
-        k_cg_d<<<RED_BLOCKS, RED_THREADS, 0, st>>>(r, N, ws.scal, d);
-        EPLL_LAUNCHED(g);
-    }
     return EPLL_OK;
 }
 

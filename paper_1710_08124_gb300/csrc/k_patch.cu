@@ -732,7 +732,7 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 __global__ void __launch_bounds__(256)
 k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             const float *xhat, int H, int W, const float *__restrict__ y,
-            const float *__restrict__ a, const double *__restrict__ d_lambda, double bmult,
+            const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
             float *xout)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -758,7 +758,7 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
     }
     const float xt = cnt ? sum / (float)cnt : xhat[p];
     if (y) {
-        const float bs = (float)(d_lambda[0] * bmult);
+        const float bs = lamf[0] * bmult;
         const float ap = a ? a[p] : 1.0f;
         xout[p] = (ap * y[p] + bs * xt) / (ap * ap + bs);
     } else {
@@ -767,11 +767,11 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
 }
 
 epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
-                             const float *y, const float *a, const double *d_lambda, double bmult,
+                             const float *y, const float *a, const float *lamf, double bmult,
                              float *xout, cudaStream_t st)
 {
     const int N = H * W;
-    k_aggregate<<<(N + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, d_lambda, bmult,
+    k_aggregate<<<(N + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
                                                  xout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;

@@ -265,9 +265,6 @@ k_frac_pick(int pass, int M, unsigned *__restrict__ scratch, size_t sstride)
     }
 }
 
-constexpr int FRAC_ITEMS = 8;
-constexpr int FRAC_TILE = 256 * FRAC_ITEMS;
-
 // phase 1: per-tile counts of keys below / equal to the threshold
 __global__ void __launch_bounds__(256)
 k_frac_count(int N, uint64_t seed, int t0, unsigned *__restrict__ scratch, size_t sstride)
@@ -391,7 +388,7 @@ int sample_count(int H, int W, const epll_options &o)
     return N;
 }
 
-size_t sampler_stride(size_t N) { return 1040 + 2 * (N / FRAC_TILE + 2); }
+size_t sampler_stride(size_t N) { return sampler_words(N); }
 
 epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb, int *n,
                           int *anchors, unsigned *mult, unsigned *scratch, size_t sstride,

@@ -10,50 +10,34 @@
 // only the output buffer.
 #include "epll_internal.cuh"
 
-#include <mutex>
 #include <string>
 
 namespace epll {
 
 // Largest image served: 2^20 pixels (for example 1024 x 1024).
 constexpr int NOALLOC_MAX_PIXELS = 1 << 20;
-// Sampler scratch of that size, followed by the per-anchor multiplicity array.
-constexpr size_t NOALLOC_SAMPLER_WORDS = 1040 + 2 * ((size_t)NOALLOC_MAX_PIXELS / 2048 + 2);
+// Sampler scratch of that size (the layout of the allocating entry point),
+// followed by the per-anchor multiplicity array.
+constexpr size_t NOALLOC_SAMPLER_WORDS = sampler_words((size_t)NOALLOC_MAX_PIXELS);
 constexpr size_t NOALLOC_WORDS = NOALLOC_SAMPLER_WORDS + (size_t)NOALLOC_MAX_PIXELS;
 
 // About 4.2 MB on every device that loads the library, held until exit.
 static __device__ __align__(256) unsigned g_noalloc_scratch[NOALLOC_WORDS];
 
-// Device address of g_noalloc_scratch per device.  In host code the array's
-// name is only a host-side stand-in, so the address is fetched once per
-// device with that device current.
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::mutex g_noalloc_mu;
-static unsigned *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
-
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// on every call with the device current (a lookup allocates nothing; the
+// first one on a device loads the library's device code there if that has
+// not happened yet).
 static epll_status noalloc_scratch(unsigned **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         return EPLL_ECUDA;
     }
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
-        set_error("epll_sample_noalloc: device index out of range");
-        return EPLL_EUNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            return EPLL_ECUDA;
-        }
-        g_noalloc_ptr[dev] = static_cast<unsigned *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned *>(p);
     return EPLL_OK;
 }
 
@@ -74,33 +58,17 @@ extern "C" epll_status epll_sample_noalloc(int H, int W, const epll_options *opt
         set_error("epll_sample_noalloc: null output pointer");
         return EPLL_EINVAL;
     }
-    if (H < PS || W < PS) {
-        set_error("epll_sample_noalloc: image must be at least 8 x 8");
-        return EPLL_EINVAL;
-    }
+    epll_options o;
+    if (opt) o = *opt; else epll_options_default(&o);
+    epll_status s;
+    if ((s = check_image(H, W))) return s;
     if ((long long)H * W > NOALLOC_MAX_PIXELS) {
         set_error("epll_sample_noalloc: image has more than 2^20 pixels, the size its static scratch serves");
         return EPLL_EINVAL;
     }
-    epll_options o;
-    if (opt) o = *opt; else epll_options_default(&o);
-    if (o.subset == EPLL_SUBSET_FRACTION) {
-        if (!(o.subset_param > 0.0 && o.subset_param <= 1.0)) {
-            set_error("epll_sample_noalloc: fraction must be in (0, 1]");
-            return EPLL_EINVAL;
-        }
-    } else if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
-        const int s = (int)o.subset_param;
-        if ((double)s != o.subset_param || s < 1 || s > PS) {
-            set_error("epll_sample_noalloc: grid spacing must be an integer in 1..8");
-            return EPLL_EINVAL;
-        }
-    } else if (o.subset != EPLL_SUBSET_ALL) {
-        set_error("epll_sample_noalloc: unknown subset kind");
-        return EPLL_EINVAL;
-    }
+    if ((s = check_options(o, H, W))) return s;
     unsigned *scratch = nullptr;
-    epll_status s = noalloc_scratch(&scratch);
+    s = noalloc_scratch(&scratch);
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)H * W;

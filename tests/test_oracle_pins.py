@@ -491,6 +491,73 @@ def test_mlp_gelu_and_softmax_closed_forms():
     assert abs(mlp.loss(p, np.ones((3, 64)), np.zeros(3), np.array([0, 2, 4])) - np.log(K)) < 1e-14
 
 
+def _adamw_variant(p, g, m, v, step, lr, wd, bias_correction=True, coupled=False):
+    """AdamW with a planted mistake (test of the pins' and the GPU test's
+    sensitivity): no bias correction, or the decay folded into the gradient
+    (Adam with L2 regularisation instead of decoupled decay)."""
+    from oracle import mlp
+    c1 = 1.0 - mlp.ADAM_B1 ** step if bias_correction else 1.0
+    c2 = 1.0 - mlp.ADAM_B2 ** step if bias_correction else 1.0
+    p2, m2, v2 = {}, {}, {}
+    for k in p:
+        gk = g[k] + (wd * p[k] if coupled and k in mlp.DECAYED else 0.0)
+        m2[k] = mlp.ADAM_B1 * m[k] + (1 - mlp.ADAM_B1) * gk
+        v2[k] = mlp.ADAM_B2 * v[k] + (1 - mlp.ADAM_B2) * gk * gk
+        u = (m2[k] / c1) / (np.sqrt(v2[k] / c2) + mlp.ADAM_EPS)
+        if k in mlp.DECAYED and not coupled:
+            u = u + wd * p[k]
+        p2[k] = p[k] - lr * u
+    return p2, m2, v2
+
+
+def test_adamw_matches_torch_and_closed_form():
+    """The AdamW oracle against an independent implementation (torch.optim.AdamW
+    on the weight matrices, torch.optim.Adam without decay on the biases and wb,
+    float64) over several steps; the first step in closed form (m_hat = g,
+    v_hat = g^2: the update is lr (g / (|g| + eps) + wd theta)); and planted
+    mistakes (no bias correction, decay coupled into the gradient) are far off."""
+    import torch
+    from oracle import mlp
+    K = 6
+    rng = np.random.default_rng(21)
+    p = mlp.unpack(rng.standard_normal(mlp.n_params(K)) * 0.3, K)
+    grads = [mlp.unpack(rng.standard_normal(mlp.n_params(K)) * 10.0 ** rng.uniform(-4, 0), K) for _ in range(5)]
+    lr, wd = 1e-2, 0.5
+    tp = {k: torch.tensor(p[k], dtype=torch.float64, requires_grad=True) for k in p}
+    opt_w = torch.optim.AdamW([tp[k] for k in mlp.DECAYED], lr=lr, betas=(mlp.ADAM_B1, mlp.ADAM_B2),
+                              eps=mlp.ADAM_EPS, weight_decay=wd)
+    opt_b = torch.optim.Adam([tp[k] for k in p if k not in mlp.DECAYED], lr=lr,
+                             betas=(mlp.ADAM_B1, mlp.ADAM_B2), eps=mlp.ADAM_EPS, weight_decay=0.0)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(x) for k, x in p.items()}
+    q = dict(p)
+    for t, g in enumerate(grads, start=1):
+        if t == 1:
+            q1, _, _ = mlp.adamw_step(q, g, m, v, 1, lr, wd)
+            for k in q:
+                ref = q[k] - lr * (g[k] / (np.abs(g[k]) + mlp.ADAM_EPS) + (wd * q[k] if k in mlp.DECAYED else 0.0))
+                np.testing.assert_allclose(q1[k], ref, rtol=0, atol=1e-15)
+        q, m, v = mlp.adamw_step(q, g, m, v, t, lr, wd)
+        for k in tp:
+            tp[k].grad = torch.tensor(g[k], dtype=torch.float64)
+        opt_w.step()
+        opt_b.step()
+        for k in q:
+            np.testing.assert_allclose(q[k], tp[k].detach().numpy(), rtol=0, atol=1e-14)
+    # planted mistakes, three steps from the same start: the moved parameters
+    # differ from the oracle's by a sizeable fraction of the step length
+    # (also at the GPU test's lr = 1e-3, wd = 2)
+    for lr_, wd_ in ((lr, wd), (1e-3, 2.0)):
+        for kw in (dict(bias_correction=False), dict(coupled=True)):
+            a, am, av = dict(p), {k: np.zeros_like(x) for k, x in p.items()}, {k: np.zeros_like(x) for k, x in p.items()}
+            b, bm, bv = dict(p), dict(am), dict(av)
+            for t, g in enumerate(grads[:3], start=1):
+                a, am, av = mlp.adamw_step(a, g, am, av, t, lr_, wd_)
+                b, bm, bv = _adamw_variant(b, g, bm, bv, t, lr_, wd_, **kw)
+            d = max(np.abs(a[k] - b[k]).max() for k in mlp.DECAYED)
+            assert d > 0.1 * lr_, (kw, lr_, d)
+
+
 def test_bf16_rounding_matches_torch_and_ties_to_even():
     import torch
     from oracle import mlp

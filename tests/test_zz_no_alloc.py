@@ -32,6 +32,8 @@ CASES = [
     (512, 512, ep.SUBSET_FRACTION, 1 / 3),
     (50, 37, ep.SUBSET_JITTER, 6),
     (1024, 1024, ep.SUBSET_JITTER, 3),
+    (1024, 1024, ep.SUBSET_FRACTION, 1 / 3),   # the largest image the static scratch serves
+    (1024, 1023, ep.SUBSET_FRACTION, 0.01),
     (50, 37, ep.SUBSET_REGULAR, 4),
     (33, 40, ep.SUBSET_ALL, 0.0),
 ]
@@ -62,3 +64,26 @@ def test_rejects_images_beyond_the_static_scratch():
     st = L.epll_sample_noalloc(1025, 1024, C.byref(opt), 0, out.data_ptr(), C.byref(n), None)
     assert st == ep.EINVAL
     assert "2^20" in ep.last_error()
+
+
+def test_binding_rejects_a_short_or_misplaced_output():
+    short = torch.empty(64 * 64 - 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        ep.sample_noalloc(64, 64, ep.Options(subset=ep.SUBSET_FRACTION, subset_param=0.5), out=short)
+    with pytest.raises(ValueError):
+        ep.sample_noalloc(16, 16, ep.Options(), out=torch.empty(256, dtype=torch.int32))
+    got = ep.sample_noalloc(64, 64, ep.Options(subset=ep.SUBSET_FRACTION, subset_param=0.5),
+                            out=torch.empty(64 * 64, dtype=torch.int32, device="cuda"))
+    ref = ep.sample(64, 64, ep.Options(subset=ep.SUBSET_FRACTION, subset_param=0.5))
+    assert torch.equal(got, ref)
+
+
+def test_rejects_what_the_allocating_sampler_rejects():
+    L = ep.lib()
+    out = torch.empty(256, dtype=torch.int32, device="cuda")
+    n = C.c_int(0)
+    for bad in (ep.Options(precision=99), ep.Options(cg_iters=-1), ep.Options(select=7),
+                ep.Options(subset=ep.SUBSET_JITTER, subset_param=2.5)):
+        opt = bad._c()
+        assert L.epll_sample_noalloc(16, 16, C.byref(opt), 0, out.data_ptr(), C.byref(n), None) == ep.EINVAL
+        assert L.epll_sample(16, 16, C.byref(opt), 0, out.data_ptr(), C.byref(n), None) == ep.EINVAL
