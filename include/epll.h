@@ -45,8 +45,10 @@ typedef enum {
 
 /* flat-tail rank selection (Sec. "Speed-up via flat tail spectrum approximation") */
 enum { EPLL_RANK_FIXED = 0, EPLL_RANK_RHO = 1 };
-/* degradation operator A of y = A x + w (Sec. 2) */
-enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2 };
+/* degradation operator A of y = A x + w (Sec. 2); CONV_DECIMATE is the
+ * super-resolution operator: the periodic blur followed by keeping pixel
+ * (f i, f j) of every f x f block (f = `factor`) */
+enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2, EPLL_CONV_DECIMATE = 3 };
 /* patch subset (Sec. "Speed-up via the restriction to a random subset of patches"):
  * ALL every pixel's patch; FRACTION ceil(f N) distinct anchors redrawn every
  * iteration; JITTER the jittered grid of Eq. 20 (spacing s); REGULAR the
@@ -90,12 +92,17 @@ typedef struct epll_proposal epll_proposal; /* opaque, library-owned */
 
 /* Degradation A.  PIXELWISE: A = diag(a) (a = 0/1 mask for inpainting, a
  * smooth gain for devignetting).  CONV_PERIODIC: circular convolution with a
- * kh x kw kernel whose centre (kh/2, kw/2) maps to pixel offset (0, 0). */
+ * kh x kw kernel whose centre (kh/2, kw/2) maps to pixel offset (0, 0).
+ * CONV_DECIMATE (super-resolution, Sec. "Complexity via eigenspace
+ * implementation" and Fig. 8): the same convolution followed by decimation by
+ * `factor`; the observation y is then (H/factor) x (W/factor) while x is
+ * H x W. */
 typedef struct {
     int kind;
     const float *a;      /* PIXELWISE: H*W gains; device for epll_restore, host for epll_restore_host */
-    const float *kernel; /* CONV_PERIODIC: host, kh*kw row-major, copied during the call */
+    const float *kernel; /* CONV_PERIODIC, CONV_DECIMATE: host, kh*kw row-major, copied during the call */
     int kh, kw;          /* 1..min(H, W) each */
+    int factor;          /* CONV_DECIMATE: 1..8, dividing H and W; ignored otherwise */
 } epll_degradation;
 
 typedef struct {
@@ -169,13 +176,15 @@ epll_status epll_gmm_ranks(const epll_gmm *g, int *ranks, double *lambdas);
  * settings"): beta_t = lambda * beta_mult[t] / sigma^2 with
  * lambda = min{N^-1 ||A^T A||_F^2 / ||A||_2^2, 250 sigma_255^2} computed on the
  * device; initialisation x = y for denoising, (A^T A + 0.2 sigma^2/lambda L)^-1
- * A^T y otherwise (FFT for CONV_PERIODIC, conjugate gradients for PIXELWISE).
+ * A^T y otherwise (FFT for CONV_PERIODIC and CONV_DECIMATE, conjugate
+ * gradients for PIXELWISE).
  * Each iteration: per-beta tables (FP64), patch sampling, extraction,
  * projection + Gaussian selection (FP32 SIMT or BF16 tcgen05 with a fused
  * score/argmin epilogue), near-tie rescoring, Wiener patch estimation
  * (Eqs. 15-16), reprojection by overlap-add averaging and the closed-form
  * image update (Eq. 6).
- *   y, x_out     device [H][W]; x_out may alias y
+ *   y, x_out     device [H][W]; x_out may alias y (CONV_DECIMATE: y is
+ *                [H/factor][W/factor] and must not alias x_out)
  *   H, W         8 <= H, W and H*W <= 2^26
  *   sigma        noise standard deviation in image units, > 0
  *   beta_mult    host [T], > 0 (the paper uses {1, 4, 8, 16, 32}); T in 0..64;
@@ -222,7 +231,8 @@ epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const d
 
 /* Same as epll_restore with HOST buffers: y, deg->a (PIXELWISE) and x_out are
  * host pointers; the copies to and from the workspace are part of the call,
- * which returns after x_out is written (synchronises `stream`). */
+ * which returns after x_out is written (synchronises `stream`).  y is H x W
+ * ((H/factor) x (W/factor) for CONV_DECIMATE). */
 epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W,
                               const epll_degradation *deg, float sigma,
                               const double *beta_mult, int T, const epll_options *opt,
@@ -258,8 +268,12 @@ epll_status epll_patch_step(epll_gmm *g, const float *xhat, int H, int W, double
  *   x = (A^T A + bs I)^-1 (A^T y + bs xtilde),  bs = lambda * beta_mult,
  * with lambda computed from the degradation as in epll_restore.  Pixelwise A
  * (and denoising, a = 1): x = (a y + bs xtilde) / (a^2 + bs) per pixel;
- * CONV_PERIODIC: the same division frequency by frequency (cuFFT).
- *   y, xtilde, x_out  device [H][W]; x_out must not alias y or xtilde
+ * CONV_PERIODIC: the same division frequency by frequency (cuFFT);
+ * CONV_DECIMATE: A^T A couples the factor^2 frequencies that alias onto one
+ * low-resolution frequency through a rank-one block, solved in closed form
+ * per block (Woodbury) between full complex FFTs.
+ *   y                 device [H][W] ([H/factor][W/factor] for CONV_DECIMATE)
+ *   xtilde, x_out     device [H][W]; x_out must not alias y or xtilde
  *   beta_mult         > 0 (the iteration's multiplier m_t)
  * Asynchronous on `stream`.  Errors: EPLL_EINVAL, EPLL_ENOMEM, EPLL_ECUDA.
  */

@@ -27,7 +27,7 @@ _lib = None
 
 P = 64
 FULL, FRACTION, JITTER, REGULAR = 0, 1, 2, 3
-DENOISE, PIXELWISE, CONV = 0, 1, 2
+DENOISE, PIXELWISE, CONV, SR = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -73,8 +73,16 @@ def _L():
             lib.or_init_conv.restype = None
             lib.or_init_cg.argtypes = [vp, vp, i, i, d, i, vp]
             lib.or_init_cg.restype = None
-            lib.or_restore.argtypes = [i, vp, vp, vp, vp, vp, vp, i, i, i, vp, vp, i, i, d,
+            lib.or_restore.argtypes = [i, vp, vp, vp, vp, vp, vp, i, i, i, vp, vp, i, i, i, d,
                                        vp, i, i, d, u64, i, vp, vp, vp, vp]
+            lib.or_sr_apply.argtypes = [vp, i, i, vp, i, i, i, vp]
+            lib.or_sr_apply.restype = None
+            lib.or_sr_adjoint.argtypes = [vp, i, i, vp, i, i, i, vp]
+            lib.or_sr_adjoint.restype = None
+            lib.or_xupdate_sr.argtypes = [vp, i, i, vp, vp, i, i, i, d, vp]
+            lib.or_init_sr.argtypes = [vp, i, i, vp, i, i, i, d, vp]
+            lib.or_lambda_sr.restype = d
+            lib.or_lambda_sr.argtypes = [vp, i, i, i, i, i, d]
             _lib = lib
     return _lib
 
@@ -217,23 +225,65 @@ def init_cg(a, y, c: float, iters: int):
     return out
 
 
+def sr_apply(kernel, x, d: int):
+    """A x = decimation by d (keep pixel (d i, d j)) of the periodic blur of x."""
+    k, x = _f64(kernel), _f64(x)
+    H, W = x.shape
+    out = np.zeros((H // d, W // d))
+    _L().or_sr_apply(_p(k), k.shape[0], k.shape[1], _p(x), H, W, int(d), _p(out))
+    return out
+
+
+def sr_adjoint(kernel, ylow, d: int):
+    """A^T y: zero insertion to (d h) x (d w), then correlation with the kernel."""
+    k, y = _f64(kernel), _f64(ylow)
+    H, W = y.shape[0] * d, y.shape[1] * d
+    out = np.zeros((H, W))
+    _L().or_sr_adjoint(_p(k), k.shape[0], k.shape[1], _p(y), H, W, int(d), _p(out))
+    return out
+
+
+def lam_sr(kernel, H: int, W: int, d: int, sigma: float) -> float:
+    k = _f64(kernel)
+    return float(_L().or_lambda_sr(_p(k), k.shape[0], k.shape[1], H, W, int(d), float(sigma)))
+
+
+def xupdate_sr(kernel, ylow, xtilde, d: int, bs: float):
+    k, y, xt = _f64(kernel), _f64(ylow), _f64(xtilde)
+    H, W = xt.shape
+    out = np.zeros_like(xt)
+    _L().or_xupdate_sr(_p(k), k.shape[0], k.shape[1], _p(y), _p(xt), H, W, int(d), float(bs), _p(out))
+    return out
+
+
+def init_sr(kernel, ylow, d: int, c: float):
+    k, y = _f64(kernel), _f64(ylow)
+    H, W = y.shape[0] * d, y.shape[1] * d
+    out = np.zeros((H, W))
+    _L().or_init_sr(_p(k), k.shape[0], k.shape[1], _p(y), H, W, int(d), float(c), _p(out))
+    return out
+
+
 def restore(m: Model, y, sigma: float, beta_mult=(1, 4, 8, 16, 32), deg: int = DENOISE,
             a=None, kernel=None, subset: int = FULL, subset_param: float = 0.0,
-            seed: int = 0, cg_iters: int = 100, record: bool = False):
+            seed: int = 0, cg_iters: int = 100, record: bool = False, factor: int = 1):
     """Full restoration.  With record=True also returns per-iteration
-    (kstar list, gap list) in sampling order."""
+    (kstar list, gap list) in sampling order.  deg=SR: y is the
+    (H/factor) x (W/factor) observation and the result is H x W."""
     y = _f64(y)
     H, W = y.shape
+    if deg == SR:
+        H, W = H * factor, W * factor
     a = None if a is None else _f64(a)
     k = None if kernel is None else _f64(kernel)
     kh, kw = (0, 0) if k is None else k.shape
     bm = _f64(beta_mult)
     T = bm.shape[0]
-    x = np.zeros_like(y)
+    x = np.zeros((H, W))
     ks = np.zeros((T, H * W), np.int32) if record else None
     gp = np.zeros((T, H * W)) if record else None
     ns = np.zeros(T, np.int32)
-    rc = _L().or_restore(*m._args(), _p(y), H, W, deg, _p(a), _p(k), kh, kw, float(sigma),
+    rc = _L().or_restore(*m._args(), _p(y), H, W, deg, _p(a), _p(k), kh, kw, int(factor), float(sigma),
                          _p(bm), T, subset, float(subset_param), seed, cg_iters, _p(x),
                          _p(ks), _p(gp), _p(ns))
     if rc:

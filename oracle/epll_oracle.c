@@ -572,9 +572,164 @@ void or_init_cg(const double *a, const double *y, int H, int W, double c, int it
 }
 
 /* ------------------------------------------------------------------------ */
+/* Super-resolution, A = S B (Sec. "Complexity via eigenspace                 */
+/* implementation" counts super-resolution among the problems whose image    */
+/* update is an O(N log N) Fourier computation; Fig. 8 shows x3).  B is the  */
+/* periodic blur above and S keeps pixel (d i, d j) of every d x d block, so  */
+/* y is (H/d) x (W/d).  The oracle applies A and A^T in the pixel domain and  */
+/* solves the image update and the initialisation by conjugate gradients in  */
+/* FP64 run to convergence: a route independent of any Fourier-domain        */
+/* closed form.                                                              */
+/* ------------------------------------------------------------------------ */
+/* out = kern (*) x (adjoint: correlation), periodic, kernel centre (kh/2, kw/2) */
+static void or_blur(const double *kern, int kh, int kw, const double *x, int H, int W, int adjoint,
+                    double *out)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double acc = 0.0;
+            for (int u = 0; u < kh; ++u)
+                for (int v = 0; v < kw; ++v) {
+                    int di = u - kh / 2, dj = v - kw / 2;
+                    if (adjoint) { di = -di; dj = -dj; }
+                    int ii = ((i - di) % H + H) % H, jj = ((j - dj) % W + W) % W;
+                    acc += kern[u * kw + v] * x[(size_t)ii * W + jj];
+                }
+            out[(size_t)i * W + j] = acc;
+        }
+}
+
+/* ylow = S B x */
+void or_sr_apply(const double *kern, int kh, int kw, const double *x, int H, int W, int d, double *ylow)
+{
+    double *bx = (double *)malloc(sizeof(double) * (size_t)H * W);
+    or_blur(kern, kh, kw, x, H, W, 0, bx);
+    int h = H / d, w = W / d;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) ylow[(size_t)i * w + j] = bx[(size_t)(d * i) * W + d * j];
+    free(bx);
+}
+
+/* x = B^T S^T ylow (zero insertion, then correlation with the kernel) */
+void or_sr_adjoint(const double *kern, int kh, int kw, const double *ylow, int H, int W, int d, double *x)
+{
+    double *up = (double *)calloc((size_t)H * W, sizeof(double));
+    int h = H / d, w = W / d;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) up[(size_t)(d * i) * W + d * j] = ylow[(size_t)i * w + j];
+    or_blur(kern, kh, kw, up, H, W, 1, x);
+    free(up);
+}
+
+/* (A^T A + shift M) v with M = I (lap = 0) or the negative Laplacian (lap = 1) */
+typedef struct { const double *kern; int kh, kw, H, W, d, lap; double shift; double *low; } or_sr_op;
+static void or_sr_normal(const or_sr_op *o, const double *v, double *out)
+{
+    or_sr_apply(o->kern, o->kh, o->kw, v, o->H, o->W, o->d, o->low);
+    or_sr_adjoint(o->kern, o->kh, o->kw, o->low, o->H, o->W, o->d, out);
+    for (int i = 0; i < o->H; ++i)
+        for (int j = 0; j < o->W; ++j) {
+            size_t p = (size_t)i * o->W + j;
+            double m = v[p];
+            if (o->lap) {
+                int H = o->H, W = o->W;
+                m = 4.0 * v[p] - v[(size_t)((i + H - 1) % H) * W + j] - v[(size_t)((i + 1) % H) * W + j]
+                  - v[(size_t)i * W + (j + W - 1) % W] - v[(size_t)i * W + (j + 1) % W];
+            }
+            out[p] += o->shift * m;
+        }
+}
+
+/* Conjugate gradients on (A^T A + shift M) x = b from the given x, until the
+ * residual norm is below rtol |b| (or maxit iterations); returns iterations. */
+static int or_sr_cg(const or_sr_op *o, const double *b, double *x, double rtol, int maxit)
+{
+    size_t N = (size_t)o->H * o->W;
+    double *r = (double *)malloc(sizeof(double) * N), *dd = (double *)malloc(sizeof(double) * N),
+           *q = (double *)malloc(sizeof(double) * N);
+    or_sr_normal(o, x, q);
+    double rr = 0.0, bb = 0.0;
+    for (size_t p = 0; p < N; ++p) { r[p] = b[p] - q[p]; dd[p] = r[p]; rr += r[p] * r[p]; bb += b[p] * b[p]; }
+    int it = 0;
+    while (it < maxit && rr > rtol * rtol * bb) {
+        or_sr_normal(o, dd, q);
+        double dq = 0.0;
+        for (size_t p = 0; p < N; ++p) dq += dd[p] * q[p];
+        if (!(dq > 0.0)) break;
+        double alpha = rr / dq, rr2 = 0.0;
+        for (size_t p = 0; p < N; ++p) { x[p] += alpha * dd[p]; r[p] -= alpha * q[p]; rr2 += r[p] * r[p]; }
+        double bt = rr2 / rr;
+        for (size_t p = 0; p < N; ++p) dd[p] = r[p] + bt * dd[p];
+        rr = rr2;
+        ++it;
+    }
+    free(r); free(dd); free(q);
+    return it;
+}
+
+/* Image update (Eq. 6): x = (A^T A + bs I)^-1 (A^T y + bs xtilde). */
+int or_xupdate_sr(const double *kern, int kh, int kw, const double *ylow, const double *xtilde, int H, int W,
+                  int d, double bs, double *x)
+{
+    size_t N = (size_t)H * W;
+    double *b = (double *)malloc(sizeof(double) * N);
+    or_sr_adjoint(kern, kh, kw, ylow, H, W, d, b);
+    for (size_t p = 0; p < N; ++p) { b[p] += bs * xtilde[p]; x[p] = xtilde[p]; }
+    or_sr_op o = {kern, kh, kw, H, W, d, 0, bs, (double *)malloc(sizeof(double) * N / ((size_t)d * d))};
+    int it = or_sr_cg(&o, b, x, 1e-15, 100000);
+    free(o.low); free(b);
+    return it;
+}
+
+/* Initialisation (Sec. "Parameter settings"): x0 = (A^T A + c L)^-1 A^T y. */
+int or_init_sr(const double *kern, int kh, int kw, const double *ylow, int H, int W, int d, double c, double *x)
+{
+    size_t N = (size_t)H * W;
+    double *b = (double *)malloc(sizeof(double) * N);
+    or_sr_adjoint(kern, kh, kw, ylow, H, W, d, b);
+    for (size_t p = 0; p < N; ++p) x[p] = 0.0;
+    or_sr_op o = {kern, kh, kw, H, W, d, 1, c, (double *)malloc(sizeof(double) * N / ((size_t)d * d))};
+    int it = or_sr_cg(&o, b, x, 1e-14, 1000000);
+    free(o.low); free(b);
+    return it;
+}
+
+/* lambda for A = S B: A^T A is block diagonal in the Fourier basis, one
+ * d^2 x d^2 block per low-resolution frequency w' coupling the d^2
+ * frequencies that alias onto it; the block is (1/d^2) g g^H with g the
+ * transfer function at those frequencies, so its one non-zero eigenvalue
+ * is e(w') = d^-2 sum |B(w'_k)|^2 and its squared Frobenius norm e(w')^2.
+ * Hence ||A^T A||_F^2 = sum e^2 and ||A||_2^2 = max e. */
+double or_lambda_sr(const double *kern, int kh, int kw, int H, int W, int d, double sigma)
+{
+    size_t N = (size_t)H * W;
+    double complex *Hh = (double complex *)malloc(sizeof(double complex) * N);
+    or_kernel_otf(kern, kh, kw, H, W, Hh);
+    int h = H / d, w = W / d;
+    double f = 0.0, mx = 0.0;
+    for (int u = 0; u < h; ++u)
+        for (int v = 0; v < w; ++v) {
+            double e = 0.0;
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    double complex z = Hh[(size_t)(u + a * h) * W + (v + b * w)];
+                    e += creal(z) * creal(z) + cimag(z) * cimag(z);
+                }
+            e /= (double)d * d;
+            f += e * e;
+            if (e > mx) mx = e;
+        }
+    free(Hh);
+    double v = (f / (double)N) / mx;
+    double s255 = 255.0 * sigma, cap = 250.0 * s255 * s255;
+    return v < cap ? v : cap;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole restoration: Algorithm 1 iterated T times with                       */
 /* beta_t = lambda * beta_mult[t] / sigma^2 (Sec. "Parameter settings").      */
-/* deg_kind 0 denoise, 1 pixelwise a, 2 periodic blur.  subset 0 full set,    */
+/* deg_kind 0 denoise, 1 pixelwise a, 2 periodic blur, 3 blur then          */
+/* decimation by `factor` (y is (H/factor) x (W/factor)).  subset 0 full set, */
 /* 1 random fraction subset_param, 2 jitter with spacing (int)subset_param,  */
 /* 3 regular grid with spacing (int)subset_param.                            */
 /* ks_out / gap_out (nullable) receive each iteration's selections, at       */
@@ -582,17 +737,19 @@ void or_init_cg(const double *a, const double *y, int H, int W, double c, int it
 /* ------------------------------------------------------------------------ */
 int or_restore(int K, const double *w, const double *U, const double *S, const int *r,
                const double *lam, const double *y, int H, int W, int deg_kind,
-               const double *a, const double *kern, int kh, int kw, double sigma,
+               const double *a, const double *kern, int kh, int kw, int factor, double sigma,
                const double *beta_mult, int T, int subset, double subset_param,
                uint64_t seed, int cg_iters, double *x,
                int *ks_out, double *gap_out, int *nsel_out)
 {
     size_t N = (size_t)H * W;
-    double lmb = or_lambda(deg_kind, a, kern, kh, kw, H, W, sigma);
+    double lmb = deg_kind == 3 ? or_lambda_sr(kern, kh, kw, H, W, factor, sigma)
+                               : or_lambda(deg_kind, a, kern, kh, kw, H, W, sigma);
     double c0 = 0.2 * sigma * sigma / lmb;
     if (deg_kind == 0) memcpy(x, y, sizeof(double) * N);
     else if (deg_kind == 1) or_init_cg(a, y, H, W, c0, cg_iters, x);
-    else or_init_conv(kern, kh, kw, y, H, W, c0, x);
+    else if (deg_kind == 2) or_init_conv(kern, kh, kw, y, H, W, c0, x);
+    else or_init_sr(kern, kh, kw, y, H, W, factor, c0, x);
 
     int *anchors = (int *)malloc(sizeof(int) * N);
     double *xt = (double *)malloc(sizeof(double) * N);
@@ -613,6 +770,7 @@ int or_restore(int K, const double *w, const double *U, const double *S, const i
             free(anchors); free(xt); return -1;
         }
         if (deg_kind == 2) or_xupdate_conv(kern, kh, kw, y, xt, H, W, bs, x);
+        else if (deg_kind == 3) or_xupdate_sr(kern, kh, kw, y, xt, H, W, factor, bs, x);
         else or_xupdate_pixelwise(deg_kind == 1 ? a : NULL, y, xt, (int)N, bs, x);
     }
     free(anchors); free(xt);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libepll.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RANK_FIXED, RANK_RHO = 0, 1
-DENOISE, PIXELWISE, CONV_PERIODIC = 0, 1, 2
+DENOISE, PIXELWISE, CONV_PERIODIC, CONV_DECIMATE = 0, 1, 2, 3
 SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER, SUBSET_REGULAR = 0, 1, 2, 3
 FP32, BF16, FP16, BF16X3, FP8, AUTO = 0, 1, 2, 3, 4, 5
 SELECT_EXHAUSTIVE, SELECT_PROPOSAL, SELECT_TREE = 0, 1, 2
@@ -50,7 +50,7 @@ BATCH_SEQUENTIAL, BATCH_GRAPH = 0, 1
 
 class _Degradation(C.Structure):
     _fields_ = [("kind", C.c_int), ("a", C.c_void_p), ("kernel", C.c_void_p),
-                ("kh", C.c_int), ("kw", C.c_int)]
+                ("kh", C.c_int), ("kw", C.c_int), ("factor", C.c_int)]
 
 
 @dataclass
@@ -190,21 +190,24 @@ def gmm_load(w, U, S, rank_mode: int = RANK_FIXED, rank_param: float = 64) -> GM
     return GMM(w, U, S, rank_mode, rank_param)
 
 
-def _degradation(kind, a_ptr, kernel):
+def _degradation(kind, a_ptr, kernel, factor: int = 1):
     if kernel is not None:
         k = np.ascontiguousarray(kernel, np.float32)
-        deg = _Degradation(kind, a_ptr, k.ctypes.data, k.shape[0], k.shape[1])
+        deg = _Degradation(kind, a_ptr, k.ctypes.data, k.shape[0], k.shape[1], int(factor))
         return deg, k
-    return _Degradation(kind, a_ptr, None, 0, 0), None
+    return _Degradation(kind, a_ptr, None, 0, 0, int(factor)), None
 
 
 def restore(g: GMM, y, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE, a=None,
-            kernel=None, options: Options | None = None, out=None, stream=None):
-    """Device-buffer restoration; y (and a) are float32 CUDA tensors [H, W]."""
+            kernel=None, options: Options | None = None, out=None, stream=None, factor: int = 1):
+    """Device-buffer restoration; y (and a) are float32 CUDA tensors [H, W]
+    (kind=CONV_DECIMATE: y is [H/factor, W/factor] and the result [H, W])."""
     import torch
     H, W = y.shape
-    out = torch.empty_like(y) if out is None else out
-    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel)
+    if kind == CONV_DECIMATE:
+        H, W = H * factor, W * factor
+    out = torch.empty((H, W), dtype=torch.float32, device=y.device) if out is None else out
+    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel, factor)
     bm = np.ascontiguousarray(beta_mult, np.float64)
     opt = (options or Options())._c()
     _check(lib().epll_restore(g.handle, _dptr(y, torch.float32), H, W, C.byref(deg), float(sigma),
@@ -215,12 +218,12 @@ def restore(g: GMM, y, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE, 
 
 
 def image_update(g: GMM, y, xtilde, sigma: float, beta_mult: float, kind: int = DENOISE, a=None,
-                 kernel=None, out=None, stream=None):
+                 kernel=None, out=None, stream=None, factor: int = 1):
     """The image estimation step alone (``epll_image_update``); float32 CUDA tensors."""
     import torch
-    H, W = y.shape
-    out = torch.empty_like(y) if out is None else out
-    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel)
+    H, W = xtilde.shape
+    out = torch.empty_like(xtilde) if out is None else out
+    deg, keep = _degradation(kind, _dptr(a, torch.float32), kernel, factor)
     _check(lib().epll_image_update(g.handle, _dptr(y, torch.float32), _dptr(xtilde, torch.float32), H, W,
                                    C.byref(deg), float(sigma), float(beta_mult), _dptr(out, torch.float32),
                                    _stream(stream)))
@@ -245,7 +248,7 @@ def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = 
 
 
 def restore_host(g: GMM, y: np.ndarray, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE,
-                 a=None, kernel=None, options: Options | None = None, out=None, stream=None):
+                 a=None, kernel=None, options: Options | None = None, out=None, stream=None, factor: int = 1):
     """Host-buffer restoration (copies inside the call); y, a, out are float32 arrays
     (pinned torch CPU tensors are accepted too)."""
     def hptr(v):
@@ -258,9 +261,11 @@ def restore_host(g: GMM, y: np.ndarray, sigma: float, beta_mult=PAPER_BETA, kind
         return v.data_ptr()
 
     H, W = y.shape
+    if kind == CONV_DECIMATE:
+        H, W = H * factor, W * factor
     if out is None:
         out = np.empty((H, W), np.float32)
-    deg, keep = _degradation(kind, hptr(a), kernel)
+    deg, keep = _degradation(kind, hptr(a), kernel, factor)
     bm = np.ascontiguousarray(beta_mult, np.float64)
     opt = (options or Options())._c()
     _check(lib().epll_restore_host(g.handle, hptr(y), H, W, C.byref(deg), float(sigma),

@@ -69,6 +69,8 @@ static void free_workspace(Workspace &ws)
         if (p) cudaFree(p);
     if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
     if (ws.plan_c2r) cufftDestroy(ws.plan_c2r);
+    if (ws.plan_c2c) cufftDestroy(ws.plan_c2c);
+    if (ws.plan_c2c_low) cufftDestroy(ws.plan_c2c_low);
     ws = Workspace();
 }
 
@@ -344,14 +346,19 @@ epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int 
     g->last_evals = 0;
     EPLL_CU(cudaMemsetAsync(ws.ctr, 0, sizeof(long long) * 4, st));
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
+    const int d = kind == EPLL_CONV_DECIMATE ? deg->factor : 1;
     if (kind == EPLL_CONV_PERIODIC) {
         if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
+    } else if (kind == EPLL_CONV_DECIMATE) {
+        if ((s = sr_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, d, st))) return s;
     }
-    if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;
+    if ((s = launch_lambda(g, kind, a, H, W, sigma, st, d))) return s;
     if (kind == EPLL_DENOISE) {
         EPLL_CU(cudaMemcpyAsync(ws.xhat, y, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
     } else if (kind == EPLL_CONV_PERIODIC) {
         if ((s = fft_init(g, H, W, sigma, st))) return s;
+    } else if (kind == EPLL_CONV_DECIMATE) {
+        if ((s = sr_init(g, H, W, d, sigma, st))) return s;
     } else {
         if ((s = cg_init(g, a, y, H, W, sigma, o.cg_iters, st))) return s;
     }
@@ -370,10 +377,14 @@ epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int 
         use_slot(g, b, N);
         if ((s = patch_phase(g, ws.xhat, H, W, o, n, nullptr, st))) return s;
         const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
-        if (kind == EPLL_CONV_PERIODIC) {
+        if (kind == EPLL_CONV_PERIODIC || kind == EPLL_CONV_DECIMATE) {
             if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.lamf, 0.0, ws.xtil, st)))
                 return s;
-            if ((s = fft_update(g, H, W, beta_mult[t], st))) return s;
+            if (kind == EPLL_CONV_PERIODIC) {
+                if ((s = fft_update(g, H, W, beta_mult[t], st))) return s;
+            } else {
+                if ((s = sr_update(g, H, W, d, beta_mult[t], st))) return s;
+            }
         } else {
             if ((s = launch_aggregate(g, ws.xhat, H, W, mult, y, kind == EPLL_PIXELWISE ? a : nullptr,
                                       ws.lamf, beta_mult[t], ws.xhat, st)))
@@ -404,9 +415,12 @@ epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
     if (deg) {
         if (deg->kind == EPLL_PIXELWISE) {
             if (!deg->a) return fail(EPLL_EINVAL, "PIXELWISE degradation needs gains a");
-        } else if (deg->kind == EPLL_CONV_PERIODIC) {
+        } else if (deg->kind == EPLL_CONV_PERIODIC || deg->kind == EPLL_CONV_DECIMATE) {
             if (!deg->kernel || deg->kh < 1 || deg->kw < 1 || deg->kh > H || deg->kw > W)
-                return fail(EPLL_EINVAL, "CONV_PERIODIC kernel must be 1..H x 1..W");
+                return fail(EPLL_EINVAL, "blur kernel must be 1..H x 1..W");
+            if (deg->kind == EPLL_CONV_DECIMATE &&
+                (deg->factor < 1 || deg->factor > 8 || H % deg->factor || W % deg->factor))
+                return fail(EPLL_EINVAL, "CONV_DECIMATE factor must be in 1..8 and divide H and W");
             double sum = 0.0;
             for (int q = 0; q < deg->kh * deg->kw; ++q) {
                 if (!std::isfinite(deg->kernel[q])) return fail(EPLL_EINVAL, "kernel is not finite");
@@ -704,7 +718,8 @@ epll_status epll_restore_host(epll_gmm *g, const float *y, int H, int W, const e
     cudaStream_t st = (cudaStream_t)stream;
     Workspace &ws = g->ws;
     const size_t bytes = sizeof(float) * (size_t)H * W;
-    EPLL_CU(cudaMemcpyAsync(ws.y, y, bytes, cudaMemcpyHostToDevice, st));
+    const size_t dd = (deg && deg->kind == EPLL_CONV_DECIMATE) ? (size_t)deg->factor * deg->factor : 1;
+    EPLL_CU(cudaMemcpyAsync(ws.y, y, bytes / dd, cudaMemcpyHostToDevice, st));
     const float *a = nullptr;
     if (deg && deg->kind == EPLL_PIXELWISE) {
         EPLL_CU(cudaMemcpyAsync(ws.a, deg->a, bytes, cudaMemcpyHostToDevice, st));
@@ -733,11 +748,20 @@ epll_status epll_image_update(epll_gmm *g, const float *y, const float *xtilde, 
     const int kind = deg ? deg->kind : EPLL_DENOISE;
     const float *a = kind == EPLL_PIXELWISE ? deg->a : nullptr;
     g->launches = 0;
-    if (kind == EPLL_CONV_PERIODIC) {
-        if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
-        if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;
+    if (kind == EPLL_CONV_PERIODIC || kind == EPLL_CONV_DECIMATE) {
+        const int d = kind == EPLL_CONV_DECIMATE ? deg->factor : 1;
+        if (kind == EPLL_CONV_PERIODIC) {
+            if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
+        } else {
+            if ((s = sr_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, d, st))) return s;
+        }
+        if ((s = launch_lambda(g, kind, a, H, W, sigma, st, d))) return s;
         EPLL_CU(cudaMemcpyAsync(ws.xtil, xtilde, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
-        if ((s = fft_update(g, H, W, beta_mult, st))) return s;
+        if (kind == EPLL_CONV_PERIODIC) {
+            if ((s = fft_update(g, H, W, beta_mult, st))) return s;
+        } else {
+            if ((s = sr_update(g, H, W, d, beta_mult, st))) return s;
+        }
         EPLL_CU(cudaMemcpyAsync(x_out, ws.xhat, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice, st));
     } else {
         if ((s = launch_lambda(g, kind, a, H, W, sigma, st))) return s;

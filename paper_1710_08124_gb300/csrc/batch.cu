@@ -126,7 +126,7 @@ static std::vector<std::vector<int>> assign(int n, const epll_job *jobs, int L)
 static epll_status run_job(epll_gmm *ctx, const epll_job &j, const double *beta, int T,
                            const epll_options &o, cudaStream_t st)
 {
-    epll_degradation deg{j.kind, j.a, nullptr, 0, 0};
+    epll_degradation deg{j.kind, j.a, nullptr, 0, 0, 1};
     epll_status s = run_restore(ctx, j.y, j.kind == EPLL_PIXELWISE ? j.a : nullptr, j.H, j.W, &deg, j.sigma,
                                 beta, T, o, st);
     if (s) return s;
@@ -251,7 +251,7 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
         const epll_job &j = jobs[i];
         if (j.kind != EPLL_DENOISE && j.kind != EPLL_PIXELWISE)
             return fail(EPLL_EINVAL, "batch jobs are EPLL_DENOISE or EPLL_PIXELWISE");
-        epll_degradation deg{j.kind, j.a, nullptr, 0, 0};
+        epll_degradation deg{j.kind, j.a, nullptr, 0, 0, 1};
         epll_status s = check_restore_args(g, j.y, j.H, j.W, &deg, j.sigma, beta_mult, T, o, j.x_out);
         if (s) return s;
         maxN = std::max(maxN, (size_t)j.H * j.W);

@@ -107,6 +107,8 @@ struct Workspace {
     float *kern = nullptr;                    // [H][W] wrapped blur kernel
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     int planH = 0, planW = 0;
+    cufftHandle plan_c2c = 0, plan_c2c_low = 0;  // super-resolution: H x W and (H/d) x (W/d)
+    int c2cH = 0, c2cW = 0, c2cd = 0;
     // search tree (allocated on first use)
     int *tnode = nullptr;                     // [N] current node of each patch
     int *tcounts = nullptr;                   // [nodes] bucket counters
@@ -303,11 +305,18 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
 
 // Image-domain steps (k_image.cu)
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
-                          cudaStream_t st);   // writes ws.scal[0] and ws.lamf
+                          cudaStream_t st, int d = 1);   // writes ws.scal[0] and ws.lamf
 epll_status fft_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *y,
                         int H, int W, cudaStream_t st);  // plans, Hh, Yh
 epll_status fft_init(epll_gmm *g, int H, int W, double sigma, cudaStream_t st);    // ws.xhat
 epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st);  // ws.xtil -> ws.xhat
+// Super-resolution (blur, then decimation by d): full complex transforms of
+// the kernel and of the low-resolution observation, the initialisation and
+// the image update (ws.xtil -> ws.xhat), each solved per aliasing block.
+epll_status sr_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *ylow, int H, int W,
+                       int d, cudaStream_t st);
+epll_status sr_init(epll_gmm *g, int H, int W, int d, double sigma, cudaStream_t st);
+epll_status sr_update(epll_gmm *g, int H, int W, int d, double bmult, cudaStream_t st);
 epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, double sigma,
                     int iters, cudaStream_t st);  // ws.xhat (one cluster launch)
 void cg_setup();  // picks the CG kernel's cluster size; call outside stream capture

@@ -89,19 +89,35 @@ __device__ void block_csum_max(float &s, float &c, float &m)
 // Partials of (sum of squared operator eigenvalues squared, max squared
 // eigenvalue): mode 1 over the gains a (A = diag(a)); mode 2 over the half
 // spectrum of the blur (weights 2 for the columns that stand for two
-// frequencies of the full spectrum).  Partial b: part[3b..3b+2] = (s, c, max).
+// frequencies of the full spectrum); mode 3 over the low-resolution
+// frequencies of a blur followed by decimation by d, whose eigenvalues are
+// the per-block values e (full complex spectrum Hh).  Partial b:
+// part[3b..3b+2] = (s, c, max).
 __global__ void __launch_bounds__(RED_THREADS)
 k_lambda_part(int mode, const float *__restrict__ a, const cufftComplex *__restrict__ Hh, int H,
-              int W, float *__restrict__ part)
+              int W, int d, float *__restrict__ part)
 {
     float s = 0.0f, c = 0.0f, m = 0.0f;
     const int Wc = W / 2 + 1;
-    const int total = mode == 1 ? H * W : H * Wc;
+    const int h = H / d, w = W / d;
+    const int total = mode == 1 ? H * W : mode == 2 ? H * Wc : h * w;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
         float e2, wgt = 1.0f;
         if (mode == 1) {
             const float v = a[p];
             e2 = __fmul_rn(v, v);
+        } else if (mode == 3) {
+            // the one non-zero eigenvalue of the block of A^T A at this
+            // low-resolution frequency: d^-2 sum over its aliases of |H|^2
+            const int u0 = p / w, v0 = p % w;
+            float es = 0.0f, ec = 0.0f;
+            for (int ia = 0; ia < d; ++ia)
+                for (int ib = 0; ib < d; ++ib) {
+                    const cufftComplex z = Hh[(size_t)(u0 + ia * h) * W + (v0 + ib * w)];
+                    csum_fma(es, ec, z.x, z.x);
+                    csum_fma(es, ec, z.y, z.y);
+                }
+            e2 = __fadd_rn(es, ec) / (float)(d * d);
         } else {
             const int col = p % Wc;
             const float re = Hh[p].x, im = Hh[p].y;
@@ -159,7 +175,7 @@ static void split_float(double v, float *hi, float *lo)
 }
 
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
-                          cudaStream_t st)
+                          cudaStream_t st, int d)
 {
     Workspace &ws = g->ws;
     const double s255 = 255.0 * sigma;
@@ -172,8 +188,8 @@ epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, d
         EPLL_LAUNCHED(g);
         return EPLL_OK;
     }
-    const int mode = kind == EPLL_PIXELWISE ? 1 : 2;
-    k_lambda_part<<<RED_BLOCKS, RED_THREADS, 0, st>>>(mode, a, ws.Hh, H, W, part);
+    const int mode = kind == EPLL_PIXELWISE ? 1 : kind == EPLL_CONV_PERIODIC ? 2 : 3;
+    k_lambda_part<<<RED_BLOCKS, RED_THREADS, 0, st>>>(mode, a, ws.Hh, H, W, d, part);
     EPLL_LAUNCHED(g);
     k_lambda_final<<<1, RED_THREADS, 0, st>>>(mode, part, RED_BLOCKS, (float)((double)H * W), cap_hi, cap_lo,
                                              ws.lamf, ws.scal);
@@ -279,6 +295,158 @@ epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st)
     k_fft_update<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, H, W, ws.lamf, (float)bmult, ws.Xh);
     EPLL_LAUNCHED(g);
     EPLL_FFT(cufftExecC2R(ws.plan_c2r, ws.Xh, ws.xhat));
+    return EPLL_OK;
+}
+
+// ---------------------------------------------------------------- super-resolution
+// A = S B (blur, then keep pixel (d i, d j)).  In the Fourier basis A^T A is
+// block diagonal: the block at a low-resolution frequency w' couples the d^2
+// high-resolution frequencies w'_k = w' + (a H/d, b W/d) that alias onto it and
+// equals s g g^H with s = d^-2 and g_k = conj(B(w'_k)), while
+// F(A^T y)(w'_k) = g_k Y(w'), Y the transform of the low-resolution
+// observation.  Each block is solved in closed form (a rank-one update of a
+// diagonal, as in Zhao et al., "Fast single image super-resolution using a
+// new analytical solution for l2-l2 problems", IEEE TIP 2016):
+//  - image update, (s g g^H + bs I) X = g Y + bs Xt (Woodbury):
+//      X_k = Xt_k + g_k (Y - s g^H Xt) / (bs + s |g|^2);
+//  - initialisation, (s g g^H + D) X = g Y with D_k = c L(w'_k) >= 0
+//    (Sherman-Morrison, arranged so that no term is divided by a vanishing
+//    D; D vanishes only at the zero frequency, where g_0 = 1):
+//      X_k = g_k Y / (D_k + s (|g_k|^2 + sum_{j != k} |g_j|^2 D_k / D_j)),
+//    X_k = 0 when some other D_j of the block is zero.
+// Transforms are full complex (C2C) at both resolutions; the inverse's 1/N
+// is folded into the solve.
+__device__ __forceinline__ float neg_lap_symbol(int u, int v, int H, int W)
+{
+    return 4.0f - 2.0f * cospif(2.0f * (float)u / (float)H) - 2.0f * cospif(2.0f * (float)v / (float)W);
+}
+
+__global__ void k_real_to_complex(const float *__restrict__ x, int N, cufftComplex *__restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) out[p] = make_float2(x[p], 0.0f);
+}
+
+__global__ void k_real_part(const cufftComplex *__restrict__ X, int N, float *__restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) out[p] = X[p].x;
+}
+
+// mode 0: initialisation (c = c_num / lambda); mode 1: image update (bs = lambda * bmult, X holds Xt)
+__global__ void k_sr_solve(int mode, const cufftComplex *__restrict__ Hh, const cufftComplex *__restrict__ Yl,
+                           cufftComplex *__restrict__ X, int H, int W, int d, float c_num,
+                           const float *__restrict__ lamf, float bmult)
+{
+    const int h = H / d, w = W / d;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= h * w) return;
+    const int u0 = q / w, v0 = q % w;
+    const float s = 1.0f / (float)(d * d);
+    const float invN = 1.0f / ((float)H * (float)W);
+    const cufftComplex Y = Yl[q];
+    const int nk = d * d;
+    auto at = [&](int k) { return (size_t)(u0 + (k / d) * h) * W + (v0 + (k % d) * w); };
+    if (mode == 0) {
+        const float c = c_num / lamf[0];
+        for (int k = 0; k < nk; ++k) {
+            const size_t pk = at(k);
+            const cufftComplex hk = Hh[pk];
+            const float Dk = c * neg_lap_symbol(u0 + (k / d) * h, v0 + (k % d) * w, H, W);
+            float den = hk.x * hk.x + hk.y * hk.y;
+            bool zero = false;
+            for (int j = 0; j < nk; ++j) {
+                if (j == k) continue;
+                const float Dj = c * neg_lap_symbol(u0 + (j / d) * h, v0 + (j % d) * w, H, W);
+                if (Dj == 0.0f) { zero = true; break; }
+                const cufftComplex hj = Hh[at(j)];
+                den = fmaf(hj.x * hj.x + hj.y * hj.y, Dk / Dj, den);
+            }
+            const float inv = zero ? 0.0f : invN / fmaf(s, den, Dk);
+            // g_k Y with g_k = conj(H_k)
+            X[pk] = make_float2((hk.x * Y.x + hk.y * Y.y) * inv, (hk.x * Y.y - hk.y * Y.x) * inv);
+        }
+    } else {
+        const float bs = lamf[0] * bmult;
+        // g^H Xt = sum_k H_k Xt_k, |g|^2
+        float gr = 0.0f, gi = 0.0f, ng = 0.0f;
+        for (int k = 0; k < nk; ++k) {
+            const size_t pk = at(k);
+            const cufftComplex hk = Hh[pk], xk = X[pk];
+            gr += hk.x * xk.x - hk.y * xk.y;
+            gi += hk.x * xk.y + hk.y * xk.x;
+            ng += hk.x * hk.x + hk.y * hk.y;
+        }
+        const float inv = 1.0f / (bs + s * ng);
+        const float tr = (Y.x - s * gr) * inv, ti = (Y.y - s * gi) * inv;
+        for (int k = 0; k < nk; ++k) {
+            const size_t pk = at(k);
+            const cufftComplex hk = Hh[pk], xk = X[pk];
+            // Xt_k + conj(H_k) t
+            X[pk] = make_float2((xk.x + hk.x * tr + hk.y * ti) * invN, (xk.y + hk.x * ti - hk.y * tr) * invN);
+        }
+    }
+}
+
+epll_status sr_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *ylow, int H, int W,
+                       int d, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int h = H / d, w = W / d;
+    if (ws.c2cH != H || ws.c2cW != W || ws.c2cd != d) {
+        if (ws.plan_c2c) cufftDestroy(ws.plan_c2c);
+        if (ws.plan_c2c_low) cufftDestroy(ws.plan_c2c_low);
+        ws.plan_c2c = ws.plan_c2c_low = 0;
+        ws.c2cH = ws.c2cW = ws.c2cd = 0;
+        EPLL_FFT(cufftPlan2d(&ws.plan_c2c, H, W, CUFFT_C2C));
+        EPLL_FFT(cufftPlan2d(&ws.plan_c2c_low, h, w, CUFFT_C2C));
+        ws.c2cH = H;
+        ws.c2cW = W;
+        ws.c2cd = d;
+    }
+    EPLL_FFT(cufftSetStream(ws.plan_c2c, st));
+    EPLL_FFT(cufftSetStream(ws.plan_c2c_low, st));
+    const size_t N = (size_t)H * W;
+    float *dk = ws.cg;  // scratch: kh*kw <= N floats
+    EPLL_CU(cudaMemcpyAsync(dk, kernel_host, sizeof(float) * (size_t)kh * kw, cudaMemcpyHostToDevice, st));
+    EPLL_CU(cudaMemsetAsync(ws.kern, 0, sizeof(float) * N, st));
+    k_wrap_kernel<<<(kh * kw + 255) / 256, 256, 0, st>>>(dk, kh, kw, H, W, ws.kern);
+    EPLL_LAUNCHED(g);
+    k_real_to_complex<<<(int)((N + 255) / 256), 256, 0, st>>>(ws.kern, (int)N, ws.Hh);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2C(ws.plan_c2c, ws.Hh, ws.Hh, CUFFT_FORWARD));
+    const int n = h * w;
+    k_real_to_complex<<<(n + 255) / 256, 256, 0, st>>>(ylow, n, ws.Yh);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2C(ws.plan_c2c_low, ws.Yh, ws.Yh, CUFFT_FORWARD));
+    return EPLL_OK;
+}
+
+epll_status sr_init(epll_gmm *g, int H, int W, int d, double sigma, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int n = (H / d) * (W / d), N = H * W;
+    k_sr_solve<<<(n + 127) / 128, 128, 0, st>>>(0, ws.Hh, ws.Yh, ws.Xh, H, W, d, (float)(0.2 * sigma * sigma),
+                                                ws.lamf, 0.0f);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2C(ws.plan_c2c, ws.Xh, ws.Xh, CUFFT_INVERSE));
+    k_real_part<<<(N + 255) / 256, 256, 0, st>>>(ws.Xh, N, ws.xhat);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
+epll_status sr_update(epll_gmm *g, int H, int W, int d, double bmult, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const int n = (H / d) * (W / d), N = H * W;
+    k_real_to_complex<<<(N + 255) / 256, 256, 0, st>>>(ws.xtil, N, ws.Xh);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2C(ws.plan_c2c, ws.Xh, ws.Xh, CUFFT_FORWARD));
+    k_sr_solve<<<(n + 127) / 128, 128, 0, st>>>(1, ws.Hh, ws.Yh, ws.Xh, H, W, d, 0.0f, ws.lamf, (float)bmult);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2C(ws.plan_c2c, ws.Xh, ws.Xh, CUFFT_INVERSE));
+    k_real_part<<<(N + 255) / 256, 256, 0, st>>>(ws.Xh, N, ws.xhat);
+    EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
 

@@ -2,7 +2,9 @@
 C ABI: the initialisation of the inverse problems (Sec. "Parameter settings":
 x0 = (A^T A + c L)^-1 A^T y, c = 0.2 sigma^2 / lambda; an FFT solve for a
 periodic blur, conjugate gradients for a pixelwise A) and the image
-estimation step alone (last step of Algorithm 1, Eq. 6).
+estimation step alone (last step of Algorithm 1, Eq. 6), for periodic
+deblurring, pixelwise operators and super-resolution (blur then decimation,
+solved per aliasing block of frequencies).
 
 Every bound here is derived from the conditioning of the step and FP32
 arithmetic (unit roundoff u = 2^-24), not chosen:
@@ -16,7 +18,9 @@ arithmetic (unit roundoff u = 2^-24), not chosen:
   its exact result (Higham, Accuracy and Stability of Numerical Algorithms,
   Sec. 24.1), amplified by the operator norm max |G| of the diagonal
   multiplier; the bound is that sum over the inputs;
-* the pixelwise update is a handful of FP32 operations per pixel: 8 u |x|.
+* the pixelwise update is a handful of FP32 operations per pixel: 8 u |x|;
+* super-resolution: the same FFT rounding at both resolutions, amplified by
+  the gain of the per-block solve (computed in FP64 from numpy's transform).
 """
 import math
 
@@ -180,3 +184,86 @@ def test_image_update_pixelwise(kind):
                          a=None if a is None else dev(a)).cpu().numpy()
     err = np.abs(xg - xo).max()
     assert err <= 8 * U * max(np.abs(xo).max(), 1.0), err
+
+
+# ---------------------------------------------------------------- super-resolution
+def sr_problem(i, H, W, d, sigma, ks=9, sb=1.0):
+    x = synth.image(i, H, W)
+    k = synth.gaussian_kernel(ks, sb)
+    yl = synth.blur_periodic(x, k)[::d, ::d] + synth.noise(i, H // d, W // d, sigma)
+    return x, k, yl.astype(np.float32)
+
+
+def sr_blocks(k, H, W, d):
+    """Transfer function at the d^2 aliases of every low-resolution frequency:
+    array [d^2, H/d, W/d] (numpy FP64 FFT, independent of both paths)."""
+    Hh = otf(k, H, W)
+    h, w = H // d, W // d
+    return np.stack([Hh[a * h:(a + 1) * h, b * w:(b + 1) * w] for a in range(d) for b in range(d)])
+
+
+@pytest.mark.parametrize("H,W,d,sigma", [(48, 48, 3, 2 / 255), (48, 36, 2, 5 / 255), (40, 40, 1, 2 / 255)])
+def test_init_sr(H, W, d, sigma):
+    """Initialisation of super-resolution (one solve per aliasing block
+    between FP32 FFTs) against the oracle's FP64 conjugate gradients; bound:
+    the FFT rounding of both transforms amplified by the block solve's gain
+    Gamma / d, Gamma^2 = max over blocks of sum_k |X_k / Y|^2."""
+    x, k, yl = sr_problem(3, H, W, d, sigma)
+    k64 = k.astype(np.float32).astype(np.float64)
+    y64 = yl.astype(np.float64)
+    lam = oracle.lam_sr(k64, H, W, d, sigma)
+    c = 0.2 * sigma ** 2 / lam
+    xo = oracle.init_sr(k64, y64, d, c)
+    gm = model()
+    xg = ep.restore(gm, dev(yl), sigma, beta_mult=(), kind=ep.CONV_DECIMATE, kernel=k, factor=d).cpu().numpy()
+    assert xg.shape == (H, W)
+    Hb = sr_blocks(k64, H, W, d)
+    h, w = H // d, W // d
+    L = np.stack([laplacian_symbol(H, W)[a * h:(a + 1) * h, b * w:(b + 1) * w] for a in range(d) for b in range(d)])
+    # X = (D + s g g^H)^-1 g Y per block: gain of each entry relative to Y
+    s = 1.0 / d ** 2
+    G = np.zeros_like(Hb, dtype=np.float64)
+    for u in range(h):
+        for v in range(w):
+            g = np.conj(Hb[:, u, v])
+            M = np.diag(c * L[:, u, v]) + s * np.outer(g, np.conj(g))
+            G[:, u, v] = np.abs(np.linalg.solve(M, g))
+    gamma = np.sqrt((G ** 2).sum(axis=0).max())
+    bound = gamma / d * (math.ceil(math.log2(h * w)) + math.ceil(math.log2(H * W))) * U * np.abs(y64).max()
+    err = np.abs(xg - xo).max()
+    assert err <= bound, (err, bound)
+
+
+@pytest.mark.parametrize("H,W,d", [(48, 48, 3), (48, 36, 2)])
+def test_image_update_sr(H, W, d):
+    sigma = 2 / 255
+    x, k, yl = sr_problem(4, H, W, d, sigma)
+    k64 = k.astype(np.float32).astype(np.float64)
+    xt = (x + 0.02 * np.random.default_rng(5).standard_normal(x.shape)).astype(np.float32)
+    lam = oracle.lam_sr(k64, H, W, d, sigma)
+    mult = 4.0
+    bs = lam * mult
+    xo = oracle.xupdate_sr(k64, yl.astype(np.float64), xt.astype(np.float64), d, bs)
+    gm = model()
+    xg = ep.image_update(gm, dev(yl), dev(xt), sigma, mult, kind=ep.CONV_DECIMATE, kernel=k,
+                         factor=d).cpu().numpy()
+    Hb = np.abs(sr_blocks(k64, H, W, d))
+    s = 1.0 / d ** 2
+    ng = (Hb ** 2).sum(axis=0)
+    gamma_y = np.sqrt(((Hb / (bs + s * ng)) ** 2).sum(axis=0).max())
+    n_lo, n_hi = math.ceil(math.log2(H * W / d ** 2)), math.ceil(math.log2(H * W))
+    bound = U * (gamma_y / d * (n_lo + n_hi) * np.abs(yl).max() + 2 * n_hi * np.abs(xt).max())
+    err = np.abs(xg - xo).max()
+    assert err <= bound, (err, bound)
+
+
+def test_sr_factor_one_equals_deconvolution_path():
+    """CONV_DECIMATE with factor 1 solves the deconvolution through the
+    aliasing-block kernels and C2C transforms; it must agree with the
+    CONV_PERIODIC path (R2C transforms, pointwise kernels) to FP32 rounding."""
+    sigma = 2 / 255
+    x, k, y = synth.deblur_problem(6, 48, sigma, W=40)
+    gm = model()
+    a = ep.restore(gm, dev(y), sigma, kind=ep.CONV_PERIODIC, kernel=k).cpu().numpy()
+    b = ep.restore(gm, dev(y), sigma, kind=ep.CONV_DECIMATE, kernel=k, factor=1).cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-4

@@ -198,6 +198,28 @@ def test_restore_inpaint(prec):
     assert np.abs(xg - xo).max() <= 1e-4
 
 
+@pytest.mark.parametrize("H,W,d,sub", [(48, 48, 3, False), (64, 48, 2, True)])
+def test_restore_super_resolution(H, W, d, sub):
+    """Super-resolution (blur then decimation by d; Sec. "Complexity via
+    eigenspace implementation", Fig. 8): the whole restoration, from the
+    low-resolution observation, within 1e-4 of the oracle's."""
+    gm, om = models(12, "fixed", 8)
+    sigma = 2 / 255
+    x = synth.image(8, H, W)
+    k = synth.gaussian_kernel(9, 1.0)
+    yl = (synth.blur_periodic(x, k)[::d, ::d] + synth.noise(8, H // d, W // d, sigma)).astype(np.float32)
+    kw = dict(subset=oracle.FRACTION, subset_param=1 / 3, seed=4) if sub else {}
+    o = ep.Options(subset=ep.SUBSET_FRACTION, subset_param=1 / 3, seed=4) if sub else ep.Options()
+    xo = oracle.restore(om, yl.astype(np.float64), sigma, deg=oracle.SR, kernel=k.astype(np.float32).astype(np.float64),
+                        factor=d, **kw)
+    xg = ep.restore(gm, dev(yl), sigma, kind=ep.CONV_DECIMATE, kernel=k, factor=d, options=o).cpu().numpy()
+    assert xg.shape == (H, W)
+    assert abs(psnr(xg, x) - psnr(xo, x)) <= 0.05
+    assert np.abs(xg - xo).max() <= 1e-4
+    xh = ep.restore_host(gm, yl, sigma, kind=ep.CONV_DECIMATE, kernel=k, factor=d, options=o)
+    assert np.abs(xh - xg).max() == 0.0
+
+
 def test_restore_inpaint_ragged_large():
     """A larger, ragged inpainting problem (the CG splits unevenly over its
     CTAs), K = 20 at full rank, every patch."""

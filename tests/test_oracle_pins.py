@@ -288,6 +288,65 @@ def test_pixelwise_update_and_cg_match_dense_solve():
     np.testing.assert_allclose(oracle.init_cg(a, y, c, 600).ravel(), ref0, atol=1e-9)
 
 
+def _dense_sr(k, H, W, d):
+    """Dense matrix of A = decimation after the periodic blur, built column by
+    column from unit images with the input generator's blur."""
+    cols = []
+    for p in range(H * W):
+        e = np.zeros(H * W)
+        e[p] = 1.0
+        cols.append(synth.blur_periodic(e.reshape(H, W), k)[::d, ::d].ravel())
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("H,W,d", [(12, 12, 3), (12, 18, 2), (10, 10, 1)])
+def test_sr_operator_lambda_and_solves_match_dense(H, W, d):
+    """Super-resolution A = S B: the oracle's A and A^T are the dense matrix
+    and its transpose; lambda = N^-1 ||A^T A||_F^2 / ||A||_2^2 computed from
+    the dense matrix; the image update and the initialisation equal dense
+    solves of (A^T A + bs I) x = A^T y + bs xt and (A^T A + c L) x = A^T y."""
+    k = synth.gaussian_kernel(7, 1.1)
+    A = _dense_sr(k, H, W, d)
+    rng = np.random.default_rng(H + W + d)
+    x = rng.random((H, W))
+    yl = rng.random((H // d, W // d))
+    np.testing.assert_allclose(oracle.sr_apply(k, x, d).ravel(), A @ x.ravel(), atol=1e-13)
+    np.testing.assert_allclose(oracle.sr_adjoint(k, yl, d).ravel(), A.T @ yl.ravel(), atol=1e-13)
+    AtA = A.T @ A
+    lam_dense = (np.sum(AtA ** 2) / (H * W)) / np.linalg.norm(A, 2) ** 2
+    sigma = 40 / 255  # cap 250 (40)^2 far above
+    assert abs(oracle.lam_sr(k, H, W, d, sigma) - lam_dense) <= 1e-12 * lam_dense
+    xt = rng.random((H, W))
+    bs = 0.21
+    ref = np.linalg.solve(AtA + bs * np.eye(H * W), A.T @ yl.ravel() + bs * xt.ravel())
+    np.testing.assert_allclose(oracle.xupdate_sr(k, yl, xt, d, bs).ravel(), ref, atol=1e-11)
+    c = 0.017
+    ref0 = np.linalg.solve(AtA + c * neg_laplacian(H, W), A.T @ yl.ravel())
+    np.testing.assert_allclose(oracle.init_sr(k, yl, d, c).ravel(), ref0, atol=1e-9)
+
+
+def test_sr_factor_one_is_the_deconvolution():
+    """With d = 1 the super-resolution operator is the periodic blur: lambda,
+    the initialisation, the image update and a whole restoration equal those
+    of the deconvolution (a Fourier-domain route)."""
+    H, W = 24, 20
+    k = synth.gaussian_kernel(9, 1.3)
+    rng = np.random.default_rng(4)
+    y = synth.blur_periodic(synth.image(3, H, W), k) + 0.01 * rng.standard_normal((H, W))
+    sigma = 0.01
+    assert abs(oracle.lam_sr(k, H, W, 1, sigma) - oracle.lam(oracle.CONV, H, W, sigma, kernel=k)) < 1e-14
+    c = 0.2 * sigma ** 2 / oracle.lam(oracle.CONV, H, W, sigma, kernel=k)
+    np.testing.assert_allclose(oracle.init_sr(k, y, 1, c), oracle.init_conv(k, y, c), atol=1e-8)
+    xt = rng.random((H, W))
+    np.testing.assert_allclose(oracle.xupdate_sr(k, y, xt, 1, 0.05), oracle.xupdate_conv(k, y, xt, 0.05),
+                               atol=1e-11)
+    g = synth.tiny_gmm(3, seed=2)
+    m = oracle.Model(g.w, g.U, g.S, "fixed", 8)
+    a = oracle.restore(m, y, sigma, (1, 4), deg=oracle.SR, kernel=k, factor=1)
+    b = oracle.restore(m, y, sigma, (1, 4), deg=oracle.CONV, kernel=k)
+    np.testing.assert_allclose(a, b, atol=1e-8)
+
+
 def test_lambda_closed_forms():
     H = W = 16
     assert oracle.lam(oracle.DENOISE, H, W, 20 / 255) == 1.0
