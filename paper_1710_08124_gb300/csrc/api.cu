@@ -588,6 +588,8 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
         return fail(EPLL_ECUDA, std::string("model upload: ") + cudaGetErrorString(e));
     }
     cg_setup();
+    group_setup();
+    sampler_setup();
     *out = g;
     return EPLL_OK;
 }

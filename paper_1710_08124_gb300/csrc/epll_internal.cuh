@@ -216,9 +216,10 @@ epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mul
 epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb, int *n,
                           int *anchors, unsigned *mult, unsigned *scratch, size_t sstride,
                           cudaStream_t st);
-// The random-fraction sampler works on tiles of FRAC_TILE anchors (256
-// threads x FRAC_ITEMS); its scratch per iteration is 1024 histogram words,
-// 16 words of selection state and two words per tile (plus two spare tiles).
+// Scratch words per iteration reserved for the samplers (histograms,
+// selection state and per-tile counts of FRAC_TILE anchors); the current
+// random-fraction sampler keeps all of it in shared memory, the reservation
+// stays part of the workspace layout.
 constexpr int FRAC_ITEMS = 8;
 constexpr int FRAC_TILE = 256 * FRAC_ITEMS;
 constexpr size_t sampler_words(size_t N) { return 1040 + 2 * (N / FRAC_TILE + 2); }
@@ -319,7 +320,9 @@ epll_status sr_init(epll_gmm *g, int H, int W, int d, double sigma, cudaStream_t
 epll_status sr_update(epll_gmm *g, int H, int W, int d, double bmult, cudaStream_t st);
 epll_status cg_init(epll_gmm *g, const float *a, const float *y, int H, int W, double sigma,
                     int iters, cudaStream_t st);  // ws.xhat (one cluster launch)
-void cg_setup();  // picks the CG kernel's cluster size; call outside stream capture
+void cg_setup();     // picks the CG kernel's cluster size; call outside stream capture
+void group_setup();  // the same for the grouping kernel
+void sampler_setup();  // the same for the random-fraction sampler
 // x = (a y + bs xt)/(a^2 + bs), bs = lambda * bmult (a == nullptr: a = 1)
 epll_status launch_pixel_update(epll_gmm *g, const float *a, const float *y, const float *xt, int H, int W,
                                 double bmult, float *x, cudaStream_t st);

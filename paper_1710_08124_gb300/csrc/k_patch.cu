@@ -4,6 +4,8 @@
 // patch reprojection by overlap-add averaging fused with the image update.
 #include "epll_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <climits>
 
@@ -443,100 +445,138 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
 __device__ __forceinline__ int clamp_k(int k, int K) { return k < 0 ? -1 : (k >= K ? K - 1 : k); }
 
 // ============================================================================
-// Grouping by component (counting sort): histogram, exclusive scan, scatter.
-// The order inside a group does not matter: every patch's estimate depends
-// only on the patch and its component.
+// Grouping by component (counting sort): histogram, exclusive scan, scatter,
+// in one launch of one thread-block cluster (16 CTAs where the device allows
+// it, else 8).  Each CTA counts the keys of its slice in shared memory; after
+// a cluster barrier every CTA reads all histograms through distributed shared
+// memory, scans the totals over the components and places its own slice
+// after the lower-ranked CTAs' entries of each component; CTA 0 also writes
+// the work items.  The order inside a group does not matter: every patch's
+// estimate depends only on the patch and its component.
 // ============================================================================
-// n_dev (nullable): the key count is min(n, mult * *n_dev).
-__global__ void k_bucket_hist(const int *__restrict__ kstar, int n, int K, int *__restrict__ counts,
-                              const int *__restrict__ n_dev, int mult)
+constexpr int EST_T = 128;  // patches per work item
+constexpr int GRP_THREADS = 1024;
+
+// Exclusive block-wide scans of two integers (fixed order); totals in *ta, *tb.
+__device__ void block_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb)
 {
-    extern __shared__ int h[];
-    if (n_dev) n = min(n, mult * *n_dev);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = 0;
-    __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int k = clamp_k(kstar[i], K);
-        if (k >= 0) atomicAdd(&h[k], 1);
+    __shared__ int wa[GRP_THREADS / 32], wb[GRP_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int ia = a, ib = b;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int va = __shfl_up_sync(0xffffffffu, ia, o), vb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += va;
+            ib += vb;
+        }
+    }
+    if (lane == 31) {
+        wa[wid] = ia;
+        wb[wid] = ib;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        if (h[k]) atomicAdd(&counts[k], h[k]);
+    if (wid == 0) {
+        int xa = wa[lane], xb = wb[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int va = __shfl_up_sync(0xffffffffu, xa, o), vb = __shfl_up_sync(0xffffffffu, xb, o);
+            if (lane >= o) {
+                xa += va;
+                xb += vb;
+            }
+        }
+        wa[lane] = xa;
+        wb[lane] = xb;
+    }
+    __syncthreads();
+    const int pa = wid ? wa[wid - 1] : 0, pb = wid ? wb[wid - 1] : 0;
+    ea = pa + ia - a;
+    eb = pb + ib - b;
+    ta = wa[31];
+    tb = wb[31];
+    __syncthreads();
 }
 
-// Exclusive scan of the per-component counts (in place, they become the
-// scatter cursors) and the work items of the estimation kernel: one item per
-// group of up to EST_T patches of one component, {k, first list position,
-// count}; items[0].w holds the number of items.
-constexpr int EST_T = 128;
-
-__global__ void __launch_bounds__(1024) k_bucket_scan(int K, int *__restrict__ counts,
-                                                      int4 *__restrict__ items)
+__global__ void __launch_bounds__(GRP_THREADS, 1)
+k_group(const int *__restrict__ keys, int n, int K, const int *__restrict__ n_dev, int mult,
+        int *__restrict__ perm, int4 *__restrict__ items)
 {
-    __shared__ int c[1024], ci[1024];
-    __shared__ int carry, icarry;
-    if (threadIdx.x == 0) carry = icarry = 0;
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    extern __shared__ int gsh[];
+    int *hist = gsh, *base = gsh + K;
+    const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+    if (n_dev) n = min(n, mult * *n_dev);
+    const int chunk = (n + nb - 1) / nb;
+    const int i0 = min(n, rank * chunk), i1 = min(n, i0 + chunk);
+    for (int k = threadIdx.x; k < K; k += GRP_THREADS) hist[k] = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < K; b0 += 1024) {
+    for (int i = i0 + threadIdx.x; i < i1; i += GRP_THREADS) {
+        const int k = clamp_k(keys[i], K);
+        if (k >= 0) atomicAdd(&hist[k], 1);
+    }
+    cl.sync();
+    int carry = 0, icarry = 0;
+    for (int b0 = 0; b0 < K; b0 += GRP_THREADS) {
         const int k = b0 + threadIdx.x;
-        const int v = k < K ? counts[k] : 0;
-        const int nv = (v + EST_T - 1) / EST_T;
-        c[threadIdx.x] = v;
-        ci[threadIdx.x] = nv;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            const int u = threadIdx.x >= off ? c[threadIdx.x - off] : 0;
-            const int ui = threadIdx.x >= off ? ci[threadIdx.x - off] : 0;
-            __syncthreads();
-            c[threadIdx.x] += u;
-            ci[threadIdx.x] += ui;
-            __syncthreads();
-        }
+        int tot = 0, below = 0;
+        if (k < K)
+            for (int r = 0; r < nb; ++r) {
+                const int v = cl.map_shared_rank(hist, r)[k];
+                tot += v;
+                below += r < rank ? v : 0;
+            }
+        const int nv = (tot + EST_T - 1) / EST_T;
+        int et, ev, tt, tv;
+        block_scan2(tot, nv, et, ev, tt, tv);
         if (k < K) {
-            const int start = carry + c[threadIdx.x] - v;
-            const int item0 = icarry + ci[threadIdx.x] - nv;
-            counts[k] = start;
-            for (int t = 0; t < nv; ++t)
-                items[1 + item0 + t] = make_int4(k, start + t * EST_T, min(EST_T, v - t * EST_T), 0);
+            const int start = carry + et;
+            base[k] = start + below;
+            if (rank == 0) {
+                const int item0 = icarry + ev;
+                for (int t = 0; t < nv; ++t)
+                    items[1 + item0 + t] = make_int4(k, start + t * EST_T, min(EST_T, tot - t * EST_T), 0);
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == 1023) {
-            carry += c[1023];
-            icarry += ci[1023];
-        }
-        __syncthreads();
+        carry += tt;
+        icarry += tv;
     }
-    if (threadIdx.x == 0) items[0] = make_int4(0, 0, 0, icarry);
+    if (rank == 0 && threadIdx.x == 0) items[0] = make_int4(0, 0, 0, icarry);
+    cl.sync();  // every CTA has read the others' histograms; base[] is local from here on
+    for (int i = i0 + threadIdx.x; i < i1; i += GRP_THREADS) {
+        const int k = clamp_k(keys[i], K);
+        if (k >= 0) perm[atomicAdd(&base[k], 1)] = i;
+    }
 }
 
-// A block places 1024 keys: per-key ranks from shared-memory counters, one
-// global reservation per key present in the block, then the writes.
-constexpr int SCAT_T = 256, SCAT_PER = 4;
-__global__ void __launch_bounds__(SCAT_T)
-k_bucket_scatter(const int *__restrict__ keys, int n, int K, int *__restrict__ cursor, int *__restrict__ perm,
-                 const int *__restrict__ n_dev, int mult)
+// Cluster size of the grouping kernel (16 where one such cluster fits with
+// the largest key range's shared memory, else 8).
+static int group_cluster_size()
 {
-    extern __shared__ int sh[];  // [K]: block counts, then the block's base in each bucket
-    if (n_dev) n = min(n, mult * *n_dev);
-    if ((int)blockIdx.x * SCAT_T * SCAT_PER >= n) return;  // whole block past the keys
-    for (int k = threadIdx.x; k < K; k += SCAT_T) sh[k] = 0;
-    __syncthreads();
-    const int i0 = blockIdx.x * SCAT_T * SCAT_PER + threadIdx.x;
-    int key[SCAT_PER], loc[SCAT_PER];
-#pragma unroll
-    for (int u = 0; u < SCAT_PER; ++u) {
-        const int i = i0 + u * SCAT_T;
-        key[u] = i < n ? clamp_k(keys[i], K) : -1;
-        loc[u] = key[u] >= 0 ? atomicAdd(&sh[key[u]], 1) : 0;
+    static int size = 0;
+    if (size) return size;
+    size = 8;
+    const int smem = 2 * 4096 * (int)sizeof(int);
+    cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaFuncSetAttribute(k_group, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(GRP_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_group, &cfg) == cudaSuccess && nclusters > 0) size = 16;
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += SCAT_T)
-        if (sh[k]) sh[k] = atomicAdd(&cursor[k], sh[k]);
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < SCAT_PER; ++u)
-        if (key[u] >= 0) perm[sh[key[u]] + loc[u]] = i0 + u * SCAT_T;
+    cudaGetLastError();
+    return size;
 }
+
+void group_setup() { (void)group_cluster_size(); }
 
 // ============================================================================
 // Patch estimation (Eqs. 15-16): chat_j = (gamma_j - gamma_P) c_j,
@@ -687,16 +727,22 @@ epll_status group_by_component(epll_gmm *g, const int *keys, int n, int *perm, i
 epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts, int *perm, int4 *items,
                          cudaStream_t st, const int *n_dev, int mult)
 {
-    // counts: [K] counts -> cursors
-    EPLL_CU(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)K, st));
-    int hb = (n + 255) / 256;
-    if (hb > 152 * 2) hb = 152 * 2;
-    k_bucket_hist<<<hb, 256, sizeof(int) * (size_t)K, st>>>(keys, n, K, counts, n_dev, mult);
-    EPLL_LAUNCHED(g);
-    k_bucket_scan<<<1, 1024, 0, st>>>(K, counts, items);
-    EPLL_LAUNCHED(g);
-    k_bucket_scatter<<<(n + SCAT_T * SCAT_PER - 1) / (SCAT_T * SCAT_PER), SCAT_T, sizeof(int) * (size_t)K, st>>>(
-        keys, n, K, counts, perm, n_dev, mult);
+    (void)counts;
+    if (K > 4096) return fail(EPLL_EUNSUPPORTED, "grouping supports at most 4096 keys");
+    const int cl = group_cluster_size();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(GRP_THREADS);
+    cfg.dynamicSmemBytes = 2 * (size_t)K * sizeof(int);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    EPLL_CU(cudaLaunchKernelEx(&cfg, k_group, keys, n, K, n_dev, mult, perm, items));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -728,41 +774,110 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // subset), divides by their number, and keeps the current estimate where no
 // sampled patch covers it.  Optionally fused with the pixelwise image update
 // xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult.
+//
+// A pair of threads owns 8 consecutive pixels of an image row, each thread
+// four of the eight patch rows u.  For each u it visits the 15 anchors
+// (i - u, j0 - 7 .. j0 + 7) whose patches cover some of the pixels; an anchor
+// outside the subset costs only its multiplicity load, a sampled one two
+// 16-byte loads of its patch row u (the 8 estimates that fall on this image
+// row), each added to the pixels it covers.  Every estimate is thus read once
+// per covering pixel group rather than once per pixel in 4-byte pieces.
+// Summation order per pixel: u = 0..3 and u = 4..7 separately (u, then anchor
+// column ascending), then the two partial sums.
 // ============================================================================
+constexpr int AG_GROUP = 8;  // pixels per thread pair
+constexpr int AG_SPLIT = 2;  // threads per pixel group, each summing PS / AG_SPLIT patch rows
+
 __global__ void __launch_bounds__(256)
 k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             const float *xhat, int H, int W, const float *__restrict__ y,
             const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
             float *xout)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= H * W) return;
-    const int i = p / W, j = p % W;
-    float sum = 0.0f;
-    unsigned cnt = 0;
+    const int gw = (W + AG_GROUP - 1) / AG_GROUP;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) / AG_SPLIT;
+    const int half = threadIdx.x & (AG_SPLIT - 1);
+    const bool live = q < H * gw;  // both threads of a pair share this
+    const int i = live ? q / gw : 0, j0 = live ? (q % gw) * AG_GROUP : 0;
+    // anchor columns j0-7 .. j0+7 need no wrap; the multiplicities load as
+    // four aligned uint4 (columns j0-8 .. j0+7) when rows start 16-byte aligned
+    const bool interior = j0 >= PS && j0 + 2 * PS - 2 < W;
+    const bool vec = interior && (W & 3) == 0 && mult;
+    float sum[AG_GROUP];
+    unsigned cnt[AG_GROUP];
 #pragma unroll
-    for (int u = 0; u < PS; ++u) {
-        int ai = i - u;
-        if (ai < 0) ai += H;
+    for (int t = 0; t < AG_GROUP; ++t) {
+        sum[t] = 0.0f;
+        cnt[t] = 0u;
+    }
+    if (live) {
+#pragma unroll 1
+        for (int uu = 0; uu < PS / AG_SPLIT; ++uu) {
+            const int u = half * (PS / AG_SPLIT) + uu;
+            int ai = i - u;
+            if (ai < 0) ai += H;
+            const size_t rowb = (size_t)ai * W;
+            unsigned m[2 * PS - 1];
+            if (vec) {
+                const uint4 *mp = reinterpret_cast<const uint4 *>(mult + rowb + j0 - PS);
+                const uint4 m0 = mp[0], m1 = mp[1], m2 = mp[2], m3 = mp[3];
+                const unsigned mm[16] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w,
+                                         m2.x, m2.y, m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
 #pragma unroll
-        for (int v = 0; v < PS; ++v) {
-            int aj = j - v;
-            if (aj < 0) aj += W;
-            const size_t an = (size_t)ai * W + aj;
-            // both loads issued together; an unsampled anchor's row is never used
-            const unsigned m = mult ? mult[an] : 1u;
-            const float z = zrow[an * PD + u * PS + v];
-            sum = m ? fmaf((float)m, z, sum) : sum;
-            cnt += m;
+                for (int o = 0; o < 2 * PS - 1; ++o) m[o] = mm[o + 1];
+            } else {
+#pragma unroll
+                for (int o = 0; o < 2 * PS - 1; ++o) {
+                    int jj = j0 - (PS - 1) + o;
+                    if (jj < 0) jj += W;
+                    else if (jj >= W) jj -= W;
+                    m[o] = mult ? mult[rowb + jj] : 1u;
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2 * PS - 1; ++o) {
+                int jj = j0 - (PS - 1) + o;
+                if (!interior) {
+                    if (jj < 0) jj += W;
+                    else if (jj >= W) jj -= W;
+                }
+                const float4 *src = reinterpret_cast<const float4 *>(zrow + (rowb + jj) * PD + u * PS);
+                const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float4 z0 = m[o] ? src[0] : zero4, z1 = m[o] ? src[1] : zero4;
+                const float zz[PS] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                const float fm = (float)m[o];
+#pragma unroll
+                for (int t = 0; t < AG_GROUP; ++t) {
+                    const int v = t + (PS - 1) - o;  // element column of this anchor that lands on pixel j0 + t
+                    if (v >= 0 && v < PS) {
+                        sum[t] = fmaf(fm, zz[v], sum[t]);
+                        cnt[t] += m[o];
+                    }
+                }
+            }
         }
     }
-    const float xt = cnt ? sum / (float)cnt : xhat[p];
-    if (y) {
-        const float bs = lamf[0] * bmult;
-        const float ap = a ? a[p] : 1.0f;
-        xout[p] = (ap * y[p] + bs * xt) / (ap * ap + bs);
-    } else {
-        xout[p] = xt;
+    // the pair's partial sums: patch rows 0..3 (even thread) then 4..7 (odd thread)
+#pragma unroll
+    for (int t = 0; t < AG_GROUP; ++t) {
+        const float so = __shfl_down_sync(0xffffffffu, sum[t], 1);
+        const unsigned co = __shfl_down_sync(0xffffffffu, cnt[t], 1);
+        sum[t] += so;
+        cnt[t] += co;
+    }
+    if (!live || half) return;
+    const float bs = y ? lamf[0] * bmult : 0.0f;
+#pragma unroll
+    for (int t = 0; t < AG_GROUP; ++t) {
+        if (j0 + t >= W) break;
+        const size_t p = (size_t)i * W + j0 + t;
+        const float xt = cnt[t] ? sum[t] / (float)cnt[t] : xhat[p];
+        if (y) {
+            const float ap = a ? a[p] : 1.0f;
+            xout[p] = (ap * y[p] + bs * xt) / (ap * ap + bs);
+        } else {
+            xout[p] = xt;
+        }
     }
 }
 
@@ -770,9 +885,9 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
                              const float *y, const float *a, const float *lamf, double bmult,
                              float *xout, cudaStream_t st)
 {
-    const int N = H * W;
-    k_aggregate<<<(N + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                 xout);
+    const int threads = H * ((W + AG_GROUP - 1) / AG_GROUP) * AG_SPLIT;
+    k_aggregate<<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+                                                      xout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

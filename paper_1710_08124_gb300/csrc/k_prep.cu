@@ -2,6 +2,7 @@
 // Gaussian selection / patch estimation steps, and the patch samplers.
 #include "epll_internal.cuh"
 
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -14,10 +15,12 @@ namespace epll {
 // compensated rescoring).  1/beta = sigma^2 / (lambda * mult) with lambda read
 // from device memory, or 1/beta_direct when beta_direct > 0.
 // ============================================================================
+// Sum over the first 64 threads of the block (fixed order); every thread of
+// the block must call it.
 __device__ double block64_sum(double v, double *red)
 {
     int j = threadIdx.x;
-    red[j] = v;
+    if (j < 64) red[j] = v;
     __syncthreads();
     for (int s = 32; s > 0; s >>= 1) {
         if (j < s) red[j] += red[j + s];
@@ -44,8 +47,11 @@ struct Mults {
     double m[TB_MAX];
 };
 
-// Grid (K, nb): component k of batch slot blockIdx.y.
-__global__ void __launch_bounds__(64)
+// Grid (K, nb): component k of batch slot blockIdx.y; 256 threads: the
+// first 64 compute the per-component and per-column quantities, all of them
+// then scale the basis four columns at a time.
+constexpr int TAB_THREADS = 256;
+__global__ void __launch_bounds__(TAB_THREADS)
 k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restrict__ roff,
          const double *__restrict__ S, const double *__restrict__ w, const double *__restrict__ lam,
          const double *__restrict__ d_lambda, Mults mults, double sigma2, double beta_direct,
@@ -54,7 +60,8 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
     __shared__ float tile[PD][PD + 1];  // one 64-column chunk of the basis, padded rows
-    const int k = blockIdx.x, j = threadIdx.x;
+    const int k = blockIdx.x, j = threadIdx.x & (PD - 1), cg4 = threadIdx.x >> 6;
+    const bool lead = threadIdx.x < PD;
     const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
     const double mult = mults.m[blockIdx.y];
     const double ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
@@ -65,7 +72,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     const double nuP = lam[k] + ib;
     const double t = rk < PD ? 1.0 / nuP : 0.0;
     const double gP = rk < PD ? lam[k] / nuP : 0.0;
-    if (j == 0) {
+    if (threadIdx.x == 0) {
         double cst = ck - c0;
         float h = (float)cst;
         tab.cst_hi[k] = h;
@@ -81,7 +88,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
         atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int((float)(1.0 / numin)));
     }
     const int o = roff[k], rp = roff[k + 1] - o;
-    for (int jj = j; jj < rp; jj += 64) {
+    for (int jj = j; lead && jj < rp; jj += 64) {
         double q = 0.0, gw = 0.0;
         if (jj < rk) {
             double nu = S[(size_t)k * PD + jj] + ib;
@@ -100,15 +107,15 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     if (fmt & 8) {
         // per-component scale of the E4M3 basis: the largest |value| maps to 448
         float m = 0.0f;
-        for (int jj = 0; jj < rk; ++jj) m = fmaxf(m, fabsf(B[(size_t)j * Rtot + o + jj] * sq[jj]));
-        red[j] = m;
+        for (int jj = 0; lead && jj < rk; ++jj) m = fmaxf(m, fabsf(B[(size_t)j * Rtot + o + jj] * sq[jj]));
+        if (lead) red[j] = m;
         __syncthreads();
         for (int st = 32; st > 0; st >>= 1) {
-            if (j < st) red[j] = fmax(red[j], red[j + st]);
+            if (threadIdx.x < st) red[j] = fmax(red[j], red[j + st]);
             __syncthreads();
         }
         s8 = red[0] > 0.0 ? (float)red[0] / 448.0f : 1.0f;
-        if (j == 0) tab.k8s2[k] = s8 * s8;
+        if (threadIdx.x == 0) tab.k8s2[k] = s8 * s8;
     }
     // scaled basis, K-major: B[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
     // split form stores the BF16 value and the BF16 remainder.  B is e-major,
@@ -116,14 +123,14 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     // (coalesced), written along e (coalesced).
     for (int c0 = 0; c0 < rp; c0 += PD) {
         __syncthreads();  // the previous chunk's reads of tile are done
-#pragma unroll 8
-        for (int e = 0; e < PD; ++e) {
+#pragma unroll 4
+        for (int e = cg4; e < PD; e += TAB_THREADS / PD) {
             const int jj = c0 + j;
             tile[e][j] = (jj < rk) ? B[(size_t)e * Rtot + o + jj] : 0.0f;
         }
         __syncthreads();
         const int nc = min(PD, rp - c0);
-        for (int jl = 0; jl < nc; ++jl) {
+        for (int jl = cg4; jl < nc; jl += TAB_THREADS / PD) {
             const int jj = c0 + jl;
             const float v = (jj < rk) ? tile[j][jl] * sq[jj] : 0.0f;
             const size_t dst = (size_t)(o + jj) * PD + j;
@@ -145,7 +152,7 @@ epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mul
     Mults m{};
     for (int b = 0; b < nb; ++b) m.m[b] = mult[b];
     EPLL_CU(cudaMemsetAsync(g->tab0.tmax, 0, sizeof(float) * nb, st));
-    k_tables<<<dim3(g->K, nb), 64, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
+    k_tables<<<dim3(g->K, nb), TAB_THREADS, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
                                             g->d_lam, d_lambda, m, sigma2, beta_direct, g->d_B, g->tab0, fmt);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
@@ -214,165 +221,160 @@ __device__ __forceinline__ uint32_t frac_key(uint64_t st, int a)
     return (uint32_t)(draw(st, (uint64_t)a) >> 32);
 }
 
-// Scratch of batch slot b (t = t0 + b) starts at scratch + b * sstride:
-// [0, 1024) histograms of the 4 passes, [1024, 1027) sel, from 1040 the tiles.
-__global__ void __launch_bounds__(256)
-k_frac_hist(int N, uint64_t seed, int t0, int pass, unsigned *__restrict__ scratch, size_t sstride)
+// One launch: a thread-block cluster per iteration of the batch (16 CTAs
+// where the device allows it, else 8) splits the N anchors into contiguous
+// slices.  Each radix pass, every CTA builds the 256-bin histogram of its
+// slice's keys that match the threshold determined so far; after a cluster
+// barrier every CTA sums all histograms through distributed shared memory (in
+// rank order) and takes the same digit.  The compaction then counts, per CTA,
+// the keys below / equal to the threshold, exchanges the counts the same way
+// (each CTA's base is the sum over lower ranks), and writes its slice's
+// selected anchors in anchor order: tiles of 1024 x 8 consecutive anchors,
+// each thread eight of them, positions from a block-wide scan.
+constexpr int FS_THREADS = 1024;
+
+__device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long &total)
 {
-    __shared__ unsigned h[256];
-    const int t = t0 + blockIdx.y;
-    unsigned *hist = scratch + blockIdx.y * sstride;
-    const unsigned *sel = hist + 1024;
-    h[threadIdx.x] = 0;
+    __shared__ unsigned long long ws_[FS_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws_[wid] = x;
     __syncthreads();
-    const uint64_t st = stream_state(seed, (uint64_t)t);
-    const int shift = 24 - 8 * pass;
-    const unsigned prefix = pass ? sel[0] : 0u, mask = pass ? sel[1] : 0u;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
-        uint32_t key = frac_key(st, a);
-        if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+    if (wid == 0) {
+        unsigned long long z = ws_[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        ws_[lane] = z;
     }
     __syncthreads();
-    if (h[threadIdx.x]) atomicAdd(&hist[pass * 256 + threadIdx.x], h[threadIdx.x]);
+    const unsigned long long before = (wid ? ws_[wid - 1] : 0ull) + x - v;
+    total = ws_[31];
+    __syncthreads();
+    return before;
 }
 
-__global__ void __launch_bounds__(256)
-k_frac_pick(int pass, int M, unsigned *__restrict__ scratch, size_t sstride)
+__global__ void __launch_bounds__(FS_THREADS, 1)
+k_frac_cluster(int N, int M, uint64_t seed, int t0, int *__restrict__ anchors_all,
+               unsigned *__restrict__ mult_all)
 {
-    __shared__ unsigned c[256];
-    const unsigned *hist = scratch + blockIdx.y * sstride;
-    unsigned *sel = scratch + blockIdx.y * sstride + 1024;
-    const int d = threadIdx.x;
-    const unsigned hd = hist[pass * 256 + d];
-    c[d] = hd;
-    __syncthreads();
-    // inclusive scan (Hillis-Steele)
-    for (int off = 1; off < 256; off <<= 1) {
-        unsigned v = d >= off ? c[d - off] : 0u;
-        __syncthreads();
-        c[d] += v;
-        __syncthreads();
-    }
-    const unsigned before = c[d] - hd;
-    const unsigned R = pass ? sel[2] : (unsigned)(M - 1);
-    const unsigned prefix = pass ? sel[0] : 0u, mask = pass ? sel[1] : 0u;
-    __syncthreads();
-    if (hd && before <= R && R < before + hd) {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long cnt_s;  // (less << 32) | eq of this CTA's slice
+    __shared__ unsigned sel[3];           // prefix, mask, rank
+    const int nb = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int slot = blockIdx.x / nb;
+    const int t = t0 + slot;
+    int *anchors = anchors_all + (size_t)slot * N;
+    unsigned *mult = mult_all + (size_t)slot * N;
+    const uint64_t st = stream_state(seed, (uint64_t)t);
+    const int chunk = (N + nb - 1) / nb;
+    const int a0 = min(N, rank * chunk), a1 = min(N, a0 + chunk);
+    unsigned prefix = 0u, mask = 0u, R = (unsigned)(M - 1);
+    for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
-        sel[0] = prefix | ((unsigned)d << shift);
-        sel[1] = mask | (255u << shift);
-        sel[2] = R - before;
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
+        __syncthreads();
+        for (int a = a0 + threadIdx.x; a < a1; a += FS_THREADS) {
+            const uint32_t key = frac_key(st, a);
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        cl.sync();
+        unsigned hd = 0u;
+        if (threadIdx.x < 256)
+            for (int r = 0; r < nb; ++r) hd += cl.map_shared_rank(hist, r)[threadIdx.x];
+        unsigned long long tot;
+        const unsigned before = (unsigned)block_excl_scan_u64(threadIdx.x < 256 ? hd : 0u, tot);
+        if (threadIdx.x < 256 && hd && before <= R && R < before + hd) {
+            sel[0] = prefix | ((unsigned)threadIdx.x << shift);
+            sel[1] = mask | (255u << shift);
+            sel[2] = R - before;
+        }
+        cl.sync();  // the digit is known and nobody reads the histograms any more
+        prefix = sel[0];
+        mask = sel[1];
+        R = sel[2];
+    }
+    const uint32_t thr = prefix;
+    const unsigned need = R + 1u;  // keys equal to thr that are selected
+    // counts of this slice, then the sums over the lower ranks
+    unsigned less = 0u, eq = 0u;
+    for (int a = a0 + threadIdx.x; a < a1; a += FS_THREADS) {
+        const uint32_t key = frac_key(st, a);
+        less += key < thr;
+        eq += key == thr;
+    }
+    unsigned long long tot;
+    (void)block_excl_scan_u64(((unsigned long long)less << 32) | eq, tot);
+    if (threadIdx.x == 0) cnt_s = tot;
+    cl.sync();
+    unsigned long long base = 0ull;
+    for (int r = 0; r < rank; ++r) base += *cl.map_shared_rank(&cnt_s, r);
+    cl.sync();  // no CTA reads another's shared memory after this
+    unsigned lb = (unsigned)(base >> 32), eb = (unsigned)(base & 0xffffffffu);
+    for (int tb = a0; tb < a1; tb += FS_THREADS * FRAC_ITEMS) {
+        const int b = tb + threadIdx.x * FRAC_ITEMS;
+        uint32_t keys[FRAC_ITEMS];
+        unsigned l = 0u, e = 0u;
+#pragma unroll
+        for (int q = 0; q < FRAC_ITEMS; ++q) {
+            const int a = b + q;
+            keys[q] = a < a1 ? frac_key(st, a) : 0xffffffffu;
+            if (a < a1) {
+                l += keys[q] < thr;
+                e += keys[q] == thr;
+            }
+        }
+        unsigned long long ttot;
+        const unsigned long long pre = block_excl_scan_u64(((unsigned long long)l << 32) | e, ttot);
+        unsigned ml = lb + (unsigned)(pre >> 32), me = eb + (unsigned)(pre & 0xffffffffu);
+#pragma unroll
+        for (int q = 0; q < FRAC_ITEMS; ++q) {
+            const int a = b + q;
+            if (a >= a1) break;
+            const bool take = keys[q] < thr || (keys[q] == thr && me < need);
+            if (take) anchors[ml + (me < need ? me : need)] = a;
+            mult[a] = take ? 1u : 0u;
+            ml += keys[q] < thr;
+            me += keys[q] == thr;
+        }
+        lb += (unsigned)(ttot >> 32);
+        eb += (unsigned)(ttot & 0xffffffffu);
     }
 }
 
-// phase 1: per-tile counts of keys below / equal to the threshold
-__global__ void __launch_bounds__(256)
-k_frac_count(int N, uint64_t seed, int t0, unsigned *__restrict__ scratch, size_t sstride)
+// Cluster size of the fraction sampler (16 where one such cluster fits, else 8).
+static int frac_cluster_size()
 {
-    __shared__ unsigned long long red[256];
-    const int t = t0 + blockIdx.y;
-    const unsigned *sel = scratch + blockIdx.y * sstride + 1024;
-    unsigned long long *tile = reinterpret_cast<unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
-    const uint64_t st = stream_state(seed, (uint64_t)t);
-    const uint32_t thr = sel[0];
-    unsigned less = 0, eq = 0;
-    const int base = blockIdx.x * FRAC_TILE + threadIdx.x * FRAC_ITEMS;
-    for (int q = 0; q < FRAC_ITEMS; ++q) {
-        int a = base + q;
-        if (a < N) {
-            uint32_t key = frac_key(st, a);
-            less += key < thr;
-            eq += key == thr;
-        }
+    static int size = 0;
+    if (size) return size;
+    size = 8;
+    if (cudaFuncSetAttribute(k_frac_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(FS_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_frac_cluster, &cfg) == cudaSuccess && nclusters > 0)
+            size = 16;
     }
-    red[threadIdx.x] = ((unsigned long long)less << 32) | eq;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) tile[blockIdx.x] = red[0];
+    cudaGetLastError();
+    return size;
 }
 
-// phase 2: exclusive scan of the tile counts (one block)
-__global__ void __launch_bounds__(1024)
-k_frac_scan(int ntiles, unsigned *__restrict__ scratch, size_t sstride)
-{
-    unsigned long long *tile = reinterpret_cast<unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
-    __shared__ unsigned long long c[1024];
-    __shared__ unsigned long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
-        int b = b0 + threadIdx.x;
-        unsigned long long v = b < ntiles ? tile[b] : 0ull;
-        c[threadIdx.x] = v;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            unsigned long long u = threadIdx.x >= off ? c[threadIdx.x - off] : 0ull;
-            __syncthreads();
-            c[threadIdx.x] += u;
-            __syncthreads();
-        }
-        if (b < ntiles) tile[b] = carry + c[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += c[1023];
-        __syncthreads();
-    }
-}
-
-// phase 3: write the selected anchors in increasing order
-__global__ void __launch_bounds__(256)
-k_frac_write(int N, uint64_t seed, int t0, const unsigned *__restrict__ scratch, size_t sstride,
-             int *__restrict__ anchors_all, unsigned *__restrict__ mult_all)
-{
-    __shared__ unsigned long long c[256];
-    const int t = t0 + blockIdx.y;
-    const unsigned *sel = scratch + blockIdx.y * sstride + 1024;
-    const unsigned long long *tile =
-        reinterpret_cast<const unsigned long long *>(scratch + blockIdx.y * sstride + 1040);
-    int *anchors = anchors_all + (size_t)blockIdx.y * N;
-    unsigned *mult = mult_all + (size_t)blockIdx.y * N;
-    const uint64_t st = stream_state(seed, (uint64_t)t);
-    const uint32_t thr = sel[0];
-    const unsigned need = sel[2] + 1u;  // keys equal to thr that are selected
-    const int base = blockIdx.x * FRAC_TILE + threadIdx.x * FRAC_ITEMS;
-    uint32_t keys[FRAC_ITEMS];
-    unsigned less = 0, eq = 0;
-    for (int q = 0; q < FRAC_ITEMS; ++q) {
-        int a = base + q;
-        keys[q] = a < N ? frac_key(st, a) : 0xffffffffu;
-        if (a < N) {
-            less += keys[q] < thr;
-            eq += keys[q] == thr;
-        }
-    }
-    const unsigned long long mine = ((unsigned long long)less << 32) | eq;
-    c[threadIdx.x] = mine;
-    __syncthreads();
-    for (int off = 1; off < 256; off <<= 1) {
-        unsigned long long u = threadIdx.x >= off ? c[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        c[threadIdx.x] += u;
-        __syncthreads();
-    }
-    unsigned long long before = tile[blockIdx.x] + c[threadIdx.x] - mine;
-    unsigned lb = (unsigned)(before >> 32), eb = (unsigned)(before & 0xffffffffu);
-    for (int q = 0; q < FRAC_ITEMS; ++q) {
-        int a = base + q;
-        if (a >= N) break;
-        bool take = false;
-        if (keys[q] < thr) {
-            take = true;
-        } else if (keys[q] == thr) {
-            take = eb < need;
-        }
-        if (take) anchors[lb + (eb < need ? eb : need)] = a;
-        mult[a] = take ? 1u : 0u;
-        lb += keys[q] < thr;
-        eb += keys[q] == thr;
-    }
-}
+void sampler_setup() { (void)frac_cluster_size(); }
 
 int sample_count(int H, int W, const epll_options &o)
 {
@@ -406,23 +408,22 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
         EPLL_LAUNCHED(g);
         return EPLL_OK;
     }
-    // FRACTION
-    for (int b = 0; b < nb; ++b)
-        EPLL_CU(cudaMemsetAsync(scratch + b * sstride, 0, sizeof(unsigned) * 1024, st));
-    int hb = (N + 255) / 256;
-    if (hb > 152 * 4) hb = 152 * 4;
-    for (int pass = 0; pass < 4; ++pass) {
-        k_frac_hist<<<dim3(hb, nb), 256, 0, st>>>(N, o.seed, t0, pass, scratch, sstride);
-        EPLL_LAUNCHED(g);
-        k_frac_pick<<<dim3(1, nb), 256, 0, st>>>(pass, *n, scratch, sstride);
-        EPLL_LAUNCHED(g);
-    }
-    const int ntiles = (N + FRAC_TILE - 1) / FRAC_TILE;
-    k_frac_count<<<dim3(ntiles, nb), 256, 0, st>>>(N, o.seed, t0, scratch, sstride);
-    EPLL_LAUNCHED(g);
-    k_frac_scan<<<dim3(1, nb), 1024, 0, st>>>(ntiles, scratch, sstride);
-    EPLL_LAUNCHED(g);
-    k_frac_write<<<dim3(ntiles, nb), 256, 0, st>>>(N, o.seed, t0, scratch, sstride, anchors, mult);
+    // FRACTION: one cluster per iteration of the batch
+    (void)scratch;
+    (void)sstride;
+    const int cls = frac_cluster_size();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cls * nb);
+    cfg.blockDim = dim3(FS_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cls;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    EPLL_CU(cudaLaunchKernelEx(&cfg, k_frac_cluster, N, *n, o.seed, t0, anchors, mult));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
