@@ -132,10 +132,12 @@ cudaError_t alloc_tables(epll_gmm *g)
     A(dalloc(&T0.B1, (size_t)TB_MAX * R * PD));
     A(dalloc(&T0.Bs, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.Bs_lo, (size_t)TB_MAX * R * PD));
     A(dalloc(&T0.B8, (size_t)TB_MAX * R * PD)); A(dalloc(&T0.k8s2, TB_MAX * K));
+    A(dalloc(&T0.k8s, TB_MAX * K)); A(dalloc(&T0.sq, (size_t)TB_MAX * Rp));
     if (e != cudaSuccess) return e;
     A(cudaMemset(T0.q_hi, 0, sizeof(float) * (size_t)TB_MAX * Rp));
     A(cudaMemset(T0.q_lo, 0, sizeof(float) * (size_t)TB_MAX * Rp));
     A(cudaMemset(T0.gw, 0, sizeof(float) * (size_t)TB_MAX * Rp));
+    A(cudaMemset(T0.sq, 0, sizeof(float) * (size_t)TB_MAX * Rp));
     A(cudaMemset(T0.B1, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
     A(cudaMemset(T0.Bs, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
     A(cudaMemset(T0.Bs_lo, 0, sizeof(uint16_t) * (size_t)TB_MAX * R * PD));
@@ -148,7 +150,7 @@ static void free_tables(epll_gmm *g)
 {
     void *ptrs[] = {g->tab0.cst_hi, g->tab0.cst_lo, g->tab0.t_hi, g->tab0.t_lo, g->tab0.gp, g->tab0.sgn,
                     g->tab0.q_hi, g->tab0.q_lo, g->tab0.gw, g->tab0.tmax, g->tab0.ibeta, g->tab0.B1, g->tab0.Bs,
-                    g->tab0.Bs_lo, g->tab0.B8, g->tab0.k8s2};
+                    g->tab0.Bs_lo, g->tab0.B8, g->tab0.k8s2, g->tab0.k8s, g->tab0.sq};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->tab0 = Tables();

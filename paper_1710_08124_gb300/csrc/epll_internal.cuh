@@ -41,6 +41,8 @@ struct Tables {
     uint16_t *Bs_lo = nullptr;                   // [Rtot][64]: BF16 remainder (split form)
     uint8_t *B8 = nullptr;                       // [Rtot][64]: E4M3 Ubar * sqrt|q| / s_k
     float *k8s2 = nullptr;                       // [K]: s_k^2 of the E4M3 basis
+    float *k8s = nullptr;                        // [K]: s_k
+    float *sq = nullptr;                         // [Rtot]: sqrt|q_kj| (0 beyond each rank), the basis scale
 };
 
 // Relative score error bound of the split BF16 form (hi*hi + lo*hi + hi*lo):
@@ -65,6 +67,7 @@ __host__ __device__ inline Tables slot_tables(Tables t, int slot, int K, int Rp,
     t.ibeta += slot;
     t.B1 += (size_t)slot * Rtot * 64; t.Bs += (size_t)slot * Rtot * 64; t.Bs_lo += (size_t)slot * Rtot * 64;
     t.B8 += (size_t)slot * Rtot * 64; t.k8s2 += (size_t)slot * K;
+    t.k8s += (size_t)slot * K; t.sq += (size_t)slot * Rp;
     return t;
 }
 

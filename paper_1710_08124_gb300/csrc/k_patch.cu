@@ -775,17 +775,17 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // sampled patch covers it.  Optionally fused with the pixelwise image update
 // xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult.
 //
-// A pair of threads owns 8 consecutive pixels of an image row, each thread
-// four of the eight patch rows u.  For each u it visits the 15 anchors
+// Two threads own 8 consecutive pixels of an image row, each thread four of
+// the eight patch rows u.  For each u it visits the 15 anchors
 // (i - u, j0 - 7 .. j0 + 7) whose patches cover some of the pixels; an anchor
 // outside the subset costs only its multiplicity load, a sampled one two
 // 16-byte loads of its patch row u (the 8 estimates that fall on this image
 // row), each added to the pixels it covers.  Every estimate is thus read once
 // per covering pixel group rather than once per pixel in 4-byte pieces.
-// Summation order per pixel: u = 0..3 and u = 4..7 separately (u, then anchor
-// column ascending), then the two partial sums.
+// Summation order per pixel: each thread's four rows (u, then anchor column
+// ascending), then the two partial sums.
 // ============================================================================
-constexpr int AG_GROUP = 8;  // pixels per thread pair
+constexpr int AG_GROUP = 8;  // pixels per thread group
 constexpr int AG_SPLIT = 2;  // threads per pixel group, each summing PS / AG_SPLIT patch rows
 
 __global__ void __launch_bounds__(256)
@@ -797,7 +797,7 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
     const int gw = (W + AG_GROUP - 1) / AG_GROUP;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / AG_SPLIT;
     const int half = threadIdx.x & (AG_SPLIT - 1);
-    const bool live = q < H * gw;  // both threads of a pair share this
+    const bool live = q < H * gw;  // every thread of a group shares this
     const int i = live ? q / gw : 0, j0 = live ? (q % gw) * AG_GROUP : 0;
     // anchor columns j0-7 .. j0+7 need no wrap; the multiplicities load as
     // four aligned uint4 (columns j0-8 .. j0+7) when rows start 16-byte aligned
@@ -857,13 +857,16 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             }
         }
     }
-    // the pair's partial sums: patch rows 0..3 (even thread) then 4..7 (odd thread)
+    // the group's partial sums (patch rows 4h .. 4h + 3 in thread h)
 #pragma unroll
-    for (int t = 0; t < AG_GROUP; ++t) {
-        const float so = __shfl_down_sync(0xffffffffu, sum[t], 1);
-        const unsigned co = __shfl_down_sync(0xffffffffu, cnt[t], 1);
-        sum[t] += so;
-        cnt[t] += co;
+    for (int o = 1; o < AG_SPLIT; o <<= 1) {
+#pragma unroll
+        for (int t = 0; t < AG_GROUP; ++t) {
+            const float so = __shfl_down_sync(0xffffffffu, sum[t], o);
+            const unsigned co = __shfl_down_sync(0xffffffffu, cnt[t], o);
+            sum[t] += so;
+            cnt[t] += co;
+        }
     }
     if (!live || half) return;
     const float bs = y ? lamf[0] * bmult : 0.0f;

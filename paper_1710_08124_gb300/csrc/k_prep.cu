@@ -47,11 +47,10 @@ struct Mults {
     double m[TB_MAX];
 };
 
-// Grid (K, nb): component k of batch slot blockIdx.y; 256 threads: the
-// first 64 compute the per-component and per-column quantities, all of them
-// then scale the basis four columns at a time.
-constexpr int TAB_THREADS = 256;
-__global__ void __launch_bounds__(TAB_THREADS)
+// Grid (K, nb): component k of batch slot blockIdx.y, 64 threads: the
+// per-component constants, the per-column q, Wiener gains and basis scale
+// sqrt|q|, and (E4M3 basis) the component's scale.
+__global__ void __launch_bounds__(64)
 k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restrict__ roff,
          const double *__restrict__ S, const double *__restrict__ w, const double *__restrict__ lam,
          const double *__restrict__ d_lambda, Mults mults, double sigma2, double beta_direct,
@@ -59,9 +58,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
 {
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
-    __shared__ float tile[PD][PD + 1];  // one 64-column chunk of the basis, padded rows
-    const int k = blockIdx.x, j = threadIdx.x & (PD - 1), cg4 = threadIdx.x >> 6;
-    const bool lead = threadIdx.x < PD;
+    const int k = blockIdx.x, j = threadIdx.x;
     const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
     const double mult = mults.m[blockIdx.y];
     const double ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
@@ -72,7 +69,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
     const double nuP = lam[k] + ib;
     const double t = rk < PD ? 1.0 / nuP : 0.0;
     const double gP = rk < PD ? lam[k] / nuP : 0.0;
-    if (threadIdx.x == 0) {
+    if (j == 0) {
         double cst = ck - c0;
         float h = (float)cst;
         tab.cst_hi[k] = h;
@@ -88,7 +85,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
         atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int((float)(1.0 / numin)));
     }
     const int o = roff[k], rp = roff[k + 1] - o;
-    for (int jj = j; lead && jj < rp; jj += 64) {
+    for (int jj = j; jj < rp; jj += 64) {
         double q = 0.0, gw = 0.0;
         if (jj < rk) {
             double nu = S[(size_t)k * PD + jj] + ib;
@@ -99,49 +96,63 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
         tab.q_hi[o + jj] = qh;
         tab.q_lo[o + jj] = (float)(q - (double)qh);
         tab.gw[o + jj] = (float)gw;
-        sq[jj] = (float)sqrt(fabs(q));
+        const float sv = jj < rk ? sqrtf(fabsf(qh)) : 0.0f;  // basis scale: FP32 suffices
+        sq[jj] = sv;
+        tab.sq[o + jj] = sv;
     }
-    if (!fmt) return;
+    if (!(fmt & 8)) return;
     __syncthreads();
-    float s8 = 1.0f;
-    if (fmt & 8) {
-        // per-component scale of the E4M3 basis: the largest |value| maps to 448
-        float m = 0.0f;
-        for (int jj = 0; lead && jj < rk; ++jj) m = fmaxf(m, fabsf(B[(size_t)j * Rtot + o + jj] * sq[jj]));
-        if (lead) red[j] = m;
+    // per-component scale of the E4M3 basis: the largest |value| maps to 448
+    float m = 0.0f;
+    for (int jj = 0; jj < rk; ++jj) m = fmaxf(m, fabsf(B[(size_t)j * Rtot + o + jj] * sq[jj]));
+    red[j] = m;
+    __syncthreads();
+    for (int st = 32; st > 0; st >>= 1) {
+        if (j < st) red[j] = fmax(red[j], red[j + st]);
         __syncthreads();
-        for (int st = 32; st > 0; st >>= 1) {
-            if (threadIdx.x < st) red[j] = fmax(red[j], red[j + st]);
-            __syncthreads();
-        }
-        s8 = red[0] > 0.0 ? (float)red[0] / 448.0f : 1.0f;
-        if (threadIdx.x == 0) tab.k8s2[k] = s8 * s8;
     }
-    // scaled basis, K-major: B[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
-    // split form stores the BF16 value and the BF16 remainder.  B is e-major,
-    // so 64-column chunks go through shared memory: read along the columns
-    // (coalesced), written along e (coalesced).
-    for (int c0 = 0; c0 < rp; c0 += PD) {
-        __syncthreads();  // the previous chunk's reads of tile are done
-#pragma unroll 4
-        for (int e = cg4; e < PD; e += TAB_THREADS / PD) {
-            const int jj = c0 + j;
-            tile[e][j] = (jj < rk) ? B[(size_t)e * Rtot + o + jj] : 0.0f;
+    const float s8 = red[0] > 0.0 ? (float)red[0] / 448.0f : 1.0f;
+    if (j == 0) {
+        tab.k8s2[k] = s8 * s8;
+        tab.k8s[k] = s8;
+    }
+}
+
+// Scaled bases, K-major: Bx[col][e] = 16-bit(U[e][col] * sqrt|q_col|); the
+// split form stores the BF16 value and the BF16 remainder; E4M3 divides by
+// the component's scale.  B is e-major, so a block transposes a 32-column x
+// 64-row tile through shared memory: read along the columns, written along e.
+// Grid (Rtot / 32, nb), 256 threads.
+__global__ void __launch_bounds__(256)
+k_scale_basis(int K, int Rtot, int Rp, const int *__restrict__ colk, const float *__restrict__ B, Tables tab0,
+              int fmt)
+{
+    __shared__ float tile[PD][33];
+    const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
+    const int c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+#pragma unroll
+    for (int e = ty; e < PD; e += 8) tile[e][tx] = B[(size_t)e * Rtot + c0 + tx] * tab.sq[c0 + tx];
+    __syncthreads();
+    // write: column c0 + cl, elements e = 2 tx, 2 tx + 1 (32 threads cover one 64-element row)
+#pragma unroll
+    for (int cl = ty; cl < 32; cl += 8) {
+        const int col = c0 + cl;
+        const size_t dst = (size_t)col * PD + 2 * tx;
+        const float v0 = tile[2 * tx][cl], v1 = tile[2 * tx + 1][cl];
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        if (fmt & 1) *reinterpret_cast<__nv_bfloat162 *>(tab.B1 + dst) = h;
+        if (fmt & 2) *reinterpret_cast<__half2 *>(tab.B1 + dst) = __floats2half2_rn(v0, v1);
+        if (fmt & 4) {
+            *reinterpret_cast<__nv_bfloat162 *>(tab.Bs + dst) = h;
+            *reinterpret_cast<__nv_bfloat162 *>(tab.Bs_lo + dst) =
+                __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
         }
-        __syncthreads();
-        const int nc = min(PD, rp - c0);
-        for (int jl = cg4; jl < nc; jl += TAB_THREADS / PD) {
-            const int jj = c0 + jl;
-            const float v = (jj < rk) ? tile[j][jl] * sq[jj] : 0.0f;
-            const size_t dst = (size_t)(o + jj) * PD + j;
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            if (fmt & 1) tab.B1[dst] = __bfloat16_as_ushort(h);
-            if (fmt & 2) tab.B1[dst] = __half_as_ushort(__float2half_rn(v));
-            if (fmt & 4) {
-                tab.Bs[dst] = __bfloat16_as_ushort(h);
-                tab.Bs_lo[dst] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
-            }
-            if (fmt & 8) tab.B8[dst] = (uint8_t)__nv_cvt_float_to_fp8(v / s8, __NV_SATFINITE, __NV_E4M3);
+        if (fmt & 8) {
+            const int k = colk[col];
+            const float s8 = k >= 0 && k < K ? tab.k8s[k] : 1.0f;
+            tab.B8[dst] = (uint8_t)__nv_cvt_float_to_fp8(v0 / s8, __NV_SATFINITE, __NV_E4M3);
+            tab.B8[dst + 1] = (uint8_t)__nv_cvt_float_to_fp8(v1 / s8, __NV_SATFINITE, __NV_E4M3);
         }
     }
 }
@@ -152,9 +163,14 @@ epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mul
     Mults m{};
     for (int b = 0; b < nb; ++b) m.m[b] = mult[b];
     EPLL_CU(cudaMemsetAsync(g->tab0.tmax, 0, sizeof(float) * nb, st));
-    k_tables<<<dim3(g->K, nb), TAB_THREADS, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
+    k_tables<<<dim3(g->K, nb), 64, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
                                             g->d_lam, d_lambda, m, sigma2, beta_direct, g->d_B, g->tab0, fmt);
     EPLL_LAUNCHED(g);
+    if (fmt) {
+        k_scale_basis<<<dim3(g->Rtot / 32, nb), 256, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_colk, g->d_B, g->tab0,
+                                                              fmt);
+        EPLL_LAUNCHED(g);
+    }
     return EPLL_OK;
 }
 
@@ -230,7 +246,8 @@ __device__ __forceinline__ uint32_t frac_key(uint64_t st, int a)
 // the keys below / equal to the threshold, exchanges the counts the same way
 // (each CTA's base is the sum over lower ranks), and writes its slice's
 // selected anchors in anchor order: tiles of 1024 x 8 consecutive anchors,
-// each thread eight of them, positions from a block-wide scan.
+// each thread eight of them, positions from a block-wide scan.  The keys are
+// hashed once when the slice fits in shared memory.
 constexpr int FS_THREADS = 1024;
 
 __device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long &total)
@@ -259,10 +276,15 @@ __device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned
     return before;
 }
 
+// Keys of a slice are cached in dynamic shared memory when the slice fits
+// (`cached`), else recomputed in every pass.
+constexpr int FS_CACHE_BYTES = 160 * 1024;
+
 __global__ void __launch_bounds__(FS_THREADS, 1)
-k_frac_cluster(int N, int M, uint64_t seed, int t0, int *__restrict__ anchors_all,
+k_frac_cluster(int N, int M, uint64_t seed, int t0, int cached, int *__restrict__ anchors_all,
                unsigned *__restrict__ mult_all)
 {
+    extern __shared__ uint32_t kc[];
     namespace cgx = cooperative_groups;
     cgx::cluster_group cl = cgx::this_cluster();
     __shared__ unsigned hist[256];
@@ -282,7 +304,13 @@ k_frac_cluster(int N, int M, uint64_t seed, int t0, int *__restrict__ anchors_al
         if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
         __syncthreads();
         for (int a = a0 + threadIdx.x; a < a1; a += FS_THREADS) {
-            const uint32_t key = frac_key(st, a);
+            uint32_t key;
+            if (cached && pass) {
+                key = kc[a - a0];
+            } else {
+                key = frac_key(st, a);
+                if (cached) kc[a - a0] = key;
+            }
             if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
         }
         cl.sync();
@@ -306,7 +334,7 @@ k_frac_cluster(int N, int M, uint64_t seed, int t0, int *__restrict__ anchors_al
     // counts of this slice, then the sums over the lower ranks
     unsigned less = 0u, eq = 0u;
     for (int a = a0 + threadIdx.x; a < a1; a += FS_THREADS) {
-        const uint32_t key = frac_key(st, a);
+        const uint32_t key = cached ? kc[a - a0] : frac_key(st, a);
         less += key < thr;
         eq += key == thr;
     }
@@ -325,7 +353,7 @@ k_frac_cluster(int N, int M, uint64_t seed, int t0, int *__restrict__ anchors_al
 #pragma unroll
         for (int q = 0; q < FRAC_ITEMS; ++q) {
             const int a = b + q;
-            keys[q] = a < a1 ? frac_key(st, a) : 0xffffffffu;
+            keys[q] = a < a1 ? (cached ? kc[a - a0] : frac_key(st, a)) : 0xffffffffu;
             if (a < a1) {
                 l += keys[q] < thr;
                 e += keys[q] == thr;
@@ -355,10 +383,12 @@ static int frac_cluster_size()
     static int size = 0;
     if (size) return size;
     size = 8;
+    cudaFuncSetAttribute(k_frac_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_CACHE_BYTES);
     if (cudaFuncSetAttribute(k_frac_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(16);
         cfg.blockDim = dim3(FS_THREADS);
+        cfg.dynamicSmemBytes = FS_CACHE_BYTES;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = 16;
@@ -412,9 +442,12 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     (void)scratch;
     (void)sstride;
     const int cls = frac_cluster_size();
+    const size_t slice = ((size_t)N + cls - 1) / cls;
+    const int cached = slice * sizeof(uint32_t) <= (size_t)FS_CACHE_BYTES;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cls * nb);
     cfg.blockDim = dim3(FS_THREADS);
+    cfg.dynamicSmemBytes = cached ? slice * sizeof(uint32_t) : 0;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -423,7 +456,7 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    EPLL_CU(cudaLaunchKernelEx(&cfg, k_frac_cluster, N, *n, o.seed, t0, anchors, mult));
+    EPLL_CU(cudaLaunchKernelEx(&cfg, k_frac_cluster, N, *n, o.seed, t0, cached, anchors, mult));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
