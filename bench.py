@@ -526,6 +526,15 @@ def run_proposal(args):
                      "share_of_step": sel_ms / 1e3 / sel["_tot"] if sel["_tot"] else None,
                      "peak_source": peak_note},
         "proposal": {str(m): {k: v for k, v in d.items() if not k.startswith("_")} for m, d in per_m.items()},
+        # training on the tensor cores: algorithmic FLOPs per sample are the
+        # forward and backward products, 2 (2 * 64 * 256 + 3 * 256 * 256 + 3 * 256 * K)
+        "training": {"samples_per_s": args.train_steps * 4096 / train_s,
+                     "algorithmic_tflops": args.train_steps * 4096 * 2.0 * (2 * 64 * 256 + 3 * 256 * 256 + 3 * 256 * K)
+                     / train_s / 1e12,
+                     "frac_of_bf16_peak": args.train_steps * 4096 * 2.0 * (2 * 64 * 256 + 3 * 256 * 256 + 3 * 256 * K)
+                     / train_s / 1e12 / peak,
+                     "note": "whole training loop (host-issued steps of about 20 launches), split-BF16 tcgen05 "
+                             "products, SIMT elementwise steps"},
         "exhaustive_bf16x3": {"restores_per_s": ex_rate, "psnr_db": psnr(x_ex, x)},
         "exhaustive_auto": {"restores_per_s": auto_rate, "psnr_db": psnr(x_auto, x)},
         "plain_fp32": {"restores_per_s": r32, "psnr_db": psnr(x_32, x),

@@ -330,6 +330,13 @@ void sampler_setup();  // the same for the random-fraction sampler
 epll_status launch_pixel_update(epll_gmm *g, const float *a, const float *y, const float *xt, int H, int W,
                                 double bmult, float *x, cudaStream_t st);
 
+// Training product C[m * ldc + n] = sum_k A[m sam + k sak] B[k sbk + n sbn]
+// (FP32 in and out) on the tensor cores, split BF16 operands; long
+// reductions are split across CTAs into `partial` (capacity in floats).
+// N <= 256.  err is set if a bounded wait gave up.
+epll_status gemm_tc(const float *A, long sam, long sak, const float *B, long sbk, long sbn, float *C, int ldc, int M,
+                    int N, int Kd, float *partial, size_t partial_cap, int *err, cudaStream_t st);
+
 epll_status ensure_workspace(epll_gmm *g, size_t N);
 epll_status fail(epll_status s, const std::string &msg);
 cudaError_t alloc_tables(epll_gmm *g);

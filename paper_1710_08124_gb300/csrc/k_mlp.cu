@@ -14,7 +14,8 @@
 // rescoring): exhaustive scoring is both the fallback and the judge.
 //
 // Training (BF16-rounded weights, FP32 activations and accumulation, FP32
-// master weights, AdamW) uses plain register-tiled SIMT kernels; it runs
+// master weights, AdamW) runs its products on the tensor cores in the split
+// BF16 form (k_train_tc.cu) and the elementwise steps in SIMT FP32; it runs
 // offline on (patch, exact selection) pairs produced by the exhaustive path.
 #include "epll_internal.cuh"
 #include "tc_ptx.cuh"
@@ -50,6 +51,7 @@ struct epll_proposal {
     int Bmax = 0;
     float *X = nullptr, *cond = nullptr, *A1 = nullptr, *H1 = nullptr, *A2 = nullptr, *H2 = nullptr;
     float *L = nullptr, *dH = nullptr, *dA = nullptr, *loss = nullptr;
+    float *partial = nullptr;  // split-K partial products
 };
 
 namespace epll {
@@ -80,48 +82,10 @@ __device__ __forceinline__ float gelu_fast(float x)
 }
 
 // ============================================================================
-// Training kernels (SIMT FP32)
+// Training kernels: the products run on the tensor cores (k_train_tc.cu); the
+// elementwise steps (gather, bias + GELU, softmax cross-entropy, GELU
+// derivative, column sums, AdamW, BF16 rounding) are SIMT FP32.
 // ============================================================================
-// C[m][n] (+)= sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
-constexpr int GT = 64, GKC = 16;
-__global__ void __launch_bounds__(256)
-k_gemm(int M, int N, int Kd, const float *__restrict__ A, long sam, long sak, const float *__restrict__ Bm,
-       long sbk, long sbn, float *__restrict__ C, int ldc, int accumulate)
-{
-    __shared__ float As[GKC][GT + 1], Bs[GKC][GT + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < Kd; k0 += GKC) {
-        for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
-            const int kk = idx / GT, mm = idx % GT;
-            As[kk][mm] = (m0 + mm < M && k0 + kk < Kd) ? A[(long)(m0 + mm) * sam + (long)(k0 + kk) * sak] : 0.0f;
-            Bs[kk][mm] = (n0 + mm < N && k0 + kk < Kd) ? Bm[(long)(k0 + kk) * sbk + (long)(n0 + mm) * sbn] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GKC; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m < M && n < N) C[(long)m * ldc + n] = accumulate ? C[(long)m * ldc + n] + acc[i][j] : acc[i][j];
-        }
-}
-
 // X[b] = (patch - mean) * exp(-log_ib/2), cond[b] = log_ib; one warp per sample
 __global__ void k_mlp_gather(const float *__restrict__ images, int n_img, int H, int W,
                              const int *__restrict__ img_idx, const int *__restrict__ anchors,
@@ -172,31 +136,50 @@ __global__ void k_bias_gelu(float *__restrict__ A, const float *__restrict__ bia
     Hout[i] = gelu_f(v);
 }
 
-// logits += b3; dL = (softmax - onehot) / B; loss += mean cross-entropy
-__global__ void k_softmax_ce(float *__restrict__ Lg, const float *__restrict__ b3, const int *__restrict__ labels,
-                             const int *__restrict__ sel, int n_all, int B, int K, float *__restrict__ loss,
-                             int *__restrict__ bad)
+// logits += b3; dL = (softmax - onehot) / B; loss += mean cross-entropy.
+// One warp per sample (lanes over the components), the block's loss terms
+// summed before one atomic per block.
+constexpr int SM_WARPS = 8;
+__global__ void __launch_bounds__(32 * SM_WARPS)
+k_softmax_ce(float *__restrict__ Lg, const float *__restrict__ b3, const int *__restrict__ labels,
+             const int *__restrict__ sel, int n_all, int B, int K, float *__restrict__ loss, int *__restrict__ bad)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    const int s = sel ? sel[b] : b;
-    const int lab = (s >= 0 && s < n_all) ? labels[s] : -1;
-    if (lab < 0 || lab >= K) {  // invalid label: no gradient from this sample
-        atomicExch(bad, 1);
-        for (int k = 0; k < K; ++k) Lg[(size_t)b * K + k] = 0.0f;
-        return;
+    __shared__ float part[SM_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * SM_WARPS + warp;
+    float term = 0.0f;
+    if (b < B) {
+        const int s = sel ? sel[b] : b;
+        const int lab = (s >= 0 && s < n_all) ? labels[s] : -1;
+        float *l = Lg + (size_t)b * K;
+        if (lab < 0 || lab >= K) {  // invalid label: no gradient from this sample
+            if (lane == 0) atomicExch(bad, 1);
+            for (int k = lane; k < K; k += 32) l[k] = 0.0f;
+        } else {
+            float mx = -FLT_MAX;
+            for (int k = lane; k < K; k += 32) {
+                const float v = l[k] + b3[k];
+                l[k] = v;
+                mx = fmaxf(mx, v);
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            float se = 0.0f;
+            for (int k = lane; k < K; k += 32) se += expf(l[k] - mx);
+            for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+            const float lse = mx + logf(se);
+            __syncwarp();
+            if (lane == 0) term = (lse - l[lab]) / (float)B;
+            __syncwarp();
+            for (int k = lane; k < K; k += 32) l[k] = (expf(l[k] - lse) - (k == lab ? 1.0f : 0.0f)) / (float)B;
+        }
     }
-    float *l = Lg + (size_t)b * K;
-    float mx = -FLT_MAX;
-    for (int k = 0; k < K; ++k) {
-        l[k] += b3[k];
-        mx = fmaxf(mx, l[k]);
+    if (lane == 0) part[warp] = term;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < SM_WARPS; ++w) t += part[w];
+        atomicAdd(loss, t);
     }
-    float se = 0.0f;
-    for (int k = 0; k < K; ++k) se += expf(l[k] - mx);
-    const float lse = mx + logf(se);
-    atomicAdd(loss, (lse - l[lab]) / (float)B);
-    for (int k = 0; k < K; ++k) l[k] = (expf(l[k] - lse) - (k == lab ? 1.0f : 0.0f)) / (float)B;
 }
 
 __global__ void k_gelu_back(float *__restrict__ dH, const float *__restrict__ A, long n)
@@ -205,15 +188,24 @@ __global__ void k_gelu_back(float *__restrict__ dH, const float *__restrict__ A,
     if (i < n) dH[i] *= gelu_grad_f(A[i]);
 }
 
-// out[n] = sum_b D[b][n] (optionally weighted by cond[b]); rows summed in order
-__global__ void k_colsum(const float *__restrict__ D, int B, int N, const float *__restrict__ cond,
-                         float *__restrict__ out)
+// out[n] = sum_b D[b][n] (optionally weighted by cond[b]).  Block (32 x 32):
+// thread (x, y) sums the rows b = y (mod 32) of column 32 blockIdx.x + x in
+// increasing b, then the 32 partial sums of a column are added in order of y.
+__global__ void __launch_bounds__(1024) k_colsum(const float *__restrict__ D, int B, int N,
+                                                 const float *__restrict__ cond, float *__restrict__ out)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float ps[32][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s = fmaf(cond ? cond[b] : 1.0f, D[(size_t)b * N + n], s);
-    out[n] = s;
+    if (n < N)
+        for (int b = threadIdx.y; b < B; b += 32) s = fmaf(cond ? cond[b] : 1.0f, D[(size_t)b * N + n], s);
+    ps[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.0f;
+        for (int y = 0; y < 32; ++y) t += ps[y][threadIdx.x];
+        out[n] = t;
+    }
 }
 
 // AdamW (decoupled weight decay on the weight matrices only), then the BF16
@@ -246,19 +238,20 @@ __global__ void k_round_weights(const float *__restrict__ th, long np, int K, fl
     else if (i >= OFF_W3 && i < (long)off_b3(K)) W3b[i - OFF_W3] = __bfloat16_as_ushort(h);
 }
 
-static epll_status gemm(const float *A, long sam, long sak, const float *B, long sbk, long sbn, float *C, int ldc,
-                        int M, int N, int Kd, cudaStream_t st)
+// split-K partial tiles of the training products (up to 74 splits of a 256 x 256 result)
+constexpr size_t TRAIN_PARTIAL = (size_t)74 * HID * HID;
+
+static epll_status gemm(epll_proposal *p, const float *A, long sam, long sak, const float *B, long sbk, long sbn,
+                        float *C, int ldc, int M, int N, int Kd, cudaStream_t st)
 {
-    const dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-    k_gemm<<<grid, 256, 0, st>>>(M, N, Kd, A, sam, sak, B, sbk, sbn, C, ldc, 0);
-    EPLL_CU(cudaGetLastError());
-    return EPLL_OK;
+    return gemm_tc(A, sam, sak, B, sbk, sbn, C, ldc, M, N, Kd, p->partial, TRAIN_PARTIAL,
+                   reinterpret_cast<int *>(p->loss + 2), st);
 }
 
 static epll_status ensure_train(epll_proposal *p, int B)
 {
     if (B <= p->Bmax) return EPLL_OK;
-    float *ptrs[] = {p->X, p->cond, p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA};
+    float *ptrs[] = {p->X, p->cond, p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA, p->partial};
     for (float *q : ptrs)
         if (q) cudaFree(q);
     const size_t HB = (size_t)B * HID;
@@ -266,6 +259,7 @@ static epll_status ensure_train(epll_proposal *p, int B)
     auto A = [&](float **q, size_t n) { if (e == cudaSuccess) e = cudaMalloc(q, sizeof(float) * n); };
     A(&p->X, (size_t)B * PD); A(&p->cond, B); A(&p->A1, HB); A(&p->H1, HB); A(&p->A2, HB); A(&p->H2, HB);
     A(&p->L, (size_t)B * p->K); A(&p->dH, HB > (size_t)B * p->K ? HB : (size_t)B * p->K); A(&p->dA, HB);
+    A(&p->partial, TRAIN_PARTIAL);
     if (e != cudaSuccess) {
         p->Bmax = 0;
         return fail(EPLL_ENOMEM, std::string("proposal training buffers: ") + cudaGetErrorString(e));
@@ -293,33 +287,33 @@ static epll_status forward_backward(epll_proposal *p, const Batch &d, cudaStream
     int *bad = reinterpret_cast<int *>(p->loss + 1);
     const float *w = p->wr;
     float *g = p->grad;
-    EPLL_CU(cudaMemsetAsync(p->loss, 0, 2 * sizeof(float), st));
+    EPLL_CU(cudaMemsetAsync(p->loss, 0, 3 * sizeof(float), st));
     k_mlp_gather<<<(B + 3) / 4, 128, 0, st>>>(d.images, d.n_img, d.H, d.W, d.img_idx, d.anchors, d.log_ib, d.sel,
                                               d.n_all, B, p->X, p->cond, bad);
     EPLL_CU(cudaGetLastError());
     const long HB = (long)B * HID;
     const int eb = (int)((HB + 255) / 256);
     // forward
-    if ((s = gemm(p->X, PD, 1, w + OFF_W1, 1, PD, p->A1, HID, B, HID, PD, st))) return s;
+    if ((s = gemm(p, p->X, PD, 1, w + OFF_W1, 1, PD, p->A1, HID, B, HID, PD, st))) return s;
     k_bias_gelu<<<eb, 256, 0, st>>>(p->A1, w + OFF_B1, w + OFF_WB, p->cond, B, p->H1);
-    if ((s = gemm(p->H1, HID, 1, w + OFF_W2, 1, HID, p->A2, HID, B, HID, HID, st))) return s;
+    if ((s = gemm(p, p->H1, HID, 1, w + OFF_W2, 1, HID, p->A2, HID, B, HID, HID, st))) return s;
     k_bias_gelu<<<eb, 256, 0, st>>>(p->A2, w + OFF_B2, nullptr, nullptr, B, p->H2);
-    if ((s = gemm(p->H2, HID, 1, w + OFF_W3, 1, HID, p->L, K, B, K, HID, st))) return s;
-    k_softmax_ce<<<(B + 127) / 128, 128, 0, st>>>(p->L, w + off_b3(K), d.labels, d.sel, d.n_all, B, K, p->loss,
+    if ((s = gemm(p, p->H2, HID, 1, w + OFF_W3, 1, HID, p->L, K, B, K, HID, st))) return s;
+    k_softmax_ce<<<(B + SM_WARPS - 1) / SM_WARPS, 32 * SM_WARPS, 0, st>>>(p->L, w + off_b3(K), d.labels, d.sel, d.n_all, B, K, p->loss,
                                                   bad);
     EPLL_CU(cudaGetLastError());
     // backward (p->L now holds dL)
-    if ((s = gemm(p->L, 1, K, p->H2, HID, 1, g + OFF_W3, HID, K, HID, B, st))) return s;    // dW3 = dL^T H2
-    k_colsum<<<(K + 127) / 128, 128, 0, st>>>(p->L, B, K, nullptr, g + off_b3(K));
-    if ((s = gemm(p->L, K, 1, w + OFF_W3, HID, 1, p->dH, HID, B, HID, K, st))) return s;    // dH2 = dL W3
+    if ((s = gemm(p, p->L, 1, K, p->H2, HID, 1, g + OFF_W3, HID, K, HID, B, st))) return s;    // dW3 = dL^T H2
+    k_colsum<<<(K + 31) / 32, dim3(32, 32), 0, st>>>(p->L, B, K, nullptr, g + off_b3(K));
+    if ((s = gemm(p, p->L, K, 1, w + OFF_W3, HID, 1, p->dH, HID, B, HID, K, st))) return s;    // dH2 = dL W3
     k_gelu_back<<<eb, 256, 0, st>>>(p->dH, p->A2, HB);                                      // dA2
-    if ((s = gemm(p->dH, 1, HID, p->H1, HID, 1, g + OFF_W2, HID, HID, HID, B, st))) return s;  // dW2
-    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dH, B, HID, nullptr, g + OFF_B2);
-    if ((s = gemm(p->dH, HID, 1, w + OFF_W2, HID, 1, p->dA, HID, B, HID, HID, st))) return s;  // dH1
+    if ((s = gemm(p, p->dH, 1, HID, p->H1, HID, 1, g + OFF_W2, HID, HID, HID, B, st))) return s;  // dW2
+    k_colsum<<<(HID + 31) / 32, dim3(32, 32), 0, st>>>(p->dH, B, HID, nullptr, g + OFF_B2);
+    if ((s = gemm(p, p->dH, HID, 1, w + OFF_W2, HID, 1, p->dA, HID, B, HID, HID, st))) return s;  // dH1
     k_gelu_back<<<eb, 256, 0, st>>>(p->dA, p->A1, HB);                                         // dA1
-    if ((s = gemm(p->dA, 1, HID, p->X, PD, 1, g + OFF_W1, PD, HID, PD, B, st))) return s;     // dW1
-    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dA, B, HID, nullptr, g + OFF_B1);
-    k_colsum<<<(HID + 127) / 128, 128, 0, st>>>(p->dA, B, HID, p->cond, g + OFF_WB);
+    if ((s = gemm(p, p->dA, 1, HID, p->X, PD, 1, g + OFF_W1, PD, HID, PD, B, st))) return s;     // dW1
+    k_colsum<<<(HID + 31) / 32, dim3(32, 32), 0, st>>>(p->dA, B, HID, nullptr, g + OFF_B1);
+    k_colsum<<<(HID + 31) / 32, dim3(32, 32), 0, st>>>(p->dA, B, HID, p->cond, g + OFF_WB);
     EPLL_CU(cudaGetLastError());
     return EPLL_OK;
 }
@@ -1019,7 +1013,7 @@ void epll_proposal_free(epll_proposal *p)
     if (!p) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {p->theta, p->mom1, p->mom2, p->grad, p->wr, p->W1b, p->W2b, p->W3b, p->X, p->cond,
-                    p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA, p->loss};
+                    p->A1, p->H1, p->A2, p->H2, p->L, p->dH, p->dA, p->loss, p->partial};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1038,7 +1032,7 @@ epll_status epll_proposal_create(int K, uint64_t seed, epll_proposal **out)
     A((void **)&p->theta, p->np * 4); A((void **)&p->mom1, p->np * 4); A((void **)&p->mom2, p->np * 4);
     A((void **)&p->grad, p->np * 4); A((void **)&p->wr, p->np * 4);
     A((void **)&p->W1b, HID * PD * 2); A((void **)&p->W2b, HID * HID * 2); A((void **)&p->W3b, HID * HID * 2);
-    A((void **)&p->loss, 8);
+    A((void **)&p->loss, 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         epll_proposal_free(p);
@@ -1107,11 +1101,13 @@ static epll_status check_batch(const epll_proposal *p, const Batch &d)
 // Reads the loss and the invalid-sample flag (synchronises st).
 static epll_status read_loss(epll_proposal *p, float *loss, cudaStream_t st)
 {
-    float h[2];
+    float h[3];
     EPLL_CU(cudaMemcpyAsync(h, p->loss, sizeof(h), cudaMemcpyDeviceToHost, st));
     EPLL_CU(cudaStreamSynchronize(st));
-    int bad;
+    int bad, tc_err;
     std::memcpy(&bad, &h[1], sizeof(int));
+    std::memcpy(&tc_err, &h[2], sizeof(int));
+    if (tc_err) return fail(EPLL_ETIMEOUT, "a training GEMM gave up on a bounded wait");
     if (bad) return fail(EPLL_EINVAL, "a sample had an out-of-range image index, anchor, label or log(1/beta)");
     *loss = h[0];
     return EPLL_OK;
