@@ -198,14 +198,16 @@ epll_status epll_restore(epll_gmm *g, const float *y, int H, int W,
                          const double *beta_mult, int T, const epll_options *opt,
                          float *x_out, void *stream);
 
-/* One image of a batch (all pointers are device memory of the current device). */
+/* One image of a batch (y, x_out and a are device memory of the current device). */
 typedef struct {
     const float *y;  /* H*W observation */
     float *x_out;    /* H*W result; must not alias another job's buffers */
-    const float *a;  /* H*W gains for EPLL_PIXELWISE, NULL for EPLL_DENOISE */
+    const float *a;  /* H*W gains for EPLL_PIXELWISE, NULL otherwise */
     int H, W;
-    int kind;        /* EPLL_DENOISE or EPLL_PIXELWISE */
+    int kind;        /* EPLL_DENOISE, EPLL_PIXELWISE or EPLL_CONV_PERIODIC */
     float sigma;     /* noise standard deviation in image units */
+    const float *kernel; /* EPLL_CONV_PERIODIC: host kh*kw blur kernel, copied at every call */
+    int kh, kw;
 } epll_job;
 
 enum { EPLL_BATCH_SEQUENTIAL = 0, EPLL_BATCH_GRAPH = 1 };
@@ -218,8 +220,11 @@ enum { EPLL_BATCH_SEQUENTIAL = 0, EPLL_BATCH_GRAPH = 1 };
  *         with its own tables and workspace, sharing the model) running on
  *         their own streams, and the whole batch is captured once into a CUDA
  *         graph that later calls with the same jobs replay with one launch.
- *         lanes = 0 lets the library pick the lane count: on the first call it
- *         times the graph for 1, 2, 4 and 8 lanes and keeps the fastest.
+ *         lanes = 0 lets the library tune the batch: on the first call for a
+ *         job list it times the graph for 1, 2, 4 and 8 lanes, then, at the
+ *         fastest lane count, for the tile shapes of the selection kernel (256
+ *         or 128 basis columns per stage) and of the reprojection (2 or 4
+ *         threads per 8-pixel group), and keeps the fastest combination.
  * The first call for a job list (and any call with a different one) allocates
  * the lanes' workspaces, runs the batch once eagerly and captures the graph;
  * those calls synchronise the device.  Replays are asynchronous on `stream`.
@@ -228,6 +233,19 @@ enum { EPLL_BATCH_SEQUENTIAL = 0, EPLL_BATCH_GRAPH = 1 };
  */
 epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const double *beta_mult,
                                int T, const epll_options *opt, int mode, int lanes, void *stream);
+
+/* Tile shapes of this handle's kernels: basis columns per stage of the
+ * tensor-core selection (256 or 128) and threads per 8-pixel group of the
+ * reprojection (2 or 4).  Every shape computes the same restoration (up to
+ * the order of FP32 sums); the batch autotuner starts from these values.
+ * Defaults 256 and 2.  Errors: EPLL_EINVAL. */
+epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg);
+
+/* The configuration the batch autotuner chose for the last tuned job list of
+ * this handle (host out, each nullable): lane count (0 if nothing was tuned),
+ * selection basis columns per stage (256 or 128) and reprojection threads per
+ * 8-pixel group (2 or 4).  Errors: EPLL_EINVAL. */
+epll_status epll_batch_config(epll_gmm *g, int *lanes, int *tile_bn, int *tile_agg);
 
 /* Same as epll_restore with HOST buffers: y, deg->a (PIXELWISE) and x_out are
  * host pointers; the copies to and from the workspace are part of the call,

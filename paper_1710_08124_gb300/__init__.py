@@ -42,7 +42,8 @@ class _Options(C.Structure):
 
 class _Job(C.Structure):
     _fields_ = [("y", C.c_void_p), ("x_out", C.c_void_p), ("a", C.c_void_p), ("H", C.c_int),
-                ("W", C.c_int), ("kind", C.c_int), ("sigma", C.c_float)]
+                ("W", C.c_int), ("kind", C.c_int), ("sigma", C.c_float), ("kernel", C.c_void_p),
+                ("kh", C.c_int), ("kw", C.c_int)]
 
 
 BATCH_SEQUENTIAL, BATCH_GRAPH = 0, 1
@@ -99,6 +100,8 @@ def lib():
         L.epll_sample.argtypes = [i, i, C.POINTER(_Options), i, vp, C.POINTER(C.c_int), vp]
         L.epll_sample_noalloc.argtypes = L.epll_sample.argtypes
         L.epll_restore_batch.argtypes = [vp, i, C.POINTER(_Job), vp, i, C.POINTER(_Options), i, i, vp]
+        L.epll_set_tiles.argtypes = [vp, i, i]
+        L.epll_batch_config.argtypes = [vp, vp, vp, vp]
         L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                          C.POINTER(C.c_longlong)]
         L.epll_profile_enable.argtypes = [vp, i]
@@ -234,17 +237,40 @@ def image_update(g: GMM, y, xtilde, sigma: float, beta_mult: float, kind: int = 
 def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = None,
                   mode: int = BATCH_GRAPH, lanes: int = 0, stream=None):
     """Batched restoration (``epll_restore_batch``).  ``jobs`` is a list of
-    (y, x_out, a_or_None, kind, sigma) with float32 CUDA tensors."""
+    (y, x_out, a_or_None, kind, sigma) or (y, x_out, a_or_None, kind, sigma,
+    kernel) with float32 CUDA tensors (kernel: a host array for
+    CONV_PERIODIC jobs)."""
     import torch
     arr = (_Job * len(jobs))()
-    for i, (y, xo, a, kind, sigma) in enumerate(jobs):
+    keep = []
+    for i, job in enumerate(jobs):
+        y, xo, a, kind, sigma = job[:5]
+        kern = job[5] if len(job) > 5 else None
         H, W = y.shape
+        kp, kh, kw = None, 0, 0
+        if kern is not None:
+            k = np.ascontiguousarray(kern, np.float32)
+            keep.append(k)
+            kp, kh, kw = k.ctypes.data, k.shape[0], k.shape[1]
         arr[i] = _Job(_dptr(y, torch.float32), _dptr(xo, torch.float32), _dptr(a, torch.float32), H, W,
-                      int(kind), float(sigma))
+                      int(kind), float(sigma), kp, kh, kw)
     bm = np.ascontiguousarray(beta_mult, np.float64)
     opt = (options or Options())._c()
     _check(lib().epll_restore_batch(g.handle, len(jobs), arr, bm.ctypes.data, bm.shape[0], C.byref(opt),
                                     int(mode), int(lanes), _stream(stream)))
+    del keep
+
+
+def set_tiles(g: GMM, tile_bn: int = 256, tile_agg: int = 2):
+    """Tile shapes of the handle's selection and reprojection kernels (``epll_set_tiles``)."""
+    _check(lib().epll_set_tiles(g.handle, int(tile_bn), int(tile_agg)))
+
+
+def batch_config(g: GMM):
+    """(lanes, tile_bn, tile_agg) the batch autotuner chose (``epll_batch_config``)."""
+    l, b, a = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(lib().epll_batch_config(g.handle, C.byref(l), C.byref(b), C.byref(a)))
+    return l.value, b.value, a.value
 
 
 def restore_host(g: GMM, y: np.ndarray, sigma: float, beta_mult=PAPER_BETA, kind: int = DENOISE,

@@ -67,8 +67,10 @@ static void free_workspace(Workspace &ws)
                     ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore, ws.tnode, ws.tcounts, ws.titems};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
-    if (ws.plan_c2r) cufftDestroy(ws.plan_c2r);
+    for (int i = 0; i < ws.nplans; ++i) {
+        cufftDestroy(ws.plan_fw[i]);
+        cufftDestroy(ws.plan_bw[i]);
+    }
     if (ws.plan_c2c) cufftDestroy(ws.plan_c2c);
     if (ws.plan_c2c_low) cufftDestroy(ws.plan_c2c_low);
     ws = Workspace();
@@ -339,7 +341,7 @@ static epll_status patch_phase(epll_gmm *g, const float *xhat, int H, int W, con
 
 epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
                                const epll_degradation *deg, float sigma, const double *beta_mult,
-                               int T, const epll_options &o, cudaStream_t st)
+                               int T, const epll_options &o, cudaStream_t st, bool kernel_dev)
 {
     Workspace &ws = g->ws;
     const int kind = deg ? deg->kind : EPLL_DENOISE;
@@ -350,7 +352,7 @@ epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int 
     EPLL_CU(cudaMemsetAsync(cnt(g, CNT_ERR), 0, sizeof(int), st));
     const int d = kind == EPLL_CONV_DECIMATE ? deg->factor : 1;
     if (kind == EPLL_CONV_PERIODIC) {
-        if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st))) return s;
+        if ((s = fft_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, st, kernel_dev))) return s;
     } else if (kind == EPLL_CONV_DECIMATE) {
         if ((s = sr_prepare(g, deg->kernel, deg->kh, deg->kw, y, H, W, d, st))) return s;
     }

@@ -9,7 +9,9 @@
 // one origin stream -- is captured once into a CUDA graph; later calls with
 // the same job list replay it with a single launch.  With lanes = 0 the lane
 // count is tuned on the first call by timing the graph for 1, 2, 4 and 8
-// lanes.
+// lanes, then the tile shapes (selection basis columns per stage,
+// reprojection threads per pixel group) at that lane count.  Periodic-blur
+// jobs read their kernels from a device copy made at every call.
 #include "epll_internal.cuh"
 
 #include <algorithm>
@@ -29,8 +31,16 @@ struct BatchState {
     std::vector<cudaEvent_t> join;
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;        // what the captured graph runs
-    std::vector<unsigned char> tuned_key;  // job list the tuned lane count belongs to
-    int tuned_lanes = 0;
+    std::vector<unsigned char> tuned_key;  // job list the tuned configuration belongs to
+    int tuned_lanes = 0, tuned_bn = 256, tuned_agg = 2;
+    float *d_kern = nullptr;               // device copies of the jobs' blur kernels
+    size_t kern_cap = 0;
+    std::vector<size_t> kern_off;          // per job: offset in d_kern (CONV jobs)
+};
+
+// One tile configuration of the autotuner.
+struct TileCfg {
+    int bn, agg;
 };
 
 epll_gmm *make_lane(const epll_gmm *g)
@@ -78,6 +88,7 @@ void free_batch(epll_gmm *g)
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
+    if (b->d_kern) cudaFree(b->d_kern);
     delete b;
     g->batch = nullptr;
 }
@@ -123,12 +134,16 @@ static std::vector<std::vector<int>> assign(int n, const epll_job *jobs, int L)
     return lanes;
 }
 
+// dkern: the job's blur kernel in device memory (CONV jobs in a graph), or
+// nullptr to use the host kernel of the job.
 static epll_status run_job(epll_gmm *ctx, const epll_job &j, const double *beta, int T,
-                           const epll_options &o, cudaStream_t st)
+                           const epll_options &o, cudaStream_t st, const float *dkern = nullptr)
 {
-    epll_degradation deg{j.kind, j.a, nullptr, 0, 0, 1};
+    const bool conv = j.kind == EPLL_CONV_PERIODIC;
+    epll_degradation deg{j.kind, j.a, conv ? (dkern ? dkern : j.kernel) : nullptr, conv ? j.kh : 0,
+                         conv ? j.kw : 0, 1};
     epll_status s = run_restore(ctx, j.y, j.kind == EPLL_PIXELWISE ? j.a : nullptr, j.H, j.W, &deg, j.sigma,
-                                beta, T, o, st);
+                                beta, T, o, st, conv && dkern != nullptr);
     if (s) return s;
     EPLL_CU(cudaMemcpyAsync(j.x_out, ctx->ws.xhat, sizeof(float) * (size_t)j.H * j.W,
                             cudaMemcpyDeviceToDevice, st));
@@ -192,7 +207,8 @@ static epll_status issue(BatchState *b, const std::vector<std::vector<int>> &par
     for (size_t l = 0; l < part.size(); ++l) {
         EPLL_CU(cudaStreamWaitEvent(b->streams[l], b->fork, 0));
         for (int j : part[l]) {
-            epll_status s = run_job(b->lanes[l], jobs[j], beta, T, o, b->streams[l]);
+            const float *dk = jobs[j].kind == EPLL_CONV_PERIODIC ? b->d_kern + b->kern_off[j] : nullptr;
+            epll_status s = run_job(b->lanes[l], jobs[j], beta, T, o, b->streams[l], dk);
             if (s) return s;
         }
         EPLL_CU(cudaEventRecord(b->join[l], b->streams[l]));
@@ -203,11 +219,15 @@ static epll_status issue(BatchState *b, const std::vector<std::vector<int>> &par
 
 // Eager run (lazy initialisations happen here), then capture and instantiate.
 static epll_status build_graph(epll_gmm *g, BatchState *b, int n, const epll_job *jobs, const double *beta,
-                               int T, const epll_options &o, int L, cudaStream_t st)
+                               int T, const epll_options &o, int L, TileCfg tc, cudaStream_t st)
 {
     const auto part = assign(n, jobs, L);
     epll_status s;
     if ((s = prepare_lanes(g, b, part, jobs))) return s;
+    for (int l = 0; l < L; ++l) {
+        b->lanes[l]->tile_bn = tc.bn;
+        b->lanes[l]->tile_agg = tc.agg;
+    }
     if ((s = issue(b, part, jobs, beta, T, o, st))) return s;
     EPLL_CU(cudaStreamSynchronize(st));
     if (b->exec) {
@@ -246,15 +266,17 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
     if (lanes < 0 || lanes > MAX_LANES) return fail(EPLL_EINVAL, "lanes must be in 0..8");
     epll_options o;
     if (opt) o = *opt; else epll_options_default(&o);
-    size_t maxN = 0;
+    size_t maxN = 0, kern_total = 0;
     for (int i = 0; i < n; ++i) {
         const epll_job &j = jobs[i];
-        if (j.kind != EPLL_DENOISE && j.kind != EPLL_PIXELWISE)
-            return fail(EPLL_EINVAL, "batch jobs are EPLL_DENOISE or EPLL_PIXELWISE");
-        epll_degradation deg{j.kind, j.a, nullptr, 0, 0, 1};
+        if (j.kind != EPLL_DENOISE && j.kind != EPLL_PIXELWISE && j.kind != EPLL_CONV_PERIODIC)
+            return fail(EPLL_EINVAL, "batch jobs are EPLL_DENOISE, EPLL_PIXELWISE or EPLL_CONV_PERIODIC");
+        const bool conv = j.kind == EPLL_CONV_PERIODIC;
+        epll_degradation deg{j.kind, j.a, conv ? j.kernel : nullptr, conv ? j.kh : 0, conv ? j.kw : 0, 1};
         epll_status s = check_restore_args(g, j.y, j.H, j.W, &deg, j.sigma, beta_mult, T, o, j.x_out);
         if (s) return s;
         maxN = std::max(maxN, (size_t)j.H * j.W);
+        if (conv) kern_total += (size_t)j.kh * j.kw;
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (mode == EPLL_BATCH_SEQUENTIAL) {
@@ -266,46 +288,112 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
     }
     if (!g->batch) g->batch = new BatchState();
     BatchState *b = g->batch;
+    // device copies of the blur kernels (before any capture; refreshed at every call)
+    b->kern_off.assign((size_t)n, 0);
+    if (kern_total) {
+        if (kern_total > b->kern_cap) {
+            EPLL_CU(cudaDeviceSynchronize());
+            if (b->d_kern) cudaFree(b->d_kern);
+            b->d_kern = nullptr;
+            b->kern_cap = 0;
+            EPLL_CU(cudaMalloc(&b->d_kern, sizeof(float) * kern_total));
+            b->kern_cap = kern_total;
+        }
+        std::vector<float> hk(kern_total);
+        size_t off = 0;
+        for (int i = 0; i < n; ++i)
+            if (jobs[i].kind == EPLL_CONV_PERIODIC) {
+                b->kern_off[i] = off;
+                std::memcpy(hk.data() + off, jobs[i].kernel, sizeof(float) * (size_t)jobs[i].kh * jobs[i].kw);
+                off += (size_t)jobs[i].kh * jobs[i].kw;
+            }
+        EPLL_CU(cudaMemcpyAsync(b->d_kern, hk.data(), sizeof(float) * kern_total, cudaMemcpyHostToDevice, st));
+        EPLL_CU(cudaStreamSynchronize(st));
+    }
     const std::vector<unsigned char> jk = job_key(g, n, jobs, beta_mult, T, o);
     int L = lanes;
+    TileCfg tc{g->tile_bn, g->tile_agg};
     if (L == 0) {
         if (b->tuned_key == jk && b->tuned_lanes > 0) {
             L = b->tuned_lanes;
+            tc = TileCfg{b->tuned_bn, b->tuned_agg};
         } else {
-            // time the captured batch for 1, 2, 4, 8 lanes (two replays each)
-            float best = 0.0f;
-            int bestL = 1;
-            for (int cand = 1; cand <= MAX_LANES && cand <= n; cand *= 2) {
-                epll_status s = build_graph(g, b, n, jobs, beta_mult, T, o, cand, st);
+            // time a captured configuration (one warm replay, then two timed)
+            auto time_cfg = [&](int cand, TileCfg c, float *ms) -> epll_status {
+                epll_status s = build_graph(g, b, n, jobs, beta_mult, T, o, cand, c, st);
                 if (s) return s;
+                b->key.clear();  // the tuning graphs are not reused
                 EPLL_CU(cudaGraphLaunch(b->exec, st));
                 EPLL_CU(cudaEventRecord(b->t0, st));
                 EPLL_CU(cudaGraphLaunch(b->exec, st));
                 EPLL_CU(cudaGraphLaunch(b->exec, st));
                 EPLL_CU(cudaEventRecord(b->t1, st));
                 EPLL_CU(cudaEventSynchronize(b->t1));
+                EPLL_CU(cudaEventElapsedTime(ms, b->t0, b->t1));
+                return EPLL_OK;
+            };
+            // lanes 1, 2, 4, 8 with the handle's tiles, then the tile shapes
+            float best = 0.0f;
+            int bestL = 1;
+            for (int cand = 1; cand <= MAX_LANES && cand <= n; cand *= 2) {
                 float ms = 0.0f;
-                EPLL_CU(cudaEventElapsedTime(&ms, b->t0, b->t1));
+                epll_status s = time_cfg(cand, tc, &ms);
+                if (s) return s;
                 if (cand == 1 || ms < best) {
                     best = ms;
                     bestL = cand;
                 }
-                b->key = jk;
-                put(b->key, cand);
+            }
+            TileCfg bestT = tc;
+            const TileCfg alts[] = {{128, tc.agg}, {tc.bn, tc.agg == 2 ? 4 : 2}};
+            for (const TileCfg &c : alts) {
+                if (c.bn == tc.bn && c.agg == tc.agg) continue;
+                float ms = 0.0f;
+                epll_status s = time_cfg(bestL, c, &ms);
+                if (s) return s;
+                if (ms < best) {
+                    best = ms;
+                    bestT = c;
+                }
             }
             b->tuned_key = jk;
             b->tuned_lanes = bestL;
+            b->tuned_bn = bestT.bn;
+            b->tuned_agg = bestT.agg;
             L = bestL;
+            tc = bestT;
         }
     }
     L = std::min(L, n);
     std::vector<unsigned char> key = jk;
     put(key, L);
+    put(key, tc.bn);
+    put(key, tc.agg);
     if (!(b->exec && b->key == key)) {
-        epll_status s = build_graph(g, b, n, jobs, beta_mult, T, o, L, st);
+        epll_status s = build_graph(g, b, n, jobs, beta_mult, T, o, L, tc, st);
         if (s) return s;
         b->key = key;
     }
     EPLL_CU(cudaGraphLaunch(b->exec, st));
+    return EPLL_OK;
+}
+
+extern "C" epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg)
+{
+    if (!g || g->lane) return fail(EPLL_EINVAL, "null model handle");
+    if ((tile_bn != 128 && tile_bn != 256) || (tile_agg != 2 && tile_agg != 4))
+        return fail(EPLL_EINVAL, "tile_bn must be 128 or 256 and tile_agg 2 or 4");
+    g->tile_bn = tile_bn;
+    g->tile_agg = tile_agg;
+    return EPLL_OK;
+}
+
+extern "C" epll_status epll_batch_config(epll_gmm *g, int *lanes, int *tile_bn, int *tile_agg)
+{
+    if (!g || g->lane) return fail(EPLL_EINVAL, "null model handle");
+    const BatchState *b = g->batch;
+    if (lanes) *lanes = b ? b->tuned_lanes : 0;
+    if (tile_bn) *tile_bn = b && b->tuned_lanes ? b->tuned_bn : g->tile_bn;
+    if (tile_agg) *tile_agg = b && b->tuned_lanes ? b->tuned_agg : g->tile_agg;
     return EPLL_OK;
 }

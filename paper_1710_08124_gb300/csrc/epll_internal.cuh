@@ -108,8 +108,14 @@ struct Workspace {
     long long *ctr = nullptr;                 // [4] device counters: rescored patches
     cufftComplex *Yh = nullptr, *Hh = nullptr, *Xh = nullptr;  // [H][W/2+1]
     float *kern = nullptr;                    // [H][W] wrapped blur kernel
-    cufftHandle plan_r2c = 0, plan_c2r = 0;
-    int planH = 0, planW = 0;
+    cufftHandle plan_r2c = 0, plan_c2r = 0;   // the plans of the current size (a cache entry)
+    // periodic-blur plans of every size used with this workspace (a batch lane
+    // restores several sizes; plans are never created while a graph is captured
+    // because the eager run before the capture creates them)
+    static constexpr int FFT_CACHE = 8;
+    int plan_h[FFT_CACHE] = {}, plan_w[FFT_CACHE] = {};
+    cufftHandle plan_fw[FFT_CACHE] = {}, plan_bw[FFT_CACHE] = {};
+    int nplans = 0;
     cufftHandle plan_c2c = 0, plan_c2c_low = 0;  // super-resolution: H x W and (H/d) x (W/d)
     int c2cH = 0, c2cW = 0, c2cd = 0;
     // search tree (allocated on first use)
@@ -182,6 +188,11 @@ struct epll_gmm {
     const epll_proposal *prop = nullptr;
     int prop_topm = 0;
     float prop_pmin = 0.0f;
+    // tile shapes (chosen per lane by the batch autotuner): basis columns per
+    // stage of the tensor-core selection (256 or 128), threads per 8-pixel
+    // group of the reprojection (2 or 4)
+    int tile_bn = 256;
+    int tile_agg = 2;
 };
 
 namespace epll {
@@ -310,8 +321,9 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
 // Image-domain steps (k_image.cu)
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,
                           cudaStream_t st, int d = 1);   // writes ws.scal[0] and ws.lamf
-epll_status fft_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *y,
-                        int H, int W, cudaStream_t st);  // plans, Hh, Yh
+// plans, Hh, Yh; the kh x kw kernel is host memory, or device memory when kernel_dev
+epll_status fft_prepare(epll_gmm *g, const float *kernel, int kh, int kw, const float *y,
+                        int H, int W, cudaStream_t st, bool kernel_dev = false);
 epll_status fft_init(epll_gmm *g, int H, int W, double sigma, cudaStream_t st);    // ws.xhat
 epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st);  // ws.xtil -> ws.xhat
 // Super-resolution (blur, then decimation by d): full complex transforms of
@@ -342,9 +354,10 @@ epll_status fail(epll_status s, const std::string &msg);
 cudaError_t alloc_tables(epll_gmm *g);
 void free_batch(epll_gmm *g);
 // One restoration on g's workspace and tables (no allocation, no synchronisation).
+// kernel_dev: deg->kernel (CONV_PERIODIC) is device memory (batch lanes).
 epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int W,
                         const epll_degradation *deg, float sigma, const double *beta_mult, int T,
-                        const epll_options &o, cudaStream_t st);
+                        const epll_options &o, cudaStream_t st, bool kernel_dev = false);
 epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W, const epll_degradation *deg,
                                float sigma, const double *beta_mult, int T, const epll_options &o,
                                const float *x_out);

@@ -249,26 +249,50 @@ __global__ void k_fft_update(const cufftComplex *__restrict__ Hh, const cufftCom
         }                                                                            \
     } while (0)
 
-epll_status fft_prepare(epll_gmm *g, const float *kernel_host, int kh, int kw, const float *y,
-                        int H, int W, cudaStream_t st)
+epll_status fft_prepare(epll_gmm *g, const float *kernel, int kh, int kw, const float *y,
+                        int H, int W, cudaStream_t st, bool kernel_dev)
 {
     Workspace &ws = g->ws;
-    if (ws.planH != H || ws.planW != W) {
-        if (ws.plan_r2c) cufftDestroy(ws.plan_r2c);
-        if (ws.plan_c2r) cufftDestroy(ws.plan_c2r);
-        ws.plan_r2c = ws.plan_c2r = 0;
-        ws.planH = ws.planW = 0;
-        EPLL_FFT(cufftPlan2d(&ws.plan_r2c, H, W, CUFFT_R2C));
-        EPLL_FFT(cufftPlan2d(&ws.plan_c2r, H, W, CUFFT_C2R));
-        ws.planH = H;
-        ws.planW = W;
+    int slot = -1;
+    for (int i = 0; i < ws.nplans; ++i)
+        if (ws.plan_h[i] == H && ws.plan_w[i] == W) slot = i;
+    if (slot < 0) {
+        if (ws.nplans == Workspace::FFT_CACHE) {  // drop the oldest size
+            cufftDestroy(ws.plan_fw[0]);
+            cufftDestroy(ws.plan_bw[0]);
+            for (int i = 1; i < ws.nplans; ++i) {
+                ws.plan_h[i - 1] = ws.plan_h[i];
+                ws.plan_w[i - 1] = ws.plan_w[i];
+                ws.plan_fw[i - 1] = ws.plan_fw[i];
+                ws.plan_bw[i - 1] = ws.plan_bw[i];
+            }
+            --ws.nplans;
+        }
+        cufftHandle fw = 0, bw = 0;
+        EPLL_FFT(cufftPlan2d(&fw, H, W, CUFFT_R2C));
+        cufftResult r = cufftPlan2d(&bw, H, W, CUFFT_C2R);
+        if (r != CUFFT_SUCCESS) {
+            cufftDestroy(fw);
+            set_error("cufftPlan2d (C2R) failed with cufftResult " + std::to_string((int)r));
+            return EPLL_ECUDA;
+        }
+        slot = ws.nplans++;
+        ws.plan_h[slot] = H;
+        ws.plan_w[slot] = W;
+        ws.plan_fw[slot] = fw;
+        ws.plan_bw[slot] = bw;
     }
+    ws.plan_r2c = ws.plan_fw[slot];
+    ws.plan_c2r = ws.plan_bw[slot];
     EPLL_FFT(cufftSetStream(ws.plan_r2c, st));
     EPLL_FFT(cufftSetStream(ws.plan_c2r, st));
-    // stage the small kernel through the tail of the wrapped-kernel buffer
     const size_t N = (size_t)H * W;
-    float *dk = ws.cg;  // scratch: kh*kw <= N floats
-    EPLL_CU(cudaMemcpyAsync(dk, kernel_host, sizeof(float) * (size_t)kh * kw, cudaMemcpyHostToDevice, st));
+    const float *dk = kernel;
+    if (!kernel_dev) {
+        // stage the small kernel through the CG buffer (kh*kw <= N floats)
+        EPLL_CU(cudaMemcpyAsync(ws.cg, kernel, sizeof(float) * (size_t)kh * kw, cudaMemcpyHostToDevice, st));
+        dk = ws.cg;
+    }
     EPLL_CU(cudaMemsetAsync(ws.kern, 0, sizeof(float) * N, st));
     k_wrap_kernel<<<(kh * kw + 255) / 256, 256, 0, st>>>(dk, kh, kw, H, W, ws.kern);
     EPLL_LAUNCHED(g);

@@ -775,19 +775,20 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // sampled patch covers it.  Optionally fused with the pixelwise image update
 // xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult.
 //
-// Two threads own 8 consecutive pixels of an image row, each thread four of
-// the eight patch rows u.  For each u it visits the 15 anchors
+// AG_SPLIT (2 or 4) threads own 8 consecutive pixels of an image row, each
+// thread 8 / AG_SPLIT of the eight patch rows u.  For each u it visits the 15 anchors
 // (i - u, j0 - 7 .. j0 + 7) whose patches cover some of the pixels; an anchor
 // outside the subset costs only its multiplicity load, a sampled one two
 // 16-byte loads of its patch row u (the 8 estimates that fall on this image
 // row), each added to the pixels it covers.  Every estimate is thus read once
 // per covering pixel group rather than once per pixel in 4-byte pieces.
-// Summation order per pixel: each thread's four rows (u, then anchor column
-// ascending), then the two partial sums.
+// Summation order per pixel: each thread's rows (u, then anchor column
+// ascending), then the partial sums pairwise.
 // ============================================================================
 constexpr int AG_GROUP = 8;  // pixels per thread group
-constexpr int AG_SPLIT = 2;  // threads per pixel group, each summing PS / AG_SPLIT patch rows
 
+// AG_SPLIT: threads per pixel group, each summing PS / AG_SPLIT patch rows
+template <int AG_SPLIT>
 __global__ void __launch_bounds__(256)
 k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             const float *xhat, int H, int W, const float *__restrict__ y,
@@ -857,7 +858,8 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             }
         }
     }
-    // the group's partial sums (patch rows 4h .. 4h + 3 in thread h)
+    // the group's partial sums (patch rows (PS / AG_SPLIT) h .. in thread h),
+    // added pairwise in a fixed order
 #pragma unroll
     for (int o = 1; o < AG_SPLIT; o <<= 1) {
 #pragma unroll
@@ -888,9 +890,14 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
                              const float *y, const float *a, const float *lamf, double bmult,
                              float *xout, cudaStream_t st)
 {
-    const int threads = H * ((W + AG_GROUP - 1) / AG_GROUP) * AG_SPLIT;
-    k_aggregate<<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                      xout);
+    const int split = g->tile_agg == 4 ? 4 : 2;
+    const int threads = H * ((W + AG_GROUP - 1) / AG_GROUP) * split;
+    if (split == 4)
+        k_aggregate<4><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+                                                             xout);
+    else
+        k_aggregate<2><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+                                                             xout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

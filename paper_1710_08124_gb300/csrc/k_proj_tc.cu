@@ -560,6 +560,8 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Zhi = ws.Zb, *Zlo = ws.Zb + ws.zrows * PD;
     epll_status s;
+    const bool bn128 = g->tile_bn == 128;
+    const int BNs = bn128 ? 128 : 256;
     if (fmt == 2) {
         if ((s = ensure_prop_ws(g, n))) return s;  // ws.cand, the pair buffers
         // FP16 operand rows in ws.Z2 (free until the rescoring's score dump)
@@ -572,9 +574,11 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
         EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
         CUtensorMap a, b;
         if ((s = make_map(&a, Zf, rows, TC_M))) return s;
-        if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
-        if ((s = dispatch_rr<256, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 0),
-                                           tau_abs, tau_rel, ws.flag1, nflag1, st)))
+        if ((s = make_map(&b, g->tab.B1, g->Rtot, BNs))) return s;
+        if ((s = bn128 ? dispatch_rr<128, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 0),
+                                                   tau_abs, tau_rel, ws.flag1, nflag1, st)
+                       : dispatch_rr<256, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 0),
+                                                   tau_abs, tau_rel, ws.flag1, nflag1, st)))
             return s;
         if ((s = launch_pair_scores(g, xhat, H, W, anchors, n, 4, ws.flag1, nflag1, st))) return s;
         return launch_cand_combine(g, n, 4, ws.flag1, nflag1, tau_abs, ws.flag, cnt(g, CNT_NFLAG), st);
@@ -590,10 +594,12 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     if ((s = make_map(&a, Zhi, rows, TC_M))) return s;
     if ((s = make_map(&alo, Zlo, rows, TC_M))) return s;
     if (split_first) {
-        if ((s = make_map(&b, g->tab.Bs, g->Rtot, 256))) return s;
-        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, 256))) return s;
-        return dispatch_rr<256, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1),
-                                   tau_abs, tau_rel, flag1, nflag1, st);
+        if ((s = make_map(&b, g->tab.Bs, g->Rtot, BNs))) return s;
+        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, BNs))) return s;
+        return bn128 ? dispatch_rr<128, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 1),
+                                           tau_abs, tau_rel, flag1, nflag1, st)
+                     : dispatch_rr<256, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1),
+                                           tau_abs, tau_rel, flag1, nflag1, st);
     }
     if (fp8) {
         CUtensorMap a8, b8;
@@ -629,10 +635,13 @@ epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, cons
     CUtensorMap a2, a2lo, bs, bslo;
     if ((s = make_map(&a2, Z2hi, rows, TC_M))) return s;
     if ((s = make_map(&a2lo, Z2lo, rows, TC_M))) return s;
-    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, 256))) return s;
-    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, 256))) return s;
-    return dispatch_rr<256, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 256, 1),
-                               tau_abs, SPLIT_REL, ws.flag, cnt(g, CNT_NFLAG), st);
+    const bool bn128 = g->tile_bn == 128;
+    if ((s = make_map(&bs, g->tab.Bs, g->Rtot, bn128 ? 128 : 256))) return s;
+    if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, bn128 ? 128 : 256))) return s;
+    return bn128 ? dispatch_rr<128, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 128, 1),
+                                       tau_abs, SPLIT_REL, ws.flag, cnt(g, CNT_NFLAG), st)
+                 : dispatch_rr<256, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 256, 1),
+                                       tau_abs, SPLIT_REL, ws.flag, cnt(g, CNT_NFLAG), st);
 }
 
 }  // namespace epll
