@@ -52,8 +52,14 @@ enum { EPLL_DENOISE = 0, EPLL_PIXELWISE = 1, EPLL_CONV_PERIODIC = 2, EPLL_CONV_D
 /* patch subset (Sec. "Speed-up via the restriction to a random subset of patches"):
  * ALL every pixel's patch; FRACTION ceil(f N) distinct anchors redrawn every
  * iteration; JITTER the jittered grid of Eq. 20 (spacing s); REGULAR the
- * regular grid of spacing s, anchors (s n, s m), the same at every iteration */
-enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2, EPLL_SUBSET_REGULAR = 3 };
+ * regular grid of spacing s, anchors (s n, s m), the same at every iteration;
+ * VALID the `valid` boundary: every patch that lies inside the image (no
+ * periodic wrap), with Eq. 6 taken with its non-constant overlap: the image
+ * update weighs each pixel's patch average by its patch count / P (for a
+ * periodic blur the update then runs cg_iters conjugate-gradient iterations
+ * from the patch average instead of the Fourier solve) */
+enum { EPLL_SUBSET_ALL = 0, EPLL_SUBSET_FRACTION = 1, EPLL_SUBSET_JITTER = 2, EPLL_SUBSET_REGULAR = 3,
+       EPLL_SUBSET_VALID = 4 };
 /* arithmetic of the projection that drives the Gaussian selection:
  * FP32   SIMT FP32 dot products;
  * BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation;
@@ -114,9 +120,11 @@ typedef struct {
                            1e-1 FP8; AUTO that of the form it stands for);
                            < 0 selects the default 1e-3 */
     int subset;         /* EPLL_SUBSET_* */
-    double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER / REGULAR: grid spacing s in 1..8 */
+    double subset_param; /* FRACTION: fraction f in (0, 1], ceil(f*H*W) patches; JITTER / REGULAR: grid spacing s in 1..8;
+                            ignored for ALL and VALID */
     uint64_t seed;      /* sampler seed (counter-based splitmix64 draws) */
-    int cg_iters;       /* PIXELWISE initialisation: conjugate-gradient iterations (>= 0) */
+    int cg_iters;       /* conjugate-gradient iterations (>= 0): PIXELWISE initialisation, and
+                           the image update of CONV_PERIODIC with the VALID boundary */
     int select;         /* EPLL_SELECT_EXHAUSTIVE, EPLL_SELECT_PROPOSAL or EPLL_SELECT_TREE */
 } epll_options;
 

@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 P = 64
-FULL, FRACTION, JITTER, REGULAR = 0, 1, 2, 3
+FULL, FRACTION, JITTER, REGULAR, VALID = 0, 1, 2, 3, 4
 DENOISE, PIXELWISE, CONV, SR = 0, 1, 2, 3
 
 
@@ -57,6 +57,11 @@ def _L():
             lib.or_sample_fraction.argtypes = [i, i, d, u64, i, vp]
             lib.or_sample_jitter.argtypes = [i, i, i, u64, i, vp]
             lib.or_sample_regular.argtypes = [i, i, i, vp]
+            lib.or_sample_valid.argtypes = [i, i, vp]
+            lib.or_valid_weights.argtypes = [i, i, vp]
+            lib.or_valid_weights.restype = None
+            lib.or_xupdate_weighted.argtypes = [i, vp, vp, i, i, vp, vp, vp, i, i, d, i, vp]
+            lib.or_xupdate_weighted.restype = None
             lib.or_scores.argtypes = [i, vp, vp, vp, vp, vp, d, vp, i, i, vp, i, vp]
             lib.or_scores.restype = None
             lib.or_patch_step.argtypes = [i, vp, vp, vp, vp, vp, d, vp, i, i, vp, i, vp,
@@ -131,6 +136,8 @@ def sample(H: int, W: int, kind: int = FULL, param: float = 0.0, seed: int = 0, 
         n = L.or_sample_jitter(H, W, int(param), seed, t, _p(out))
     elif kind == REGULAR:
         n = L.or_sample_regular(H, W, int(param), _p(out))
+    elif kind == VALID:
+        n = L.or_sample_valid(H, W, _p(out))
     else:
         raise ValueError("unknown sampler kind")
     if n < 0:
@@ -222,6 +229,26 @@ def init_cg(a, y, c: float, iters: int):
     H, W = y.shape
     out = np.zeros_like(y)
     _L().or_init_cg(_p(a), _p(y), H, W, float(c), int(iters), _p(out))
+    return out
+
+
+def valid_weights(H: int, W: int):
+    """Per-pixel count of the patches lying inside the image, divided by P."""
+    out = np.zeros((H, W))
+    _L().or_valid_weights(H, W, _p(out))
+    return out
+
+
+def xupdate_weighted(deg: int, y, xtilde, wgt, bs: float, a=None, kernel=None, iters: int = 100):
+    """Image update of Eq. 6 with the per-pixel overlap weights wgt."""
+    y, xt, w = _f64(y), _f64(xtilde), _f64(wgt)
+    H, W = y.shape
+    a = None if a is None else _f64(a)
+    k = None if kernel is None else _f64(kernel)
+    kh, kw = (0, 0) if k is None else k.shape
+    out = np.zeros_like(y)
+    _L().or_xupdate_weighted(deg, _p(a), _p(k), kh, kw, _p(y), _p(xt), _p(w), H, W, float(bs), int(iters),
+                             _p(out))
     return out
 
 

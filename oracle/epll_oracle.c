@@ -198,6 +198,30 @@ int or_sample_regular(int H, int W, int s, int *anchors)
     return g;
 }
 
+/* `valid` boundary: every patch that lies entirely inside the image (anchor */
+/* rows 0..H-8, columns 0..W-8), raster order; no patch wraps around.        */
+int or_sample_valid(int H, int W, int *anchors)
+{
+    if (H < PSIDE || W < PSIDE) return -1;
+    int g = 0;
+    for (int i = 0; i + PSIDE <= H; ++i)
+        for (int j = 0; j + PSIDE <= W; ++j) anchors[g++] = i * W + j;
+    return g;
+}
+
+/* Number of valid patches covering each pixel, divided by P: the diagonal of  */
+/* sum_i P_i^T P_i / P in Eq. 6 (1 inside, down to 1/P at a corner).           */
+void or_valid_weights(int H, int W, double *wgt)
+{
+    for (int i = 0; i < H; ++i) {
+        int ci = (i < H - PSIDE ? i : H - PSIDE) - (i - PSIDE + 1 > 0 ? i - PSIDE + 1 : 0) + 1;
+        for (int j = 0; j < W; ++j) {
+            int cj = (j < W - PSIDE ? j : W - PSIDE) - (j - PSIDE + 1 > 0 ? j - PSIDE + 1 : 0) + 1;
+            wgt[(size_t)i * W + j] = (double)(ci * cj) / (double)PDIM;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-beta quantities (Eqs. 8 and 14): nu_kj = S_kj + 1/beta for j < r_k,   */
 /* nu_kP = lambda_k + 1/beta, gamma = S / nu, iota_k = -2 log w_k.           */
@@ -571,6 +595,59 @@ void or_init_cg(const double *a, const double *y, int H, int W, double c, int it
     free(r); free(d); free(q);
 }
 
+static void or_blur(const double *kern, int kh, int kw, const double *x, int H, int W, int adjoint,
+                    double *out);
+
+/* ------------------------------------------------------------------------ */
+/* Image update with a non-constant patch overlap (Eq. 6 with the `valid`     */
+/* boundary): sum_i P_i^T P_i = P diag(w) and sum_i P_i^T zhat_i = P w xt, so */
+/*   x = (A^T A + bs diag(w))^-1 (A^T y + bs w xt).                            */
+/* Pixelwise A = diag(a) (a NULL: denoising): per pixel.  Periodic blur: the  */
+/* matrix is no longer diagonal in the Fourier basis; conjugate gradients in  */
+/* the pixel domain from x = xt, a fixed number of iterations (`iters`),      */
+/* stopping early only once the residual vanishes.                           */
+/* ------------------------------------------------------------------------ */
+void or_xupdate_weighted(int deg_kind, const double *a, const double *kern, int kh, int kw, const double *y,
+                         const double *xt, const double *wgt, int H, int W, double bs, int iters, double *x)
+{
+    size_t N = (size_t)H * W;
+    if (deg_kind != 2) {
+        for (size_t p = 0; p < N; ++p) {
+            double ap = (deg_kind == 1 && a) ? a[p] : 1.0;
+            x[p] = (ap * y[p] + bs * wgt[p] * xt[p]) / (ap * ap + bs * wgt[p]);
+        }
+        return;
+    }
+    double *b = (double *)malloc(sizeof(double) * N), *r = (double *)malloc(sizeof(double) * N),
+           *d = (double *)malloc(sizeof(double) * N), *q = (double *)malloc(sizeof(double) * N),
+           *t = (double *)malloc(sizeof(double) * N);
+    /* (B^T B + bs diag(w)) v */
+#define OR_APPLY(v, out)                                                   \
+    do {                                                                   \
+        or_blur(kern, kh, kw, v, H, W, 0, t);                              \
+        or_blur(kern, kh, kw, t, H, W, 1, out);                            \
+        for (size_t p_ = 0; p_ < N; ++p_) out[p_] += bs * wgt[p_] * v[p_]; \
+    } while (0)
+    or_blur(kern, kh, kw, y, H, W, 1, b);
+    for (size_t p = 0; p < N; ++p) { b[p] += bs * wgt[p] * xt[p]; x[p] = xt[p]; }
+    OR_APPLY(x, q);
+    double rr = 0.0;
+    for (size_t p = 0; p < N; ++p) { r[p] = b[p] - q[p]; d[p] = r[p]; rr += r[p] * r[p]; }
+    for (int it = 0; it < iters && rr > 0.0; ++it) {
+        OR_APPLY(d, q);
+        double dq = 0.0;
+        for (size_t p = 0; p < N; ++p) dq += d[p] * q[p];
+        if (!(dq > 0.0)) break;
+        double alpha = rr / dq, rr2 = 0.0;
+        for (size_t p = 0; p < N; ++p) { x[p] += alpha * d[p]; r[p] -= alpha * q[p]; rr2 += r[p] * r[p]; }
+        double bt = rr2 / rr;
+        for (size_t p = 0; p < N; ++p) d[p] = r[p] + bt * d[p];
+        rr = rr2;
+    }
+#undef OR_APPLY
+    free(b); free(r); free(d); free(q); free(t);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Super-resolution, A = S B (Sec. "Complexity via eigenspace                 */
 /* implementation" counts super-resolution among the problems whose image    */
@@ -731,7 +808,8 @@ double or_lambda_sr(const double *kern, int kh, int kw, int H, int W, int d, dou
 /* deg_kind 0 denoise, 1 pixelwise a, 2 periodic blur, 3 blur then          */
 /* decimation by `factor` (y is (H/factor) x (W/factor)).  subset 0 full set, */
 /* 1 random fraction subset_param, 2 jitter with spacing (int)subset_param,  */
-/* 3 regular grid with spacing (int)subset_param.                            */
+/* 3 regular grid with spacing (int)subset_param, 4 `valid` boundary (every  */
+/* patch inside the image, Eq. 6 with its non-constant overlap).             */
 /* ks_out / gap_out (nullable) receive each iteration's selections, at       */
 /* [t * H * W + i] for the i-th sampled patch; nsel_out[t] their count.       */
 /* ------------------------------------------------------------------------ */
@@ -761,7 +839,8 @@ int or_restore(int K, const double *w, const double *U, const double *S, const i
         if (subset == 0) n = or_sample_full(H, W, anchors);
         else if (subset == 1) n = or_sample_fraction(H, W, subset_param, seed, t, anchors);
         else if (subset == 2) n = or_sample_jitter(H, W, (int)subset_param, seed, t, anchors);
-        else n = or_sample_regular(H, W, (int)subset_param, anchors);
+        else if (subset == 3) n = or_sample_regular(H, W, (int)subset_param, anchors);
+        else n = or_sample_valid(H, W, anchors);
         if (n < 0) { free(anchors); free(xt); return -1; }
         if (nsel_out) nsel_out[t] = n;
         if (or_patch_step(K, w, U, S, r, lam, beta, x, H, W, anchors, n, NULL, xt,
@@ -769,7 +848,14 @@ int or_restore(int K, const double *w, const double *U, const double *S, const i
                           gap_out ? gap_out + (size_t)t * N : NULL, NULL)) {
             free(anchors); free(xt); return -1;
         }
-        if (deg_kind == 2) or_xupdate_conv(kern, kh, kw, y, xt, H, W, bs, x);
+        if (subset == 4) {
+            double *wgt = (double *)malloc(sizeof(double) * N);
+            double *xo = (double *)malloc(sizeof(double) * N);
+            or_valid_weights(H, W, wgt);
+            or_xupdate_weighted(deg_kind, a, kern, kh, kw, y, xt, wgt, H, W, bs, cg_iters, xo);
+            memcpy(x, xo, sizeof(double) * N);
+            free(wgt); free(xo);
+        } else if (deg_kind == 2) or_xupdate_conv(kern, kh, kw, y, xt, H, W, bs, x);
         else if (deg_kind == 3) or_xupdate_sr(kern, kh, kw, y, xt, H, W, factor, bs, x);
         else or_xupdate_pixelwise(deg_kind == 1 ? a : NULL, y, xt, (int)N, bs, x);
     }

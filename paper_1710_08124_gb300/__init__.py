@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libepll.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RANK_FIXED, RANK_RHO = 0, 1
 DENOISE, PIXELWISE, CONV_PERIODIC, CONV_DECIMATE = 0, 1, 2, 3
-SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER, SUBSET_REGULAR = 0, 1, 2, 3
+SUBSET_ALL, SUBSET_FRACTION, SUBSET_JITTER, SUBSET_REGULAR, SUBSET_VALID = 0, 1, 2, 3, 4
 FP32, BF16, FP16, BF16X3, FP8, AUTO = 0, 1, 2, 3, 4, 5
 SELECT_EXHAUSTIVE, SELECT_PROPOSAL, SELECT_TREE = 0, 1, 2
 PAPER_BETA = (1.0, 4.0, 8.0, 16.0, 32.0)

@@ -62,7 +62,7 @@ static void free_workspace(Workspace &ws)
 {
     void *ptrs[] = {ws.xhat, ws.xtil, ws.y, ws.a, ws.anchors_all, ws.mult_all, ws.kstar, ws.gap,
                     ws.flag, ws.flag1, ws.Z2, ws.zz2, ws.zsc2, ws.fscore,
-                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.mu, ws.cg, ws.red, ws.scal, ws.lamf,
+                    ws.perm, ws.items, ws.zrow, ws.Zb, ws.zz, ws.mu, ws.cg, ws.wgt, ws.red, ws.scal, ws.lamf,
                     ws.sampler, ws.counts, ws.ctr, ws.Yh, ws.Hh, ws.Xh, ws.kern,
                     ws.cand, ws.pmass, ws.pperm, ws.pitems, ws.pscore, ws.tnode, ws.tcounts, ws.titems};
     for (void *p : ptrs)
@@ -97,7 +97,7 @@ epll_status ensure_workspace(epll_gmm *g, size_t N)
     fcap /= (size_t)g->K;
     if (fcap < 4096) fcap = 4096;
     if (fcap > N) fcap = N;
-    A(dalloc(&ws.fscore, fcap * (size_t)g->K)); A(dalloc(&ws.cg, 4 * N));
+    A(dalloc(&ws.fscore, fcap * (size_t)g->K)); A(dalloc(&ws.cg, 4 * N)); A(dalloc(&ws.wgt, N));
     A(dalloc(&ws.red, 4096)); A(dalloc(&ws.scal, 16)); A(dalloc(&ws.lamf, 16));
     const size_t sstride = sampler_stride(N);
     A(dalloc(&ws.sampler, TB_MAX * sstride));
@@ -205,8 +205,8 @@ epll_status check_options(const epll_options &o, int H, int W)
         if ((double)s != o.subset_param || s < 1 || s > PS)
             return fail(EPLL_EINVAL, "options.subset_param: grid spacing must be an integer in 1..8");
         (void)H; (void)W;
-    } else if (o.subset != EPLL_SUBSET_ALL) {
-        return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION, _JITTER or _REGULAR");
+    } else if (o.subset != EPLL_SUBSET_ALL && o.subset != EPLL_SUBSET_VALID) {
+        return fail(EPLL_EINVAL, "options.subset must be EPLL_SUBSET_ALL, _FRACTION, _JITTER, _REGULAR or _VALID");
     }
     if (o.cg_iters < 0 || o.cg_iters > 100000) return fail(EPLL_EINVAL, "options.cg_iters out of range");
     if (o.select != EPLL_SELECT_EXHAUSTIVE && o.select != EPLL_SELECT_PROPOSAL && o.select != EPLL_SELECT_TREE)
@@ -381,17 +381,21 @@ epll_status run_restore(epll_gmm *g, const float *y, const float *a, int H, int 
         use_slot(g, b, N);
         if ((s = patch_phase(g, ws.xhat, H, W, o, n, nullptr, st))) return s;
         const unsigned *mult = o.subset == EPLL_SUBSET_ALL ? nullptr : ws.mult;
+        const bool valid = o.subset == EPLL_SUBSET_VALID;
         if (kind == EPLL_CONV_PERIODIC || kind == EPLL_CONV_DECIMATE) {
-            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.lamf, 0.0, ws.xtil, st)))
+            if ((s = launch_aggregate(g, ws.xhat, H, W, mult, nullptr, nullptr, ws.lamf, 0.0, ws.xtil, st, 0,
+                                      valid ? ws.wgt : nullptr)))
                 return s;
-            if (kind == EPLL_CONV_PERIODIC) {
+            if (valid) {
+                if ((s = cgw_update(g, H, W, beta_mult[t], o.cg_iters, st))) return s;
+            } else if (kind == EPLL_CONV_PERIODIC) {
                 if ((s = fft_update(g, H, W, beta_mult[t], st))) return s;
             } else {
                 if ((s = sr_update(g, H, W, d, beta_mult[t], st))) return s;
             }
         } else {
             if ((s = launch_aggregate(g, ws.xhat, H, W, mult, y, kind == EPLL_PIXELWISE ? a : nullptr,
-                                      ws.lamf, beta_mult[t], ws.xhat, st)))
+                                      ws.lamf, beta_mult[t], ws.xhat, st, valid ? 1 : 0)))
                 return s;
         }
     }
@@ -425,6 +429,8 @@ epll_status check_restore_args(epll_gmm *g, const float *y, int H, int W,
             if (deg->kind == EPLL_CONV_DECIMATE &&
                 (deg->factor < 1 || deg->factor > 8 || H % deg->factor || W % deg->factor))
                 return fail(EPLL_EINVAL, "CONV_DECIMATE factor must be in 1..8 and divide H and W");
+            if (deg->kind == EPLL_CONV_DECIMATE && o.subset == EPLL_SUBSET_VALID)
+                return fail(EPLL_EUNSUPPORTED, "the VALID boundary is not served with CONV_DECIMATE");
             double sum = 0.0;
             for (int q = 0; q < deg->kh * deg->kw; ++q) {
                 if (!std::isfinite(deg->kernel[q])) return fail(EPLL_EINVAL, "kernel is not finite");

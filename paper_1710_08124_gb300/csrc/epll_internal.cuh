@@ -100,6 +100,7 @@ struct Workspace {
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)
     float *mu = nullptr;                      // [N] patch means (split extraction)
     float *cg = nullptr;                      // [4N] CG vectors r, d (two buffers), q
+    float *wgt = nullptr;                     // [N] per-pixel overlap weights (`valid` boundary)
     float *red = nullptr;                     // reduction partials
     double *scal = nullptr;                   // [0]: lambda, input of the FP64 per-beta tables
     float *lamf = nullptr;                    // [2]: lambda as an unevaluated float pair (hi, lo)
@@ -314,9 +315,15 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
 // Reprojection.  When y != nullptr the pixelwise image update is fused
 // (xout = (a y + bs xt)/(a^2 + bs), bs = lambda*mult with lambda = lamf[0];
 // a == nullptr means a = 1), otherwise xtilde is written to xout.
+// weighted: bs is multiplied by each pixel's patch count / P (Eq. 6 with the
+// `valid` boundary); wout (nullable) receives that weight.
 epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
                              const float *y, const float *a, const float *lamf, double bmult,
-                             float *xout, cudaStream_t st);
+                             float *xout, cudaStream_t st, int weighted = 0, float *wout = nullptr);
+// Image update of a periodic blur with per-pixel overlap weights ws.wgt
+// (`valid` boundary): iters conjugate-gradient iterations on
+// (H^T H + bs diag(w)) x = H^T y + bs w xtil from x = xtil (ws.xtil -> ws.xhat).
+epll_status cgw_update(epll_gmm *g, int H, int W, double bmult, int iters, cudaStream_t st);
 
 // Image-domain steps (k_image.cu)
 epll_status launch_lambda(epll_gmm *g, int kind, const float *a, int H, int W, double sigma,

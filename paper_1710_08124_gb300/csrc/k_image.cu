@@ -322,6 +322,146 @@ epll_status fft_update(epll_gmm *g, int H, int W, double bmult, cudaStream_t st)
     return EPLL_OK;
 }
 
+// ---------------------------------------------------------------- weighted update (`valid` boundary)
+// With the `valid` boundary the patch overlap of Eq. 6 varies over the image,
+// so the periodic-blur update (H^T H + bs diag(w)) x = H^T y + bs w xtil is
+// not diagonal in any Fourier basis: it is solved by conjugate gradients from
+// x = xtil (residual H^T (y - H xtil)), H^T H applied through the R2C / C2R
+// transforms of the FFT path, dot products as compensated FP32 block partials
+// reduced by one block in a fixed order.  Scalars sc: rr, alpha, beta, done.
+__global__ void k_cgw_r0(const cufftComplex *__restrict__ Hh, const cufftComplex *__restrict__ Yh, int M,
+                         float invN, cufftComplex *__restrict__ X)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const cufftComplex h = Hh[p], x = X[p], y = Yh[p];
+    const float er = y.x - (h.x * x.x - h.y * x.y), ei = y.y - (h.x * x.y + h.y * x.x);
+    X[p] = make_float2((h.x * er + h.y * ei) * invN, (h.x * ei - h.y * er) * invN);  // conj(H) e / N
+}
+
+__global__ void k_cgw_h2(const cufftComplex *__restrict__ Hh, int M, float invN, cufftComplex *__restrict__ X)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const cufftComplex h = Hh[p], x = X[p];
+    const float g = (h.x * h.x + h.y * h.y) * invN;
+    X[p] = make_float2(x.x * g, x.y * g);
+}
+
+// q += bs w d; partial d^T q
+__global__ void __launch_bounds__(RED_THREADS)
+k_cgw_q(float *__restrict__ q, const float *__restrict__ d, const float *__restrict__ w,
+        const float *__restrict__ lamf, float bmult, int N, float *__restrict__ part)
+{
+    const float bs = lamf[0] * bmult;
+    float s = 0.0f, c = 0.0f, m = 0.0f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const float dv = d[p];
+        const float qv = fmaf(bs * w[p], dv, q[p]);
+        q[p] = qv;
+        csum_fma(s, c, dv, qv);
+    }
+    block_csum_max<RED_THREADS>(s, c, m);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s;
+        part[2 * blockIdx.x + 1] = c;
+    }
+}
+
+// partial r^T r, or (x, r updated first unless done) after x += alpha d, r -= alpha q
+__global__ void __launch_bounds__(RED_THREADS)
+k_cgw_xr(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ d, const float *__restrict__ q,
+         const float *__restrict__ sc, int N, int update, float *__restrict__ part)
+{
+    const bool go = update && sc[3] == 0.0f;
+    const float alpha = sc[1];
+    float s = 0.0f, c = 0.0f, m = 0.0f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        float rv = r[p];
+        if (go) {
+            x[p] = fmaf(alpha, d[p], x[p]);
+            rv = fmaf(-alpha, q[p], rv);
+            r[p] = rv;
+        }
+        csum_fma(s, c, rv, rv);
+    }
+    block_csum_max<RED_THREADS>(s, c, m);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s;
+        part[2 * blockIdx.x + 1] = c;
+    }
+}
+
+// which 0: rr = sum (done if not positive); 1: dq = sum, alpha = rr / dq
+// (done if dq is not positive); 2: beta = sum / rr, rr = sum (done if not positive)
+__global__ void __launch_bounds__(RED_THREADS)
+k_cgw_scalar(int which, const float *__restrict__ part, int nparts, float *__restrict__ sc)
+{
+    float s = 0.0f, c = 0.0f, m = 0.0f;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) csum_merge(s, c, part[2 * b], part[2 * b + 1]);
+    block_csum_max<RED_THREADS>(s, c, m);
+    if (threadIdx.x) return;
+    const float v = __fadd_rn(s, c);
+    if (which == 0) {
+        sc[0] = v;
+        sc[3] = v > 0.0f ? 0.0f : 1.0f;
+    } else if (sc[3] == 0.0f) {
+        if (which == 1) {
+            if (!(v > 0.0f)) sc[3] = 1.0f;
+            else sc[1] = sc[0] / v;
+        } else {
+            sc[2] = v / sc[0];
+            sc[0] = v;
+            if (!(v > 0.0f)) sc[3] = 1.0f;
+        }
+    }
+}
+
+__global__ void k_cgw_d(float *__restrict__ d, const float *__restrict__ r, const float *__restrict__ sc, int N)
+{
+    if (sc[3] != 0.0f) return;
+    const float beta = sc[2];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) d[p] = fmaf(beta, d[p], r[p]);
+}
+
+epll_status cgw_update(epll_gmm *g, int H, int W, double bmult, int iters, cudaStream_t st)
+{
+    Workspace &ws = g->ws;
+    const size_t cap = ws.capN;
+    const int N = H * W, M = H * (W / 2 + 1);
+    const float invN = 1.0f / ((float)H * (float)W);
+    float *r = ws.cg, *dd = ws.cg + cap, *q = ws.cg + 2 * cap;
+    float *part = ws.red, *sc = ws.lamf + 4;
+    EPLL_CU(cudaMemcpyAsync(ws.xhat, ws.xtil, sizeof(float) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    EPLL_FFT(cufftExecR2C(ws.plan_r2c, ws.xtil, ws.Xh));
+    k_cgw_r0<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, ws.Yh, M, invN, ws.Xh);
+    EPLL_LAUNCHED(g);
+    EPLL_FFT(cufftExecC2R(ws.plan_c2r, ws.Xh, r));
+    k_cgw_xr<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ws.xhat, r, dd, q, sc, N, 0, part);
+    EPLL_LAUNCHED(g);
+    k_cgw_scalar<<<1, RED_THREADS, 0, st>>>(0, part, RED_BLOCKS, sc);
+    EPLL_LAUNCHED(g);
+    EPLL_CU(cudaMemcpyAsync(dd, r, sizeof(float) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    const float bm = (float)bmult;
+    for (int it = 0; it < iters; ++it) {
+        EPLL_FFT(cufftExecR2C(ws.plan_r2c, dd, ws.Xh));
+        k_cgw_h2<<<(M + 255) / 256, 256, 0, st>>>(ws.Hh, M, invN, ws.Xh);
+        EPLL_LAUNCHED(g);
+        EPLL_FFT(cufftExecC2R(ws.plan_c2r, ws.Xh, q));
+        k_cgw_q<<<RED_BLOCKS, RED_THREADS, 0, st>>>(q, dd, ws.wgt, ws.lamf, bm, N, part);
+        EPLL_LAUNCHED(g);
+        k_cgw_scalar<<<1, RED_THREADS, 0, st>>>(1, part, RED_BLOCKS, sc);
+        EPLL_LAUNCHED(g);
+        k_cgw_xr<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ws.xhat, r, dd, q, sc, N, 1, part);
+        EPLL_LAUNCHED(g);
+        k_cgw_scalar<<<1, RED_THREADS, 0, st>>>(2, part, RED_BLOCKS, sc);
+        EPLL_LAUNCHED(g);
+        k_cgw_d<<<RED_BLOCKS, RED_THREADS, 0, st>>>(dd, r, sc, N);
+        EPLL_LAUNCHED(g);
+    }
+    return EPLL_OK;
+}
+
 // ---------------------------------------------------------------- super-resolution
 // A = S B (blur, then keep pixel (d i, d j)).  In the Fourier basis A^T A is
 // block diagonal: the block at a low-resolution frequency w' couples the d^2

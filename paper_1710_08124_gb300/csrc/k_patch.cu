@@ -773,7 +773,8 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // the sampled patches that cover it (weighted by their multiplicity in the
 // subset), divides by their number, and keeps the current estimate where no
 // sampled patch covers it.  Optionally fused with the pixelwise image update
-// xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult.
+// xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult
+// (with the `valid` boundary bs is weighed by the pixel's patch count / P).
 //
 // AG_SPLIT (2 or 4) threads own 8 consecutive pixels of an image row, each
 // thread 8 / AG_SPLIT of the eight patch rows u.  For each u it visits the 15 anchors
@@ -793,7 +794,7 @@ __global__ void __launch_bounds__(256)
 k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             const float *xhat, int H, int W, const float *__restrict__ y,
             const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
-            float *xout)
+            float *xout, int weighted, float *__restrict__ wout)
 {
     const int gw = (W + AG_GROUP - 1) / AG_GROUP;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / AG_SPLIT;
@@ -877,9 +878,12 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
         if (j0 + t >= W) break;
         const size_t p = (size_t)i * W + j0 + t;
         const float xt = cnt[t] ? sum[t] / (float)cnt[t] : xhat[p];
+        const float wt = (float)cnt[t] * (1.0f / (float)PD);  // patch count / P
+        if (wout) wout[p] = wt;
         if (y) {
             const float ap = a ? a[p] : 1.0f;
-            xout[p] = (ap * y[p] + bs * xt) / (ap * ap + bs);
+            const float bw = weighted ? bs * wt : bs;
+            xout[p] = (ap * y[p] + bw * xt) / (ap * ap + bw);
         } else {
             xout[p] = xt;
         }
@@ -888,16 +892,16 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
 
 epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const unsigned *mult,
                              const float *y, const float *a, const float *lamf, double bmult,
-                             float *xout, cudaStream_t st)
+                             float *xout, cudaStream_t st, int weighted, float *wout)
 {
     const int split = g->tile_agg == 4 ? 4 : 2;
     const int threads = H * ((W + AG_GROUP - 1) / AG_GROUP) * split;
     if (split == 4)
         k_aggregate<4><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                             xout);
+                                                             xout, weighted, wout);
     else
         k_aggregate<2><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                             xout);
+                                                             xout, weighted, wout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

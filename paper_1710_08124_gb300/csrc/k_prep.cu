@@ -226,6 +226,21 @@ __global__ void k_jitter(int H, int W, int s, uint64_t seed, int t0, int ni, int
     atomicAdd(&mult[a], 1u);
 }
 
+// ---------------------------------------------------------------- valid boundary
+// Every patch inside the image, raster order: anchor g is (g / nj, g % nj)
+// with nj = W - 7.
+__global__ void k_valid(int H, int W, int nb, int *__restrict__ anchors_all, unsigned *__restrict__ mult_all)
+{
+    const int nj = W - PS + 1, n = (H - PS + 1) * nj;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int a = (g / nj) * W + g % nj;
+    for (int b = 0; b < nb; ++b) {
+        anchors_all[(size_t)b * H * W + g] = a;
+        mult_all[(size_t)b * H * W + a] = 1u;
+    }
+}
+
 // ---------------------------------------------------------------- fraction
 // Exactly M = ceil(frac N) anchors: those with the smallest (key, anchor),
 // key = high 32 bits of draw(anchor).  A 4-pass radix select (8-bit digits,
@@ -417,6 +432,7 @@ int sample_count(int H, int W, const epll_options &o)
         int s = (int)o.subset_param;
         return ((H + s - 1) / s) * ((W + s - 1) / s);
     }
+    if (o.subset == EPLL_SUBSET_VALID) return (H - PS + 1) * (W - PS + 1);
     return N;
 }
 
@@ -429,6 +445,12 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     const int N = H * W;
     *n = sample_count(H, W, o);
     if (o.subset == EPLL_SUBSET_ALL) return EPLL_OK;
+    if (o.subset == EPLL_SUBSET_VALID) {
+        EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N * nb, st));
+        k_valid<<<(*n + 255) / 256, 256, 0, st>>>(H, W, nb, anchors, mult);
+        EPLL_LAUNCHED(g);
+        return EPLL_OK;
+    }
     if (o.subset == EPLL_SUBSET_JITTER || o.subset == EPLL_SUBSET_REGULAR) {
         const int s = (int)o.subset_param;
         EPLL_CU(cudaMemsetAsync(mult, 0, sizeof(unsigned) * (size_t)N * nb, st));

@@ -53,7 +53,7 @@ def test_sampler_bit_identical(H, W):
     for t in range(3):
         for kind, param in [(ep.SUBSET_FRACTION, 1 / 3), (ep.SUBSET_FRACTION, 0.05),
                             (ep.SUBSET_JITTER, 6), (ep.SUBSET_JITTER, 3),
-                            (ep.SUBSET_REGULAR, 3), (ep.SUBSET_REGULAR, 8)]:
+                            (ep.SUBSET_REGULAR, 3), (ep.SUBSET_REGULAR, 8), (ep.SUBSET_VALID, 0)]:
             o = ep.Options(subset=kind, subset_param=param, seed=1234 + t)
             g = ep.sample(H, W, o, t).cpu().numpy()
             r = oracle.sample(H, W, kind, param, seed=1234 + t, t=t)
@@ -218,6 +218,36 @@ def test_restore_super_resolution(H, W, d, sub):
     assert np.abs(xg - xo).max() <= 1e-4
     xh = ep.restore_host(gm, yl, sigma, kind=ep.CONV_DECIMATE, kernel=k, factor=d, options=o)
     assert np.abs(xh - xg).max() == 0.0
+
+
+@pytest.mark.parametrize("kind", ["denoise", "inpaint", "deblur"])
+def test_restore_valid_boundary(kind):
+    """`valid` boundary (only the patches inside the image; Eq. 6 with the
+    per-pixel patch count): denoising and inpainting update pixel by pixel
+    with the count weights, deblurring by conjugate gradients on the weighted
+    system; within 1e-4 of the oracle."""
+    gm, om = models(12, "fixed", 8)
+    o = ep.Options(subset=ep.SUBSET_VALID, cg_iters=60)
+    kw = dict(subset=oracle.VALID, cg_iters=60)
+    if kind == "denoise":
+        sigma = 20 / 255
+        x, y = synth.denoise_problem(12, 44, sigma, W=37)
+        xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, **kw)
+        xg = ep.restore(gm, dev(y), sigma, options=o).cpu().numpy()
+    elif kind == "inpaint":
+        sigma = 10 / 255
+        x, a, y = synth.inpaint_problem(13, 40, sigma, W=33)
+        xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, deg=oracle.PIXELWISE, a=a, **kw)
+        xg = ep.restore(gm, dev(y), sigma, kind=ep.PIXELWISE, a=dev(a), options=o).cpu().numpy()
+    else:
+        sigma = 5 / 255
+        x, k, y = synth.deblur_problem(14, 40, sigma, W=36, size=9, sigma_b=1.0)
+        k = k.astype(np.float32)
+        xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, deg=oracle.CONV,
+                            kernel=k.astype(np.float64), **kw)
+        xg = ep.restore(gm, dev(y), sigma, kind=ep.CONV_PERIODIC, kernel=k, options=o).cpu().numpy()
+    assert abs(psnr(xg, x) - psnr(xo, x)) <= 0.05
+    assert np.abs(xg - xo).max() <= 1e-4
 
 
 def test_restore_inpaint_ragged_large():

@@ -347,6 +347,64 @@ def test_sr_factor_one_is_the_deconvolution():
     np.testing.assert_allclose(a, b, atol=1e-8)
 
 
+def test_valid_boundary_sampler_and_weights():
+    """`valid` boundary: exactly the (H-7)(W-7) patches inside the image, in
+    raster order; the weights are the brute-force patch count over P."""
+    for H, W in ((8, 8), (10, 12), (17, 9)):
+        an = oracle.sample(H, W, oracle.VALID)
+        assert len(an) == (H - 7) * (W - 7)
+        i, j = np.divmod(an, W)
+        assert (i <= H - 8).all() and (j <= W - 8).all() and np.all(np.diff(an) > 0)
+        cnt = np.zeros((H, W))
+        for a in an:
+            r, c = divmod(int(a), W)
+            cnt[r:r + 8, c:c + 8] += 1
+        np.testing.assert_array_equal(oracle.valid_weights(H, W), cnt / 64)
+
+
+@pytest.mark.parametrize("deg", ["denoise", "mask", "blur"])
+def test_weighted_update_is_eq6_with_valid_patches(deg):
+    """The image update with the `valid` boundary equals Eq. 6 written with
+    the literal patch extraction matrices P_i of the valid patches:
+    x = (A^T A + b' sum P_i^T P_i)^-1 (A^T y + b' sum P_i^T zhat_i), b' = bs / P,
+    for random patch estimates zhat_i (the blur's conjugate gradients run to
+    convergence here)."""
+    H, W = 11, 13
+    rng = np.random.default_rng(3)
+    an = oracle.sample(H, W, oracle.VALID)
+    Ps = []
+    for a in an:
+        r, c = divmod(int(a), W)
+        P = np.zeros((64, H * W))
+        for e in range(64):
+            P[e, (r + e // 8) * W + c + e % 8] = 1.0
+        Ps.append(P)
+    zh = rng.standard_normal((len(an), 64)) * 0.1 + 0.5
+    S = sum(P.T @ P for P in Ps)
+    Z = sum(P.T @ z for P, z in zip(Ps, zh))
+    cnt = np.diag(S)
+    xt = (Z / cnt).reshape(H, W)
+    wgt = oracle.valid_weights(H, W)
+    y = rng.random((H, W))
+    bs = 0.37
+    a = kern = None
+    if deg == "denoise":
+        A, kind = np.eye(H * W), oracle.DENOISE
+    elif deg == "mask":
+        a = (rng.random((H, W)) < 0.7).astype(float)
+        A, kind = np.diag(a.ravel()), oracle.PIXELWISE
+    else:
+        kern = synth.gaussian_kernel(5, 1.0)
+        A, kind = circulant_blur(kern, H, W), oracle.CONV
+    ref = np.linalg.solve(A.T @ A + bs / 64 * S, A.T @ y.ravel() + bs / 64 * Z)
+    got = oracle.xupdate_weighted(kind, y, xt, wgt, bs, a=a, kernel=kern, iters=5000)
+    np.testing.assert_allclose(got.ravel(), ref, atol=1e-10)
+    if deg == "blur":
+        # with uniform weights the conjugate gradients reach the Fourier solve
+        got1 = oracle.xupdate_weighted(kind, y, xt, np.ones((H, W)), bs, kernel=kern, iters=5000)
+        np.testing.assert_allclose(got1, oracle.xupdate_conv(kern, y, xt, bs), atol=1e-10)
+
+
 def test_lambda_closed_forms():
     H = W = 16
     assert oracle.lam(oracle.DENOISE, H, W, 20 / 255) == 1.0

@@ -36,6 +36,7 @@ CASES = [
     (1024, 1023, ep.SUBSET_FRACTION, 0.01),
     (50, 37, ep.SUBSET_REGULAR, 4),
     (33, 40, ep.SUBSET_ALL, 0.0),
+    (30, 41, ep.SUBSET_VALID, 0.0),
 ]
 
 
