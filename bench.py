@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--pmin", type=float, default=0.0, help="proposal workload: softmax mass below which a "
                     "patch is scored exhaustively")
     ap.add_argument("--train-steps", type=int, default=3000, help="proposal workload: AdamW steps")
-    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal", "tree", "subsets", "deblur", "epll64"],
+    ap.add_argument("--workload", choices=["fepll", "uneven", "proposal", "tree", "subsets", "deblur", "epll64",
+                                           "ablation"],
                     default="fepll",
                     help="fepll: the 512x512 FEPLL denoising workload (default line); proposal: the learned "
                          "top-m proposal at 512x512, sigma 25/255, K=200, r=64; tree: the balanced search "
@@ -78,7 +79,9 @@ def parse():
                          "subsets: the fepll images and models under each patch subset (regular grid s=3, "
                          "jittered grid s=6, random 1/3, all patches); deblur: 512x512 FEPLL deblurring "
                          "(25x25 Gaussian blur, sigma 2/255, K=200, r=8) in FP8 against BF16X3 and FP32; "
-                         "epll64: the small EPLL case (64x64, K=20, full rank, every patch, FP32)")
+                         "epll64: the small EPLL case (64x64, K=20, full rank, every patch, FP32); ablation: the "
+                         "paper's three accelerations (flat tail, jittered subset, search tree) and the learned "
+                         "proposal, alone and together, on a K=200 prior fitted by EM to dead-leaves patches")
     return ap.parse_args()
 
 
@@ -997,6 +1000,136 @@ def run_epll64(args):
     return 0
 
 
+# ---------------------------------------------------------------- ablation on an EM-fitted prior
+ABL_PATCHES = 60000
+ABL_EM_ITERS = 10
+ABL_SIGMA = 25 / 255
+ABL_IMAGES = 2
+ABL_WORKLOAD = ("ingredient ablation: GMM K=200 fitted by EM (10 iterations) to 60,000 DC-free 8x8 patches of "
+                "dead-leaves images; 2 512x512 dead-leaves images at sigma 25/255, 5 HQS iterations; exact EPLL "
+                "(full rank, every patch, exhaustive) against the flat tail (rho 0.95), the jittered grid "
+                "(s = 6), the search tree (327 nodes), all three (FEPLL), and FEPLL with the learned proposal "
+                "(m = 4) in place of the tree")
+
+
+def run_ablation(args):
+    """The paper's ingredient study (Sec. "Performance analysis"): PSNR and
+    speed of each acceleration alone and of their combination, against exact
+    EPLL, on a prior fitted by EM (Sec. 2) so that PSNR is meaningful."""
+    import torch
+
+    import oracle
+    import paper_1710_08124_gb300 as ep
+    from paper_1710_08124_gb300 import gmm_em
+    from paper_1710_08124_gb300 import proposal as pr
+    from paper_1710_08124_gb300 import tree as ptree
+
+    ep.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    Z = synth.clean_patches(ABL_PATCHES, seed=0, side=256)
+    w, U, S, ll = gmm_em.fit(Z, K, iters=ABL_EM_ITERS, seed=0)
+    fit_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T = ptree.build_tree(w, U, S)
+    tree_s = time.perf_counter() - t0
+    m_exact = ep.gmm_load(w, U, S, ep.RANK_FIXED, 64)
+    m_rho = ep.gmm_load(w, U, S, ep.RANK_RHO, 0.95)
+    ranks, _ = m_rho.ranks()
+    ep.attach_tree(m_exact, T)
+    ep.attach_tree(m_rho, T)
+    # the learned proposal: trained on the method's own selections with the flat-tailed prior
+    rng = np.random.default_rng(4)
+    sig = rng.uniform(5, 50, PROP_TRAIN) / 255
+    obs = [torch.as_tensor((synth.image(500 + i, 128) + synth.noise(500 + i, 128, 128, s_)).astype(np.float32),
+                           device=dev) for i, s_ in enumerate(sig)]
+    t0 = time.perf_counter()
+    data = pr.make_pairs(m_rho, obs, sig)
+    net = ep.Proposal(K, seed=11)
+    pr.train(net, data, steps=2000, batch=4096, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del data
+    ep.attach_proposal(m_rho, net, topm=4, pmin=0.0)
+
+    probs = [synth.denoise_problem(700 + j, H, ABL_SIGMA) for j in range(ABL_IMAGES)]
+    ys = [torch.as_tensor(y.astype(np.float32), device=dev) for _, y in probs]
+    outs = [torch.empty_like(y) for y in ys]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    jit = dict(subset=ep.SUBSET_JITTER, subset_param=6, seed=3)
+    variants = [
+        ("exact", m_exact, ep.Options(precision=ep.AUTO)),
+        ("flat_tail_rho0.95", m_rho, ep.Options(precision=ep.AUTO)),
+        ("jitter_s6", m_exact, ep.Options(precision=ep.AUTO, **jit)),
+        ("tree", m_exact, ep.Options(select=ep.SELECT_TREE)),
+        ("fepll_all_three", m_rho, ep.Options(select=ep.SELECT_TREE, **jit)),
+        ("fepll_proposal_m4", m_rho, ep.Options(select=ep.SELECT_PROPOSAL, **jit)),
+    ]
+    steps = max(3, min(args.steps, 10))
+    res = {}
+    clk = None
+    for name, gm, o in variants:
+        for _ in range(max(args.warmup, 2)):
+            for j in range(ABL_IMAGES):
+                ep.restore(gm, ys[j], ABL_SIGMA, BETA, options=o, out=outs[j])
+        if name == "fepll_all_three":
+            clocks = ClockSampler(0)
+            clocks.start()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for j in range(ABL_IMAGES):
+                ep.restore(gm, ys[j], ABL_SIGMA, BETA, options=o, out=outs[j])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        if name == "fepll_all_three":
+            clk = clocks.stop()
+        ps = [psnr(outs[j].cpu().numpy(), probs[j][0]) for j in range(ABL_IMAGES)]
+        res[name] = {"restores_per_s": steps * ABL_IMAGES / tot, "psnr_db": float(np.mean(ps))}
+    ref = res["exact"]
+    for name, d in res.items():
+        d["psnr_delta_vs_exact_db"] = d["psnr_db"] - ref["psnr_db"]
+        d["speedup_vs_exact"] = d["restores_per_s"] / ref["restores_per_s"]
+    noisy = float(np.mean([psnr(y, x) for x, y in probs]))
+    main = res["fepll_all_three"]
+    line = {
+        "metric": "512x512 restores/s of FEPLL (flat tail rho 0.95 + jittered grid s=6 + search tree) on an "
+                  "EM-fitted K=200 prior, sigma 25/255",
+        "value": main["restores_per_s"], "unit": "restores/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ABL_IMAGES / main["restores_per_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": ABL_WORKLOAD, "em_fit_s": fit_s, "em_loglik": [float(v) for v in ll],
+                   "tree_build_s": tree_s, "proposal_pairs_and_training_s": train_s,
+                   "flat_tail_ranks": {"mean": float(np.mean(ranks)), "min": int(ranks.min()),
+                                       "max": int(ranks.max())},
+                   "l2": "256 MB buffer written before each step, outside the timed events"},
+        "noisy_psnr_db": noisy,
+        "ablation": res,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        # the exact variant against the FP64 oracle on a 128x128 image of the same kind
+        om = oracle.Model(w, U, S, "fixed", 64)
+        x, y = synth.denoise_problem(750, 128, ABL_SIGMA)
+        t0 = time.perf_counter()
+        xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), ABL_SIGMA, BETA)
+        dt = time.perf_counter() - t0
+        xg = ep.restore(m_exact, torch.as_tensor(y.astype(np.float32), device=dev), ABL_SIGMA, BETA,
+                        options=ep.Options(precision=ep.AUTO)).cpu().numpy()
+        line["vs_oracle"] = {"what": "exact variant, one 128x128 image", "psnr_delta_db": psnr(xg, x) - psnr(xo, x),
+                             "max_abs_err": float(np.abs(xg - xo).max())}
+        line["cpu_baseline"] = {"value": (128 * 128) / (H * W) / dt, "unit": "restores/s (512x512-equivalent)",
+                                "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": "one full 128x128 exact restoration on the EM prior, scaled by pixels"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- distance to the oracle
 TIE = 1e-4  # near-tie gap of the selection agreement (the oracle's top-2 score gap)
 
@@ -1073,6 +1206,8 @@ def main():
         return run_deblur(args) if rank == 0 else 0
     if args.workload == "epll64":
         return run_epll64(args) if rank == 0 else 0
+    if args.workload == "ablation":
+        return run_ablation(args) if rank == 0 else 0
 
     import torch
 
