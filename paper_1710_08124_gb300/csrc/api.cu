@@ -179,7 +179,8 @@ static void free_model(epll_gmm *g)
     free_tree(g);
     free_tables(g);
     if (g->lane) return;  // lanes share the model arrays of their handle
-    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo, g->d_Ub, g->d_U2b};
+    void *ptrs[] = {g->d_r, g->d_roff, g->d_colk, g->d_S, g->d_w, g->d_lam, g->d_B, g->d_Blo, g->d_Ub, g->d_U2b,
+                    g->d_tileg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_r;
@@ -465,8 +466,12 @@ void epll_options_default(epll_options *o)
     o->select = EPLL_SELECT_EXHAUSTIVE;
 }
 
-epll_status epll_gmm_load(int K, int P, const double *weights, const double *eigvecs,
-                          const double *eigvals, int rank_mode, double rank_param, epll_gmm **out)
+// tile_pack: lay the components out so that none straddles a 256-column tile
+// (the grouping of the tensor-core selection's ragged-rank epilogue); the
+// node model of a search tree keeps consecutive children contiguous instead.
+static epll_status gmm_load_impl(int K, int P, const double *weights, const double *eigvecs,
+                                 const double *eigvals, int rank_mode, double rank_param, bool tile_pack,
+                                 epll_gmm **out)
 {
     if (!out) return fail(EPLL_EINVAL, "null output handle pointer");
     *out = nullptr;
@@ -520,9 +525,22 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
         g->h_r[k] = rk;
         g->h_lam[k] = rk < PD ? tail / (double)(PD - rk) : 0.0;
     }
-    g->h_roff[0] = 0;
-    for (int k = 0; k < K; ++k)
-        g->h_roff[k + 1] = g->h_roff[k] + (g->h_r[k] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
+    // column layout: component k at h_roff[k], its rank padded to a multiple
+    // of 8 columns; with tile_pack a component that would cross a 256-column
+    // boundary starts at the next tile (the skipped columns belong to no
+    // component)
+    std::vector<int> width(K);
+    {
+        int pos = 0;
+        for (int k = 0; k < K; ++k) {
+            width[k] = (g->h_r[k] + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
+            if (tile_pack && pos % RTOT_ALIGN + width[k] > RTOT_ALIGN)
+                pos = (pos + RTOT_ALIGN - 1) / RTOT_ALIGN * RTOT_ALIGN;
+            g->h_roff[k] = pos;
+            pos += width[k];
+        }
+        g->h_roff[K] = pos;
+    }
     g->Rtot = (g->h_roff[K] + RTOT_ALIGN - 1) / RTOT_ALIGN * RTOT_ALIGN;
     g->rank_sum = 0;
     for (int k = 0; k < K; ++k) g->rank_sum += g->h_r[k];
@@ -536,9 +554,12 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     std::vector<double> w(K);
     for (int k = 0; k < K; ++k) w[k] = weights[k] / wsum;
     std::vector<float> B((size_t)PD * R, 0.0f), Blo((size_t)PD * R, 0.0f);
-    std::vector<int> colk(R);
+    std::vector<int> colk(R, -1);
     for (int k = 0; k < K; ++k) {
-        for (int c = g->h_roff[k]; c < g->h_roff[k + 1]; ++c) colk[c] = k;
+        // the component's padded width; the trailing columns of the last tile
+        // belong to the last component (zero basis columns)
+        const int cend = k + 1 < K ? g->h_roff[k] + width[k] : R;
+        for (int c = g->h_roff[k]; c < cend; ++c) colk[c] = k;
         for (int e = 0; e < PD; ++e)
             for (int j = 0; j < g->h_r[k]; ++j) {
                 const double u = eigvecs[((size_t)k * PD + e) * PD + j];
@@ -556,6 +577,7 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(dalloc(&g->d_S, (size_t)K * PD)); A(dalloc(&g->d_w, K)); A(dalloc(&g->d_lam, K));
     A(dalloc(&g->d_B, (size_t)PD * R + COL_PAD)); A(dalloc(&g->d_Blo, (size_t)PD * R + COL_PAD));
     A(dalloc(&g->d_Ub, 2 * (size_t)PD * R)); A(dalloc(&g->d_U2b, 2 * (size_t)PD * R));
+    A(dalloc(&g->d_tileg, R / RTOT_ALIGN));
     g->Rp = R + COL_PAD;
     A(alloc_tables(g));
     if (e != cudaSuccess) {
@@ -570,6 +592,28 @@ epll_status epll_gmm_load(int K, int P, const double *weights, const double *eig
     A(cudaMemset(g->d_B, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
     A(cudaMemset(g->d_Blo, 0, sizeof(float) * ((size_t)PD * R + COL_PAD)));
     A(cudaMemcpy(g->d_colk, colk.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
+    {
+        // the four epilogue column groups of every 256-column tile: group h
+        // starts at the first component starting at or after column 64 h of
+        // the tile (the tile's end when there is none); components never
+        // straddle a group when the layout is tile-packed
+        const int nt = R / RTOT_ALIGN;
+        std::vector<int4> tg(nt);
+        for (int t = 0; t < nt; ++t) {
+            int b[4] = {0, RTOT_ALIGN, RTOT_ALIGN, RTOT_ALIGN};
+            for (int h = 1; h < 4; ++h)
+                for (int k = 0; k < K; ++k) {
+                    const int rel = g->h_roff[k] - t * RTOT_ALIGN;
+                    if (rel >= 64 * h && rel < RTOT_ALIGN) {
+                        b[h] = rel;
+                        break;
+                    }
+                }
+            for (int h = 2; h < 4; ++h) b[h] = std::max(b[h], b[h - 1]);
+            tg[t] = make_int4(b[0], b[1], b[2], b[3]);
+        }
+        A(cudaMemcpy(g->d_tileg, tg.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice));
+    }
     A(cudaMemcpy(g->d_S, eigvals, sizeof(double) * K * PD, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
     A(cudaMemcpy(g->d_lam, g->h_lam, sizeof(double) * K, cudaMemcpyHostToDevice));
@@ -611,6 +655,12 @@ void epll_gmm_free(epll_gmm *g)
     free_workspace(g->ws);
     free_model(g);
     delete g;
+}
+
+epll_status epll_gmm_load(int K, int P, const double *weights, const double *eigvecs,
+                          const double *eigvals, int rank_mode, double rank_param, epll_gmm **out)
+{
+    return gmm_load_impl(K, P, weights, eigvecs, eigvals, rank_mode, rank_param, true, out);
 }
 
 epll_status epll_gmm_attach_tree(epll_gmm *g, int n_nodes, const double *weights, const double *eigvecs,
@@ -655,7 +705,7 @@ epll_status epll_gmm_attach_tree(epll_gmm *g, int n_nodes, const double *weights
         }
     if (leaf_depth < 1 || leaf_depth > 32) return fail(EPLL_EINVAL, "tree depth must be in 1..32");
     epll_gmm *tm = nullptr;
-    epll_status s = epll_gmm_load(n_nodes, PD, weights, eigvecs, eigvals, g->rank_mode, g->rank_param, &tm);
+    epll_status s = gmm_load_impl(n_nodes, PD, weights, eigvecs, eigvals, g->rank_mode, g->rank_param, false, &tm);
     if (s) return s;
     double cols = 0.0;
     int internal = 0;

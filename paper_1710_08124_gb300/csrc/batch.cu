@@ -57,6 +57,7 @@ epll_gmm *make_lane(const epll_gmm *g)
     l->d_r = g->d_r;
     l->d_roff = g->d_roff;
     l->d_colk = g->d_colk;
+    l->d_tileg = g->d_tileg;
     l->d_S = g->d_S;
     l->d_w = g->d_w;
     l->d_lam = g->d_lam;

@@ -161,7 +161,8 @@ struct epll_gmm {
     double *h_lam = nullptr;      // [K]
     int *h_roff = nullptr;        // [K+1] column offsets (padded)
     // device model
-    int *d_r = nullptr, *d_roff = nullptr, *d_colk = nullptr;   // colk: [Rtot] component of each column
+    int *d_r = nullptr, *d_roff = nullptr, *d_colk = nullptr;   // colk: [Rtot] component of each column (-1: none)
+    int4 *d_tileg = nullptr;      // [Rtot / 256] column-group starts of each tile (ragged-rank selection)
     double *d_S = nullptr, *d_w = nullptr, *d_lam = nullptr;     // [K][64], [K], [K]
     float *d_B = nullptr;         // [64][Rtot] Ubar_k concatenated (FP32 rounding of U)
     float *d_Blo = nullptr;       // [64][Rtot] U - B (the FP32 rounding error)

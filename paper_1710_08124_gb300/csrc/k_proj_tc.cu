@@ -47,8 +47,10 @@ struct TcCfg {
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int NB = 512 / BN;                        // TMEM accumulator buffers
     // epilogue column groups: each group (one warp per TMEM lane quarter)
-    // owns whole components of BN / NG columns; ragged ranks use one group
-    static constexpr int NG = RR == 0 ? 1 : (BN / RR >= 4 ? 4 : BN / RR);
+    // owns whole components of BN / NG columns; with ragged ranks the four
+    // groups split every tile at component boundaries (the model's columns
+    // are laid out so that no component straddles a 256-column tile)
+    static constexpr int NG = RR == 0 ? 4 : (BN / RR >= 4 ? 4 : BN / RR);
     static constexpr int EW = 4 * NG;                          // epilogue warps
     static constexpr int THREADS = 64 + 32 * EW;               // warp 0 TMA, warp 1 MMA, then the epilogue
     static constexpr int COLS = BN / NG;                       // columns per epilogue warp
@@ -139,7 +141,8 @@ __global__ void __launch_bounds__(TcCfg<BN, NT, RR, CAND>::THREADS, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
           const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
           int n, const int *__restrict__ rowmap, const int *__restrict__ n_dev, int K, int Rtot,
-          uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk, Tables tab,
+          uint32_t idesc, const float *__restrict__ zz, const int *__restrict__ colk,
+          const int4 *__restrict__ tileg, Tables tab,
           float tau_abs, float tau_rel, int *__restrict__ kstar, float *__restrict__ gap,
           int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err,
           float *__restrict__ scores, const float *__restrict__ zsc2, int4 *__restrict__ cand)
@@ -334,44 +337,57 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         }
                     }
                 } else {
-                uint32_t r[32];
-                for (int c = 0; c < ncol / 32; ++c) {
-                    tmem_ld32(taddr + (uint32_t)(32 * c), r);
-                    tmem_wait(r);
-                    const int cb = col0 + 32 * c;
-                    {
-                        // ragged ranks: column -> component map
+                // ragged ranks: this warp's group of the tile, [g0, g1), whole
+                // components of multiples of 8 columns; 8-column TMEM loads,
+                // four in flight; one component lookup per 8 columns
+                const int4 tg = __ldg(&tileg[tile0 + it]);
+                const int gs[5] = {0, tg.y, tg.z, tg.w, BN};
+                const int g0 = gs[h], g1 = gs[h + 1];
+                const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN);
+                const int tcol = (tile0 + it) * BN;
+                for (int c = g0; c < g1; c += 32) {
+                    uint32_t r[4][8];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int k = __ldg(&colk[cb + j]);
-                            if (k != curk) {
-                                if (curk >= 0) {
-                                    const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
-                                    const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
-                                                     __ldg(&tab.sgn[curk]) * a8;
-                                    if (CAND) top4_inc(sc, curk, cs, ck);
-                                    else top2(sc, curk, s1, s2, k1);
-                                }
-                                curk = k;
-                                acc = 0.0f;
+                    for (int u = 0; u < 4; ++u)
+                        if (c + 8 * u < g1) tmem_ld8(tq + (uint32_t)(c + 8 * u), r[u]);
+                    tmem_wait8x4(r);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (c + 8 * u >= g1) break;
+                        const int k = __ldg(&colk[tcol + c + 8 * u]);
+                        if (k != curk) {
+                            if (curk >= 0) {
+                                const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
+                                const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
+                                                 __ldg(&tab.sgn[curk]) * a8;
+                                if (CAND) top4_inc(sc, curk, cs, ck);
+                                else top2(sc, curk, s1, s2, k1);
                             }
-                            const float v = __uint_as_float(r[j]);
-                            acc = fmaf(v, v, acc);
+                            curk = k;
+                            acc = 0.0f;
                         }
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                        sq_acc2(a0, a1, __uint_as_float(r[u][0]), __uint_as_float(r[u][1]));
+                        sq_acc2(a2, a3, __uint_as_float(r[u][2]), __uint_as_float(r[u][3]));
+                        sq_acc2(a0, a1, __uint_as_float(r[u][4]), __uint_as_float(r[u][5]));
+                        sq_acc2(a2, a3, __uint_as_float(r[u][6]), __uint_as_float(r[u][7]));
+                        acc += (a0 + a1) + (a2 + a3);
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+                // the group ends with a whole component
+                if (curk >= 0) {
+                    const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
+                    const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
+                                     __ldg(&tab.sgn[curk]) * a8;
+                    if (CAND) top4_inc(sc, curk, cs, ck);
+                    else top2(sc, curk, s1, s2, k1);
                 }
-            }
-            if (RR == 0 && curk >= 0) {
-                // the last component ends with the last column
-                const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
-                const float sc = __ldg(&tab.cst_hi[curk]) + __ldg(&tab.t_hi[curk]) * zzr +
-                                 __ldg(&tab.sgn[curk]) * a8;
-                if (CAND) top4_inc(sc, curk, cs, ck);
-                else top2(sc, curk, s1, s2, k1);
+                curk = -1;
+                acc = 0.0f;
+                }
             }
             if (CAND) {
                 // merge the column groups' four best, then list the undecided patch
@@ -478,7 +494,7 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     // the instrumentation covers the pass over every sampled patch only
     if (!n_dev) prof_begin(g, st);
     kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
-                                             g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
+                                             g->d_colk, g->d_tileg, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
                                              nflag, cnt(g, CNT_ERR), scores, zsc2,
                                              reinterpret_cast<int4 *>(ws.cand));
     if (!n_dev) prof_end(g, st, n);
@@ -560,7 +576,8 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     const int rows = (n + TC_M - 1) / TC_M * TC_M;
     uint16_t *Zhi = ws.Zb, *Zlo = ws.Zb + ws.zrows * PD;
     epll_status s;
-    const bool bn128 = g->tile_bn == 128;
+    // the ragged-rank layout is packed in 256-column tiles
+    const bool bn128 = g->tile_bn == 128 && g->uniform_rank != 0;
     const int BNs = bn128 ? 128 : 256;
     if (fmt == 2) {
         if ((s = ensure_prop_ws(g, n))) return s;  // ws.cand, the pair buffers
@@ -635,7 +652,7 @@ epll_status launch_split_pass(epll_gmm *g, const float *xhat, int H, int W, cons
     CUtensorMap a2, a2lo, bs, bslo;
     if ((s = make_map(&a2, Z2hi, rows, TC_M))) return s;
     if ((s = make_map(&a2lo, Z2lo, rows, TC_M))) return s;
-    const bool bn128 = g->tile_bn == 128;
+    const bool bn128 = g->tile_bn == 128 && g->uniform_rank != 0;
     if ((s = make_map(&bs, g->tab.Bs, g->Rtot, bn128 ? 128 : 256))) return s;
     if ((s = make_map(&bslo, g->tab.Bs_lo, g->Rtot, bn128 ? 128 : 256))) return s;
     return bn128 ? dispatch_rr<128, 3>(g, a2, a2lo, bs, bslo, n, flag1, nflag1, ws.zz2, idesc_f16(TC_M, 128, 1),

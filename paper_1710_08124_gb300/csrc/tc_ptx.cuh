@@ -112,6 +112,25 @@ static __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[3
         : EPLL_R8(0), EPLL_R8(8), EPLL_R8(16), EPLL_R8(24)
         : "r"(taddr));
 }
+// 8 consecutive accumulator columns of this thread's TMEM lane (row); the
+// caller waits with tmem_wait8x4 after issuing up to four of them.
+static __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+static __device__ __forceinline__ void tmem_wait8x4(uint32_t (&r)[4][8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[0][4]), "+r"(r[0][5]),
+                   "+r"(r[0][6]), "+r"(r[0][7]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[1][2]), "+r"(r[1][3]),
+                   "+r"(r[1][4]), "+r"(r[1][5]), "+r"(r[1][6]), "+r"(r[1][7]), "+r"(r[2][0]), "+r"(r[2][1]),
+                   "+r"(r[2][2]), "+r"(r[2][3]), "+r"(r[2][4]), "+r"(r[2][5]), "+r"(r[2][6]), "+r"(r[2][7]),
+                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[3][4]), "+r"(r[3][5]),
+                   "+r"(r[3][6]), "+r"(r[3][7])::"memory");
+}
+
 // Waits for this thread's outstanding tcgen05.ld; the registers are tied to
 // the wait so no use of them is scheduled before it.
 static __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
