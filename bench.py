@@ -1174,6 +1174,15 @@ def oracle_check(ep, models, probs, ys, opts):
 
 
 # ---------------------------------------------------------------- our arm
+def selection_source_hash() -> str:
+    """sha256 over the selection kernel's sources (the kernel file, then the
+    tcgen05/TMA helper header it includes)."""
+    h = hashlib.sha256()
+    for f in ("k_proj_tc.cu", "tc_ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1710_08124_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(kernel_src_hash: str, precision: str):
     """DRAM bytes per selection-kernel launch from the committed ncu summary,
     or None when the kernel changed since the counters were taken."""
@@ -1332,8 +1341,7 @@ def main():
     if args.precision == "fp32":
         peak_note += "; FP32 SIMT path measured against the BF16 tensor peak"
     achieved = (sel_flops / (sel_ms / 1e3) / 1e12) if sel_ms > 0 else None
-    ksrc = open(os.path.join(ROOT, "paper_1710_08124_gb300", "csrc", "k_proj_tc.cu"), "rb").read()
-    khash = hashlib.sha256(ksrc).hexdigest()
+    khash = selection_source_hash()
     traffic = traffic_record(khash, args.precision)
 
     line = {
