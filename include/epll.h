@@ -243,16 +243,16 @@ epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const d
                                int T, const epll_options *opt, int mode, int lanes, void *stream);
 
 /* Tile shapes of this handle's kernels: basis columns per stage of the
- * tensor-core selection (256 or 128) and threads per 8-pixel group of the
- * reprojection (2 or 4).  Every shape computes the same restoration (up to
+ * tensor-core selection (256 or 128) and image rows per warp of the
+ * reprojection (1 or 2).  Every shape computes the same restoration (up to
  * the order of FP32 sums); the batch autotuner starts from these values.
  * Defaults 256 and 2.  Errors: EPLL_EINVAL. */
 epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg);
 
 /* The configuration the batch autotuner chose for the last tuned job list of
  * this handle (host out, each nullable): lane count (0 if nothing was tuned),
- * selection basis columns per stage (256 or 128) and reprojection threads per
- * 8-pixel group (2 or 4).  Errors: EPLL_EINVAL. */
+ * selection basis columns per stage (256 or 128) and reprojection image rows
+ * per warp (1 or 2).  Errors: EPLL_EINVAL. */
 epll_status epll_batch_config(epll_gmm *g, int *lanes, int *tile_bn, int *tile_agg);
 
 /* Same as epll_restore with HOST buffers: y, deg->a (PIXELWISE) and x_out are

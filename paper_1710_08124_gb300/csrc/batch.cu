@@ -346,7 +346,7 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
                 }
             }
             TileCfg bestT = tc;
-            const TileCfg alts[] = {{128, tc.agg}, {tc.bn, tc.agg == 2 ? 4 : 2}};
+            const TileCfg alts[] = {{128, tc.agg}, {tc.bn, tc.agg == 2 ? 1 : 2}};
             for (const TileCfg &c : alts) {
                 if (c.bn == tc.bn && c.agg == tc.agg) continue;
                 float ms = 0.0f;
@@ -382,8 +382,8 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
 extern "C" epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg)
 {
     if (!g || g->lane) return fail(EPLL_EINVAL, "null model handle");
-    if ((tile_bn != 128 && tile_bn != 256) || (tile_agg != 2 && tile_agg != 4))
-        return fail(EPLL_EINVAL, "tile_bn must be 128 or 256 and tile_agg 2 or 4");
+    if ((tile_bn != 128 && tile_bn != 256) || (tile_agg != 1 && tile_agg != 2))
+        return fail(EPLL_EINVAL, "tile_bn must be 128 or 256 and tile_agg 1 or 2");
     g->tile_bn = tile_bn;
     g->tile_agg = tile_agg;
     return EPLL_OK;

@@ -94,7 +94,7 @@ struct Workspace {
     size_t fcap = 0;
     int *perm = nullptr;                      // [N] list entries grouped by component
     int4 *items = nullptr;                    // [1 + N/128 + K] estimation work items
-    float *zrow = nullptr;                    // [N][64] patch estimates, row per anchor
+    float *zrow = nullptr;                    // [8][N][8] patch estimates: plane u = patch row u of every anchor
     uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
     size_t zrows = 0;                         // N rounded up to the 128-row tile
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)
@@ -191,8 +191,8 @@ struct epll_gmm {
     int prop_topm = 0;
     float prop_pmin = 0.0f;
     // tile shapes (chosen per lane by the batch autotuner): basis columns per
-    // stage of the tensor-core selection (256 or 128), threads per 8-pixel
-    // group of the reprojection (2 or 4)
+    // stage of the tensor-core selection (256 or 128), image rows per warp
+    // of the reprojection (1 or 2)
     int tile_bn = 256;
     int tile_agg = 2;
 };

@@ -11,18 +11,6 @@
 
 namespace epll {
 
-__device__ __forceinline__ float warp_sum_tc(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_max_tc(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 __device__ __forceinline__ uint8_t to_e4m3(float v)
 {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
@@ -42,72 +30,124 @@ __device__ __forceinline__ float from16(uint16_t v, int fmt)
 // (written beside BF16 split rows for an FP16 first pass).
 // fmt 3: 8-bit E4M3 operands scaled per row (max |z| -> 448), the square of
 // the scale in zsc2; Zhi is then read as bytes.
-constexpr int EX_ROWS = 4;  // rows per warp and pass: their loads are issued together
-__global__ void __launch_bounds__(128)
+//
+// Eight threads per patch, one per patch row: a thread loads its row's eight
+// pixels (three aligned 16-byte loads away from the right edge), the patch
+// sums (mean, |z|^2, max |z|) are reduced over the eight lanes of the patch,
+// and each thread writes its row's eight operands as one 16-byte store
+// (8 bytes for E4M3), so the eight lanes of a patch write its 128-byte
+// operand row contiguously.
+constexpr int EX_THREADS = 256;
+constexpr int EX_PATCHES = EX_THREADS / PS;  // patches per block and pass
+
+__device__ __forceinline__ float sum8(float v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+__device__ __forceinline__ float max8(float v)
+{
+    v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+    return v;
+}
+__device__ __forceinline__ uint32_t pack16(float a, float b, int fmt)
+{
+    return (uint32_t)to16(a, fmt) | ((uint32_t)to16(b, fmt) << 16);
+}
+__device__ __forceinline__ uint4 pack16x8(const float *v, int fmt)
+{
+    return make_uint4(pack16(v[0], v[1], fmt), pack16(v[2], v[3], fmt), pack16(v[4], v[5], fmt),
+                      pack16(v[6], v[7], fmt));
+}
+
+__global__ void __launch_bounds__(EX_THREADS)
 k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors, int n,
              const int *__restrict__ rowmap, const int *__restrict__ n_dev, int fmt, int split,
              uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz,
              float *__restrict__ zsc2, float *__restrict__ mu_out, uint16_t *__restrict__ Zf)
 {
-    const int lane = threadIdx.x & 31;
+    const int u = threadIdx.x & (PS - 1);  // patch row of this thread
+    // image rows start on 16-byte boundaries (vector loads allowed)
+    const bool aligned = (W & 3) == 0 && ((uintptr_t)xhat & 15) == 0;
     if (n_dev) n = *n_dev;
     const int rows = (n + 127) / 128 * 128;
-    // grid-stride over groups of EX_ROWS rows (a listed subset launches a capped grid)
-    for (int base = (blockIdx.x * 4 + (threadIdx.x >> 5)) * EX_ROWS; base < rows;
-         base += gridDim.x * 4 * EX_ROWS) {
-        float x0[EX_ROWS], x1[EX_ROWS];
+    // grid-stride over blocks of EX_PATCHES rows (a listed subset launches a capped grid)
+    for (int i = blockIdx.x * EX_PATCHES + (threadIdx.x >> 3); i - (int)(threadIdx.x >> 3) < rows;
+         i += gridDim.x * EX_PATCHES) {
+        float x[PS];
+        const bool live = i < n;
+        if (live) {
+            const int p = rowmap ? rowmap[i] : i;
+            const int a = anchors ? anchors[p] : p;
+            const int ai = a / W, aj = a - ai * W;
+            int r = ai + u;
+            if (r >= H) r -= H;
+            const float *src = xhat + (size_t)r * W;
+            const int base = aj & ~3, sh = aj & 3;
+            if (aligned && base + 12 <= W) {
+                // three aligned 16-byte loads cover the row's eight pixels
+                const float4 *s4 = reinterpret_cast<const float4 *>(src + base);
+                const float4 f0 = s4[0], f1 = s4[1];
+                const float4 f2 = sh ? s4[2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float F[12] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
 #pragma unroll
-        for (int u = 0; u < EX_ROWS; ++u) {
-            const int i = base + u;
-            x0[u] = x1[u] = 0.0f;
-            if (i < n) {
-                const int p = rowmap ? rowmap[i] : i;
-                const int a = anchors ? anchors[p] : p;
-                const int ai = a / W, aj = a % W;
-                int r0 = ai + (lane >> 3), r1 = r0 + 4, c = aj + (lane & 7);
-                if (r0 >= H) r0 -= H;
-                if (r1 >= H) r1 -= H;
-                if (c >= W) c -= W;
-                x0[u] = xhat[(size_t)r0 * W + c];
-                x1[u] = xhat[(size_t)r1 * W + c];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < EX_ROWS; ++u) {
-            const int i = base + u;
-            float z0 = 0.0f, z1 = 0.0f, q = 0.0f, mu = 0.0f;
-            if (i < n) {
-                mu = warp_sum_tc(x0[u] + x1[u]) * (1.0f / PD);
-                z0 = x0[u] - mu;
-                z1 = x1[u] - mu;
-                q = warp_sum_tc(z0 * z0 + z1 * z1);
-            }
-            if (fmt == 3) {
-                const float m = warp_max_tc(fmaxf(fabsf(z0), fabsf(z1)));
-                const float sc = m > 0.0f ? m / 448.0f : 1.0f;
-                uint8_t *Z8 = reinterpret_cast<uint8_t *>(Zhi);
-                Z8[(size_t)i * PD + lane] = to_e4m3(z0 / sc);
-                Z8[(size_t)i * PD + lane + 32] = to_e4m3(z1 / sc);
-                if (lane == 0 && i < n) {
-                    zz[i] = q;
-                    zsc2[i] = sc * sc;
-                }
+                for (int v = 0; v < PS; ++v)
+                    x[v] = sh == 0 ? F[v] : sh == 1 ? F[v + 1] : sh == 2 ? F[v + 2] : F[v + 3];
             } else {
-                const uint16_t h0 = to16(z0, fmt), h1 = to16(z1, fmt);
-                Zhi[(size_t)i * PD + lane] = h0;
-                Zhi[(size_t)i * PD + lane + 32] = h1;
-                if (split) {
-                    Zlo[(size_t)i * PD + lane] = to16(z0 - from16(h0, fmt), fmt);
-                    Zlo[(size_t)i * PD + lane + 32] = to16(z1 - from16(h1, fmt), fmt);
+#pragma unroll
+                for (int v = 0; v < PS; ++v) {
+                    int c = aj + v;
+                    if (c >= W) c -= W;
+                    x[v] = src[c];
                 }
-                if (Zf) {
-                    Zf[(size_t)i * PD + lane] = to16(z0, 2);
-                    Zf[(size_t)i * PD + lane + 32] = to16(z1, 2);
-                }
-                if (lane == 0 && i < n) {
-                    zz[i] = q;
-                    if (mu_out) mu_out[i] = mu;
-                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < PS; ++v) x[v] = 0.0f;
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int v = 0; v < PS; ++v) s += x[v];
+        const float mu = sum8(s) * (1.0f / PD);
+        float z[PS], q = 0.0f;
+#pragma unroll
+        for (int v = 0; v < PS; ++v) {
+            z[v] = live ? x[v] - mu : 0.0f;
+            q = fmaf(z[v], z[v], q);
+        }
+        q = sum8(q);
+        if (i >= rows) continue;  // after the shuffles: every lane of the warp took part
+        const size_t off = (size_t)i * PD + (size_t)u * PS;
+        if (fmt == 3) {
+            float m = 0.0f;
+#pragma unroll
+            for (int v = 0; v < PS; ++v) m = fmaxf(m, fabsf(z[v]));
+            m = max8(m);
+            const float sc = m > 0.0f ? m / 448.0f : 1.0f;
+            uint32_t b[2] = {0u, 0u};
+#pragma unroll
+            for (int v = 0; v < PS; ++v) b[v >> 2] |= (uint32_t)to_e4m3(z[v] / sc) << (8 * (v & 3));
+            *reinterpret_cast<uint2 *>(reinterpret_cast<uint8_t *>(Zhi) + off) = make_uint2(b[0], b[1]);
+            if (u == 0 && live) {
+                zz[i] = q;
+                zsc2[i] = sc * sc;
+            }
+        } else {
+            *reinterpret_cast<uint4 *>(Zhi + off) = pack16x8(z, fmt);
+            if (split) {
+                float lo[PS];
+#pragma unroll
+                for (int v = 0; v < PS; ++v) lo[v] = z[v] - from16(to16(z[v], fmt), fmt);
+                *reinterpret_cast<uint4 *>(Zlo + off) = pack16x8(lo, fmt);
+            }
+            if (Zf) *reinterpret_cast<uint4 *>(Zf + off) = pack16x8(z, 2);
+            if (u == 0 && live) {
+                zz[i] = q;
+                if (mu_out) mu_out[i] = mu;
             }
         }
     }
@@ -116,8 +156,8 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
 // Blocks for `rows` operand rows (a listed subset: capped, the kernel strides).
 static inline int ex_grid(int rows, bool listed)
 {
-    const int b = (rows + 4 * EX_ROWS - 1) / (4 * EX_ROWS);
-    return listed && b > 152 * 16 ? 152 * 16 : b;
+    const int b = (rows + EX_PATCHES - 1) / EX_PATCHES;
+    return listed && b > 152 * 8 ? 152 * 8 : b;
 }
 
 epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,
@@ -125,7 +165,7 @@ epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const i
                            float *zz, float *zsc2, float *mu, cudaStream_t st, uint16_t *Zf)
 {
     const int rows = (n + 127) / 128 * 128;
-    k_extract_tc<<<ex_grid(rows, n_dev != nullptr), 128, 0, st>>>(xhat, H, W, anchors, n, rowmap, n_dev, fmt, split,
+    k_extract_tc<<<ex_grid(rows, n_dev != nullptr), EX_THREADS, 0, st>>>(xhat, H, W, anchors, n, rowmap, n_dev, fmt, split,
                                                                   Zhi, Zlo, zz, zsc2, mu, Zf);
     EPLL_LAUNCHED(g);
     return EPLL_OK;

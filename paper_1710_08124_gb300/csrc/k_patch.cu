@@ -710,7 +710,7 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
             const int p = 8 * pg + a;
             if (p < cnt_p) {
                 const float mu = sm.mus[p];
-                float4 *dst = reinterpret_cast<float4 *>(zrow + (size_t)sm.anchor[p] * PD + 8 * cg);
+                float4 *dst = reinterpret_cast<float4 *>(zrow + ((size_t)cg * H * W + sm.anchor[p]) * PS);
                 dst[0] = make_float4(acc[a][0] + mu, acc[a][1] + mu, acc[a][2] + mu, acc[a][3] + mu);
                 dst[1] = make_float4(acc[a][4] + mu, acc[a][5] + mu, acc[a][6] + mu, acc[a][7] + mu);
             }
@@ -776,109 +776,119 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult
 // (with the `valid` boundary bs is weighed by the pixel's patch count / P).
 //
-// AG_SPLIT (2 or 4) threads own 8 consecutive pixels of an image row, each
-// thread 8 / AG_SPLIT of the eight patch rows u.  For each u it visits the 15 anchors
-// (i - u, j0 - 7 .. j0 + 7) whose patches cover some of the pixels; an anchor
-// outside the subset costs only its multiplicity load, a sampled one two
-// 16-byte loads of its patch row u (the 8 estimates that fall on this image
-// row), each added to the pixels it covers.  Every estimate is thus read once
-// per covering pixel group rather than once per pixel in 4-byte pieces.
-// Summation order per pixel: each thread's rows (u, then anchor column
-// ascending), then the partial sums pairwise.
+// The estimates are stored by patch row: plane u holds, for every anchor, the
+// 8 estimates of its patch row u (zrow[(u N + anchor) 8 + v]), so the
+// estimates that land on one image row from one anchor row are contiguous.
+// A warp owns AG_SPAN = 24 consecutive pixels (i, j0 .. j0 + 23) of R image
+// rows; lane l stands for anchor column j0 - 7 + l.  For each anchor row the
+// lane loads its multiplicity and, where the anchor is sampled, the 32-byte
+// segment of each patch row that lands on one of the warp's image rows
+// (coalesced: consecutive lanes, consecutive segments), and adds it to eight
+// per-lane sums, one per column offset v.  The multiplicities of all anchor
+// rows are loaded before any segment, and the segments of four anchor rows
+// at a time, so a warp waits for a few memory round trips, not one per row.  A pixel's value is then the sum
+// over v of lane (l - v)'s sum v, gathered with seven shuffles; its count is
+// an 8-wide sliding sum of the lanes' multiplicity sums (three shuffles).
+// Summation order per pixel: anchor rows ascending, then v ascending.
 // ============================================================================
-constexpr int AG_GROUP = 8;  // pixels per thread group
+constexpr int AG_SPAN = 32 - (PS - 1);  // output pixels per warp
+constexpr int AG_THREADS = 256;
 
-// AG_SPLIT: threads per pixel group, each summing PS / AG_SPLIT patch rows
-template <int AG_SPLIT>
-__global__ void __launch_bounds__(256)
+template <int R>
+__global__ void __launch_bounds__(AG_THREADS)
 k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
             const float *xhat, int H, int W, const float *__restrict__ y,
             const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
             float *xout, int weighted, float *__restrict__ wout)
 {
-    const int gw = (W + AG_GROUP - 1) / AG_GROUP;
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) / AG_SPLIT;
-    const int half = threadIdx.x & (AG_SPLIT - 1);
-    const bool live = q < H * gw;  // every thread of a group shares this
-    const int i = live ? q / gw : 0, j0 = live ? (q % gw) * AG_GROUP : 0;
-    // anchor columns j0-7 .. j0+7 need no wrap; the multiplicities load as
-    // four aligned uint4 (columns j0-8 .. j0+7) when rows start 16-byte aligned
-    const bool interior = j0 >= PS && j0 + 2 * PS - 2 < W;
-    const bool vec = interior && (W & 3) == 0 && mult;
-    float sum[AG_GROUP];
-    unsigned cnt[AG_GROUP];
+    const int lane = threadIdx.x & 31;
+    const int gw = (W + AG_SPAN - 1) / AG_SPAN, gh = (H + R - 1) / R;
+    const int wid = (int)((blockIdx.x * (unsigned)AG_THREADS + threadIdx.x) >> 5);
+    if (wid >= gh * gw) return;  // the whole warp leaves together
+    const int i0 = (wid / gw) * R, j0 = (wid % gw) * AG_SPAN;
+    int c = (j0 - (PS - 1) + lane) % W;  // >= -7 >= -W
+    if (c < 0) c += W;
+    const size_t N = (size_t)H * W;
+    float V[R][PS];
+    unsigned M[R];
 #pragma unroll
-    for (int t = 0; t < AG_GROUP; ++t) {
-        sum[t] = 0.0f;
-        cnt[t] = 0u;
+    for (int r = 0; r < R; ++r) {
+        M[r] = 0u;
+#pragma unroll
+        for (int v = 0; v < PS; ++v) V[r][v] = 0.0f;
     }
-    if (live) {
-#pragma unroll 1
-        for (int uu = 0; uu < PS / AG_SPLIT; ++uu) {
-            const int u = half * (PS / AG_SPLIT) + uu;
-            int ai = i - u;
-            if (ai < 0) ai += H;
-            const size_t rowb = (size_t)ai * W;
-            unsigned m[2 * PS - 1];
-            if (vec) {
-                const uint4 *mp = reinterpret_cast<const uint4 *>(mult + rowb + j0 - PS);
-                const uint4 m0 = mp[0], m1 = mp[1], m2 = mp[2], m3 = mp[3];
-                const unsigned mm[16] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w,
-                                         m2.x, m2.y, m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
+    // anchor rows i0 - 7 .. i0 + R - 1; image row i0 + r takes patch row
+    // u = r + 7 - e of anchor row e (0 <= u < 8).  All multiplicities are
+    // loaded first, then the sampled segments AG_CHUNK anchor rows at a time
+    // (their loads issued together), then added in ascending anchor-row order.
+    constexpr int NE = PS + R - 1;
+    size_t ab[NE];
+    unsigned m[NE];
 #pragma unroll
-                for (int o = 0; o < 2 * PS - 1; ++o) m[o] = mm[o + 1];
-            } else {
+    for (int e = 0; e < NE; ++e) {
+        int ai = (i0 - (PS - 1) + e) % H;
+        if (ai < 0) ai += H;
+        ab[e] = (size_t)ai * W + c;
+        m[e] = mult ? mult[ab[e]] : 1u;
+    }
+    constexpr int AG_CHUNK = 4;
 #pragma unroll
-                for (int o = 0; o < 2 * PS - 1; ++o) {
-                    int jj = j0 - (PS - 1) + o;
-                    if (jj < 0) jj += W;
-                    else if (jj >= W) jj -= W;
-                    m[o] = mult ? mult[rowb + jj] : 1u;
-                }
-            }
+    for (int e0 = 0; e0 < NE; e0 += AG_CHUNK) {
+        float4 s[AG_CHUNK][R][2];
 #pragma unroll
-            for (int o = 0; o < 2 * PS - 1; ++o) {
-                int jj = j0 - (PS - 1) + o;
-                if (!interior) {
-                    if (jj < 0) jj += W;
-                    else if (jj >= W) jj -= W;
-                }
-                const float4 *src = reinterpret_cast<const float4 *>(zrow + (rowb + jj) * PD + u * PS);
-                const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                const float4 z0 = m[o] ? src[0] : zero4, z1 = m[o] ? src[1] : zero4;
-                const float zz[PS] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-                const float fm = (float)m[o];
+        for (int de = 0; de < AG_CHUNK; ++de) {
+            const int e = e0 + de;
 #pragma unroll
-                for (int t = 0; t < AG_GROUP; ++t) {
-                    const int v = t + (PS - 1) - o;  // element column of this anchor that lands on pixel j0 + t
-                    if (v >= 0 && v < PS) {
-                        sum[t] = fmaf(fm, zz[v], sum[t]);
-                        cnt[t] += m[o];
-                    }
+            for (int r = 0; r < R; ++r) {
+                const int u = r + (PS - 1) - e;
+                s[de][r][0] = s[de][r][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (e < NE && u >= 0 && u < PS && m[e]) {
+                    const float4 *src = reinterpret_cast<const float4 *>(zrow + ((size_t)u * N + ab[e]) * PS);
+                    s[de][r][0] = src[0];
+                    s[de][r][1] = src[1];
                 }
             }
         }
-    }
-    // the group's partial sums (patch rows (PS / AG_SPLIT) h .. in thread h),
-    // added pairwise in a fixed order
 #pragma unroll
-    for (int o = 1; o < AG_SPLIT; o <<= 1) {
+        for (int de = 0; de < AG_CHUNK; ++de) {
+            const int e = e0 + de;
+            if (e >= NE) break;
+            const float fm = (float)m[e];
 #pragma unroll
-        for (int t = 0; t < AG_GROUP; ++t) {
-            const float so = __shfl_down_sync(0xffffffffu, sum[t], o);
-            const unsigned co = __shfl_down_sync(0xffffffffu, cnt[t], o);
-            sum[t] += so;
-            cnt[t] += co;
+            for (int r = 0; r < R; ++r) {
+                const int u = r + (PS - 1) - e;
+                if (u < 0 || u >= PS) continue;
+                M[r] += m[e];
+                const float4 s0 = s[de][r][0], s1 = s[de][r][1];
+                V[r][0] = fmaf(fm, s0.x, V[r][0]);
+                V[r][1] = fmaf(fm, s0.y, V[r][1]);
+                V[r][2] = fmaf(fm, s0.z, V[r][2]);
+                V[r][3] = fmaf(fm, s0.w, V[r][3]);
+                V[r][4] = fmaf(fm, s1.x, V[r][4]);
+                V[r][5] = fmaf(fm, s1.y, V[r][5]);
+                V[r][6] = fmaf(fm, s1.z, V[r][6]);
+                V[r][7] = fmaf(fm, s1.w, V[r][7]);
+            }
         }
     }
-    if (!live || half) return;
     const float bs = y ? lamf[0] * bmult : 0.0f;
+    const int j = j0 + lane - (PS - 1);  // pixel of this lane (lanes 7 .. 30)
+    const bool out_lane = lane >= PS - 1 && lane < PS - 1 + AG_SPAN && j < W;
 #pragma unroll
-    for (int t = 0; t < AG_GROUP; ++t) {
-        if (j0 + t >= W) break;
-        const size_t p = (size_t)i * W + j0 + t;
-        const float xt = cnt[t] ? sum[t] / (float)cnt[t] : xhat[p];
-        const float wt = (float)cnt[t] * (1.0f / (float)PD);  // patch count / P
+    for (int r = 0; r < R; ++r) {
+        // pixel j gets element v of anchor column j - v, held by lane l - v
+        float sum = V[r][0];
+#pragma unroll
+        for (int v = 1; v < PS; ++v) sum += __shfl_up_sync(0xffffffffu, V[r][v], v);
+        unsigned cnt = M[r];
+        cnt += __shfl_up_sync(0xffffffffu, cnt, 1);
+        cnt += __shfl_up_sync(0xffffffffu, cnt, 2);
+        cnt += __shfl_up_sync(0xffffffffu, cnt, 4);  // lanes >= 7: anchor columns l - 7 .. l
+        const int i = i0 + r;
+        if (!out_lane || i >= H) continue;
+        const size_t p = (size_t)i * W + j;
+        const float xt = cnt ? sum / (float)cnt : xhat[p];
+        const float wt = (float)cnt * (1.0f / (float)PD);  // patch count / P
         if (wout) wout[p] = wt;
         if (y) {
             const float ap = a ? a[p] : 1.0f;
@@ -894,14 +904,15 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
                              const float *y, const float *a, const float *lamf, double bmult,
                              float *xout, cudaStream_t st, int weighted, float *wout)
 {
-    const int split = g->tile_agg == 4 ? 4 : 2;
-    const int threads = H * ((W + AG_GROUP - 1) / AG_GROUP) * split;
-    if (split == 4)
-        k_aggregate<4><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                             xout, weighted, wout);
+    const int R = g->tile_agg == 2 ? 2 : 1;
+    const long long warps = (long long)((H + R - 1) / R) * ((W + AG_SPAN - 1) / AG_SPAN);
+    const unsigned blocks = (unsigned)((warps * 32 + AG_THREADS - 1) / AG_THREADS);
+    if (R == 2)
+        k_aggregate<2><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+                                                     xout, weighted, wout);
     else
-        k_aggregate<2><<<(threads + 255) / 256, 256, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
-                                                             xout, weighted, wout);
+        k_aggregate<1><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+                                                     xout, weighted, wout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
