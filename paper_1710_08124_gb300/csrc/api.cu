@@ -273,19 +273,32 @@ static int basis_format(const epll_options &o, int precision)
     }
 }
 
-// Per-beta tables and patch subsets of iterations t0 .. t0+nb-1 (one batch).
+// Per-beta tables and patch subsets of iterations t0 .. t0+nb-1 (one batch):
+// the sampler runs on the handle's second stream while the tables kernels
+// run on st, and st waits for it.
 static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb,
                                  const double *d_lambda, const double *mult, double sigma2,
                                  double beta_direct, int *n, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     epll_status s;
+    if (!g->aux) {
+        EPLL_CU(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking));
+        EPLL_CU(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+        EPLL_CU(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    }
+    EPLL_CU(cudaEventRecord(g->ev_fork, st));
+    EPLL_CU(cudaStreamWaitEvent(g->aux, g->ev_fork, 0));
+    if ((s = launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, g->aux)))
+        return s;
+    EPLL_CU(cudaEventRecord(g->ev_join, g->aux));
     if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o, eff_precision(g, o)), st)))
         return s;
     if (o.select == EPLL_SELECT_TREE &&
         (s = launch_tables(g->tree->tm, d_lambda, mult, nb, sigma2, beta_direct, 4, st)))
         return s;
-    return launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, st);
+    EPLL_CU(cudaStreamWaitEvent(st, g->ev_join, 0));
+    return EPLL_OK;
 }
 
 // Points the current-iteration views (tables, subset) at batch slot b.
@@ -652,6 +665,9 @@ void epll_gmm_free(epll_gmm *g)
 {
     if (!g) return;
     cudaDeviceSynchronize();
+    if (g->aux) cudaStreamDestroy(g->aux);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     free_workspace(g->ws);
     free_model(g);
     delete g;

@@ -195,6 +195,10 @@ struct epll_gmm {
     // of the reprojection (1 or 2)
     int tile_bn = 256;
     int tile_agg = 2;
+    // second stream: the patch sampler runs on it beside the tables kernels
+    // (fork / join through the two events; created on first use)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace epll {

@@ -824,12 +824,13 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
     constexpr int NE = PS + R - 1;
     size_t ab[NE];
     unsigned m[NE];
+    int ai = (i0 - (PS - 1)) % H;  // >= -7 >= -H
+    if (ai < 0) ai += H;
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
-        int ai = (i0 - (PS - 1) + e) % H;
-        if (ai < 0) ai += H;
         ab[e] = (size_t)ai * W + c;
         m[e] = mult ? mult[ab[e]] : 1u;
+        if (++ai == H) ai = 0;
     }
     constexpr int AG_CHUNK = 4;
 #pragma unroll

@@ -15,34 +15,6 @@ namespace epll {
 // compensated rescoring).  1/beta = sigma^2 / (lambda * mult) with lambda read
 // from device memory, or 1/beta_direct when beta_direct > 0.
 // ============================================================================
-// Sum over the first 64 threads of the block (fixed order); every thread of
-// the block must call it.
-__device__ double block64_sum(double v, double *red)
-{
-    int j = threadIdx.x;
-    if (j < 64) red[j] = v;
-    __syncthreads();
-    for (int s = 32; s > 0; s >>= 1) {
-        if (j < s) red[j] += red[j + s];
-        __syncthreads();
-    }
-    double tot = red[0];
-    __syncthreads();
-    return tot;
-}
-
-// -2 log w_k + sum_{j<r} log(S_kj + ib) + (P - r) log(lambda_k + ib)
-__device__ double component_constant(int k, const int *r, const double *S, const double *w,
-                                     const double *lam, double ib, double *red)
-{
-    int j = threadIdx.x;
-    int rk = r[k];
-    double v = (j < rk) ? log(S[(size_t)k * PD + j] + ib) : 0.0;
-    double c = block64_sum(v, red) - 2.0 * log(w[k]);
-    if (rk < PD) c += (double)(PD - rk) * log(lam[k] + ib);
-    return c;
-}
-
 struct Mults {
     double m[TB_MAX];
 };
@@ -58,39 +30,83 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
 {
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
-    const int k = blockIdx.x, j = threadIdx.x;
+    __shared__ double s_ib;
+    const int k = blockIdx.x, j = threadIdx.x, lane = j & 31;
     const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
-    const double mult = mults.m[blockIdx.y];
-    const double ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
-
-    const double c0 = component_constant(0, r, S, w, lam, ib, red);
-    const double ck = component_constant(k, r, S, w, lam, ib, red);
     const int rk = r[k];
-    const double nuP = lam[k] + ib;
-    const double t = rk < PD ? 1.0 / nuP : 0.0;
-    const double gP = rk < PD ? lam[k] / nuP : 0.0;
-    if (j == 0) {
-        double cst = ck - c0;
-        float h = (float)cst;
-        tab.cst_hi[k] = h;
-        tab.cst_lo[k] = (float)(cst - (double)h);
-        float th = (float)t;
-        tab.t_hi[k] = th;
-        tab.t_lo[k] = (float)(t - (double)th);
-        tab.gp[k] = (float)gP;
-        tab.sgn[k] = rk < PD ? -1.0f : 1.0f;
-        if (k == 0) tab.ibeta[0] = (float)ib;
-        // error scale of the score: largest 1/nu of this component
-        const double numin = rk < PD ? nuP : S[(size_t)k * PD + PD - 1] + ib;
-        atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int((float)(1.0 / numin)));
+    // FP64 arithmetic is scarce on this GPU: block-wide scalars are formed
+    // once, and the log-determinant sums from eight partial products each
+    if (j < 32) {
+        double ib = 0.0;
+        if (lane == 0) {
+            const double mult = mults.m[blockIdx.y];
+            ib = beta_direct > 0.0 ? 1.0 / beta_direct : sigma2 / (d_lambda[0] * mult);
+        }
+        ib = __shfl_sync(0xffffffffu, ib, 0);
+        // lanes 0..7: sum_{j<r_0} log(S_0j + ib) in eight partial products (component 0,
+        // whose constant is subtracted from every component's); lanes 8..15: component k;
+        // lanes 16..19: log w_0, log w_k, log(lambda_0 + ib), log(lambda_k + ib).
+        // A partial product of eight factors rounds by at most 7 ulp, far below the
+        // float rounding the tables end in; one outside (1e-300, 1e300) falls back
+        // to one logarithm per factor.
+        double v = 0.0;
+        if (lane < 16) {
+            const int c = lane < 8 ? 0 : k, e0 = 8 * (lane & 7), e1 = min(e0 + 8, r[c]);
+            double prod = 1.0;
+            for (int e = e0; e < e1; ++e) prod *= S[(size_t)c * PD + e] + ib;
+            if (prod > 1e-300 && prod < 1e300) {
+                v = log(prod);
+            } else {
+                for (int e = e0; e < e1; ++e) v += log(S[(size_t)c * PD + e] + ib);
+            }
+        } else if (lane < 20) {
+            const int c = (lane & 1) ? k : 0;
+            v = log(lane < 18 ? w[c] : lam[c] + ib);
+        }
+        double sum8 = v;
+        sum8 += __shfl_xor_sync(0xffffffffu, sum8, 1);
+        sum8 += __shfl_xor_sync(0xffffffffu, sum8, 2);
+        sum8 += __shfl_xor_sync(0xffffffffu, sum8, 4);
+        const double l0 = __shfl_sync(0xffffffffu, sum8, 0), lk = __shfl_sync(0xffffffffu, sum8, 8);
+        const double lw0 = __shfl_sync(0xffffffffu, v, 16), lwk = __shfl_sync(0xffffffffu, v, 17);
+        const double ll0 = __shfl_sync(0xffffffffu, v, 18), llk = __shfl_sync(0xffffffffu, v, 19);
+        if (lane == 0) {
+            // -2 log w + sum_{j<r} log(S_j + ib) + (P - r) log(lambda + ib), component k minus component 0
+            const int r0 = r[0];
+            double c0 = l0 - 2.0 * lw0, ck = lk - 2.0 * lwk;
+            if (r0 < PD) c0 += (double)(PD - r0) * ll0;
+            if (rk < PD) ck += (double)(PD - rk) * llk;
+            const double cst = ck - c0;
+            const double nuP = lam[k] + ib;
+            const double t = rk < PD ? 1.0 / nuP : 0.0;
+            const double gP = rk < PD ? lam[k] * t : 0.0;
+            red[0] = t;
+            red[1] = gP;
+            s_ib = ib;
+            float h = (float)cst;
+            tab.cst_hi[k] = h;
+            tab.cst_lo[k] = (float)(cst - (double)h);
+            float th = (float)t;
+            tab.t_hi[k] = th;
+            tab.t_lo[k] = (float)(t - (double)th);
+            tab.gp[k] = (float)gP;
+            tab.sgn[k] = rk < PD ? -1.0f : 1.0f;
+            if (k == 0) tab.ibeta[0] = (float)ib;
+            // error scale of the score: largest 1/nu of this component
+            const float inumin = rk < PD ? (float)t : (float)(1.0 / (S[(size_t)k * PD + PD - 1] + ib));
+            atomicMax(reinterpret_cast<int *>(tab.tmax), __float_as_int(inumin));
+        }
     }
+    __syncthreads();
+    const double ib = s_ib, t = red[0], gP = red[1];
+    __syncthreads();  // red is reused below
     const int o = roff[k], rp = roff[k + 1] - o;
     for (int jj = j; jj < rp; jj += 64) {
         double q = 0.0, gw = 0.0;
         if (jj < rk) {
-            double nu = S[(size_t)k * PD + jj] + ib;
-            q = 1.0 / nu - t;
-            gw = S[(size_t)k * PD + jj] / nu - gP;
+            const double inu = 1.0 / (S[(size_t)k * PD + jj] + ib);
+            q = inu - t;
+            gw = S[(size_t)k * PD + jj] * inu - gP;
         }
         float qh = (float)q;
         tab.q_hi[o + jj] = qh;

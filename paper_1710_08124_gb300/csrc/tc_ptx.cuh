@@ -71,17 +71,6 @@ static __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorM
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
-// Four rows (y0..y3) of a map whose box is one row high, x .. x + box width,
-// to four consecutive box-sized rows at dst (rows past the map read zeros).
-static __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int x, int y0, int y1,
-                                                   int y2, int y3, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
-        : "memory");
-}
 static __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
