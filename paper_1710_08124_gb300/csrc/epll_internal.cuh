@@ -94,7 +94,9 @@ struct Workspace {
     size_t fcap = 0;
     int *perm = nullptr;                      // [N] list entries grouped by component
     int4 *items = nullptr;                    // [1 + N/128 + K] estimation work items
-    float *zrow = nullptr;                    // [8][N][8] patch estimates: plane u = patch row u of every anchor
+    float *zrow = nullptr;                    // [8][N][8] patch estimates: plane u holds patch row u of
+                                              // every sampled patch, by its index in the subset
+    int *inv = nullptr;                       // [N] index in the subset of a sampled anchor (estimation writes it)
     uint16_t *Zb = nullptr;                   // [2][zrows][64] 16-bit DC-free patches (tensor path)
     size_t zrows = 0;                         // N rounded up to the 128-row tile
     float *zz = nullptr;                      // [N] |z|^2 (tensor path)

@@ -23,7 +23,8 @@
 //     they read first), store gamma_kP z + mu into the second product's
 //     accumulator columns, and after the second product write the patch's 64
 //     estimates for the reprojection (eight 32-byte patch-row segments,
-//     segment u into plane u of the estimate buffer) while the producers
+//     segment u into plane u of the estimate buffer at the patch's index in
+//     the subset, and that index at the patch's anchor) while the producers
 //     already fill the stage again.
 // Every wait is bounded; a timeout reaches the host as an error.
 #include "epll_internal.cuh"
@@ -44,6 +45,7 @@ constexpr int ET_THREADS = 32 * ET_WARPS;
 
 struct EtStage {  // an item's scalars, beside its stage
     int anchor[ET_T];
+    int patch[ET_T];  // index in the subset
     float mu[ET_T];
     float gw[64];  // Wiener gains of the component (0 beyond the rank)
     int r, cnt;
@@ -61,8 +63,8 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
               const uint4 *__restrict__ Zhi_g, const uint4 *__restrict__ Zlo_g,
               const int *__restrict__ anchors, const float *__restrict__ mu_g,
               const int *__restrict__ perm, const int4 *__restrict__ items, const int *__restrict__ roff,
-              const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, long long npix,
-              int *__restrict__ err)
+              const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, int *__restrict__ inv,
+              long long npix, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char et_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)et_raw + 1023) & ~(uintptr_t)1023);
@@ -183,6 +185,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
 #pragma unroll
             for (int h = 0; h < NR; ++h) {
                 st.anchor[p + 32 * h] = anc[h];
+                st.patch[p + 32 * h] = row[h];
                 st.mu[p + 32 * h] = mu[h];
             }
             // the rows' split operands straight to their swizzled places (cp.async):
@@ -228,7 +231,9 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
             tc_fence_after();
             // the row's destination, read before the stage is handed back
             const bool live = t < st.cnt;
-            float *dst = zrow + (size_t)st.anchor[t] * PS;  // plane e8 at dst + e8 * npix * 8
+            const int pi = st.patch[t];
+            if (live && hh == 0) inv[st.anchor[t]] = pi;
+            float *dst = zrow + (size_t)pi * PS;  // plane e8 at dst + e8 * npix * 8
             {
                 // c'_j = gw_kj c_j (zero beyond the rank) split into the A operand of the
                 // second product, written over this thread's own part of the patch row,
@@ -341,7 +346,7 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
     const uint4 *zh = reinterpret_cast<const uint4 *>(ws.Zb);
     const uint4 *zl = reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD);
     k_estimate_tc<<<grid, ET_THREADS, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, zh, zl, anchors, ws.mu, ws.perm, ws.items,
-                                                   g->d_roff, g->d_r, g->tab, ws.zrow, (long long)H * W,
+                                                   g->d_roff, g->d_r, g->tab, ws.zrow, ws.inv, (long long)H * W,
                                                    cnt(g, CNT_ERR));
     EPLL_LAUNCHED(g);
     return EPLL_OK;

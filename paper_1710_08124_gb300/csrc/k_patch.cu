@@ -599,13 +599,14 @@ struct EstSmem {
     float mus[EST_T];
     float gws[PD];
     int anchor[EST_T];
+    int patch[EST_T];  // index in the subset
 };
 
 __global__ void __launch_bounds__(EST_T)
 k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__ anchors,
            const int *__restrict__ perm, const int4 *__restrict__ items, int Rtot,
            const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
-           Tables tab, float *__restrict__ zrow)
+           Tables tab, float *__restrict__ zrow, int *__restrict__ inv)
 {
     extern __shared__ __align__(16) unsigned char est_raw[];
     EstSmem &sm = *reinterpret_cast<EstSmem *>(est_raw);
@@ -617,6 +618,8 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
     if (tid < cnt_p) {
         const int i = perm[first + tid];
         sm.anchor[tid] = anchors ? anchors[i] : i;
+        sm.patch[tid] = i;
+        inv[sm.anchor[tid]] = i;
     }
     for (int idx = tid; idx < PD * PD; idx += EST_T) {
         const int e = idx >> 6, j = idx & 63;
@@ -710,7 +713,7 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
             const int p = 8 * pg + a;
             if (p < cnt_p) {
                 const float mu = sm.mus[p];
-                float4 *dst = reinterpret_cast<float4 *>(zrow + ((size_t)cg * H * W + sm.anchor[p]) * PS);
+                float4 *dst = reinterpret_cast<float4 *>(zrow + ((size_t)cg * H * W + sm.patch[p]) * PS);
                 dst[0] = make_float4(acc[a][0] + mu, acc[a][1] + mu, acc[a][2] + mu, acc[a][3] + mu);
                 dst[1] = make_float4(acc[a][4] + mu, acc[a][5] + mu, acc[a][6] + mu, acc[a][7] + mu);
             }
@@ -762,7 +765,7 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
     }
     const int max_items = (n + EST_T - 1) / EST_T + K;
     k_estimate<<<max_items, EST_T, sizeof(EstSmem), st>>>(xhat, H, W, anchors, ws.perm, ws.items, g->Rtot,
-                                                          g->d_roff, g->d_r, g->d_B, g->tab, ws.zrow);
+                                                          g->d_roff, g->d_r, g->d_B, g->tab, ws.zrow, ws.inv);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -776,9 +779,14 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
 // xhat = (a y + bs xtilde) / (a^2 + bs), bs = beta sigma^2 = lambda * mult
 // (with the `valid` boundary bs is weighed by the pixel's patch count / P).
 //
-// The estimates are stored by patch row: plane u holds, for every anchor, the
-// 8 estimates of its patch row u (zrow[(u N + anchor) 8 + v]), so the
-// estimates that land on one image row from one anchor row are contiguous.
+// The estimates are stored by patch row: plane u holds, for every sampled
+// patch, the 8 estimates of its patch row u at the patch's index in the
+// subset (zrow[(u N + i) 8 + v]; the estimation also records i at the
+// patch's anchor).  The subsets list their anchors in increasing order (the
+// jittered grid nearly so), so the sampled anchors of one anchor row have
+// consecutive indices and the estimates that land on one image row from one
+// anchor row are contiguous, and the planes are dense (a 1/3 subset fills a
+// third of the buffer, which stays in L2).
 // A warp owns AG_SPAN = 24 consecutive pixels (i, j0 .. j0 + 23) of R image
 // rows; lane l stands for anchor column j0 - 7 + l.  For each anchor row the
 // lane loads its multiplicity and, where the anchor is sampled, the 32-byte
@@ -796,7 +804,7 @@ constexpr int AG_THREADS = 256;
 
 template <int R>
 __global__ void __launch_bounds__(AG_THREADS)
-k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
+k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult, const int *__restrict__ inv,
             const float *xhat, int H, int W, const float *__restrict__ y,
             const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
             float *xout, int weighted, float *__restrict__ wout)
@@ -822,14 +830,19 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult,
     // loaded first, then the sampled segments AG_CHUNK anchor rows at a time
     // (their loads issued together), then added in ascending anchor-row order.
     constexpr int NE = PS + R - 1;
-    size_t ab[NE];
+    size_t ab[NE];  // the anchor's patch index in the subset (the anchor itself for the full set)
     unsigned m[NE];
     int ai = (i0 - (PS - 1)) % H;  // >= -7 >= -H
     if (ai < 0) ai += H;
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
-        ab[e] = (size_t)ai * W + c;
-        m[e] = mult ? mult[ab[e]] : 1u;
+        const size_t a = (size_t)ai * W + c;
+        m[e] = mult ? mult[a] : 1u;
+        ab[e] = a;
+        if (mult) {
+            const int pi = inv[a];
+            ab[e] = m[e] ? (size_t)pi : 0;
+        }
         if (++ai == H) ai = 0;
     }
     constexpr int AG_CHUNK = 4;
@@ -909,10 +922,10 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
     const long long warps = (long long)((H + R - 1) / R) * ((W + AG_SPAN - 1) / AG_SPAN);
     const unsigned blocks = (unsigned)((warps * 32 + AG_THREADS - 1) / AG_THREADS);
     if (R == 2)
-        k_aggregate<2><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+        k_aggregate<2><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
                                                      xout, weighted, wout);
     else
-        k_aggregate<1><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, xhat, H, W, y, a, lamf, (float)bmult,
+        k_aggregate<1><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
                                                      xout, weighted, wout);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
