@@ -225,6 +225,38 @@ void set_error(const std::string &msg);
         }                                                                              \
     } while (0)
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// The hot-path kernels are launched with programmatic stream serialization:
+// a kernel may be scheduled while its predecessor in the stream finishes, and
+// waits at its start (griddepcontrol.wait) until the predecessor has completed
+// and its memory is visible; every kernel lets its successor launch as soon as
+// all of its own blocks are running (griddepcontrol.launch_dependents), so the
+// launch latency and set-up of one kernel overlap the tail of the previous one.
+// Launched without the attribute, both instructions have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter()
+{
+    pdl_wait();
+    pdl_trigger();
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // ---------------------------------------------------------------- launchers
 // Each returns EPLL_OK or an error after setting the message.  All enqueue on st.
 // Tables of nb iterations at once (slot b: multiplier mult[b], or 1/beta =

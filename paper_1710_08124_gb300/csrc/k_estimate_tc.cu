@@ -66,6 +66,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
               const int *__restrict__ rk_, Tables tab, float *__restrict__ zrow, int *__restrict__ inv,
               long long npix, int *__restrict__ err)
 {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char et_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)et_raw + 1023) & ~(uintptr_t)1023);
     EtStage *sc = reinterpret_cast<EtStage *>(smem + 2 * ET_STAGE);
@@ -345,9 +346,9 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
     const int grid = max_items < sms ? max_items : sms;
     const uint4 *zh = reinterpret_cast<const uint4 *>(ws.Zb);
     const uint4 *zl = reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD);
-    k_estimate_tc<<<grid, ET_THREADS, ET_SMEM, st>>>(u1, u1lo, u2, u2lo, zh, zl, anchors, ws.mu, ws.perm, ws.items,
+    EPLL_CU(launch_pdl(k_estimate_tc, dim3(grid), dim3(ET_THREADS), ET_SMEM, st, u1, u1lo, u2, u2lo, zh, zl, anchors, ws.mu, ws.perm, ws.items,
                                                    g->d_roff, g->d_r, g->tab, ws.zrow, ws.inv, (long long)H * W,
-                                                   cnt(g, CNT_ERR));
+                                                   cnt(g, CNT_ERR)));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

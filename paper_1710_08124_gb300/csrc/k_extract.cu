@@ -70,6 +70,7 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
              uint16_t *__restrict__ Zhi, uint16_t *__restrict__ Zlo, float *__restrict__ zz,
              float *__restrict__ zsc2, float *__restrict__ mu_out, uint16_t *__restrict__ Zf)
 {
+    pdl_enter();
     const int u = threadIdx.x & (PS - 1);  // patch row of this thread
     // image rows start on 16-byte boundaries (vector loads allowed)
     const bool aligned = (W & 3) == 0 && ((uintptr_t)xhat & 15) == 0;
@@ -165,8 +166,8 @@ epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const i
                            float *zz, float *zsc2, float *mu, cudaStream_t st, uint16_t *Zf)
 {
     const int rows = (n + 127) / 128 * 128;
-    k_extract_tc<<<ex_grid(rows, n_dev != nullptr), EX_THREADS, 0, st>>>(xhat, H, W, anchors, n, rowmap, n_dev, fmt, split,
-                                                                  Zhi, Zlo, zz, zsc2, mu, Zf);
+    EPLL_CU(launch_pdl(k_extract_tc, dim3(ex_grid(rows, n_dev != nullptr)), dim3(EX_THREADS), 0, st, xhat, H, W,
+                       anchors, n, rowmap, n_dev, fmt, split, Zhi, Zlo, zz, zsc2, mu, Zf));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

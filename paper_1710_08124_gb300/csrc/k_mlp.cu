@@ -708,6 +708,7 @@ k_pair_score_tc(const __grid_constant__ CUtensorMap mapBs, const __grid_constant
                 const int *__restrict__ rowlist, const int *__restrict__ roff, const int *__restrict__ rk_,
                 Tables tab, const float *__restrict__ zz, float *__restrict__ pscore, int *__restrict__ err)
 {
+    pdl_enter();
     const int nitems = items[0].w;
     if ((int)blockIdx.x >= nitems) return;
     extern __shared__ __align__(1024) unsigned char ps_raw[];
@@ -846,6 +847,7 @@ __global__ void k_prop_combine(int n, const int *__restrict__ list, const int *_
                                int *__restrict__ kstar, float *__restrict__ gap, int *__restrict__ flag,
                                int *__restrict__ nflag, long long *__restrict__ nfallback)
 {
+    pdl_enter();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int total = list ? min(n, *nlist) : n;
     bool unsure = false;
@@ -962,8 +964,8 @@ epll_status launch_pair_scores(epll_gmm *g, const float *xhat, int H, int W, con
     // persistent over the work items (their count is known on the device only)
     const int max_items = (npairs + PS_T - 1) / PS_T + g->K;
     const int grid = max_items < 152 * 4 ? max_items : 152 * 4;
-    k_pair_score_tc<<<grid, PS_T, PS_SMEM, st>>>(bs, bslo, xhat, H, W, anchors, ws.pperm, ws.pitems, m, list,
-                                                 g->d_roff, g->d_r, g->tab, ws.zz, ws.pscore, cnt(g, CNT_ERR));
+    EPLL_CU(launch_pdl(k_pair_score_tc, dim3(grid), dim3(PS_T), PS_SMEM, st, bs, bslo, xhat, H, W, anchors, ws.pperm, ws.pitems, m, list,
+                                                 g->d_roff, g->d_r, g->tab, ws.zz, ws.pscore, cnt(g, CNT_ERR)));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -972,9 +974,9 @@ epll_status launch_cand_combine(epll_gmm *g, int n, int m, const int *list, cons
                                 int *flag, int *nflag, cudaStream_t st)
 {
     Workspace &ws = g->ws;
-    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, list, nlist, m, ws.cand, ws.pscore, nullptr, 0.0f, ws.zz,
+    EPLL_CU(launch_pdl(k_prop_combine, dim3((n + 255) / 256), dim3(256), 0, st, n, list, nlist, m, ws.cand, ws.pscore, nullptr, 0.0f, ws.zz,
                                                    g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, flag, nflag,
-                                                   nullptr);
+                                                   nullptr));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -991,10 +993,10 @@ epll_status launch_select_proposal(epll_gmm *g, const float *xhat, int H, int W,
     if (topm > 1 && (s = launch_pair_scores(g, xhat, H, W, anchors, n, topm, nullptr, nullptr, st))) return s;
     int *nflag1 = cnt(g, CNT_NFLAG1);
     EPLL_CU(cudaMemsetAsync(nflag1, 0, sizeof(int), st));
-    k_prop_combine<<<(n + 255) / 256, 256, 0, st>>>(n, nullptr, nullptr, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
+    EPLL_CU(launch_pdl(k_prop_combine, dim3((n + 255) / 256), dim3(256), 0, st, n, nullptr, nullptr, topm, ws.cand, topm > 1 ? ws.pscore : nullptr, ws.pmass,
                                                    g->prop_pmin, ws.zz,
                                                    g->tab.tmax, tau_abs, SPLIT_REL, ws.kstar, ws.gap, ws.flag1,
-                                                   nflag1, ws.ctr + 1);
+                                                   nflag1, ws.ctr + 1));
     EPLL_LAUNCHED(g);
     // exhaustive split-BF16 pass over the undecided patches
     return launch_split_pass(g, xhat, H, W, anchors, n, ws.flag1, nflag1, tau_abs, st);

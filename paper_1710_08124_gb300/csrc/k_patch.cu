@@ -52,6 +52,7 @@ k_select_fp32(const float *__restrict__ xhat, int H, int W, const int *__restric
               const int *__restrict__ nlist, int f0, int fcap, int K, const int *__restrict__ roff,
               float *__restrict__ scores)
 {
+    pdl_enter();
     __shared__ __align__(16) float Bs[PD][SEL_CH];
     __shared__ float qs[SEL_CH];
     __shared__ int ks[SEL_CH];
@@ -163,9 +164,9 @@ epll_status launch_select_fp32(epll_gmm *g, const float *xhat, int H, int W, con
     int *nflag = cnt(g, CNT_NFLAG);
     EPLL_CU(cudaMemsetAsync(nflag, 0, sizeof(int), st));
     prof_begin(g, st);
-    k_select_fp32<false><<<(n + SEL_THREADS - 1) / SEL_THREADS, SEL_THREADS, 0, st>>>(
+    EPLL_CU(launch_pdl(k_select_fp32<false>, dim3((n + SEL_THREADS - 1) / SEL_THREADS), dim3(SEL_THREADS), 0, st, 
         xhat, H, W, anchors, n, g->d_B, g->Rtot, g->d_colk, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap,
-        ws.flag, nflag, nullptr, nullptr, 0, 0, g->K, g->d_roff, nullptr);
+        ws.flag, nflag, nullptr, nullptr, 0, 0, g->K, g->d_roff, nullptr));
     prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
@@ -259,6 +260,7 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
           const float *__restrict__ scores, float band_abs, float band_rel, int *__restrict__ kstar,
           float *__restrict__ gap, long long *__restrict__ ctr)
 {
+    pdl_enter();
     __shared__ float zh[PD], zl[PD];
     __shared__ df s_zz;
     __shared__ float s_red[RS_WARPS];
@@ -412,10 +414,10 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
             // band: twice the split form's near-tie threshold (its error bound is half of it)
             int blocks = n < 152 * 8 ? n : 152 * 8;
             if (blocks < 1) blocks = 1;
-            k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), 0,
+            EPLL_CU(launch_pdl(k_rescore, dim3(blocks), dim3(32 * RS_WARPS), 0, st, xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), 0,
                                                         fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
                                                         g->d_Blo, g->tab, ws.fscore, 2.0f * tau_abs, 8e-5f,
-                                                        ws.kstar, ws.gap, ws.ctr);
+                                                        ws.kstar, ws.gap, ws.ctr));
             EPLL_LAUNCHED(g);
             return EPLL_OK;
         }
@@ -424,16 +426,16 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
     for (int f0 = 0; f0 < n; f0 += fcap) {
         const int rows = min(fcap, n - f0);
         const dim3 grid((rows + SEL_THREADS - 1) / SEL_THREADS, g->K < 16 ? g->K : 16);
-        k_select_fp32<true><<<grid, SEL_THREADS, 0, st>>>(
+        EPLL_CU(launch_pdl(k_select_fp32<true>, dim3(grid), dim3(SEL_THREADS), 0, st, 
             xhat, H, W, anchors, 0, g->d_B, g->Rtot, g->d_colk, g->tab, 0.0f, 0.0f, nullptr, nullptr,
-            nullptr, nullptr, ws.flag, cnt(g, CNT_NFLAG), f0, fcap, g->K, g->d_roff, ws.fscore);
+            nullptr, nullptr, ws.flag, cnt(g, CNT_NFLAG), f0, fcap, g->K, g->d_roff, ws.fscore));
         EPLL_LAUNCHED(g);
         int blocks = rows < 152 * 8 ? rows : 152 * 8;
         if (blocks < 1) blocks = 1;
-        k_rescore<<<blocks, 32 * RS_WARPS, 0, st>>>(xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
+        EPLL_CU(launch_pdl(k_rescore, dim3(blocks), dim3(32 * RS_WARPS), 0, st, xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
                                                     fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
                                                     g->d_Blo, g->tab, ws.fscore, RESCORE_ABS, RESCORE_REL,
-                                                    ws.kstar, ws.gap, ws.ctr);
+                                                    ws.kstar, ws.gap, ws.ctr));
         EPLL_LAUNCHED(g);
     }
     return EPLL_OK;
@@ -500,6 +502,7 @@ __global__ void __launch_bounds__(GRP_THREADS, 1)
 k_group(const int *__restrict__ keys, int n, int K, const int *__restrict__ n_dev, int mult,
         int *__restrict__ perm, int4 *__restrict__ items)
 {
+    pdl_enter();
     namespace cgx = cooperative_groups;
     cgx::cluster_group cl = cgx::this_cluster();
     extern __shared__ int gsh[];
@@ -608,6 +611,7 @@ k_estimate(const float *__restrict__ xhat, int H, int W, const int *__restrict__
            const int *__restrict__ roff, const int *__restrict__ rk_, const float *__restrict__ B,
            Tables tab, float *__restrict__ zrow, int *__restrict__ inv)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char est_raw[];
     EstSmem &sm = *reinterpret_cast<EstSmem *>(est_raw);
     if ((int)blockIdx.x >= items[0].w) return;
@@ -738,13 +742,15 @@ epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts
     cfg.blockDim = dim3(GRP_THREADS);
     cfg.dynamicSmemBytes = 2 * (size_t)K * sizeof(int);
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cl;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     EPLL_CU(cudaLaunchKernelEx(&cfg, k_group, keys, n, K, n_dev, mult, perm, items));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
@@ -764,8 +770,8 @@ epll_status launch_estimate(epll_gmm *g, const float *xhat, int H, int W, const 
         attr = true;
     }
     const int max_items = (n + EST_T - 1) / EST_T + K;
-    k_estimate<<<max_items, EST_T, sizeof(EstSmem), st>>>(xhat, H, W, anchors, ws.perm, ws.items, g->Rtot,
-                                                          g->d_roff, g->d_r, g->d_B, g->tab, ws.zrow, ws.inv);
+    EPLL_CU(launch_pdl(k_estimate, dim3(max_items), dim3(EST_T), sizeof(EstSmem), st, xhat, H, W, anchors, ws.perm, ws.items, g->Rtot,
+                                                          g->d_roff, g->d_r, g->d_B, g->tab, ws.zrow, ws.inv));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }
@@ -809,6 +815,7 @@ k_aggregate(const float *__restrict__ zrow, const unsigned *__restrict__ mult, c
             const float *__restrict__ a, const float *__restrict__ lamf, float bmult,
             float *xout, int weighted, float *__restrict__ wout)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int gw = (W + AG_SPAN - 1) / AG_SPAN, gh = (H + R - 1) / R;
     const int wid = (int)((blockIdx.x * (unsigned)AG_THREADS + threadIdx.x) >> 5);
@@ -922,11 +929,11 @@ epll_status launch_aggregate(epll_gmm *g, const float *xhat, int H, int W, const
     const long long warps = (long long)((H + R - 1) / R) * ((W + AG_SPAN - 1) / AG_SPAN);
     const unsigned blocks = (unsigned)((warps * 32 + AG_THREADS - 1) / AG_THREADS);
     if (R == 2)
-        k_aggregate<2><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
-                                                     xout, weighted, wout);
+        EPLL_CU(launch_pdl(k_aggregate<2>, dim3(blocks), dim3(AG_THREADS), 0, st, g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
+                                                     xout, weighted, wout));
     else
-        k_aggregate<1><<<blocks, AG_THREADS, 0, st>>>(g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
-                                                     xout, weighted, wout);
+        EPLL_CU(launch_pdl(k_aggregate<1>, dim3(blocks), dim3(AG_THREADS), 0, st, g->ws.zrow, mult, g->ws.inv, xhat, H, W, y, a, lamf, (float)bmult,
+                                                     xout, weighted, wout));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
 }

@@ -28,6 +28,7 @@ k_tables(int K, int Rtot, int Rp, const int *__restrict__ r, const int *__restri
          const double *__restrict__ d_lambda, Mults mults, double sigma2, double beta_direct,
          const float *__restrict__ B, Tables tab0, int fmt)
 {
+    pdl_enter();
     __shared__ double red[64];
     __shared__ float sq[64 + RTOT_ALIGN];
     __shared__ double s_ib;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(256)
 k_scale_basis(int K, int Rtot, int Rp, const int *__restrict__ colk, const float *__restrict__ B, Tables tab0,
               int fmt)
 {
+    pdl_enter();
     __shared__ float tile[PD][33];
     const Tables tab = slot_tables(tab0, blockIdx.y, K, Rp, Rtot);
     const int c0 = blockIdx.x * 32;
@@ -179,12 +181,12 @@ epll_status launch_tables(epll_gmm *g, const double *d_lambda, const double *mul
     Mults m{};
     for (int b = 0; b < nb; ++b) m.m[b] = mult[b];
     EPLL_CU(cudaMemsetAsync(g->tab0.tmax, 0, sizeof(float) * nb, st));
-    k_tables<<<dim3(g->K, nb), 64, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
-                                            g->d_lam, d_lambda, m, sigma2, beta_direct, g->d_B, g->tab0, fmt);
+    EPLL_CU(launch_pdl(k_tables, dim3(dim3(g->K, nb)), dim3(64), 0, st, g->K, g->Rtot, g->Rp, g->d_r, g->d_roff, g->d_S, g->d_w,
+                                            g->d_lam, d_lambda, m, sigma2, beta_direct, g->d_B, g->tab0, fmt));
     EPLL_LAUNCHED(g);
     if (fmt) {
-        k_scale_basis<<<dim3(g->Rtot / 32, nb), 256, 0, st>>>(g->K, g->Rtot, g->Rp, g->d_colk, g->d_B, g->tab0,
-                                                              fmt);
+        EPLL_CU(launch_pdl(k_scale_basis, dim3(dim3(g->Rtot / 32, nb)), dim3(256), 0, st, g->K, g->Rtot, g->Rp, g->d_colk, g->d_B, g->tab0,
+                                                              fmt));
         EPLL_LAUNCHED(g);
     }
     return EPLL_OK;
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
 k_frac_cluster(int N, int M, uint64_t seed, int t0, int cached, int *__restrict__ anchors_all,
                unsigned *__restrict__ mult_all)
 {
+    pdl_enter();
     extern __shared__ uint32_t kc[];
     namespace cgx = cooperative_groups;
     cgx::cluster_group cl = cgx::this_cluster();
@@ -487,13 +490,15 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     cfg.blockDim = dim3(FS_THREADS);
     cfg.dynamicSmemBytes = cached ? slice * sizeof(uint32_t) : 0;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cls;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     EPLL_CU(cudaLaunchKernelEx(&cfg, k_frac_cluster, N, *n, o.seed, t0, cached, anchors, mult));
     EPLL_LAUNCHED(g);
     return EPLL_OK;

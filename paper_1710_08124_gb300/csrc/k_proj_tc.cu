@@ -151,6 +151,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     static_assert(!(DUMP && CAND), "one output form");
     static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
     static_assert(RR == 0 || C::COLS % (RR ? RR : 1) == 0, "an epilogue warp owns whole components");
+    pdl_enter();
     if (n_dev) n = *n_dev;                       // rows listed on the device
     const int mtiles = (n + TC_M - 1) / TC_M;
     if ((int)blockIdx.x >= mtiles) return;       // whole CTA idle, before any setup
@@ -493,10 +494,10 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     const dim3 grid(gx, slices);
     // the instrumentation covers the pass over every sampled patch only
     if (!n_dev) prof_begin(g, st);
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
+    EPLL_CU(launch_pdl(kern, grid, dim3(Cfg::THREADS), Cfg::SMEM, st, a, alo, b, blo, n, rowmap, n_dev, g->K, g->Rtot, idesc, zz,
                                              g->d_colk, g->d_tileg, g->tab, tau_abs, tau_rel, ws.kstar, ws.gap, flag,
                                              nflag, cnt(g, CNT_ERR), scores, zsc2,
-                                             reinterpret_cast<int4 *>(ws.cand));
+                                             reinterpret_cast<int4 *>(ws.cand)));
     if (!n_dev) prof_end(g, st, n);
     EPLL_LAUNCHED(g);
     return EPLL_OK;
