@@ -246,7 +246,7 @@ epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const d
  * tensor-core selection (256 or 128) and image rows per warp of the
  * reprojection (1 or 2).  Every shape computes the same restoration (up to
  * the order of FP32 sums); the batch autotuner starts from these values.
- * Defaults 256 and 2.  Errors: EPLL_EINVAL. */
+ * Defaults 256 and 1.  Errors: EPLL_EINVAL. */
 epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg);
 
 /* The configuration the batch autotuner chose for the last tuned job list of

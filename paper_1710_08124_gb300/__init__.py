@@ -261,7 +261,7 @@ def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = 
     del keep
 
 
-def set_tiles(g: GMM, tile_bn: int = 256, tile_agg: int = 2):
+def set_tiles(g: GMM, tile_bn: int = 256, tile_agg: int = 1):
     """Tile shapes of the handle's selection and reprojection kernels (``epll_set_tiles``)."""
     _check(lib().epll_set_tiles(g.handle, int(tile_bn), int(tile_agg)))
 

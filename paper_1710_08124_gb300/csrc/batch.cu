@@ -32,7 +32,7 @@ struct BatchState {
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;        // what the captured graph runs
     std::vector<unsigned char> tuned_key;  // job list the tuned configuration belongs to
-    int tuned_lanes = 0, tuned_bn = 256, tuned_agg = 2;
+    int tuned_lanes = 0, tuned_bn = 256, tuned_agg = 1;
     float *d_kern = nullptr;               // device copies of the jobs' blur kernels
     size_t kern_cap = 0;
     std::vector<size_t> kern_off;          // per job: offset in d_kern (CONV jobs)

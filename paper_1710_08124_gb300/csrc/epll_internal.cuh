@@ -196,7 +196,7 @@ struct epll_gmm {
     // stage of the tensor-core selection (256 or 128), image rows per warp
     // of the reprojection (1 or 2)
     int tile_bn = 256;
-    int tile_agg = 2;
+    int tile_agg = 1;
     // second stream: the patch sampler runs on it beside the tables kernels
     // (fork / join through the two events; created on first use)
     cudaStream_t aux = nullptr;

@@ -53,7 +53,8 @@ struct EtStage {  // an item's scalars, beside its stage
     int pad;
 };
 // barriers per stage: full, mma1, cprep, mma2
-constexpr int ET_SMEM = 1024 + 2 * ET_STAGE + 2 * (int)sizeof(EtStage) + 8 * 8 + 16;
+constexpr int ET_STG = 40;  // floats per row of an epilogue warp's staging tile (32 rows x 32 values)
+constexpr int ET_SMEM = 1024 + 2 * ET_STAGE + 2 * (int)sizeof(EtStage) + 8 * 8 + 16 + 2 * ET_EPI * 32 * ET_STG * 4;
 
 // 96 registers: the register file is split between the SM's four sub-partitions,
 // each holding at most five of the 20 warps (5 x 32 x 96 <= 16384)
@@ -73,6 +74,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(sc + 2);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    float *stg_all = reinterpret_cast<float *>(tslot + 4);  // epilogue warps' staging tiles
     const uint32_t bar0 = smem_u32(bars);
 #define ET_FULL(s) (bar0 + 8u * (uint32_t)(s))
 #define ET_MMA1(s) (bar0 + 8u * (uint32_t)(2 + (s)))
@@ -223,6 +225,7 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
         const uint32_t tl = tbase + ((uint32_t)(32 * qd) << 16) + 128 * s + 32 * hh;
         unsigned char *A = ET_STAGE_PTR(s);
         const EtStage &st = sc[s];
+        float *stg = stg_all + ew * 32 * ET_STG;
         for (int j = s; (int)blockIdx.x + j * (int)gridDim.x < n_items; j += 2) {
             const uint32_t ph = (j >> 1) & 1;
             // tcgen05.ld is warp-collective: every lane takes the same branch
@@ -231,10 +234,10 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
             if (!ok) break;
             tc_fence_after();
             // the row's destination, read before the stage is handed back
-            const bool live = t < st.cnt;
+            const int cnt_item = st.cnt;
+            const bool live = t < cnt_item;
             const int pi = st.patch[t];
             if (live && hh == 0) inv[st.anchor[t]] = pi;
-            float *dst = zrow + (size_t)pi * PS;  // plane e8 at dst + e8 * npix * 8
             {
                 // c'_j = gw_kj c_j (zero beyond the rank) split into the A operand of the
                 // second product, written over this thread's own part of the patch row,
@@ -282,22 +285,34 @@ k_estimate_tc(const __grid_constant__ CUtensorMap mapU1, const __grid_constant__
             ok = __all_sync(0xffffffffu, mbar_wait(ET_MMA2(s), ph, abort_flag));
             if (!ok) break;
             tc_fence_after();
+            // the warp's 32 rows x 32 estimates (patch rows 4 hh .. 4 hh + 3) through its
+            // staging tile, then written two lanes per 32-byte segment: a store
+            // instruction covers sixteen whole segments of one plane
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 uint32_t v[16];
-                tmem_ld16_wait(tl + 64 + 16 * half, v);  // whole warp, before the per-row test
-                if (live) {
+                tmem_ld16_wait(tl + 64 + 16 * half, v);  // whole warp
 #pragma unroll
-                    for (int el = 0; el < 2; ++el) {
-                        const int e8 = 4 * hh + 2 * half + el;
-                        float4 *seg = reinterpret_cast<float4 *>(dst + (size_t)e8 * npix * PS);
-                        seg[0] = make_float4(__uint_as_float(v[8 * el]), __uint_as_float(v[8 * el + 1]),
-                                             __uint_as_float(v[8 * el + 2]), __uint_as_float(v[8 * el + 3]));
-                        seg[1] = make_float4(__uint_as_float(v[8 * el + 4]), __uint_as_float(v[8 * el + 5]),
-                                             __uint_as_float(v[8 * el + 6]), __uint_as_float(v[8 * el + 7]));
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(stg + lane * ET_STG + 16 * half + 4 * q) =
+                        make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            __syncwarp();
+            {
+                const int cntw = cnt_item - 32 * qd;  // live rows of this warp
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int rr = 16 * h2 + (lane >> 1), part = lane & 1;
+                    const int prow = __shfl_sync(0xffffffffu, pi, rr);
+#pragma unroll
+                    for (int el = 0; el < 4; ++el) {
+                        const float4 val = *reinterpret_cast<const float4 *>(stg + rr * ET_STG + 8 * el + 4 * part);
+                        if (rr < cntw)
+                            *reinterpret_cast<float4 *>(zrow + ((size_t)(4 * hh + el) * npix + prow) * PS + 4 * part) = val;
                     }
                 }
             }
+            __syncwarp();  // the staging tile is rewritten by the next item
             // the next item's first epilogue writes the tail term into these columns
             tc_fence_before();
             __syncwarp();
