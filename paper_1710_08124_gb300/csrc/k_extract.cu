@@ -15,15 +15,6 @@ __device__ __forceinline__ uint8_t to_e4m3(float v)
 {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
-__device__ __forceinline__ uint16_t to16(float v, int fmt)
-{
-    return fmt == 2 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
-__device__ __forceinline__ float from16(uint16_t v, int fmt)
-{
-    return fmt == 2 ? __half2float(__ushort_as_half(v)) : __bfloat162float(__ushort_as_bfloat16(v));
-}
-
 // Row i of the operand is sampled patch i, or patch rowmap[i] when a row map
 // (a device list with device count *n_dev) is given.  mu_out (nullable)
 // receives each row's patch mean; Zf (nullable) an FP16 copy of the rows
@@ -54,9 +45,24 @@ __device__ __forceinline__ float max8(float v)
     v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
     return v;
 }
+// two values rounded to nearest (even) as one packed 16-bit pair (one
+// conversion instruction; the same roundings as two scalar conversions)
 __device__ __forceinline__ uint32_t pack16(float a, float b, int fmt)
 {
-    return (uint32_t)to16(a, fmt) | ((uint32_t)to16(b, fmt) << 16);
+    if (fmt == 2) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ float lo16f(uint32_t p, int fmt)
+{
+    return fmt == 2 ? __half2float(__ushort_as_half((unsigned short)(p & 0xffffu))) : __uint_as_float(p << 16);
+}
+__device__ __forceinline__ float hi16f(uint32_t p, int fmt)
+{
+    return fmt == 2 ? __half2float(__ushort_as_half((unsigned short)(p >> 16))) : __uint_as_float(p & 0xffff0000u);
 }
 __device__ __forceinline__ uint4 pack16x8(const float *v, int fmt)
 {
@@ -138,11 +144,16 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
                 zsc2[i] = sc * sc;
             }
         } else {
-            *reinterpret_cast<uint4 *>(Zhi + off) = pack16x8(z, fmt);
+            const uint4 hi = pack16x8(z, fmt);
+            *reinterpret_cast<uint4 *>(Zhi + off) = hi;
             if (split) {
+                const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w};
                 float lo[PS];
 #pragma unroll
-                for (int v = 0; v < PS; ++v) lo[v] = z[v] - from16(to16(z[v], fmt), fmt);
+                for (int q = 0; q < 4; ++q) {
+                    lo[2 * q] = z[2 * q] - lo16f(hw[q], fmt);
+                    lo[2 * q + 1] = z[2 * q + 1] - hi16f(hw[q], fmt);
+                }
                 *reinterpret_cast<uint4 *>(Zlo + off) = pack16x8(lo, fmt);
             }
             if (Zf) *reinterpret_cast<uint4 *>(Zf + off) = pack16x8(z, 2);
