@@ -371,7 +371,7 @@ def run_uneven(args):
                    "images_per_step": len(bj), "pixels_per_step": int(sum(j.side ** 2 for j in jobs)),
                    "precision": args.precision, "l2": "256 MB buffer written before each step, outside the events"},
         "per_image_launches": {"value": seq_rate, "unit": "images/s", "speedup": graph_rate / seq_rate},
-        "autotuned": dict(zip(("lanes", "selection_basis_columns_per_stage", "reprojection_threads_per_group"),
+        "autotuned": dict(zip(("lanes", "selection_basis_columns_per_stage", "reprojection_rows_per_warp"),
                               ep.batch_config(gm))),
         "clocks": clk,
     }

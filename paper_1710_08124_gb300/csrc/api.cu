@@ -275,13 +275,23 @@ static int basis_format(const epll_options &o, int precision)
 
 // Per-beta tables and patch subsets of iterations t0 .. t0+nb-1 (one batch):
 // the sampler runs on the handle's second stream while the tables kernels
-// run on st, and st waits for it.
+// run on st, and st waits for it (batch lanes run both on st).
 static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb,
                                  const double *d_lambda, const double *mult, double sigma2,
                                  double beta_direct, int *n, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     epll_status s;
+    if (g->lane) {
+        // a batch lane runs beside other lanes already: one stream (forks inside
+        // the captured batch graph cost more than they overlap)
+        if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o, eff_precision(g, o)), st)))
+            return s;
+        if (o.select == EPLL_SELECT_TREE &&
+            (s = launch_tables(g->tree->tm, d_lambda, mult, nb, sigma2, beta_direct, 4, st)))
+            return s;
+        return launch_sample(g, H, W, o, t0, nb, n, ws.anchors_all, ws.mult_all, ws.sampler, ws.sstride, st);
+    }
     if (!g->aux) {
         EPLL_CU(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking));
         EPLL_CU(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));

@@ -204,6 +204,11 @@ static epll_status prepare_lanes(epll_gmm *g, BatchState *b, const std::vector<s
 static epll_status issue(BatchState *b, const std::vector<std::vector<int>> &part, const epll_job *jobs,
                          const double *beta, int T, const epll_options &o, cudaStream_t origin)
 {
+    // lanes run side by side: no programmatic early launch (see t_pdl)
+    struct PdlOff {
+        PdlOff() { t_pdl = false; }
+        ~PdlOff() { t_pdl = true; }
+    } pdl_off;
     EPLL_CU(cudaEventRecord(b->fork, origin));
     for (size_t l = 0; l < part.size(); ++l) {
         EPLL_CU(cudaStreamWaitEvent(b->streams[l], b->fork, 0));

@@ -240,6 +240,9 @@ __device__ __forceinline__ void pdl_enter()
     pdl_wait();
     pdl_trigger();
 }
+// Off while the batch issues its lanes: kernels of other lanes' streams could
+// then find the SMs held by blocks that launched early and only wait.
+inline thread_local bool t_pdl = true;
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args &&...args)
@@ -253,7 +256,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = t_pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
 }
 

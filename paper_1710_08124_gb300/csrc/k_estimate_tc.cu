@@ -32,6 +32,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace epll {
 
 constexpr int ET_T = 128;                     // patches per work item (the MMA's M)
@@ -358,7 +360,13 @@ epll_status launch_estimate_tc(epll_gmm *g, const float *xhat, int H, int W, con
         EPLL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
     const int max_items = (n + ET_T - 1) / ET_T + g->K;
-    const int grid = max_items < sms ? max_items : sms;
+    int grid = max_items < sms ? max_items : sms;
+    // a batch lane shares the GPU with the other lanes' kernels: its CTAs
+    // (one per SM, which they fill) take three work items each at least
+    if (g->lane) {
+        const int cap = (max_items + 2) / 3;
+        grid = std::max(1, std::min(grid, cap));
+    }
     const uint4 *zh = reinterpret_cast<const uint4 *>(ws.Zb);
     const uint4 *zl = reinterpret_cast<const uint4 *>(ws.Zb + ws.zrows * PD);
     EPLL_CU(launch_pdl(k_estimate_tc, dim3(grid), dim3(ET_THREADS), ET_SMEM, st, u1, u1lo, u2, u2lo, zh, zl, anchors, ws.mu, ws.perm, ws.items,

@@ -750,7 +750,7 @@ epll_status group_by_key(epll_gmm *g, const int *keys, int n, int K, int *counts
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = t_pdl ? 2 : 1;
     EPLL_CU(cudaLaunchKernelEx(&cfg, k_group, keys, n, K, n_dev, mult, perm, items));
     EPLL_LAUNCHED(g);
     return EPLL_OK;

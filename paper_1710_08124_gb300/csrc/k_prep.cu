@@ -498,7 +498,7 @@ epll_status launch_sample(epll_gmm *g, int H, int W, const epll_options &o, int 
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = t_pdl ? 2 : 1;
     EPLL_CU(cudaLaunchKernelEx(&cfg, k_frac_cluster, N, *n, o.seed, t0, cached, anchors, mult));
     EPLL_LAUNCHED(g);
     return EPLL_OK;
