@@ -275,16 +275,18 @@ static int basis_format(const epll_options &o, int precision)
 
 // Per-beta tables and patch subsets of iterations t0 .. t0+nb-1 (one batch):
 // the sampler runs on the handle's second stream while the tables kernels
-// run on st, and st waits for it (batch lanes run both on st).
+// run on st, and st waits for it (batch lanes, the full set and small images
+// run both on st).
 static epll_status prepare_batch(epll_gmm *g, int H, int W, const epll_options &o, int t0, int nb,
                                  const double *d_lambda, const double *mult, double sigma2,
                                  double beta_direct, int *n, cudaStream_t st)
 {
     Workspace &ws = g->ws;
     epll_status s;
-    if (g->lane) {
-        // a batch lane runs beside other lanes already: one stream (forks inside
-        // the captured batch graph cost more than they overlap)
+    if (g->lane || o.subset == EPLL_SUBSET_ALL || (size_t)H * W < ((size_t)1 << 16)) {
+        // one stream: a batch lane runs beside other lanes already (forks inside
+        // the captured batch graph cost more than they overlap), the full set
+        // launches no sampler, and a small image's sampler is shorter than a fork
         if ((s = launch_tables(g, d_lambda, mult, nb, sigma2, beta_direct, basis_format(o, eff_precision(g, o)), st)))
             return s;
         if (o.select == EPLL_SELECT_TREE &&
