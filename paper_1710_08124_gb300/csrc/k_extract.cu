@@ -169,7 +169,7 @@ k_extract_tc(const float *__restrict__ xhat, int H, int W, const int *__restrict
 static inline int ex_grid(int rows, bool listed)
 {
     const int b = (rows + EX_PATCHES - 1) / EX_PATCHES;
-    return listed && b > 152 * 8 ? 152 * 8 : b;
+    return listed && b > 152 * 2 ? 152 * 2 : b;
 }
 
 epll_status launch_extract(epll_gmm *g, const float *xhat, int H, int W, const int *anchors, int n,

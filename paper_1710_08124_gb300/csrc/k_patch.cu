@@ -412,7 +412,7 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
         epll_status s = launch_dump_split(g, xhat, H, W, anchors, n, st);
         if (s == EPLL_OK) {
             // band: twice the split form's near-tie threshold (its error bound is half of it)
-            int blocks = n < 152 * 8 ? n : 152 * 8;
+            int blocks = n < 152 * 2 ? n : 152 * 2;
             if (blocks < 1) blocks = 1;
             EPLL_CU(launch_pdl(k_rescore, dim3(blocks), dim3(32 * RS_WARPS), 0, st, xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), 0,
                                                         fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
@@ -430,7 +430,7 @@ epll_status launch_rescore(epll_gmm *g, const float *xhat, int H, int W, const i
             xhat, H, W, anchors, 0, g->d_B, g->Rtot, g->d_colk, g->tab, 0.0f, 0.0f, nullptr, nullptr,
             nullptr, nullptr, ws.flag, cnt(g, CNT_NFLAG), f0, fcap, g->K, g->d_roff, ws.fscore));
         EPLL_LAUNCHED(g);
-        int blocks = rows < 152 * 8 ? rows : 152 * 8;
+        int blocks = rows < 152 * 2 ? rows : 152 * 2;
         if (blocks < 1) blocks = 1;
         EPLL_CU(launch_pdl(k_rescore, dim3(blocks), dim3(32 * RS_WARPS), 0, st, xhat, H, W, anchors, ws.flag, cnt(g, CNT_NFLAG), f0,
                                                     fcap, g->K, g->Rtot, g->d_roff, g->d_r, g->d_B,
