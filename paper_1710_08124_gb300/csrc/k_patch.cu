@@ -265,6 +265,7 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
     __shared__ df s_zz;
     __shared__ float s_red[RS_WARPS];
     __shared__ int s_cand[RS_KMAX];
+    __shared__ int s_cor[RS_KMAX];  // the candidate's column offset << 7 | its rank
     __shared__ int s_nc;
     __shared__ df s_part[RS_CPR][RS_QW][PD];
     __shared__ df r_b1[RS_WARPS], r_b2[RS_WARPS];
@@ -310,8 +311,13 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
         float outside = FLT_MAX;
         for (int k = threadIdx.x; k < K; k += 32 * RS_WARPS) {
             const float sk = sc[k];
-            if (!(sk > best + band)) s_cand[atomicAdd(&s_nc, 1)] = k;
-            else outside = fminf(outside, sk);
+            if (!(sk > best + band)) {
+                const int idx = atomicAdd(&s_nc, 1);
+                s_cand[idx] = k;
+                s_cor[idx] = (roff[k] << 7) | rk_[k];
+            } else {
+                outside = fminf(outside, sk);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) outside = fminf(outside, __shfl_xor_sync(0xffffffffu, outside, o));
@@ -325,10 +331,18 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
             const int ci = c0 + slot;
             const bool mine = ci < nc;  // warp-uniform
             int k = 0, o = 0, r = 0;
+            df q0 = {0.0f, 0.0f}, q1 = {0.0f, 0.0f}, tk = {0.0f, 0.0f}, ck = {0.0f, 0.0f};
             if (mine) {
                 k = s_cand[ci];
-                o = roff[k];
-                r = rk_[k];
+                o = s_cor[ci] >> 7;
+                r = s_cor[ci] & 127;
+                if (qq == 0) {
+                    // the scalars of the score, loaded beside the basis
+                    if (lane < r) q0 = {tab.q_hi[o + lane], tab.q_lo[o + lane]};
+                    if (lane + 32 < r) q1 = {tab.q_hi[o + lane + 32], tab.q_lo[o + lane + 32]};
+                    tk = {tab.t_hi[k], tab.t_lo[k]};
+                    ck = {tab.cst_hi[k], tab.cst_lo[k]};
+                }
                 const int j0 = lane, j1 = lane + 32;
                 const float *b0 = B + o + j0, *bl0 = Blo + o + j0;
                 df c0s = {0.0f, 0.0f}, c1s = {0.0f, 0.0f};
@@ -355,13 +369,12 @@ k_rescore(const float *__restrict__ xhat, int H, int W, const int *__restrict__ 
                         c = df_add(c, s_part[slot][1][j]);
                         c = df_add(c, s_part[slot][2][j]);
                         c = df_add(c, s_part[slot][3][j]);
-                        df q = {tab.q_hi[o + j], tab.q_lo[o + j]};
-                        part = df_add(part, df_mul(q, df_mul(c, c)));
+                        part = df_add(part, df_mul(h ? q1 : q0, df_mul(c, c)));
                     }
                 }
                 df sv = df_warp_sum(part);
-                sv = df_add(sv, df_mul({tab.t_hi[k], tab.t_lo[k]}, zz));
-                sv = df_add(sv, {tab.cst_hi[k], tab.cst_lo[k]});
+                sv = df_add(sv, df_mul(tk, zz));
+                sv = df_add(sv, ck);
                 if (df_less(sv, b1) || (!df_less(b1, sv) && kb >= 0 && k < kb)) {
                     b2 = b1; b1 = sv; kb = k;
                 } else if (df_less(sv, b2)) {
