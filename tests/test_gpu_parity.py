@@ -99,6 +99,29 @@ def test_patch_step_subsets_ragged(r, subset, param):
         _check_step(gm, om, y, 8 / sigma ** 2, ep.Options(subset=subset, subset_param=param, seed=5), t)
 
 
+@pytest.mark.parametrize("prec", [ep.AUTO, ep.FP32])
+@pytest.mark.parametrize("r", [8, 64])
+def test_reprojection_with_duplicate_anchors(r, prec):
+    """The jittered grid on a side its spacing does not divide places some
+    anchors twice across the wrap seam, and such an anchor counts twice.  The
+    reprojection reads one estimate per anchor through its index in the subset
+    and weighs it by the multiplicity: patch averages within 1e-5 of the
+    oracle's, and the whole restoration within 1e-4."""
+    H, W, seed = 50, 37, 1
+    an = oracle.sample(H, W, oracle.JITTER, 6, seed, 0)
+    _, cnt = np.unique(an, return_counts=True)
+    assert (cnt > 1).any()
+    gm, om = models(37, "fixed", r)
+    sigma = 25 / 255
+    x, y = synth.denoise_problem(1, H, sigma, W=W)
+    o = ep.Options(precision=prec, subset=ep.SUBSET_JITTER, subset_param=6, seed=seed)
+    _check_step(gm, om, y, 8 / sigma ** 2, o, 0)
+    xo = oracle.restore(om, y.astype(np.float32).astype(np.float64), sigma, subset=oracle.JITTER,
+                        subset_param=6, seed=seed)
+    xg = ep.restore(gm, dev(y), sigma, options=o).cpu().numpy()
+    assert np.abs(xg - xo).max() <= 1e-4
+
+
 def test_patch_step_rho_ranks():
     g = synth.tiny_gmm(9, seed=31)
     gm, om = models(9, "rho", 0.9, gmm=g)
