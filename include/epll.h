@@ -231,8 +231,8 @@ enum { EPLL_BATCH_SEQUENTIAL = 0, EPLL_BATCH_GRAPH = 1 };
  *         lanes = 0 lets the library tune the batch: on the first call for a
  *         job list it times the graph for 1, 2, 4 and 8 lanes, then, at the
  *         fastest lane count, for the tile shapes of the selection kernel (256
- *         or 128 basis columns per stage) and of the reprojection (2 or 4
- *         threads per 8-pixel group), and keeps the fastest combination.
+ *         or 128 basis columns per stage) and of the reprojection (1 or 2
+ *         image rows per warp), and keeps the fastest combination.
  * The first call for a job list (and any call with a different one) allocates
  * the lanes' workspaces, runs the batch once eagerly and captures the graph;
  * those calls synchronise the device.  Replays are asynchronous on `stream`.
