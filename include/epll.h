@@ -249,6 +249,16 @@ epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const d
  * Defaults 256 and 1.  Errors: EPLL_EINVAL. */
 epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg);
 
+/* Selection's first pass over the sampled patches (Eq. 14 for every
+ * component, Sec. "Complexity via eigenspace implementation") in clusters of
+ * two CTAs (enable = 1) that share each tensor-core product (tcgen05
+ * cta_group::2, 256 patch rows): each SM then streams half of every basis
+ * tile.  Applies with 256-column tiles to the 16-bit forms (FP16, BF16,
+ * split BF16); FP8 and 128-column tiles keep one CTA per product.  The
+ * selections are the same either way (the products accumulate in the same
+ * order).  Errors: EPLL_EINVAL (null handle, enable not 0 or 1). */
+epll_status epll_set_cta_pairs(epll_gmm *g, int enable);
+
 /* The configuration the batch autotuner chose for the last tuned job list of
  * this handle (host out, each nullable): lane count (0 if nothing was tuned),
  * selection basis columns per stage (256 or 128) and reprojection image rows

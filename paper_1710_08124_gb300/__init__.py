@@ -101,6 +101,7 @@ def lib():
         L.epll_sample_noalloc.argtypes = L.epll_sample.argtypes
         L.epll_restore_batch.argtypes = [vp, i, C.POINTER(_Job), vp, i, C.POINTER(_Options), i, i, vp]
         L.epll_set_tiles.argtypes = [vp, i, i]
+        L.epll_set_cta_pairs.argtypes = [vp, i]
         L.epll_batch_config.argtypes = [vp, vp, vp, vp]
         L.epll_last_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                          C.POINTER(C.c_longlong)]
@@ -264,6 +265,12 @@ def restore_batch(g: GMM, jobs, beta_mult=PAPER_BETA, options: Options | None = 
 def set_tiles(g: GMM, tile_bn: int = 256, tile_agg: int = 1):
     """Tile shapes of the handle's selection and reprojection kernels (``epll_set_tiles``)."""
     _check(lib().epll_set_tiles(g.handle, int(tile_bn), int(tile_agg)))
+
+
+def set_cta_pairs(g: GMM, enable: bool = True):
+    """Selection's first pass in clusters of two CTAs sharing each tensor-core
+    product (``epll_set_cta_pairs``)."""
+    _check(lib().epll_set_cta_pairs(g.handle, int(bool(enable))))
 
 
 def batch_config(g: GMM):

@@ -180,6 +180,7 @@ static epll_status prepare_lanes(epll_gmm *g, BatchState *b, const std::vector<s
         b->lanes[l]->prop = g->prop;
         b->lanes[l]->prop_topm = g->prop_topm;
         b->lanes[l]->prop_pmin = g->prop_pmin;
+        b->lanes[l]->tc_pair = g->tc_pair;
         // the tree: a lane of the node model (own tables), the handle's arrays
         epll_gmm *ln = b->lanes[l];
         if (!(ln->tree && ln->tree->src == g->tree)) {
@@ -375,6 +376,7 @@ extern "C" epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jo
     put(key, L);
     put(key, tc.bn);
     put(key, tc.agg);
+    put(key, g->tc_pair);
     if (!(b->exec && b->key == key)) {
         epll_status s = build_graph(g, b, n, jobs, beta_mult, T, o, L, tc, st);
         if (s) return s;
@@ -391,6 +393,14 @@ extern "C" epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg)
         return fail(EPLL_EINVAL, "tile_bn must be 128 or 256 and tile_agg 1 or 2");
     g->tile_bn = tile_bn;
     g->tile_agg = tile_agg;
+    return EPLL_OK;
+}
+
+extern "C" epll_status epll_set_cta_pairs(epll_gmm *g, int enable)
+{
+    if (!g || g->lane) return fail(EPLL_EINVAL, "null model handle");
+    if (enable != 0 && enable != 1) return fail(EPLL_EINVAL, "enable must be 0 or 1");
+    g->tc_pair = enable;
     return EPLL_OK;
 }
 

@@ -197,6 +197,7 @@ struct epll_gmm {
     // of the reprojection (1 or 2)
     int tile_bn = 256;
     int tile_agg = 1;
+    int tc_pair = 0;  // selection first pass in CTA pairs (tcgen05 cta_group::2)
     // second stream: the patch sampler runs on it beside the tables kernels
     // (fork / join through the two events; created on first use)
     cudaStream_t aux = nullptr;

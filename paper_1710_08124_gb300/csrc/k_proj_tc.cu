@@ -35,13 +35,16 @@ namespace epll {
 constexpr int TC_M = 128;
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
 
-template <int BN, int NT, int RR, bool CAND = false>
+template <int BN, int NT, int RR, bool CAND = false, bool PAIR = false>
 struct TcCfg {
     // NT: 1 one 16-bit product, 3 split BF16 (three products), 8 one E4M3 product
+    // PAIR: a CTA pair shares each MMA (M = 256); each CTA holds its own 128
+    // patch rows and half of every basis tile
     static constexpr int ROWB = NT == 8 ? 64 : 128;            // bytes per 64-element row
     static constexpr int A_TILE = TC_M * ROWB;
     static constexpr int A_BYTES = A_TILE * (NT == 3 ? 2 : 1); // one A buffer (hi [+ lo])
-    static constexpr int B_TILE = BN * ROWB;
+    static constexpr int B_ROWS = PAIR ? BN / 2 : BN;          // basis rows this CTA loads per tile
+    static constexpr int B_TILE = B_ROWS * ROWB;
     static constexpr int B_STAGE = B_TILE * (NT == 3 ? 2 : 1);
     static constexpr int STAGES_RAW = (TC_SMEM_BUDGET - 2 * A_BYTES) / B_STAGE;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
@@ -64,6 +67,10 @@ struct TcCtrl {
     unsigned long long b_full[8], b_empty[8];
     unsigned long long t_full[4], t_empty[4];
     unsigned long long drain;
+    // CTA pairs: rank 1's operand tiles landed (relayed to rank 0's MMA
+    // thread), and the end-of-kernel handshake
+    unsigned long long ap_full[2], bp_full[8];
+    unsigned long long bye;
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -136,8 +143,16 @@ __device__ __forceinline__ void top4(float s, int k, float (&cs)[4], int (&ck)[4
 // with its candidates, the components within that bound of the best, in
 // cand[f] (-1: absent); a first candidate of -1 means the band may hold more
 // than four components.
-template <int BN, int NT, int RR, bool DUMP, bool CAND>
-__global__ void __launch_bounds__(TcCfg<BN, NT, RR, CAND>::THREADS, 1)
+// PAIR = true (launched in clusters of two, n given by the host): the two
+// CTAs of a cluster take 256-row tiles together, rank r the rows
+// 128 r .. 128 r + 127 of each and the basis rows BN/2 r .. BN/2 r + BN/2 - 1
+// of each basis tile.  Rank 0's MMA thread issues cta_group::2 MMAs
+// (M = 256) once both CTAs' tiles have landed (rank 1's warp 1 relays its
+// TMA completions), and its commits arrive on the barriers of both CTAs; the
+// epilogue warps of both hand each accumulator buffer back to rank 0.  Each
+// SM thus streams half of every basis tile through its shared memory.
+template <int BN, int NT, int RR, bool DUMP, bool CAND, bool PAIR = false>
+__global__ void __launch_bounds__(TcCfg<BN, NT, RR, CAND, PAIR>::THREADS, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
           const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
           int n, const int *__restrict__ rowmap, const int *__restrict__ n_dev, int K, int Rtot,
@@ -147,20 +162,27 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           int *__restrict__ flag, int *__restrict__ nflag, int *__restrict__ err,
           float *__restrict__ scores, const float *__restrict__ zsc2, int4 *__restrict__ cand)
 {
-    using C = TcCfg<BN, NT, RR, CAND>;
+    using C = TcCfg<BN, NT, RR, CAND, PAIR>;
     static_assert(!(DUMP && CAND), "one output form");
+    static_assert(!PAIR || (!DUMP && NT != 8), "CTA pairs: first pass, 16-bit operands");
+    static_assert(sizeof(TcCtrl) <= 1024, "control block");
     static_assert(!DUMP || RR > 0, "score dump needs uniform ranks");
     static_assert(RR == 0 || C::COLS % (RR ? RR : 1) == 0, "an epilogue warp owns whole components");
     pdl_enter();
     if (n_dev) n = *n_dev;                       // rows listed on the device
-    const int mtiles = (n + TC_M - 1) / TC_M;
-    if ((int)blockIdx.x >= mtiles) return;       // whole CTA idle, before any setup
+    // work unit: one CTA (128-row tiles) or one CTA pair (256-row tiles)
+    constexpr int UM = PAIR ? 2 * TC_M : TC_M;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int mtiles = (n + UM - 1) / UM;
+    if (unit >= mtiles) return;                  // whole CTA (pair) idle, before any setup
     const int ntiles_all = Rtot / BN;
     const int tile0 = DUMP ? (int)((long long)ntiles_all * blockIdx.y / gridDim.y) : 0;
     const int tile1 = DUMP ? (int)((long long)ntiles_all * (blockIdx.y + 1) / gridDim.y) : ntiles_all;
     if (tile1 <= tile0) return;
     const int ntiles = tile1 - tile0;
-    const int my_m = (mtiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int my_m = (mtiles - unit + nunits - 1) / nunits;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -171,34 +193,57 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &ctl->abort_flag;
+    // pairs: waits on barriers that the other CTA (or its commits) arrive on
+    // use cluster-scope acquire, and a timeout aborts both CTAs
+#define TC_WAIT(bar, par) (PAIR ? mbar_wait_cluster((bar), (par), abort_flag) : mbar_wait((bar), (par), abort_flag))
+    // an epilogue warp hands accumulator buffer b back to the MMA thread (of rank 0)
+#define TC_FREE(b)                                                                  \
+    do {                                                                            \
+        if (PAIR && rank != 0u) mbar_arrive_cluster(mapa_rank(smem_u32(&ctl->t_empty[b]), 0u)); \
+        else mbar_arrive(smem_u32(&ctl->t_empty[b]));                               \
+    } while (0)
 
     if (threadIdx.x == 0) {
         ctl->abort_flag = 0;
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&ctl->a_full[i]), 1);
             mbar_init(smem_u32(&ctl->a_empty[i]), 1);
+            mbar_init(smem_u32(&ctl->ap_full[i]), 1);
         }
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->b_full[s]), 1);
             mbar_init(smem_u32(&ctl->b_empty[s]), 1);
+            mbar_init(smem_u32(&ctl->bp_full[s]), 1);
         }
         for (int b = 0; b < C::NB; ++b) {
             mbar_init(smem_u32(&ctl->t_full[b]), 1);
-            mbar_init(smem_u32(&ctl->t_empty[b]), C::EW);
+            mbar_init(smem_u32(&ctl->t_empty[b]), PAIR ? 2 * C::EW : C::EW);
         }
         mbar_init(smem_u32(&ctl->drain), 1);
+        mbar_init(smem_u32(&ctl->bye), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tma_prefetch_desc(&mapA);
         tma_prefetch_desc(&mapB);
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                         smem_u32(&ctl->tmem_base))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // pairs: one warp of each CTA takes part in the pair's allocation (the
+        // same columns in both)
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                             smem_u32(&ctl->tmem_base))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                             smem_u32(&ctl->tmem_base))
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    // pairs: both CTAs' barriers are initialised before either arrives remotely
+    if constexpr (PAIR) cluster_sync_all();
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ctl->tmem_base;
 
@@ -207,9 +252,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         if (lane == 0) {
             bool ok = true;
             for (int mt = 0; ok && mt < my_m; ++mt) {
-                const int m0 = ((int)blockIdx.x + mt * (int)gridDim.x) * TC_M;
+                const int m0 = (unit + mt * nunits) * UM + (int)rank * TC_M;
                 const int ab = mt & 1, around = mt >> 1;
-                if (!mbar_wait(smem_u32(&ctl->a_empty[ab]), (around & 1) ^ 1, abort_flag)) break;
+                if (!TC_WAIT(smem_u32(&ctl->a_empty[ab]), (around & 1) ^ 1)) break;
                 const uint32_t af = smem_u32(&ctl->a_full[ab]);
                 unsigned char *dA = sA + ab * C::A_BYTES;
                 mbar_expect_tx(af, C::A_BYTES);
@@ -218,15 +263,37 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 for (int it = 0; it < ntiles; ++it) {
                     const int gi = mt * ntiles + it;
                     const int s = gi % C::STAGES, round = gi / C::STAGES;
-                    if (!mbar_wait(smem_u32(&ctl->b_empty[s]), (round & 1) ^ 1, abort_flag)) {
+                    if (!TC_WAIT(smem_u32(&ctl->b_empty[s]), (round & 1) ^ 1)) {
                         ok = false;
                         break;
                     }
                     const uint32_t bf = smem_u32(&ctl->b_full[s]);
                     mbar_expect_tx(bf, C::B_STAGE);
                     unsigned char *dst = sB + s * C::B_STAGE;
-                    tma_load_2d(smem_u32(dst), &mapB, 0, (tile0 + it) * BN, bf);
-                    if (NT == 3) tma_load_2d(smem_u32(dst + C::B_TILE), &mapBlo, 0, (tile0 + it) * BN, bf);
+                    const int brow = (tile0 + it) * BN + (int)rank * C::B_ROWS;
+                    tma_load_2d(smem_u32(dst), &mapB, 0, brow, bf);
+                    if (NT == 3) tma_load_2d(smem_u32(dst + C::B_TILE), &mapBlo, 0, brow, bf);
+                }
+            }
+        }
+    } else if (warp == 1 && PAIR && rank == 1) {
+        // ------------------------------------------------ relay (pair rank 1)
+        // forwards each of this CTA's operand tiles, once landed, to rank 0's
+        // MMA thread (in the order that thread consumes them)
+        if (lane == 0) {
+            bool ok = true;
+            for (int mt = 0; ok && mt < my_m; ++mt) {
+                const int ab = mt & 1, around = mt >> 1;
+                if (!TC_WAIT(smem_u32(&ctl->a_full[ab]), around & 1)) break;
+                mbar_arrive_cluster(mapa_rank(smem_u32(&ctl->ap_full[ab]), 0u));
+                for (int it = 0; it < ntiles; ++it) {
+                    const int gi = mt * ntiles + it;
+                    const int s = gi % C::STAGES, round = gi / C::STAGES;
+                    if (!TC_WAIT(smem_u32(&ctl->b_full[s]), round & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_rank(smem_u32(&ctl->bp_full[s]), 0u));
                 }
             }
         }
@@ -236,15 +303,17 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             bool ok = true;
             for (int mt = 0; ok && mt < my_m; ++mt) {
                 const int ab = mt & 1, around = mt >> 1;
-                if (!mbar_wait(smem_u32(&ctl->a_full[ab]), around & 1, abort_flag)) break;
+                if (!TC_WAIT(smem_u32(&ctl->a_full[ab]), around & 1)) break;
+                if (PAIR && !TC_WAIT(smem_u32(&ctl->ap_full[ab]), around & 1)) break;
                 tc_fence_after();
                 const uint32_t aHi = smem_u32(sA + ab * C::A_BYTES), aLo = aHi + C::A_TILE;
                 for (int it = 0; it < ntiles; ++it) {
                     const int gi = mt * ntiles + it;
                     const int s = gi % C::STAGES, round = gi / C::STAGES;
                     const int b = gi % C::NB, tround = gi / C::NB;
-                    if (!mbar_wait(smem_u32(&ctl->b_full[s]), round & 1, abort_flag) ||
-                        !mbar_wait(smem_u32(&ctl->t_empty[b]), (tround & 1) ^ 1, abort_flag)) {
+                    if (!TC_WAIT(smem_u32(&ctl->b_full[s]), round & 1) ||
+                        (PAIR && !TC_WAIT(smem_u32(&ctl->bp_full[s]), round & 1)) ||
+                        !TC_WAIT(smem_u32(&ctl->t_empty[b]), (tround & 1) ^ 1)) {
                         ok = false;
                         break;
                     }
@@ -256,6 +325,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         const uint32_t off = (uint32_t)(k * 32);
                         if constexpr (NT == 8) {
                             mma_f8(d, sdesc_sw64(aHi + off), sdesc_sw64(bHi + off), idesc, k > 0 ? 1u : 0u);
+                        } else if constexpr (PAIR) {
+                            mma_f16_pair(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
+                            if (NT == 3) {
+                                mma_f16_pair(d, sdesc_sw128(aLo + off), sdesc_sw128(bHi + off), idesc, 1u);
+                                mma_f16_pair(d, sdesc_sw128(aHi + off), sdesc_sw128(bLo + off), idesc, 1u);
+                            }
                         } else {
                             mma_f16(d, sdesc_sw128(aHi + off), sdesc_sw128(bHi + off), idesc, k > 0 ? 1u : 0u);
                             if (NT == 3) {
@@ -264,14 +339,28 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                             }
                         }
                     }
-                    mma_commit(smem_u32(&ctl->b_empty[s]));
-                    mma_commit(smem_u32(&ctl->t_full[b]));
+                    if constexpr (PAIR) {
+                        mma_commit_pair(smem_u32(&ctl->b_empty[s]), 3);
+                        mma_commit_pair(smem_u32(&ctl->t_full[b]), 3);
+                    } else {
+                        mma_commit(smem_u32(&ctl->b_empty[s]));
+                        mma_commit(smem_u32(&ctl->t_full[b]));
+                    }
                 }
-                mma_commit(smem_u32(&ctl->a_empty[ab]));  // A buffer free once these MMAs complete
+                // A buffer free once these MMAs complete
+                if constexpr (PAIR) mma_commit_pair(smem_u32(&ctl->a_empty[ab]), 3);
+                else mma_commit(smem_u32(&ctl->a_empty[ab]));
             }
             // drain: every MMA issued above has completed once this arrives
-            mma_commit(smem_u32(&ctl->drain));
-            mbar_wait(smem_u32(&ctl->drain), 0, abort_flag);
+            if constexpr (PAIR) {
+                // the pair's MMAs write the other CTA's tensor memory: wait for
+                // them even after an abort, before the teardown handshake
+                mma_commit_pair(smem_u32(&ctl->drain), 1);
+                if (!mbar_wait_bounded(smem_u32(&ctl->drain), 0)) *abort_flag = 1;
+            } else {
+                mma_commit(smem_u32(&ctl->drain));
+                mbar_wait(smem_u32(&ctl->drain), 0, abort_flag);
+            }
         }
     } else {
         // ------------------------------------------------ epilogue (EW warps)
@@ -280,7 +369,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int row = 32 * q + lane;
         bool ok = true;
         for (int mt = 0; ok && mt < my_m; ++mt) {
-            const int m0 = ((int)blockIdx.x + mt * (int)gridDim.x) * TC_M;
+            const int m0 = (unit + mt * nunits) * UM + (int)rank * TC_M;
             const int grow = m0 + row;
             const float zzr = grow < n ? zz[grow] : 0.0f;
             const float rs2 = (NT == 8 && grow < n) ? zsc2[grow] : 1.0f;  // 8-bit: row scale squared
@@ -292,7 +381,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 const int gi = mt * ntiles + it;
                 const int b = gi % C::NB, tround = gi / C::NB;
                 // tcgen05.ld is warp-collective: every lane takes the same branch
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&ctl->t_full[b]), tround & 1, abort_flag))) {
+                if (!__all_sync(0xffffffffu, TC_WAIT(smem_u32(&ctl->t_full[b]), tround & 1))) {
                     ok = false;
                     break;
                 }
@@ -311,7 +400,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     tmem_ld_all<C::COLS>(taddr, r);
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+                    if (lane == 0) TC_FREE(b);
 #pragma unroll
                     for (int p = 0; p < C::COLS / RR; ++p) {
                         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -377,7 +466,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl->t_empty[b]));
+                if (lane == 0) TC_FREE(b);
                 // the group ends with a whole component
                 if (curk >= 0) {
                     const float a8 = NT == 8 ? acc * rs2 * __ldg(&tab.k8s2[curk]) : acc;
@@ -459,11 +548,28 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) {
+        // neither CTA frees its tensor memory or leaves while the other may
+        // still reach into it: rank 0's MMAs have drained, and every remote
+        // arrival of rank 1 precedes its side of this handshake
+        if (threadIdx.x == 0) {
+            mbar_arrive_cluster(mapa_rank(smem_u32(&ctl->bye), rank ^ 1u));
+            // (longer than any wait of the other CTA, which ends within one
+            // bound of its last progress)
+            if (!mbar_wait_bounded(smem_u32(&ctl->bye), 0, 3)) ctl->abort_flag = 1;
+        }
+        __syncthreads();
+    }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
     }
     if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
+#undef TC_WAIT
+#undef TC_FREE
 }
 
 template <int BN, int NT, int RR, bool DUMP = false, bool CAND = false>
@@ -503,13 +609,79 @@ static epll_status launch_tc(epll_gmm *g, const CUtensorMap &a, const CUtensorMa
     return EPLL_OK;
 }
 
+// The first pass over n sampled patches (n known on the host) in clusters of
+// two CTAs sharing each MMA (M = 256).  The basis maps have boxes of BN / 2
+// rows (each CTA loads half of every basis tile); idesc is that of M = 128.
+template <int BN, int NT, int RR, bool CAND>
+static epll_status launch_tc_pair(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
+                                  const CUtensorMap &b, const CUtensorMap &blo, int n, const float *zz,
+                                  uint32_t idesc, float tau_abs, float tau_rel, int *flag, int *nflag,
+                                  cudaStream_t st)
+{
+    using Cfg = TcCfg<BN, NT, RR, CAND, true>;
+    auto kern = k_proj_tc<BN, NT, RR, false, CAND, true>;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(Cfg::THREADS);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = st;
+    cfg.attrs = at;
+    static int clusters = -1;  // pairs resident at once
+    if (clusters < 0) {
+        EPLL_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+        cfg.gridDim = dim3(2);
+        cfg.numAttrs = 1;
+        int nc = 0;
+        EPLL_CU(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
+        if (nc < 1) {
+            set_error("selection: a cluster of two CTAs cannot be resident (disable CTA pairs)");
+            return EPLL_ECUDA;
+        }
+        clusters = nc;
+    }
+    const int mtiles = (n + 2 * TC_M - 1) / (2 * TC_M);
+    int pairs = clusters < mtiles ? clusters : mtiles;
+    if (pairs < 1) pairs = 1;
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.numAttrs = t_pdl ? 2 : 1;
+    const uint32_t idesc2 = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(2 * TC_M >> 4) << 24);  // M = 256
+    Workspace &ws = g->ws;
+    prof_begin(g, st);
+    EPLL_CU(cudaLaunchKernelEx(&cfg, kern, a, alo, b, blo, n, (const int *)nullptr, (const int *)nullptr, g->K,
+                               g->Rtot, idesc2, zz, (const int *)g->d_colk, (const int4 *)g->d_tileg, g->tab,
+                               tau_abs, tau_rel, ws.kstar, ws.gap, flag, nflag, cnt(g, CNT_ERR), (float *)nullptr,
+                               (const float *)nullptr, reinterpret_cast<int4 *>(ws.cand)));
+    prof_end(g, st, n);
+    EPLL_LAUNCHED(g);
+    return EPLL_OK;
+}
+
 template <int BN, int NT, bool CAND = false>
 static epll_status dispatch_rr(epll_gmm *g, const CUtensorMap &a, const CUtensorMap &alo,
                                const CUtensorMap &b, const CUtensorMap &blo, int n, const int *rowmap,
                                const int *n_dev, const float *zz, uint32_t idesc, float tau_abs,
                                float tau_rel, int *flag, int *nflag, cudaStream_t st,
-                               const float *zsc2 = nullptr)
+                               const float *zsc2 = nullptr, bool pair = false)
 {
+    if constexpr (BN == 256 && NT != 8) {
+        if (pair) {
+            if (rowmap || n_dev) return fail(EPLL_EINVAL, "selection: CTA pairs serve the first pass only");
+#define EPLL_TCP_ARGS g, a, alo, b, blo, n, zz, idesc, tau_abs, tau_rel, flag, nflag, st
+            switch (g->uniform_rank) {
+            case 64: return launch_tc_pair<BN, NT, 64, CAND>(EPLL_TCP_ARGS);
+            case 16: return launch_tc_pair<BN, NT, 16, CAND>(EPLL_TCP_ARGS);
+            case 8: return launch_tc_pair<BN, NT, 8, CAND>(EPLL_TCP_ARGS);
+            default: return launch_tc_pair<BN, NT, 0, CAND>(EPLL_TCP_ARGS);
+            }
+#undef EPLL_TCP_ARGS
+        }
+    }
 #define EPLL_TC_ARGS g, a, alo, b, blo, n, rowmap, n_dev, zz, idesc, tau_abs, tau_rel, flag, nflag, st, nullptr, 1, zsc2
     switch (g->uniform_rank) {
     case 64: return launch_tc<BN, NT, 64, false, CAND>(EPLL_TC_ARGS);
@@ -580,6 +752,10 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     // the ragged-rank layout is packed in 256-column tiles
     const bool bn128 = g->tile_bn == 128 && g->uniform_rank != 0;
     const int BNs = bn128 ? 128 : 256;
+    // CTA pairs (first pass, 256-column tiles, 16-bit operands): each CTA of
+    // a pair loads half of every basis tile
+    const bool pair = g->tc_pair && !bn128 && !fp8;
+    const int bbox = pair ? BNs / 2 : BNs;
     if (fmt == 2) {
         if ((s = ensure_prop_ws(g, n))) return s;  // ws.cand, the pair buffers
         // FP16 operand rows in ws.Z2 (free until the rescoring's score dump)
@@ -592,11 +768,11 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
         EPLL_CU(cudaMemsetAsync(cnt(g, CNT_NFLAG), 0, sizeof(int), st));
         CUtensorMap a, b;
         if ((s = make_map(&a, Zf, rows, TC_M))) return s;
-        if ((s = make_map(&b, g->tab.B1, g->Rtot, BNs))) return s;
+        if ((s = make_map(&b, g->tab.B1, g->Rtot, bbox))) return s;
         if ((s = bn128 ? dispatch_rr<128, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 0),
                                                    tau_abs, tau_rel, ws.flag1, nflag1, st)
                        : dispatch_rr<256, 1, true>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 0),
-                                                   tau_abs, tau_rel, ws.flag1, nflag1, st)))
+                                                   tau_abs, tau_rel, ws.flag1, nflag1, st, nullptr, pair)))
             return s;
         if ((s = launch_pair_scores(g, xhat, H, W, anchors, n, 4, ws.flag1, nflag1, st))) return s;
         return launch_cand_combine(g, n, 4, ws.flag1, nflag1, tau_abs, ws.flag, cnt(g, CNT_NFLAG), st);
@@ -612,12 +788,12 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
     if ((s = make_map(&a, Zhi, rows, TC_M))) return s;
     if ((s = make_map(&alo, Zlo, rows, TC_M))) return s;
     if (split_first) {
-        if ((s = make_map(&b, g->tab.Bs, g->Rtot, BNs))) return s;
-        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, BNs))) return s;
+        if ((s = make_map(&b, g->tab.Bs, g->Rtot, bbox))) return s;
+        if ((s = make_map(&blo, g->tab.Bs_lo, g->Rtot, bbox))) return s;
         return bn128 ? dispatch_rr<128, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 128, 1),
                                            tau_abs, tau_rel, flag1, nflag1, st)
                      : dispatch_rr<256, 3>(g, a, alo, b, blo, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1),
-                                           tau_abs, tau_rel, flag1, nflag1, st);
+                                           tau_abs, tau_rel, flag1, nflag1, st, nullptr, pair);
     }
     if (fp8) {
         CUtensorMap a8, b8;
@@ -628,10 +804,10 @@ epll_status launch_select_tc(epll_gmm *g, const float *xhat, int H, int W, const
                                      tau_abs, tau_rel, flag1, nflag1, st, ws.zsc2)))
             return s;
     } else {
-        if ((s = make_map(&b, g->tab.B1, g->Rtot, 256))) return s;
+        if ((s = make_map(&b, g->tab.B1, g->Rtot, pair ? 128 : 256))) return s;
         // one-term BF16 pass: no lo operands (the lo map arguments are unused)
         if ((s = dispatch_rr<256, 1>(g, a, a, b, b, n, nullptr, nullptr, ws.zz, idesc_f16(TC_M, 256, 1), tau_abs,
-                                     tau_rel, flag1, nflag1, st)))
+                                     tau_rel, flag1, nflag1, st, nullptr, pair)))
             return s;
     }
     return launch_split_pass(g, xhat, H, W, anchors, n, flag1, nflag1, tau_abs, st);

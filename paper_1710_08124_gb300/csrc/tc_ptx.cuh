@@ -97,6 +97,96 @@ static __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// Two CTAs of a cluster of two (ranks 0 and 1) share each MMA
+// (tcgen05 cta_group::2): rank 0 issues it for M = 256 rows, half from each
+// CTA's shared memory, and each CTA's tensor memory receives its own 128
+// rows.  Barriers that the other CTA arrives on are waited for with
+// cluster-scope acquire.
+static __device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Shared::cluster address of this CTA's variable at `addr` in CTA `rank`.
+static __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+static __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+static __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+static __device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(10000000u)
+        : "memory");
+    return ok != 0;
+}
+// Bounded like mbar_wait; a CTA that gives up also raises the abort flag of
+// the other CTA of its pair (the flag at the same shared-memory offset), so
+// that both reach their teardown without waiting out their own limits.
+static __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_cluster(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_cluster(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            st_cluster_u32(mapa_rank(smem_u32((const void *)abort_flag), cluster_rank() ^ 1u), 1u);
+            return false;
+        }
+    }
+}
+// Bounded wait (`limit` times the usual bound) that does not give up on the
+// abort flag: teardown handshakes and draining the MMAs in flight, which
+// must end before memory is freed.
+static __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = 1)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_cluster(bar, parity))
+        if (clock64() - t0 > limit * WAIT_CYCLES) return false;
+    return true;
+}
+static __device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+static __device__ __forceinline__ void mma_f16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Arrives on the barrier at the same shared-memory offset in every CTA of
+// cta_mask once the pair MMAs issued so far have completed.
+static __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t cta_mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(cta_mask)
+        : "memory");
+}
+
 #define EPLL_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
                    "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
 #define EPLL_W8(i) "+r"(r[i + 0]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), \

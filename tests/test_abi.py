@@ -91,6 +91,11 @@ def test_attach_tree_rejects_null_handle(L):
     assert L.epll_gmm_attach_tree(None, 0, None, None, None, None, None) == ep.EINVAL
 
 
+def test_tile_setters_reject_null_handle(L):
+    assert L.epll_set_tiles(None, 256, 1) == ep.EINVAL
+    assert L.epll_set_cta_pairs(None, 1) == ep.EINVAL
+
+
 def test_header_enums_match_binding():
     """Every EPLL_* enum constant of include/epll.h has the value the Python
     binding passes for it (precision forms including EPLL_AUTO, selection
