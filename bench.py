@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--cta-pairs", type=int, choices=[0, 1], default=None,
                     help="selection first pass in clusters of two CTAs sharing each MMA (1) or one CTA per "
                          "MMA (0); default: the library's")
+    ap.add_argument("--tile-bn", type=int, choices=[128, 256], default=None,
+                    help="basis columns per selection tile (epll_set_tiles); default: the library's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain-FP32 comparison leg")
     ap.add_argument("--no-oracle-check", action="store_true",
@@ -1240,6 +1242,9 @@ def main():
     if args.cta_pairs is not None:
         for m in models.values():
             ep.set_cta_pairs(m, bool(args.cta_pairs))
+    if args.tile_bn is not None:
+        for m in models.values():
+            ep.set_tiles(m, args.tile_bn, 1)
     probs = problems(rank)
     dev = torch.device("cuda", local)
     ys = [torch.as_tensor(y, device=dev) for _, _, y in probs]
@@ -1357,7 +1362,7 @@ def main():
         "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD, "restores_per_step": RESTORES_PER_STEP,
                    "precision": args.precision, "patches_per_iteration": M_PATCH,
-                   "cta_pairs": args.cta_pairs,
+                   "cta_pairs": args.cta_pairs, "tile_bn": args.tile_bn,
                    "l2": "256 MB buffer written before each step, outside the timed events",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "mpatch_evals_per_s": restores * len(BETA) * M_PATCH / dev_s / 1e6,

@@ -243,8 +243,9 @@ epll_status epll_restore_batch(epll_gmm *g, int n, const epll_job *jobs, const d
                                int T, const epll_options *opt, int mode, int lanes, void *stream);
 
 /* Tile shapes of this handle's kernels: basis columns per stage of the
- * tensor-core selection (256 or 128) and image rows per warp of the
- * reprojection (1 or 2).  Every shape computes the same restoration (up to
+ * tensor-core selection (256 or 128; 128 keeps four accumulator buffers in
+ * flight instead of two) and image rows per warp of the reprojection (1 or
+ * 2).  Every shape computes the same restoration (up to
  * the order of FP32 sums); the batch autotuner starts from these values.
  * Defaults 256 and 1.  Errors: EPLL_EINVAL. */
 epll_status epll_set_tiles(epll_gmm *g, int tile_bn, int tile_agg);

@@ -54,11 +54,17 @@ struct TcCfg {
     // groups split every tile at component boundaries (the model's columns
     // are laid out so that no component straddles a 256-column tile)
     static constexpr int NG = RR == 0 ? 4 : (BN / RR >= 4 ? 4 : BN / RR);
-    static constexpr int EW = 4 * NG;                          // epilogue warps
+    static constexpr int EWS = 4 * NG;                         // epilogue warps of one set
+    // With four accumulator buffers and at most eight warps to a set, two
+    // sets take alternate buffers (each has two tiles' time for one), so the
+    // MMA may run three tiles ahead of the slowest warp.
+    static constexpr int SETS = (EWS <= 8 && NB >= 4) ? 2 : 1;
+    static constexpr int EW = EWS * SETS;                      // epilogue warps
+    static constexpr int NP = NG * SETS;                       // partial results per row to merge
     static constexpr int THREADS = 64 + 32 * EW;               // warp 0 TMA, warp 1 MMA, then the epilogue
     static constexpr int COLS = BN / NG;                       // columns per epilogue warp
-    static constexpr int MW = CAND ? 8 : 3;                    // merge words per row and group
-    static constexpr int CTRL = 1024 + (NG - 1) * TC_M * MW * 4; // barriers + the [NG-1][128][MW] merge buffer
+    static constexpr int MW = CAND ? 8 : 3;                    // merge words per row and part
+    static constexpr int CTRL = 1024 + (NP - 1) * TC_M * MW * 4; // barriers + the [NP-1][128][MW] merge buffer
     static constexpr int SMEM = 1024 + 2 * A_BYTES + STAGES * B_STAGE + CTRL;
 };
 
@@ -217,7 +223,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
         for (int b = 0; b < C::NB; ++b) {
             mbar_init(smem_u32(&ctl->t_full[b]), 1);
-            mbar_init(smem_u32(&ctl->t_empty[b]), PAIR ? 2 * C::EW : C::EW);
+            mbar_init(smem_u32(&ctl->t_empty[b]), PAIR ? 2 * C::EWS : C::EWS);  // one set reads a buffer
         }
         mbar_init(smem_u32(&ctl->drain), 1);
         mbar_init(smem_u32(&ctl->bye), 1);
@@ -364,8 +370,10 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
     } else {
         // ------------------------------------------------ epilogue (EW warps)
-        const int q = warp & 3;        // TMEM lane quarter this warp may access
-        const int h = (warp - 2) >> 2; // column group of each accumulator tile
+        const int q = warp & 3;                    // TMEM lane quarter this warp may access
+        const int set = (warp - 2) / C::EWS;       // the set's tiles: those of its parity (two sets)
+        const int h = ((warp - 2) % C::EWS) >> 2;  // column group of each accumulator tile
+        const int part = set * C::NG + h;          // this warp's partial result of its rows
         const int row = 32 * q + lane;
         bool ok = true;
         for (int mt = 0; ok && mt < my_m; ++mt) {
@@ -379,6 +387,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             int ck[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
             for (int it = 0; it < ntiles; ++it) {
                 const int gi = mt * ntiles + it;
+                if (C::SETS > 1 && (gi & 1) != set) continue;  // buffer gi % NB belongs to the other set
                 const int b = gi % C::NB, tround = gi / C::NB;
                 // tcgen05.ld is warp-collective: every lane takes the same branch
                 if (!__all_sync(0xffffffffu, TC_WAIT(smem_u32(&ctl->t_full[b]), tround & 1))) {
@@ -480,19 +489,19 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 }
             }
             if (CAND) {
-                // merge the column groups' four best, then list the undecided patch
-                if (C::NG > 1 && h > 0) {
-                    float *m = mrg + ((h - 1) * TC_M + row) * 8;
+                // merge the parts' four best, then list the undecided patch
+                if (C::NP > 1 && part > 0) {
+                    float *m = mrg + ((part - 1) * TC_M + row) * 8;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         m[j] = cs[j];
                         m[4 + j] = __int_as_float(ck[j]);
                     }
                 }
-                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
-                if (h == 0 && grow < n && ok) {
+                if (C::NP > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
+                if (part == 0 && grow < n && ok) {
 #pragma unroll
-                    for (int o = 1; o < C::NG; ++o) {
+                    for (int o = 1; o < C::NP; ++o) {
                         const float *m = mrg + ((o - 1) * TC_M + row) * 8;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) top4(m[j], __float_as_int(m[4 + j]), cs, ck);
@@ -509,23 +518,24 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                                               : make_int4(ck[0], ck[1], cs[2] < lim ? ck[2] : -1, -1);
                     }
                 }
-                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");  // mrg is reused
+                // mrg is reused; every warp leaves the tile loop together
+                if (C::NP > 1) ok = bar_and(ok, 1, 32 * C::EW);
             } else if (!DUMP) {
-                // merge the column groups (their components interleave); among
-                // equal scores the lowest component index wins
-                if (C::NG > 1 && h > 0) {
-                    float *m = mrg + ((h - 1) * TC_M + row) * 3;
+                // merge the parts (their components interleave); among equal
+                // scores the lowest component index wins
+                if (C::NP > 1 && part > 0) {
+                    float *m = mrg + ((part - 1) * TC_M + row) * 3;
                     m[0] = s1;
                     m[1] = s2;
                     m[2] = __int_as_float(k1);
                 }
-                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
-                if (h == 0 && grow < n && ok) {
+                if (C::NP > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");
+                if (part == 0 && grow < n && ok) {
                     const int out = rowmap ? rowmap[grow] : grow;
                     float b1 = s1, b2 = s2;
                     int bk = k1;
 #pragma unroll
-                    for (int o = 1; o < C::NG; ++o) {
+                    for (int o = 1; o < C::NP; ++o) {
                         const float *m = mrg + ((o - 1) * TC_M + row) * 3;
                         const float t1 = m[0], t2 = m[1];
                         const int tk = __float_as_int(m[2]);
@@ -541,7 +551,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     const float thr = tau_abs + tau_rel * zzr * __ldg(tab.tmax);
                     if (!(gp >= thr)) flag[atomicAdd(nflag, 1)] = out;
                 }
-                if (C::NG > 1) asm volatile("bar.sync 1, %0;" ::"n"(32 * C::EW) : "memory");  // mrg is reused
+                // mrg is reused; every warp leaves the tile loop together
+                if (C::NP > 1) ok = bar_and(ok, 1, 32 * C::EW);
             }
         }
     }

@@ -97,6 +97,22 @@ static __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+// Named barrier `id` over `nthreads` threads that also ANDs `ok` across them:
+// the warps of a group agree to go on (or to stop after an abort) together.
+static __device__ __forceinline__ bool bar_and(bool ok, int id, int nthreads)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\n"
+        "setp.ne.b32 q, %1, 0;\n"
+        "bar.red.and.pred p, %2, %3, q;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // ---------------------------------------------------------------- CTA pairs
 // Two CTAs of a cluster of two (ranks 0 and 1) share each MMA
 // (tcgen05 cta_group::2): rank 0 issues it for M = 256 rows, half from each

@@ -1,12 +1,14 @@
-"""The selection's first pass in CTA pairs (tcgen05 cta_group::2: 256 patch
-rows per pair, each CTA holding half of every basis tile) against the
-one-CTA pass and the FP64 oracle, through the C ABI.
+"""The selection's first pass in its other launch forms against the default
+one (one CTA per MMA, 256-column basis tiles) and the FP64 oracle, through
+the C ABI: CTA pairs (tcgen05 cta_group::2: 256 patch rows per pair, each CTA
+holding half of every basis tile) and 128-column basis tiles (four
+accumulator buffers; at rank 64 two sets of epilogue warps on alternate
+buffers).
 
-The pair form changes which SM holds which operand rows, not the sums: each
-accumulator of Eq. 14's projections is the same products added in the same
-order.  So the selections, gaps and patch estimates must equal those of the
-one-CTA pass, and the selection must match the oracle wherever the oracle's
-top-2 gap is >= 1e-4.  The shapes cover one pair whose second CTA holds no
+Neither form changes the sums: each accumulator of Eq. 14's projections is
+the same products added in the same order.  So the selections, gaps and
+patch estimates must equal those of the default form, and the selection must
+match the oracle wherever the oracle's top-2 gap is >= 1e-4.  The shapes cover one pair whose second CTA holds no
 patch (n < 128), one partly filled pair, several 256-row tiles with a ragged
 tail, ragged ranks (flat tail, rho rule), and the FEPLL size (512 x 512,
 K = 200, 1/3 subset: 87,382 patches, several tiles per pair).
@@ -38,17 +40,19 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
 
 
-def step(gm, x, beta, prec, pair, subset=ep.SUBSET_ALL, param=0.0):
+def step(gm, x, beta, prec, pair, subset=ep.SUBSET_ALL, param=0.0, bn=256):
     ep.set_cta_pairs(gm, pair)
+    ep.set_tiles(gm, bn, 1)
     o = ep.Options(precision=prec, subset=subset, subset_param=param, seed=17)
     out = [v.cpu().numpy() for v in ep.patch_step(gm, dev(x), beta, o, 0)]
     ep.last_counters(gm)  # raises if a bounded device wait gave up
     return out
 
 
-def compare(gm, om, x, beta, prec, subset=ep.SUBSET_ALL, param=0.0):
+def compare(gm, om, x, beta, prec, subset=ep.SUBSET_ALL, param=0.0, bn=256):
+    """The default form against pairs (bn = 256) or 128-column tiles (bn = 128)."""
     xt1, an1, ks1, gp1 = step(gm, x, beta, prec, False, subset, param)
-    xt2, an2, ks2, gp2 = step(gm, x, beta, prec, True, subset, param)
+    xt2, an2, ks2, gp2 = step(gm, x, beta, prec, bn == 256, subset, param, bn)
     assert np.array_equal(an1, an2)
     assert np.array_equal(ks1, ks2), f"{(ks1 != ks2).sum()} selections differ"
     assert np.array_equal(gp1, gp2)
@@ -120,3 +124,21 @@ def test_pairs_restore_and_batch():
         for j, ref in zip(jobs, outs[True]):
             assert np.array_equal(j[1].cpu().numpy(), ref), rep
     ep.last_counters(gm)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("r", [64, 8])
+def test_tiles_128_equal_256(prec, r):
+    """128-column basis tiles (at r = 64 two epilogue warp sets on alternate
+    accumulator buffers) on several tiles with a ragged tail, and at the FEPLL
+    size."""
+    g = synth.synthetic_gmm(37)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r)
+    om = oracle.Model(g.w, g.U, g.S, "fixed", r)
+    sigma = 25 / 255
+    x = synth.image(1, 40, 29) + synth.noise(1, 40, 29, sigma)
+    compare(gm, om, x, 4 / sigma ** 2, prec, bn=128)
+    g = synth.synthetic_gmm(200)
+    gm = ep.gmm_load(g.w, g.U, g.S, ep.RANK_FIXED, r)
+    x = synth.image(3, 512) + synth.noise(3, 512, 512, sigma)
+    compare(gm, None, x, 8 / sigma ** 2, prec, ep.SUBSET_FRACTION, 1 / 3, bn=128)
