@@ -1,6 +1,7 @@
 """Host logic of the multi-rank benchmark path on CPU (gloo, world size 2):
 the job time is the slowest rank's, the throughput counts every rank's
 work, and the reference arm prints on rank 0 only."""
+import json
 import os
 import subprocess
 import sys
@@ -64,3 +65,16 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "restores/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The stored DRAM bytes are reported only for the kernel source they were
+    taken on."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"kernel_source_sha256": "abc", "per_launch_bytes_full_size": {"auto": 123}}
+    (prof / "selection_kernel_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_record("abc", "auto") == 123
+    assert bench.traffic_record("abd", "auto") is None
+    assert bench.traffic_record("abc", "fp32") is None
